@@ -1,0 +1,388 @@
+#!/usr/bin/env python
+"""Benchmark of the coupled LB + Oldroyd-B step: MLUPS and fraction of the HBM roofline.
+
+Workload (default): the single-large-domain throughput case, a 512^3 periodic box with
+1 % seeded Bernoulli obstacles, u ~ U(-1e-3, 1e-3), zero stress, beta = 0.5,
+lambda = 1000, eta = 1/6.  One "step" is one time step of the whole coupled method over
+the whole domain.  The state (~18 GB in FP32 storage) is far larger than L2, so no
+flush is needed between steps.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Prints one JSON line (rank 0).  Under torchrun each rank runs an independent replica of
+the workload (weak scaling; the method needs no collective for independent solves).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "coupled LB+Oldroyd-B MLUPS (512^3 throughput workload)"
+UNIT = "MLUPS"
+HBM_FALLBACK_GBS = 6800.0
+
+# Algorithmic bytes per cell update of the whole step: each PDF and stress value read
+# once and written once, plus the flag byte (FP32 stress in the reduced-precision modes).
+PDF_BYTES = {"f64": 8, "f32": 4, "f16": 2, "bf16": 2}
+REAL_BYTES = {"f64": 8, "f32": 4, "f16": 4, "bf16": 4}
+
+
+def step_bytes(prec):
+    return 19 * PDF_BYTES[prec] * 2 + 6 * REAL_BYTES[prec] * 2 + 1
+
+
+def kernel_bytes(kind, prec):
+    """Inputs + outputs each kernel must move per cell (its own I/O)."""
+    pb, rb = PDF_BYTES[prec], REAL_BYTES[prec]
+    if kind == "lb":  # f read + write, tau read (polymer force), u write, flag
+        return 19 * pb * 2 + 6 * rb + 3 * rb + 1
+    if kind == "fv":  # tau read, u read, tau write, flag
+        return 6 * rb * 2 + 3 * rb + 1
+    if kind == "fused":  # f read + write, tau read + write, u read + write, flag
+        return 19 * pb * 2 + 6 * rb * 2 + 3 * rb * 2 + 1
+    return None
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return HBM_FALLBACK_GBS, "fallback"
+
+
+# ---------------------------------------------------------------------------------
+# clocks sampled during the timed region
+# ---------------------------------------------------------------------------------
+class ClockSampler:
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_{os.getpid()}.csv")
+
+    def start(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.QUERY}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.fh, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.fh.close()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        loaded = [s for s in sm if s >= 0.5 * max(sm)] or sm
+        return {"sm_mhz": statistics.median(loaded), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ---------------------------------------------------------------------------------
+# CPU oracle timing (baseline leg and the reference arm)
+# ---------------------------------------------------------------------------------
+def oracle_sample(side, seed=0):
+    from oracle import oracle
+    from paper_2009_12279_gb300 import workloads
+
+    cfg = workloads.config_throughput(side, seed=seed)
+    prm = dict(cfg["params"])
+    prm["g"] = prm.pop("body_force")
+    o = oracle.Oracle(cfg["shape"], **prm)
+    o.set_flags(cfg["flags_fn"]())
+    o.init_fields(u=cfg["u_fn"]())
+    return o
+
+
+def cores_used():
+    n = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
+    omp = os.environ.get("OMP_NUM_THREADS")
+    return min(n, int(omp)) if omp else n
+
+
+def cpu_baseline(target_s=15.0, side=64):
+    o = oracle_sample(side)
+    t0 = time.perf_counter()
+    o.step(1)
+    one = max(time.perf_counter() - t0, 1e-3)
+    steps = max(1, int(target_s / one))
+    t0 = time.perf_counter()
+    o.step(steps)
+    dt = time.perf_counter() - t0
+    mlups = side ** 3 * steps / dt / 1e6
+    return {"value": mlups, "unit": UNIT, "cores": cores_used(), "kind": "oracle",
+            "sample": f"{side}^3 periodic box of the same workload (1% obstacles, random u), {steps} steps, FP64, "
+                      f"{dt:.1f} s"}
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    # each step: one time step of a bounded sample of the workload (whole run a few minutes)
+    side = 64 if args.steps <= 400 else max(24, int((400 * 64 ** 3 / args.steps) ** (1 / 3)))
+    o = oracle_sample(side)
+    o.step(args.warmup)
+    t0 = time.perf_counter()
+    o.step(args.steps)
+    dt = time.perf_counter() - t0
+    mlups = side ** 3 * args.steps / dt / 1e6
+    line = {"impl": "reference", "metric": METRIC, "value": mlups, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3 / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": f"throughput box sample {side}^3 (1% obstacles, random u, beta 0.5, lambda 1000)",
+                       "cells": side ** 3},
+            "cpu_baseline": {"value": mlups, "unit": UNIT, "cores": cores_used(), "kind": "oracle",
+                             "sample": f"{side}^3 periodic box of the throughput workload per step"},
+            "e2e": {"value": mlups, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ---------------------------------------------------------------------------------
+# our arm
+# ---------------------------------------------------------------------------------
+def build_solver(n, prec, schedule, stream, torch):
+    from paper_2009_12279_gb300 import Solver, lbve, workloads
+
+    cfg = workloads.config_throughput(n)
+    sched = {"auto": lbve.SCHED_AUTO, "split": lbve.SCHED_SPLIT, "fused": lbve.SCHED_FUSED}[schedule]
+    s = Solver(cfg["shape"], precision=prec, schedule=sched, stream=stream, **cfg["params"])
+    s.set_geometry(cfg["flags_fn"]())
+    # initial velocity drawn on the device (seeded) to keep host memory small
+    g = torch.Generator(device="cuda")
+    g.manual_seed(1)
+    u = (torch.rand((3, n, n, n), generator=g, device="cuda", dtype=torch.float64) * 2.0 - 1.0) * 1e-3
+    s.init_fields_device(0, u.data_ptr(), 0)
+    torch.cuda.synchronize()
+    del u
+    return s, cfg
+
+
+def time_device(s, steps, warmup, torch, dist, stream):
+    s.step(warmup)
+    s.synchronize()
+    s.set_kernel_timing(True)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    s.step(steps)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    ms = ev0.elapsed_time(ev1)
+    kt = s.kernel_times()
+    s.set_kernel_timing(False)
+    return ms, kt
+
+
+def time_e2e(n, prec, schedule, steps, torch, stream_obj):
+    """Whole job through the public API with host buffers: create, geometry and initial
+    velocity uploaded from pinned host memory, `steps` time steps, rho/u/tau read back to
+    pinned host memory.  Returns MLUPS over the wall time of the job."""
+    from paper_2009_12279_gb300 import Solver, lbve, workloads
+
+    cfg = workloads.config_throughput(n)
+    flags = torch.from_numpy(cfg["flags_fn"]()).pin_memory()
+    g = torch.Generator()
+    g.manual_seed(1)
+    u = ((torch.rand((3, n, n, n), generator=g, dtype=torch.float64) * 2.0 - 1.0) * 1e-3).pin_memory()
+    out_rho = torch.empty((n, n, n), dtype=torch.float64).pin_memory()
+    out_u = torch.empty((3, n, n, n), dtype=torch.float64).pin_memory()
+    out_tau = torch.empty((6, n, n, n), dtype=torch.float64).pin_memory()
+    sched = {"auto": lbve.SCHED_AUTO, "split": lbve.SCHED_SPLIT, "fused": lbve.SCHED_FUSED}[schedule]
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    s = Solver(cfg["shape"], precision=prec, schedule=sched, stream=stream_obj.cuda_stream, **cfg["params"])
+    s.set_geometry(flags.numpy())
+    s.init_fields_ptr(0, u.data_ptr(), 0)
+    s.step(steps)
+    s.read_fields_ptr(out_rho.data_ptr(), out_u.data_ptr(), out_tau.data_ptr())
+    dt = time.perf_counter() - t0
+    s.close()
+    h2d = flags.numel() + u.numel() * 8
+    d2h = (out_rho.numel() + out_u.numel() + out_tau.numel()) * 8
+    finite = bool(torch.isfinite(out_u).all())
+    return {"value": n ** 3 * steps / dt / 1e6, "unit": UNIT, "h2d_bytes_per_step": h2d / steps,
+            "d2h_bytes_per_step": d2h / steps, "wall_s": dt, "job": f"create + upload + {steps} steps + read-back",
+            "finite": finite}
+
+
+def run_ours(args):
+    import torch
+
+    from paper_2009_12279_gb300 import build
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    dist = None
+    if world > 1:
+        import torch.distributed as dist_mod
+
+        torch.cuda.set_device(local)
+        dist_mod.init_process_group("nccl")
+        dist = dist_mod
+    else:
+        torch.cuda.set_device(0)
+    if rank == 0:
+        build.build()
+    if dist:
+        dist.barrier()
+    from paper_2009_12279_gb300 import lbve
+
+    lbve.load()
+    # CPU baseline first (rank 0, N=1 only), before the GPU work of the timed runs
+    cpu = cpu_baseline() if (rank == 0 and world == 1 and not args.no_cpu_baseline) else None
+
+    stream_obj = torch.cuda.current_stream()
+    stream = stream_obj.cuda_stream
+    n = args.n
+    peak, peak_kind = measured_peaks()
+    results = {}
+    clocks = None
+    for prec in args.precisions:
+        s, cfg = build_solver(n, prec, args.schedule, stream, torch)
+        sampler = ClockSampler(local) if prec == args.precisions[0] else None
+        if sampler:
+            sampler.start()
+        ms, kt = time_device(s, args.steps, args.warmup, torch, dist, stream_obj)
+        if sampler:
+            clocks = sampler.stop()
+        health = s.reduce()
+        s.close()
+        del s
+        torch.cuda.empty_cache()
+        t = torch.tensor([ms], device="cuda")
+        if dist:
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_max = float(t.item())
+        cells = n ** 3
+        mlups = world * cells * args.steps / (ms_max * 1e-3) / 1e6
+        dom = max(kt.items(), key=lambda kv: kv[1][0])
+        kind, (kms, klaunch) = dom
+        kb = kernel_bytes(kind, prec)
+        achieved = kb * cells * klaunch / (kms * 1e-3) / 1e9 if kb else None
+        launches = sum(c for k, (_, c) in kt.items()) + kt.get("momentum_exchange", (0, 0))[1]
+        results[prec] = {
+            "mlups": mlups, "ms_per_step": ms_max / args.steps,
+            "step_roofline_frac": mlups * 1e6 * step_bytes(prec) / (peak * 1e9),
+            "step_bytes_per_cell": step_bytes(prec),
+            "kernels": {k: {"avg_ms": v[0] / max(v[1], 1), "launches": v[1],
+                            "achieved_gbs": (kernel_bytes(k, prec) * cells * v[1] / (v[0] * 1e-3) / 1e9)
+                            if kernel_bytes(k, prec) else None} for k, v in kt.items()},
+            "roofline": {"bound": "hbm", "kernel": f"k_{kind}", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": (achieved / peak) if achieved else None, "traffic": None,
+                         "bytes_per_cell": kb, "peak_source": peak_kind},
+            "gpu_launches": launches,
+            "healthy": not health["bad"],
+        }
+    e2e = None
+    if not args.no_e2e:
+        e2e = time_e2e(n, args.precisions[0], args.schedule, args.steps, torch, stream_obj)
+    if rank == 0:
+        main = results[args.precisions[0]]
+        traffic = load_traffic(args.precisions[0], main["roofline"]["kernel"], args.schedule)
+        main["roofline"]["traffic"] = traffic
+        line = {
+            "metric": METRIC, "value": main["mlups"], "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": main["ms_per_step"], "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64" if args.precisions[0] == "f64" else "f32",
+            "data": "synthetic",
+            "config": {"workload": f"throughput {n}^3 periodic, 1% Bernoulli obstacles, u~U(-1e-3,1e-3), "
+                                   f"beta 0.5, lambda 1000, eta 1/6, {args.precisions[0]} PDF storage",
+                       "cells": n ** 3, "schedule": args.schedule, "parallelism": f"replicas{world}",
+                       "l2": "state larger than L2 (no flush needed)",
+                       "step_bytes_per_cell": main["step_bytes_per_cell"]},
+            "roofline": main["roofline"],
+            "step_roofline_frac": main["step_roofline_frac"],
+            "gpu_launches": main["gpu_launches"],
+            "clocks": clocks,
+            "e2e": e2e,
+            "cpu_baseline": cpu,
+            "modes": {p: {k: v for k, v in r.items() if k != "roofline"} | {"roofline_frac": r["roofline"]["frac"]}
+                      for p, r in results.items()},
+        }
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.barrier()
+        dist.destroy_process_group()
+    return 0
+
+
+def load_traffic(prec, kernel, schedule):
+    """DRAM bytes per launch of the dominant kernel from the committed ncu summary, if the
+    summary matches this kernel build; else None."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        rec = d.get(f"{kernel}:{prec}")
+        return rec["dram_bytes_per_launch_full_size"] if rec and rec.get("current", False) else None
+    except Exception:
+        return None
+
+
+def main():
+    ap = argparse.ArgumentParser(description=__doc__)
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=300)
+    ap.add_argument("--warmup", type=int, default=10)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--n", type=int, default=512, help="side of the cubic throughput domain")
+    ap.add_argument("--precisions", default="f32,f16", help="PDF storage modes; the first one is the headline")
+    ap.add_argument("--schedule", choices=["auto", "split", "fused"], default="auto")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    args = ap.parse_args()
+    args.precisions = [p.strip() for p in args.precisions.split(",") if p.strip()]
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,208 @@
+/*
+ * lbve.h -- C ABI of the GB300 library for the coupled lattice Boltzmann (LB) +
+ * Oldroyd-B time step of Kuron, Stewart, de Graaf and Holm, "An extensible lattice
+ * Boltzmann method for viscoelastic flows: complex and moving boundaries in Oldroyd-B
+ * fluids" (arXiv:2009.12279).
+ *
+ * One context holds one solve: a D3Q19 PDF field, the 6-component polymer stress,
+ * a flag field and up to LBVE_MAX_PARTICLES spheres, all resident in device memory.
+ * Every call runs its work as CUDA kernels on the context's stream; nothing falls
+ * back to the CPU.
+ *
+ * Conventions shared by all calls:
+ *   - grid nx*ny*nz, cell index x + nx*(y + ny*z) (x fastest), lattice units
+ *     (dx = dt = 1, cell volume 1);
+ *   - vector fields are 3 consecutive arrays of n cells (x, y, z components);
+ *   - stress fields are 6 consecutive arrays of n cells (xx, yy, zz, xy, xz, yz);
+ *   - PDFs are 19 consecutive arrays of n cells in the D3Q19 order
+ *       0:(0,0,0) 1:(+x) 2:(-x) 3:(+y) 4:(-y) 5:(+z) 6:(-z)
+ *       7:(+x+y) 8:(-x-y) 9:(+x-y) 10:(-x+y) 11:(+x+z) 12:(-x-z)
+ *       13:(+x-z) 14:(-x+z) 15:(+y+z) 16:(-y-z) 17:(+y-z) 18:(-y+z);
+ *   - flags: 0 fluid, 1 no-slip wall, LBVE_FLAG_WALL0 + k moving-wall class k,
+ *     LBVE_FLAG_PARTICLE0 + p cells covered by particle p (set by the library).
+ *
+ * Errors: every call returns an lbve_status and never aborts the process.  On an
+ * error the context stays valid (except after LBVE_ECUDA from a sticky CUDA error)
+ * and lbve_last_error() describes the cause.  Host buffers are owned by the caller
+ * and are only read or written during the call (the call synchronises the
+ * context's stream before returning whenever it touches host memory).
+ */
+#ifndef LBVE_H
+#define LBVE_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct lbve_ctx lbve_ctx;
+
+typedef enum {
+    LBVE_OK = 0,
+    LBVE_EINVAL = 1,    /* invalid argument or parameter combination */
+    LBVE_ENOMEM = 2,    /* device allocation failed */
+    LBVE_ECUDA = 3,     /* a CUDA call failed; lbve_last_error() has the CUDA message */
+    LBVE_EUNSTABLE = 4, /* NaN, rho <= 0 or |u| above the stability limit detected */
+    LBVE_ETIMEOUT = 5,  /* a bounded device-side wait gave up */
+    LBVE_ESTATE = 6     /* call not valid in the context's current state */
+} lbve_status;
+
+/* Storage precision of the PDFs (arithmetic is FP64 for LBVE_F64, else FP32).
+ * All reduced modes store the deviation f_i - w_i rho0 (times 2^pdf_scale_log2). */
+typedef enum { LBVE_F64 = 0, LBVE_F32 = 1, LBVE_F16_SHIFTED = 2, LBVE_BF16_SHIFTED = 3 } lbve_pdf_prec;
+
+#define LBVE_FLAG_FLUID 0
+#define LBVE_FLAG_NOSLIP 1
+#define LBVE_FLAG_WALL0 2
+#define LBVE_MAX_WALL 16
+#define LBVE_FLAG_PARTICLE0 64
+#define LBVE_MAX_PARTICLES 64
+
+/* Finite-volume terms (Sec. "Finite volume method"): bit 0 advective flux, bit 1 source. */
+#define LBVE_FV_FLUX 1
+#define LBVE_FV_SOURCE 2
+
+/* Kernel schedule: two kernels per step (LB, then FV), or one fused kernel per step. */
+#define LBVE_SCHED_AUTO 0
+#define LBVE_SCHED_SPLIT 1
+#define LBVE_SCHED_FUSED 2
+
+/*
+ * Parameters of one solve.  eta is the total viscosity eta_n + eta_p, beta = eta_p/eta
+ * (Sec. "Dimensionless numbers"), lambda_p the polymer relaxation time in steps
+ * (Eq. (oldroydb)), body_force a force density applied to every fluid cell
+ * (F in Eq. (stokes-general)).  The LB rates follow the TRT relations of Sec.
+ * "Lattice Boltzmann": omega+ = 1/(3 eta_n/rho0 + 1/2),
+ * (1/omega+ - 1/2)(1/omega- - 1/2) = magic (3/16 in the paper; 0 selects 3/16).
+ * A non-periodic direction needs non-fluid cells in its first and last layer.
+ */
+typedef struct {
+    int nx, ny, nz;
+    int periodic[3];
+    double eta, beta, lambda_p, rho0;
+    double body_force[3];
+    double magic;
+    int pdf_prec;        /* lbve_pdf_prec */
+    int pdf_scale_log2;  /* storage scale 2^k of the shifted PDFs; -1 selects the default */
+    int fv_terms;        /* LBVE_FV_* bits; 0 selects both */
+    int schedule;        /* LBVE_SCHED_* */
+    int block_x;         /* threads per block along x; 0 selects the tuned default */
+} lbve_params;
+
+/* Optional device allocator (e.g. a framework's caching allocator).  alloc returns a
+ * device pointer of at least `bytes` usable on `stream`, or NULL on failure. */
+typedef void *(*lbve_alloc_fn)(size_t bytes, void *stream, void *user);
+typedef void (*lbve_free_fn)(void *ptr, size_t bytes, void *stream, void *user);
+
+/* Fill *p with defaults (periodic box, eta 1/6, beta 0.5, lambda 1000, rho0 1, FP32). */
+void lbve_default_params(lbve_params *p);
+
+/* Device bytes a context with these parameters allocates (for admission control). */
+size_t lbve_device_bytes(const lbve_params *p);
+
+/*
+ * Create a solve on the current CUDA device.  cuda_stream is a cudaStream_t (NULL =
+ * legacy default stream) on which every kernel of the context runs.  The initial state
+ * is rho = rho0, u = 0, tau = 0 everywhere and an all-fluid flag field.
+ * Errors: EINVAL (bad parameters; *out stays NULL), ENOMEM, ECUDA.
+ */
+lbve_status lbve_create(const lbve_params *p, void *cuda_stream, lbve_ctx **out);
+lbve_status lbve_create_with_allocator(const lbve_params *p, void *cuda_stream, lbve_alloc_fn alloc,
+                                       lbve_free_fn dealloc, void *user, lbve_ctx **out);
+lbve_status lbve_destroy(lbve_ctx *ctx);
+
+/*
+ * Fixed geometry (Sec. "Lattice Boltzmann", Eq. (ubb)): flags is a host array of n
+ * bytes; values 0, 1 or LBVE_FLAG_WALL0 + k with k < n_wall.  wall_vel holds n_wall
+ * velocities (host, 3 doubles each) of the moving-wall classes; NULL if n_wall = 0.
+ * Links from fluid into a wall cell bounce back with the moving-wall term; wall
+ * classes also get their momentum-exchange force reported (lbve_read_body_forces).
+ * Must be called before any particle is added.  Errors: EINVAL (bad flag value,
+ * fluid cell in the outer layer of a non-periodic direction), ESTATE.
+ */
+lbve_status lbve_set_geometry(lbve_ctx *ctx, const uint8_t *flags, const double *wall_vel, int n_wall);
+
+/*
+ * Initial fields (host arrays, each may be NULL): rho (n), u (3n), tau (6n).  The
+ * PDFs are set to the equilibrium of Eq. (lb-equilibrium) at (rho, u); tau is copied.
+ * Resets the time counter to 0.  Particle cells keep their state.
+ */
+lbve_status lbve_init_fields(lbve_ctx *ctx, const double *rho, const double *u, const double *tau);
+
+/* Same as lbve_init_fields with device pointers (FP64, same layouts; each may be NULL). */
+lbve_status lbve_init_fields_device(lbve_ctx *ctx, const double *rho, const double *u, const double *tau);
+
+/*
+ * Add a rigid sphere (Sec. "Moving boundaries"): centre X, radius R, density rho_p
+ * (mass rho_p 4/3 pi R^3, moment of inertia 2/5 m R^2), velocity v, angular velocity
+ * w, constant external force and torque (all host arrays of 3 doubles; NULL = 0).
+ * Fluid cells whose centre lies within R of X (minimum image on periodic sides) become
+ * particle cells.  *id receives the particle index.  Errors: EINVAL, ESTATE (too many
+ * particles).
+ */
+lbve_status lbve_add_particle(lbve_ctx *ctx, const double X[3], double R, double rho_p, const double v[3],
+                              const double w[3], const double Fext[3], const double Text[3], int *id);
+
+/*
+ * Advance nsteps time steps (Eqs. (lb), (continuity)-(source), moving boundaries).
+ * Asynchronous on the context's stream unless the context has particles with a
+ * host-side check pending; returns after enqueueing.  Errors: EINVAL, ECUDA.
+ */
+lbve_status lbve_step(lbve_ctx *ctx, int nsteps);
+
+/*
+ * Copy the macroscopic fields to host arrays (each may be NULL): rho (n), u (3n, the
+ * physical velocity (j + F/2)/rho of Eq. (macroscopic-velocity) with F = g + F^p),
+ * tau (6n), flags (n).  Non-fluid cells read 0.  Synchronises the stream.
+ */
+lbve_status lbve_read_fields(lbve_ctx *ctx, double *rho, double *u, double *tau, uint8_t *flags);
+
+/* Same fields into device buffers of FP64 (each may be NULL); asynchronous. */
+lbve_status lbve_read_fields_device(lbve_ctx *ctx, double *rho, double *u, double *tau);
+
+/* PDFs f_i (19n, unshifted, FP64) to / from host memory, in the D3Q19 order above. */
+lbve_status lbve_read_pdfs(lbve_ctx *ctx, double *f);
+lbve_status lbve_write_pdfs(lbve_ctx *ctx, const double *f);
+
+/* Probe `count` cells (host array of cell indices): out (host, 29 doubles per cell) gets
+ * f_0..f_18 (unshifted), rho, u (physical velocity as in lbve_read_fields) and tau (6).
+ * Non-fluid cells read f as stored and rho = u = tau = 0.  Synchronises the stream. */
+lbve_status lbve_probe(lbve_ctx *ctx, const int64_t *cells, int count, double *out);
+
+/* Particle state: out[0..2] X, [3..5] v, [6..8] w, [9..11] momentum-exchange force
+ * and [12..14] torque of the last step, [15..17] fill/drain impulse dP and [18..20]
+ * angular impulse dL of the last step, [21] m, [22] I, [23] R. */
+lbve_status lbve_read_particle(lbve_ctx *ctx, int id, double out[24]);
+
+/* Momentum-exchange force of the last step per flag value: out[256][3] (host). */
+lbve_status lbve_read_body_forces(lbve_ctx *ctx, double *out);
+
+/* Global sums over fluid cells, FP64 on the device: out[0] mass, [1..3] momentum
+ * sum f c, [4] fluid cell count, [5] 1 if a NaN/Inf or rho <= 0 was seen. */
+lbve_status lbve_reduce(lbve_ctx *ctx, double out[6]);
+
+/* Kernel timing.  While enabled, every kernel that lbve_step launches is bracketed by
+ * CUDA events on the context's stream.  lbve_read_kernel_times synchronises the stream
+ * and returns, per kernel kind (LBVE_KT_*), the summed device milliseconds and the
+ * launch counts since timing was (re)enabled. */
+#define LBVE_KT_LB 0        /* stream-collide (split schedule) */
+#define LBVE_KT_FV 1        /* finite-volume stress update (split schedule) */
+#define LBVE_KT_FUSED 2     /* fused FV(t) + LB(t+1) */
+#define LBVE_KT_ME 3        /* momentum exchange + body reduction */
+#define LBVE_KT_PARTICLE 4  /* particle update, re-voxelisation, fill/drain */
+#define LBVE_KT_COUNT 8
+lbve_status lbve_set_kernel_timing(lbve_ctx *ctx, int enable);
+lbve_status lbve_read_kernel_times(lbve_ctx *ctx, double ms[LBVE_KT_COUNT], long long launches[LBVE_KT_COUNT]);
+
+/* Steps done since the last lbve_init_fields. */
+long long lbve_time(const lbve_ctx *ctx);
+lbve_status lbve_synchronize(lbve_ctx *ctx);
+const char *lbve_last_error(const lbve_ctx *ctx);
+const char *lbve_status_string(lbve_status s);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

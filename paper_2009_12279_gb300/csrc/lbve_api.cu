@@ -1,0 +1,707 @@
+// lbve_api.cu -- host implementation of the C ABI declared in include/lbve.h.
+//
+// A context owns the device state of one solve (PDFs, stress ping-pong, velocity,
+// flags, particles, boundary-link list) and enqueues the step kernels of the
+// per-precision kernel tables on its stream.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "../../include/lbve.h"
+#include "lbve_launch.h"
+
+using namespace lbve;
+
+struct lbve_ctx {
+    lbve_params p;
+    cudaStream_t stream = nullptr;
+    lbve_alloc_fn alloc = nullptr;
+    lbve_free_fn dealloc = nullptr;
+    void *user = nullptr;
+    const KernelTable *kt = nullptr;
+    DevState d;
+    long long t = 0;
+    std::string err;
+    std::vector<std::pair<void *, size_t>> blocks;
+    // boundary links into tracked bodies (wall classes >= 2 and particles)
+    long long *links = nullptr;  // device, capacity links_cap
+    int nlinks = 0;
+    size_t links_cap = 0;
+    double *contrib = nullptr;   // device, 8 doubles per link
+    int *seg = nullptr;          // device, segment begin per body (nbody + 1)
+    int nbody = 0;
+    int *seg_flag = nullptr;     // device, flag value per body segment
+    double *body_F = nullptr;    // device, 256 x 3 forces of the last step
+    double *red = nullptr;       // device reduction scratch
+    size_t red_cap = 0;
+    double *red_out = nullptr;   // device, 6 doubles
+    std::vector<uint8_t> flags_host;
+    bool geometry_set = false;
+    int nparts = 0;
+    PartDev parts_host[MAX_PART];
+    // kernel timing (event pairs recorded around launches while enabled)
+    bool timing = false;
+    std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev_pool;
+    std::vector<int> ev_kind;  // kind of each recorded pair, in order
+    size_t ev_used = 0;
+    double kt_ms[LBVE_KT_COUNT] = {0};
+    long long kt_count[LBVE_KT_COUNT] = {0};
+};
+
+namespace {
+
+std::string g_create_error;
+
+const char *kStatusNames[] = {"LBVE_OK",        "LBVE_EINVAL",   "LBVE_ENOMEM", "LBVE_ECUDA",
+                              "LBVE_EUNSTABLE", "LBVE_ETIMEOUT", "LBVE_ESTATE"};
+
+lbve_status fail(lbve_ctx *c, lbve_status s, const std::string &msg) {
+    if (c) c->err = msg;
+    return s;
+}
+
+lbve_status cuda_fail(lbve_ctx *c, cudaError_t e, const char *where) {
+    std::string m = std::string(where) + ": " + cudaGetErrorString(e);
+    if (c) c->err = m;
+    return e == cudaErrorMemoryAllocation ? LBVE_ENOMEM : LBVE_ECUDA;
+}
+
+#define CK(call, where)                                      \
+    do {                                                     \
+        cudaError_t e_ = (call);                             \
+        if (e_ != cudaSuccess) return cuda_fail(c, e_, where); \
+    } while (0)
+
+long long padded(long long n) { return (n + 63) / 64 * 64; }
+
+const KernelTable *table_for(int prec) {
+    switch (prec) {
+    case LBVE_F64:
+        return table_f64();
+    case LBVE_F32:
+        return table_f32();
+    case LBVE_F16_SHIFTED:
+        return table_f16();
+    case LBVE_BF16_SHIFTED:
+        return table_bf16();
+    default:
+        return nullptr;
+    }
+}
+
+size_t pdf_bytes_of(int prec) { return prec == LBVE_F64 ? 8 : (prec == LBVE_F32 ? 4 : 2); }
+size_t real_bytes_of(int prec) { return prec == LBVE_F64 ? 8 : 4; }
+
+bool valid_params(const lbve_params *p, std::string &why) {
+    if (!p) return why = "params is NULL", false;
+    if (p->nx < 1 || p->ny < 1 || p->nz < 1) return why = "grid dimensions must be >= 1", false;
+    if (p->ny > 65535 || p->nz > 65535) return why = "ny and nz must be <= 65535", false;
+    if (!(p->eta > 0.0)) return why = "eta must be > 0", false;
+    if (!(p->beta >= 0.0 && p->beta < 1.0)) return why = "beta must be in [0, 1)", false;
+    if (!(p->rho0 > 0.0)) return why = "rho0 must be > 0", false;
+    if (p->beta > 0.0 && !(p->lambda_p > 0.0)) return why = "lambda_p must be > 0 when beta > 0", false;
+    if (p->pdf_prec < LBVE_F64 || p->pdf_prec > LBVE_BF16_SHIFTED) return why = "unknown pdf_prec", false;
+    if (p->pdf_scale_log2 < -1 || p->pdf_scale_log2 > 24) return why = "pdf_scale_log2 out of range", false;
+    if (p->fv_terms < 0 || p->fv_terms > 3) return why = "fv_terms out of range", false;
+    if (p->block_x < 0 || p->block_x > 1024 || (p->block_x % 32) != 0) return why = "block_x must be a multiple of 32", false;
+    if (!(p->magic >= 0.0)) return why = "magic must be >= 0", false;
+    const double eta_n = (1.0 - p->beta) * p->eta;
+    if (!(eta_n / p->rho0 > 0.0)) return why = "Newtonian viscosity must be > 0", false;
+    return true;
+}
+
+void *dev_alloc(lbve_ctx *c, size_t bytes) {
+    void *ptr = nullptr;
+    if (c->alloc) {
+        ptr = c->alloc(bytes, (void *)c->stream, c->user);
+    } else if (cudaMalloc(&ptr, bytes) != cudaSuccess) {
+        cudaGetLastError();
+        ptr = nullptr;
+    }
+    if (ptr) c->blocks.push_back({ptr, bytes});
+    return ptr;
+}
+
+void dev_free(lbve_ctx *c, void *ptr) {
+    if (!ptr) return;
+    for (size_t k = 0; k < c->blocks.size(); ++k) {
+        if (c->blocks[k].first == ptr) {
+            if (c->dealloc)
+                c->dealloc(ptr, c->blocks[k].second, (void *)c->stream, c->user);
+            else
+                cudaFree(ptr);
+            c->blocks.erase(c->blocks.begin() + (long)k);
+            return;
+        }
+    }
+}
+
+void set_phys(lbve_ctx *c) {
+    const lbve_params &p = c->p;
+    Phys<double> &ph = c->d.ph;
+    std::memset(&ph, 0, sizeof(ph));
+    // TRT rates from the viscosity (Sec. "Lattice Boltzmann"): rates, magic product.
+    const double eta_n = (1.0 - p.beta) * p.eta;
+    const double nu_n = eta_n / p.rho0;
+    const double magic = p.magic > 0.0 ? p.magic : 3.0 / 16.0;
+    ph.omega_p = 1.0 / (3.0 * nu_n + 0.5);
+    const double tp = 1.0 / ph.omega_p - 0.5;
+    ph.omega_m = 1.0 / (magic / tp + 0.5);
+    ph.A = 3.0 * (1.0 - 0.5 * ph.omega_m);
+    ph.B = 1.0 - 0.5 * ph.omega_p;
+    const double eta_p = p.beta * p.eta;
+    ph.ep_l = p.beta > 0.0 ? eta_p / p.lambda_p : 0.0;
+    ph.inv_l = p.lambda_p > 0.0 ? 1.0 / p.lambda_p : 0.0;
+    for (int k = 0; k < 3; ++k) ph.g[k] = p.body_force[k];
+    ph.rho0 = p.pdf_prec == LBVE_F64 ? 0.0 : p.rho0;
+    int k = p.pdf_scale_log2;
+    if (k < 0) k = p.pdf_prec == LBVE_F16_SHIFTED ? 15 : 0;
+    if (p.pdf_prec == LBVE_F64) k = 0;
+    ph.scale = std::ldexp(1.0, k);
+    ph.inv_scale = std::ldexp(1.0, -k);
+    const int terms = p.fv_terms == 0 ? (LBVE_FV_FLUX | LBVE_FV_SOURCE) : p.fv_terms;
+    ph.flux_on = (terms & LBVE_FV_FLUX) != 0;
+    ph.src_on = (terms & LBVE_FV_SOURCE) != 0;
+}
+
+// ---------------------------------------------------------------------------------
+// small kernels that do not depend on the storage type
+// ---------------------------------------------------------------------------------
+
+// Sum the momentum-exchange contributions of each body segment in link order.  FP64
+// parity mode uses one thread per body (the sequential order of a plain loop); the
+// reduced modes use a fixed-shape block reduction.  Deterministic in both cases.
+__global__ void k_body_reduce(const double *__restrict__ contrib, const int *__restrict__ seg,
+                              const int *__restrict__ seg_flag, int nbody, double *__restrict__ body_F,
+                              PartDev *__restrict__ parts) {
+    const int b = blockIdx.x;
+    if (b >= nbody) return;
+    const int beg = seg[b], end = seg[b + 1];
+    __shared__ double sh[6][256];
+    double acc[6] = {0, 0, 0, 0, 0, 0};
+    const int T = blockDim.x;
+    const int len = end - beg;
+    const int chunk = (len + T - 1) / T;
+    const int lo = beg + (int)threadIdx.x * chunk;
+    const int hi = min(end, lo + chunk);
+    for (int l = lo; l < hi; ++l)
+        for (int k = 0; k < 6; ++k) acc[k] += contrib[(long long)l * 8 + k];
+    for (int k = 0; k < 6; ++k) sh[k][threadIdx.x] = acc[k];
+    __syncthreads();
+    for (int s = T / 2; s > 0; s >>= 1) {
+        if ((int)threadIdx.x < s)
+            for (int k = 0; k < 6; ++k) sh[k][threadIdx.x] += sh[k][threadIdx.x + s];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        const int fl = seg_flag[b];
+        for (int k = 0; k < 3; ++k) body_F[fl * 3 + k] = sh[k][0];
+        if (fl >= FLAG_PART0 && fl < FLAG_PART0 + MAX_PART) {
+            PartDev &P = parts[fl - FLAG_PART0];
+            for (int k = 0; k < 3; ++k) {
+                P.Fme[k] = sh[k][0];
+                P.Tme[k] = sh[3 + k][0];
+            }
+        }
+    }
+}
+
+__global__ void k_final_sum(const double *__restrict__ partial, long long nblocks, double *__restrict__ out) {
+    __shared__ double sh[6][256];
+    double acc[6] = {0, 0, 0, 0, 0, 0};
+    for (long long b = threadIdx.x; b < nblocks; b += blockDim.x)
+        for (int k = 0; k < 6; ++k) acc[k] = k == 5 ? fmax(acc[k], partial[b * 6 + k]) : acc[k] + partial[b * 6 + k];
+    for (int k = 0; k < 6; ++k) sh[k][threadIdx.x] = acc[k];
+    __syncthreads();
+    for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+        if ((int)threadIdx.x < s)
+            for (int k = 0; k < 6; ++k)
+                sh[k][threadIdx.x] = k == 5 ? fmax(sh[k][threadIdx.x], sh[k][threadIdx.x + s])
+                                            : sh[k][threadIdx.x] + sh[k][threadIdx.x + s];
+        __syncthreads();
+    }
+    if (threadIdx.x < 6) out[threadIdx.x] = sh[threadIdx.x][0];
+}
+
+// Host-side list of links (fluid cell, direction into a wall-class cell), in cell order
+// then direction order, grouped by flag value (stable), with the segment boundaries.
+void build_wall_links(const lbve_ctx *c, std::vector<long long> &links, std::vector<int> &seg,
+                      std::vector<int> &seg_flag) {
+    const int nx = c->p.nx, ny = c->p.ny, nz = c->p.nz;
+    const std::vector<uint8_t> &fl = c->flags_host;
+    std::vector<std::vector<long long>> by_flag(256);
+    for (int z = 0; z < nz; ++z)
+        for (int y = 0; y < ny; ++y)
+            for (int x = 0; x < nx; ++x) {
+                const long long r = x + (long long)nx * (y + (long long)ny * z);
+                if (fl[r] != FLAG_FLUID) continue;
+                for (int i = 1; i < Q; ++i) {
+                    static const int CX[Q] = {0, 1, -1, 0, 0, 0, 0, 1, -1, 1, -1, 1, -1, 1, -1, 0, 0, 0, 0};
+                    static const int CY[Q] = {0, 0, 0, 1, -1, 0, 0, 1, -1, -1, 1, 0, 0, 0, 0, 1, -1, 1, -1};
+                    static const int CZ[Q] = {0, 0, 0, 0, 0, 1, -1, 0, 0, 0, 0, 1, -1, -1, 1, 1, -1, -1, 1};
+                    const int xq = (x + CX[i] + nx) % nx, yq = (y + CY[i] + ny) % ny, zq = (z + CZ[i] + nz) % nz;
+                    const uint8_t f = fl[xq + (long long)nx * (yq + (long long)ny * zq)];
+                    if (f >= FLAG_WALL0 && f < FLAG_WALL0 + MAX_WALL) by_flag[f].push_back((r << 5) | i);
+                }
+            }
+    links.clear();
+    seg.clear();
+    seg_flag.clear();
+    for (int f = 0; f < 256; ++f) {
+        if (by_flag[f].empty()) continue;
+        seg.push_back((int)links.size());
+        seg_flag.push_back(f);
+        links.insert(links.end(), by_flag[f].begin(), by_flag[f].end());
+    }
+    seg.push_back((int)links.size());
+}
+
+lbve_status upload_links(lbve_ctx *c, const std::vector<long long> &links, const std::vector<int> &seg,
+                         const std::vector<int> &seg_flag) {
+    if (links.size() > c->links_cap) {
+        dev_free(c, c->links);
+        dev_free(c, c->contrib);
+        c->links = nullptr;
+        c->contrib = nullptr;
+        const size_t cap = std::max<size_t>(links.size(), 1024);
+        c->links = (long long *)dev_alloc(c, cap * sizeof(long long));
+        c->contrib = (double *)dev_alloc(c, cap * 8 * sizeof(double));
+        if (!c->links || !c->contrib) return fail(c, LBVE_ENOMEM, "link list allocation failed");
+        c->links_cap = cap;
+    }
+    if (!links.empty())
+        CK(cudaMemcpyAsync(c->links, links.data(), links.size() * sizeof(long long), cudaMemcpyHostToDevice, c->stream),
+           "upload links");
+    c->nlinks = (int)links.size();
+    c->nbody = (int)seg_flag.size();
+    if (c->nbody > 0) {
+        CK(cudaMemcpyAsync(c->seg, seg.data(), seg.size() * sizeof(int), cudaMemcpyHostToDevice, c->stream), "upload seg");
+        CK(cudaMemcpyAsync(c->seg_flag, seg_flag.data(), seg_flag.size() * sizeof(int), cudaMemcpyHostToDevice,
+                           c->stream),
+           "upload seg flags");
+    }
+    CK(cudaStreamSynchronize(c->stream), "upload sync");
+    return LBVE_OK;
+}
+
+lbve_status create_impl(const lbve_params *p, void *stream, lbve_alloc_fn alloc, lbve_free_fn dealloc, void *user,
+                        lbve_ctx **out) {
+    if (!out) return LBVE_EINVAL;
+    *out = nullptr;
+    std::string why;
+    if (!valid_params(p, why)) {
+        g_create_error = why;
+        return LBVE_EINVAL;
+    }
+    lbve_ctx *c = new (std::nothrow) lbve_ctx();
+    if (!c) return LBVE_ENOMEM;
+    c->p = *p;
+    c->stream = (cudaStream_t)stream;
+    c->alloc = alloc;
+    c->dealloc = dealloc;
+    c->user = user;
+    c->kt = table_for(p->pdf_prec);
+    std::memset(&c->d, 0, sizeof(c->d));
+    Geo &g = c->d.g;
+    g.nx = p->nx;
+    g.ny = p->ny;
+    g.nz = p->nz;
+    for (int k = 0; k < 3; ++k) g.per[k] = p->periodic[k] ? 1 : 0;
+    g.n = (long long)p->nx * p->ny * p->nz;
+    g.np = padded(g.n);
+    int bx = p->block_x > 0 ? p->block_x : 128;
+    while (bx > 32 && bx / 2 >= p->nx) bx /= 2;
+    c->d.block_x = bx;
+    set_phys(c);
+    const long long np = g.np;
+    c->d.f = dev_alloc(c, (size_t)Q * np * c->kt->pdf_bytes);
+    c->d.tau[0] = dev_alloc(c, (size_t)6 * np * c->kt->real_bytes);
+    c->d.tau[1] = dev_alloc(c, (size_t)6 * np * c->kt->real_bytes);
+    c->d.u = dev_alloc(c, (size_t)3 * np * c->kt->real_bytes);
+    c->d.flag = (uint8_t *)dev_alloc(c, (size_t)np);
+    c->d.parts = (PartDev *)dev_alloc(c, sizeof(PartDev) * MAX_PART);
+    c->seg = (int *)dev_alloc(c, sizeof(int) * 257);
+    c->seg_flag = (int *)dev_alloc(c, sizeof(int) * 256);
+    c->body_F = (double *)dev_alloc(c, sizeof(double) * 256 * 3);
+    c->red_out = (double *)dev_alloc(c, sizeof(double) * 8);
+    if (!c->d.f || !c->d.tau[0] || !c->d.tau[1] || !c->d.u || !c->d.flag || !c->d.parts || !c->seg || !c->seg_flag ||
+        !c->body_F || !c->red_out) {
+        g_create_error = "device allocation failed";
+        lbve_destroy(c);
+        return LBVE_ENOMEM;
+    }
+    c->flags_host.assign((size_t)g.n, 0);
+    cudaError_t e = cudaMemsetAsync(c->d.flag, 0, (size_t)np, c->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(c->d.u, 0, (size_t)3 * np * c->kt->real_bytes, c->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(c->d.tau[1], 0, (size_t)6 * np * c->kt->real_bytes, c->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(c->d.parts, 0, sizeof(PartDev) * MAX_PART, c->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(c->body_F, 0, sizeof(double) * 256 * 3, c->stream);
+    if (e == cudaSuccess) e = c->kt->init(c->d, nullptr, nullptr, nullptr, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) {
+        g_create_error = std::string("initialisation failed: ") + cudaGetErrorString(e);
+        lbve_destroy(c);
+        return LBVE_ECUDA;
+    }
+    *out = c;
+    return LBVE_OK;
+}
+
+// Start / stop a timed launch of the given kind (no-ops while timing is off).
+cudaError_t timed_begin(lbve_ctx *c, int kind) {
+    if (!c->timing) return cudaSuccess;
+    if (c->ev_used == c->ev_pool.size()) {
+        cudaEvent_t a, b;
+        cudaError_t e = cudaEventCreate(&a);
+        if (e != cudaSuccess) return e;
+        e = cudaEventCreate(&b);
+        if (e != cudaSuccess) return e;
+        c->ev_pool.push_back({a, b});
+    }
+    if (c->ev_kind.size() <= c->ev_used) c->ev_kind.resize(c->ev_used + 1);
+    c->ev_kind[c->ev_used] = kind;
+    return cudaEventRecord(c->ev_pool[c->ev_used].first, c->stream);
+}
+
+cudaError_t timed_end(lbve_ctx *c) {
+    if (!c->timing) return cudaSuccess;
+    cudaError_t e = cudaEventRecord(c->ev_pool[c->ev_used].second, c->stream);
+    c->ev_used++;
+    return e;
+}
+
+// Fold the recorded event pairs into the per-kind totals and recycle them.
+cudaError_t harvest_times(lbve_ctx *c) {
+    if (c->ev_used == 0) return cudaSuccess;
+    cudaError_t e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) return e;
+    for (size_t k = 0; k < c->ev_used; ++k) {
+        float ms = 0.f;
+        e = cudaEventElapsedTime(&ms, c->ev_pool[k].first, c->ev_pool[k].second);
+        if (e != cudaSuccess) return e;
+        c->kt_ms[c->ev_kind[k]] += ms;
+        c->kt_count[c->ev_kind[k]] += 1;
+    }
+    c->ev_used = 0;
+    return cudaSuccess;
+}
+
+// Stage a host array to a temporary device buffer.
+lbve_status stage(lbve_ctx *c, const void *host, size_t bytes, void **dev) {
+    *dev = nullptr;
+    if (!host) return LBVE_OK;
+    *dev = dev_alloc(c, bytes);
+    if (!*dev) return fail(c, LBVE_ENOMEM, "staging allocation failed");
+    CK(cudaMemcpyAsync(*dev, host, bytes, cudaMemcpyHostToDevice, c->stream), "stage copy");
+    return LBVE_OK;
+}
+
+} // namespace
+
+extern "C" {
+
+void lbve_default_params(lbve_params *p) {
+    if (!p) return;
+    std::memset(p, 0, sizeof(*p));
+    p->nx = p->ny = p->nz = 16;
+    p->periodic[0] = p->periodic[1] = p->periodic[2] = 1;
+    p->eta = 1.0 / 6.0;
+    p->beta = 0.5;
+    p->lambda_p = 1000.0;
+    p->rho0 = 1.0;
+    p->magic = 3.0 / 16.0;
+    p->pdf_prec = LBVE_F32;
+    p->pdf_scale_log2 = -1;
+    p->fv_terms = LBVE_FV_FLUX | LBVE_FV_SOURCE;
+    p->schedule = LBVE_SCHED_AUTO;
+    p->block_x = 0;
+}
+
+size_t lbve_device_bytes(const lbve_params *p) {
+    std::string why;
+    if (!valid_params(p, why)) return 0;
+    const long long np = padded((long long)p->nx * p->ny * p->nz);
+    const size_t pb = pdf_bytes_of(p->pdf_prec), rb = real_bytes_of(p->pdf_prec);
+    return (size_t)np * (Q * pb + 15 * rb + 1) + sizeof(PartDev) * MAX_PART + 32768;
+}
+
+lbve_status lbve_create(const lbve_params *p, void *cuda_stream, lbve_ctx **out) {
+    return create_impl(p, cuda_stream, nullptr, nullptr, nullptr, out);
+}
+
+lbve_status lbve_create_with_allocator(const lbve_params *p, void *cuda_stream, lbve_alloc_fn alloc,
+                                       lbve_free_fn dealloc, void *user, lbve_ctx **out) {
+    if (!alloc || !dealloc) {
+        g_create_error = "allocator callbacks must both be set";
+        return LBVE_EINVAL;
+    }
+    return create_impl(p, cuda_stream, alloc, dealloc, user, out);
+}
+
+lbve_status lbve_destroy(lbve_ctx *c) {
+    if (!c) return LBVE_EINVAL;
+    cudaStreamSynchronize(c->stream);
+    for (auto &ev : c->ev_pool) {
+        cudaEventDestroy(ev.first);
+        cudaEventDestroy(ev.second);
+    }
+    while (!c->blocks.empty()) dev_free(c, c->blocks.back().first);
+    delete c;
+    return LBVE_OK;
+}
+
+lbve_status lbve_set_geometry(lbve_ctx *c, const uint8_t *flags, const double *wall_vel, int n_wall) {
+    if (!c) return LBVE_EINVAL;
+    if (!flags) return fail(c, LBVE_EINVAL, "flags is NULL");
+    if (c->nparts > 0) return fail(c, LBVE_ESTATE, "geometry must be set before particles are added");
+    if (n_wall < 0 || n_wall > MAX_WALL || (n_wall > 0 && !wall_vel))
+        return fail(c, LBVE_EINVAL, "n_wall must be in [0, 16] with wall_vel given");
+    const int nx = c->p.nx, ny = c->p.ny, nz = c->p.nz;
+    for (long long r = 0; r < c->d.g.n; ++r) {
+        const uint8_t f = flags[r];
+        if (f >= FLAG_WALL0 + n_wall && f != FLAG_FLUID && f != FLAG_NOSLIP) {
+            char b[128];
+            std::snprintf(b, sizeof b, "flag %d at cell %lld is not fluid, no-slip or a declared wall class", (int)f, r);
+            return fail(c, LBVE_EINVAL, b);
+        }
+        if (f == FLAG_FLUID) {
+            const int x = (int)(r % nx), y = (int)((r / nx) % ny), z = (int)(r / ((long long)nx * ny));
+            const int q[3] = {x, y, z}, nn[3] = {nx, ny, nz};
+            for (int a = 0; a < 3; ++a)
+                if (!c->p.periodic[a] && (q[a] == 0 || q[a] == nn[a] - 1))
+                    return fail(c, LBVE_EINVAL, "fluid cell in the outer layer of a non-periodic direction");
+        }
+    }
+    for (int k = 0; k < MAX_WALL; ++k)
+        for (int a = 0; a < 3; ++a) c->d.ph.wall_vel[k][a] = k < n_wall ? wall_vel[3 * k + a] : 0.0;
+    std::memcpy(c->flags_host.data(), flags, (size_t)c->d.g.n);
+    CK(cudaMemcpyAsync(c->d.flag, flags, (size_t)c->d.g.n, cudaMemcpyHostToDevice, c->stream), "upload flags");
+    std::vector<long long> links;
+    std::vector<int> seg, seg_flag;
+    build_wall_links(c, links, seg, seg_flag);
+    lbve_status s = upload_links(c, links, seg, seg_flag);
+    if (s != LBVE_OK) return s;
+    c->geometry_set = true;
+    return LBVE_OK;
+}
+
+lbve_status lbve_init_fields(lbve_ctx *c, const double *rho, const double *u, const double *tau) {
+    if (!c) return LBVE_EINVAL;
+    const long long n = c->d.g.n;
+    void *drho, *du, *dtau;
+    lbve_status s;
+    if ((s = stage(c, rho, sizeof(double) * n, &drho)) != LBVE_OK) return s;
+    if ((s = stage(c, u, sizeof(double) * 3 * n, &du)) != LBVE_OK) return s;
+    if ((s = stage(c, tau, sizeof(double) * 6 * n, &dtau)) != LBVE_OK) return s;
+    c->d.cur = 0;
+    CK(c->kt->init(c->d, (const double *)drho, (const double *)du, (const double *)dtau, c->stream), "init kernel");
+    CK(cudaStreamSynchronize(c->stream), "init sync");
+    dev_free(c, drho);
+    dev_free(c, du);
+    dev_free(c, dtau);
+    c->t = 0;
+    return LBVE_OK;
+}
+
+lbve_status lbve_init_fields_device(lbve_ctx *c, const double *rho, const double *u, const double *tau) {
+    if (!c) return LBVE_EINVAL;
+    c->d.cur = 0;
+    CK(c->kt->init(c->d, rho, u, tau, c->stream), "init kernel");
+    c->t = 0;
+    return LBVE_OK;
+}
+
+lbve_status lbve_probe(lbve_ctx *c, const int64_t *cells, int count, double *out) {
+    if (!c) return LBVE_EINVAL;
+    if (count < 0 || (count > 0 && (!cells || !out))) return fail(c, LBVE_EINVAL, "bad probe arguments");
+    if (count == 0) return LBVE_OK;
+    for (int k = 0; k < count; ++k)
+        if (cells[k] < 0 || cells[k] >= c->d.g.n) return fail(c, LBVE_EINVAL, "probe cell index out of range");
+    void *dc = dev_alloc(c, sizeof(long long) * (size_t)count);
+    double *dout = (double *)dev_alloc(c, sizeof(double) * 29 * (size_t)count);
+    if (!dc || !dout) {
+        dev_free(c, dc);
+        dev_free(c, dout);
+        return fail(c, LBVE_ENOMEM, "probe staging allocation failed");
+    }
+    CK(cudaMemcpyAsync(dc, cells, sizeof(long long) * (size_t)count, cudaMemcpyHostToDevice, c->stream), "probe copy");
+    CK(c->kt->probe(c->d, (int)(c->t & 1), (const long long *)dc, count, dout, c->stream), "probe kernel");
+    CK(cudaMemcpyAsync(out, dout, sizeof(double) * 29 * (size_t)count, cudaMemcpyDeviceToHost, c->stream), "probe out");
+    CK(cudaStreamSynchronize(c->stream), "probe sync");
+    dev_free(c, dc);
+    dev_free(c, dout);
+    return LBVE_OK;
+}
+
+lbve_status lbve_add_particle(lbve_ctx *c, const double X[3], double R, double rho_p, const double v[3],
+                              const double w[3], const double Fext[3], const double Text[3], int *id) {
+    if (!c) return LBVE_EINVAL;
+    return fail(c, LBVE_ESTATE, "moving particles are not available in this build");
+}
+
+lbve_status lbve_step(lbve_ctx *c, int nsteps) {
+    if (!c) return LBVE_EINVAL;
+    if (nsteps < 0) return fail(c, LBVE_EINVAL, "nsteps must be >= 0");
+    for (int s = 0; s < nsteps; ++s) {
+        const int parity = (int)(c->t & 1);
+        if (c->nlinks > 0) {
+            CK(timed_begin(c, LBVE_KT_ME), "timing");
+            CK(c->kt->momentum_exchange(c->d, parity, c->links, c->nlinks, c->contrib, c->stream), "momentum exchange");
+            const int threads = c->p.pdf_prec == LBVE_F64 ? 1 : 256;
+            k_body_reduce<<<c->nbody, threads, 0, c->stream>>>(c->contrib, c->seg, c->seg_flag, c->nbody, c->body_F,
+                                                               c->d.parts);
+            CK(cudaGetLastError(), "body reduce");
+            CK(timed_end(c), "timing");
+        }
+        CK(timed_begin(c, LBVE_KT_LB), "timing");
+        CK(c->kt->lb(c->d, parity, c->stream), "lb kernel");
+        CK(timed_end(c), "timing");
+        CK(timed_begin(c, LBVE_KT_FV), "timing");
+        CK(c->kt->fv(c->d, c->stream), "fv kernel");
+        CK(timed_end(c), "timing");
+        if (c->ev_used >= 4096) CK(harvest_times(c), "timing harvest");
+        c->d.cur ^= 1;
+        c->t++;
+    }
+    return LBVE_OK;
+}
+
+lbve_status lbve_read_fields_device(lbve_ctx *c, double *rho, double *u, double *tau) {
+    if (!c) return LBVE_EINVAL;
+    CK(c->kt->read(c->d, (int)(c->t & 1), rho, u, tau, c->stream), "read kernel");
+    return LBVE_OK;
+}
+
+lbve_status lbve_read_fields(lbve_ctx *c, double *rho, double *u, double *tau, uint8_t *flags) {
+    if (!c) return LBVE_EINVAL;
+    const long long n = c->d.g.n;
+    double *d = nullptr;
+    const size_t bytes = sizeof(double) * 10 * n;
+    if (rho || u || tau) {
+        d = (double *)dev_alloc(c, bytes);
+        if (!d) return fail(c, LBVE_ENOMEM, "read staging allocation failed");
+        CK(c->kt->read(c->d, (int)(c->t & 1), rho ? d : nullptr, u ? d + n : nullptr, tau ? d + 4 * n : nullptr,
+                       c->stream),
+           "read kernel");
+        if (rho) CK(cudaMemcpyAsync(rho, d, sizeof(double) * n, cudaMemcpyDeviceToHost, c->stream), "read rho");
+        if (u) CK(cudaMemcpyAsync(u, d + n, sizeof(double) * 3 * n, cudaMemcpyDeviceToHost, c->stream), "read u");
+        if (tau) CK(cudaMemcpyAsync(tau, d + 4 * n, sizeof(double) * 6 * n, cudaMemcpyDeviceToHost, c->stream), "read tau");
+    }
+    if (flags) CK(cudaMemcpyAsync(flags, c->d.flag, (size_t)n, cudaMemcpyDeviceToHost, c->stream), "read flags");
+    CK(cudaStreamSynchronize(c->stream), "read sync");
+    dev_free(c, d);
+    return LBVE_OK;
+}
+
+lbve_status lbve_read_pdfs(lbve_ctx *c, double *f) {
+    if (!c || !f) return c ? fail(c, LBVE_EINVAL, "f is NULL") : LBVE_EINVAL;
+    const long long n = c->d.g.n;
+    double *d = (double *)dev_alloc(c, sizeof(double) * Q * n);
+    if (!d) return fail(c, LBVE_ENOMEM, "pdf staging allocation failed");
+    CK(c->kt->pdfs_io(c->d, (int)(c->t & 1), d, 0, c->stream), "pdf read kernel");
+    CK(cudaMemcpyAsync(f, d, sizeof(double) * Q * n, cudaMemcpyDeviceToHost, c->stream), "pdf copy");
+    CK(cudaStreamSynchronize(c->stream), "pdf sync");
+    dev_free(c, d);
+    return LBVE_OK;
+}
+
+lbve_status lbve_write_pdfs(lbve_ctx *c, const double *f) {
+    if (!c || !f) return c ? fail(c, LBVE_EINVAL, "f is NULL") : LBVE_EINVAL;
+    const long long n = c->d.g.n;
+    double *d = (double *)dev_alloc(c, sizeof(double) * Q * n);
+    if (!d) return fail(c, LBVE_ENOMEM, "pdf staging allocation failed");
+    CK(cudaMemcpyAsync(d, f, sizeof(double) * Q * n, cudaMemcpyHostToDevice, c->stream), "pdf copy");
+    CK(c->kt->pdfs_io(c->d, (int)(c->t & 1), d, 1, c->stream), "pdf write kernel");
+    CK(cudaStreamSynchronize(c->stream), "pdf sync");
+    dev_free(c, d);
+    return LBVE_OK;
+}
+
+lbve_status lbve_read_particle(lbve_ctx *c, int id, double out[24]) {
+    if (!c) return LBVE_EINVAL;
+    if (id < 0 || id >= c->nparts || !out) return fail(c, LBVE_EINVAL, "no such particle");
+    PartDev P;
+    CK(cudaMemcpyAsync(&P, c->d.parts + id, sizeof(PartDev), cudaMemcpyDeviceToHost, c->stream), "read particle");
+    CK(cudaStreamSynchronize(c->stream), "read particle sync");
+    for (int a = 0; a < 3; ++a) {
+        out[a] = P.X[a];
+        out[3 + a] = P.v[a];
+        out[6 + a] = P.w[a];
+        out[9 + a] = P.Fme[a];
+        out[12 + a] = P.Tme[a];
+        out[15 + a] = P.dP[a];
+        out[18 + a] = P.dL[a];
+    }
+    out[21] = P.m;
+    out[22] = P.I;
+    out[23] = P.R;
+    return LBVE_OK;
+}
+
+lbve_status lbve_read_body_forces(lbve_ctx *c, double *out) {
+    if (!c || !out) return c ? fail(c, LBVE_EINVAL, "out is NULL") : LBVE_EINVAL;
+    CK(cudaMemcpyAsync(out, c->body_F, sizeof(double) * 256 * 3, cudaMemcpyDeviceToHost, c->stream), "read forces");
+    CK(cudaStreamSynchronize(c->stream), "read forces sync");
+    return LBVE_OK;
+}
+
+lbve_status lbve_reduce(lbve_ctx *c, double out[6]) {
+    if (!c || !out) return c ? fail(c, LBVE_EINVAL, "out is NULL") : LBVE_EINVAL;
+    long long nb = 0;
+    c->kt->reduce(c->d, 0, nullptr, &nb, c->stream);
+    if ((size_t)nb * 6 > c->red_cap) {
+        dev_free(c, c->red);
+        c->red = (double *)dev_alloc(c, sizeof(double) * 6 * (size_t)nb);
+        if (!c->red) return fail(c, LBVE_ENOMEM, "reduction scratch allocation failed");
+        c->red_cap = (size_t)nb * 6;
+    }
+    CK(c->kt->reduce(c->d, (int)(c->t & 1), c->red, &nb, c->stream), "reduce kernel");
+    k_final_sum<<<1, 256, 0, c->stream>>>(c->red, nb, c->red_out);
+    CK(cudaGetLastError(), "final sum");
+    CK(cudaMemcpyAsync(out, c->red_out, sizeof(double) * 6, cudaMemcpyDeviceToHost, c->stream), "reduce copy");
+    CK(cudaStreamSynchronize(c->stream), "reduce sync");
+    return LBVE_OK;
+}
+
+lbve_status lbve_set_kernel_timing(lbve_ctx *c, int enable) {
+    if (!c) return LBVE_EINVAL;
+    CK(harvest_times(c), "timing harvest");
+    c->timing = enable != 0;
+    for (int k = 0; k < LBVE_KT_COUNT; ++k) {
+        c->kt_ms[k] = 0.0;
+        c->kt_count[k] = 0;
+    }
+    return LBVE_OK;
+}
+
+lbve_status lbve_read_kernel_times(lbve_ctx *c, double ms[LBVE_KT_COUNT], long long launches[LBVE_KT_COUNT]) {
+    if (!c || !ms || !launches) return c ? fail(c, LBVE_EINVAL, "NULL output") : LBVE_EINVAL;
+    CK(harvest_times(c), "timing harvest");
+    for (int k = 0; k < LBVE_KT_COUNT; ++k) {
+        ms[k] = c->kt_ms[k];
+        launches[k] = c->kt_count[k];
+    }
+    return LBVE_OK;
+}
+
+long long lbve_time(const lbve_ctx *c) { return c ? c->t : -1; }
+
+lbve_status lbve_synchronize(lbve_ctx *c) {
+    if (!c) return LBVE_EINVAL;
+    CK(cudaStreamSynchronize(c->stream), "synchronize");
+    return LBVE_OK;
+}
+
+const char *lbve_last_error(const lbve_ctx *c) { return c ? c->err.c_str() : g_create_error.c_str(); }
+
+const char *lbve_status_string(lbve_status s) {
+    return (s >= 0 && s <= LBVE_ESTATE) ? kStatusNames[s] : "LBVE_UNKNOWN";
+}
+
+} // extern "C"

@@ -1,0 +1,364 @@
+// lbve_device.cuh -- device-side building blocks of the coupled LB + Oldroyd-B step
+// (Kuron et al., arXiv:2009.12279): D3Q19 lattice, PDF storage codecs, boundary
+// velocities, the TRT collision with Guo forcing, the polymer force and the
+// finite-volume stress update.  Included by the per-precision kernel translation units.
+//
+// Storage: PDFs are structure-of-arrays, 19 arrays of `np` cells (np = n padded to a
+// multiple of 64), updated in place with the AA pattern: on an even step every cell
+// reads its own slots and writes the post-collision f*_i into its own slot -i; on an
+// odd step it reads f_i from slot -i of cell r - c_i and writes f*_i into slot i of
+// r + c_i.  Both steps touch every PDF once for reading and once for writing, half the
+// traffic of a two-array scheme.  A population that would stream into a solid cell is
+// bounced back (Eq. (ubb)) into the slot the next step reads it from; solid cells'
+// slots serve as the ghost storage for those bounced populations.
+//
+// Precision: FP64 storage keeps f_i itself and every formula is evaluated in the same
+// operation order as the plain statement of the paper's equations (the FP64 build has
+// FMA contraction off), so the FP64 mode reproduces a plain IEEE evaluation.  The FP32,
+// FP16 and BF16 storage modes keep the deviation (f_i - w_i rho0) * 2^k and do all
+// arithmetic in FP32 on deviations (rho = rho0 + sum of deviations).
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "lbve_launch.h"
+
+namespace lbve {
+
+// --------------------------------------------------------------------------------
+// D3Q19 velocity set (Sec. "Lattice Boltzmann"), packed two bits per direction so
+// that the component lookups fold to constants inside unrolled loops.
+// --------------------------------------------------------------------------------
+constexpr int kCX[Q] = {0, 1, -1, 0, 0, 0, 0, 1, -1, 1, -1, 1, -1, 1, -1, 0, 0, 0, 0};
+constexpr int kCY[Q] = {0, 0, 0, 1, -1, 0, 0, 1, -1, -1, 1, 0, 0, 0, 0, 1, -1, 1, -1};
+constexpr int kCZ[Q] = {0, 0, 0, 0, 0, 1, -1, 0, 0, 0, 0, 1, -1, -1, 1, 1, -1, -1, 1};
+
+constexpr uint64_t pack_dirs(const int (&c)[Q]) {
+    uint64_t m = 0;
+    for (int i = 0; i < Q; ++i) m |= (uint64_t)(c[i] + 1) << (2 * i);
+    return m;
+}
+constexpr uint64_t kPX = pack_dirs(kCX), kPY = pack_dirs(kCY), kPZ = pack_dirs(kCZ);
+
+__host__ __device__ __forceinline__ constexpr int cx(int i) { return (int)((kPX >> (2 * i)) & 3u) - 1; }
+__host__ __device__ __forceinline__ constexpr int cy(int i) { return (int)((kPY >> (2 * i)) & 3u) - 1; }
+__host__ __device__ __forceinline__ constexpr int cz(int i) { return (int)((kPZ >> (2 * i)) & 3u) - 1; }
+__host__ __device__ __forceinline__ constexpr int copp(int i) { return i == 0 ? 0 : ((i & 1) ? i + 1 : i - 1); }
+__host__ __device__ __forceinline__ constexpr int cdir(int i, int a) { return a == 0 ? cx(i) : (a == 1 ? cy(i) : cz(i)); }
+
+template <class R>
+__host__ __device__ __forceinline__ constexpr R wgt(int i) {
+    return i == 0 ? R(1.0 / 3.0) : (i < 7 ? R(1.0 / 18.0) : R(1.0 / 36.0));
+}
+
+// symmetric tensor component of (a, b) in the layout xx, yy, zz, xy, xz, yz
+__host__ __device__ __forceinline__ constexpr int comp(int a, int b) {
+    return a == b ? a : (a + b == 1 ? 3 : (a + b == 2 ? 4 : 5));
+}
+__host__ __device__ __forceinline__ constexpr int comp_i(int c) { return c < 3 ? c : (c == 5 ? 1 : 0); }
+__host__ __device__ __forceinline__ constexpr int comp_j(int c) { return c < 3 ? c : (c == 3 ? 1 : 2); }
+
+// --------------------------------------------------------------------------------
+// PDF storage codecs
+// --------------------------------------------------------------------------------
+template <class S>
+struct Store;
+template <>
+struct Store<double> {
+    using R = double;
+    static constexpr bool shifted = false;
+    __device__ static __forceinline__ double ld(const double *p, double) { return *p; }
+    __device__ static __forceinline__ void st(double *p, double v, double) { *p = v; }
+};
+template <>
+struct Store<float> {
+    using R = float;
+    static constexpr bool shifted = true;
+    __device__ static __forceinline__ float ld(const float *p, float inv) { return *p * inv; }
+    __device__ static __forceinline__ void st(float *p, float v, float sc) { *p = v * sc; }
+};
+template <>
+struct Store<__half> {
+    using R = float;
+    static constexpr bool shifted = true;
+    __device__ static __forceinline__ float ld(const __half *p, float inv) { return __half2float(*p) * inv; }
+    __device__ static __forceinline__ void st(__half *p, float v, float sc) { *p = __float2half_rn(v * sc); }
+};
+template <>
+struct Store<__nv_bfloat16> {
+    using R = float;
+    static constexpr bool shifted = true;
+    __device__ static __forceinline__ float ld(const __nv_bfloat16 *p, float inv) {
+        return __bfloat162float(*p) * inv;
+    }
+    __device__ static __forceinline__ void st(__nv_bfloat16 *p, float v, float sc) {
+        *p = __float2bfloat16_rn(v * sc);
+    }
+};
+
+struct Cell {
+    int x, y, z;
+    int xm, xp, ym, yp, zm, zp;
+    long long nx, nxy;
+    __device__ __forceinline__ Cell(const Geo &g, int x_, int y_, int z_) : x(x_), y(y_), z(z_) {
+        xm = x == 0 ? g.nx - 1 : x - 1;
+        xp = x == g.nx - 1 ? 0 : x + 1;
+        ym = y == 0 ? g.ny - 1 : y - 1;
+        yp = y == g.ny - 1 ? 0 : y + 1;
+        zm = z == 0 ? g.nz - 1 : z - 1;
+        zp = z == g.nz - 1 ? 0 : z + 1;
+        nx = g.nx;
+        nxy = (long long)g.nx * g.ny;
+    }
+    __device__ __forceinline__ int X(int d) const { return d == 0 ? x : (d > 0 ? xp : xm); }
+    __device__ __forceinline__ int Y(int d) const { return d == 0 ? y : (d > 0 ? yp : ym); }
+    __device__ __forceinline__ int Z(int d) const { return d == 0 ? z : (d > 0 ? zp : zm); }
+    __device__ __forceinline__ long long idx(int dx, int dy, int dz) const {
+        return (long long)X(dx) + nx * Y(dy) + nxy * Z(dz);
+    }
+    __device__ __forceinline__ long long self() const { return (long long)x + nx * y + nxy * z; }
+};
+
+// Boundary velocity u_b of the solid cell (xq, yq, zq) with flag fl: zero for a no-slip
+// wall, the class velocity for a moving wall (Eq. (ubb)), v + w x (r_b - X) with the
+// minimum-image lever arm for a particle cell (Eq. (surface-velocity)).
+template <class R>
+__device__ __forceinline__ void boundary_velocity(const Geo &g, const Phys<R> &ph, const PartDev *parts, int fl,
+                                                  int xq, int yq, int zq, R ub[3]) {
+    ub[0] = R(0);
+    ub[1] = R(0);
+    ub[2] = R(0);
+    if (fl >= FLAG_WALL0 && fl < FLAG_WALL0 + MAX_WALL) {
+        ub[0] = ph.wall_vel[fl - FLAG_WALL0][0];
+        ub[1] = ph.wall_vel[fl - FLAG_WALL0][1];
+        ub[2] = ph.wall_vel[fl - FLAG_WALL0][2];
+    } else if (fl >= FLAG_PART0 && fl < FLAG_PART0 + MAX_PART) {
+        const PartDev &P = parts[fl - FLAG_PART0];
+        double q[3] = {(double)xq, (double)yq, (double)zq};
+        int nn[3] = {g.nx, g.ny, g.nz};
+        double d[3];
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            d[a] = q[a] - P.X[a];
+            if (g.per[a]) d[a] -= (double)nn[a] * floor(d[a] / (double)nn[a] + 0.5);
+        }
+        ub[0] = (R)(P.v[0] + (P.w[1] * d[2] - P.w[2] * d[1]));
+        ub[1] = (R)(P.v[1] + (P.w[2] * d[0] - P.w[0] * d[2]));
+        ub[2] = (R)(P.v[2] + (P.w[0] * d[1] - P.w[1] * d[0]));
+    }
+}
+
+// --------------------------------------------------------------------------------
+// local operators
+// --------------------------------------------------------------------------------
+
+// Polymer force Eq. (force) on the D3Q7 faces (A_0 = 1): F_j = sum_faces s tau_kj(face),
+// face value by Eq. (interpolation), or tau(r) towards a solid cell (Eq. (extrapolation)).
+template <class R>
+__device__ __forceinline__ void polymer_force(const Geo &g, const Cell &cl, long long r, const R *__restrict__ tau,
+                                              const uint8_t *__restrict__ flag, R Fp[3]) {
+    const long long np = g.np;
+    R tr[6];
+#pragma unroll
+    for (int c = 0; c < 6; ++c) tr[c] = tau[c * np + r];
+    Fp[0] = R(0);
+    Fp[1] = R(0);
+    Fp[2] = R(0);
+#pragma unroll
+    for (int l = 0; l < 6; ++l) {
+        const int k = l >> 1;
+        const int s = (l & 1) ? -1 : 1;
+        const long long nb = cl.idx(k == 0 ? s : 0, k == 1 ? s : 0, k == 2 ? s : 0);
+        const bool fl = flag[nb] == FLAG_FLUID;
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+            const int c = comp(k, j);
+            const R tf = fl ? R(0.5) * (tr[c] + tau[c * np + nb]) : tr[c];
+            if (s > 0)
+                Fp[j] = Fp[j] + tf;
+            else
+                Fp[j] = Fp[j] - tf;
+        }
+    }
+}
+
+// Macroscopic moments, Eq. (macroscopic-velocity).  FP64 mode sums in direction order;
+// shifted modes return rho = rho0 + drho with drho summed over the deviations.
+template <class R, bool SH>
+__device__ __forceinline__ void moments(const R (&f)[Q], const R F[3], R rho0, R &rho, R &drho, R u[3]) {
+    if constexpr (!SH) {
+        R s = R(0);
+#pragma unroll
+        for (int i = 0; i < Q; ++i) s = s + f[i];
+        R j[3];
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            R t = R(0);
+#pragma unroll
+            for (int i = 0; i < Q; ++i) {
+                const int c = cdir(i, a);
+                if (c == 1) t = t + f[i];
+                if (c == -1) t = t - f[i];
+            }
+            j[a] = t;
+        }
+        rho = s;
+        drho = s;
+#pragma unroll
+        for (int a = 0; a < 3; ++a) u[a] = (j[a] + R(0.5) * F[a]) / s;
+    } else {
+        const R d0 = (f[0] + f[1]) + (f[2] + f[3]) + (f[4] + f[5]) + f[6];
+        const R d1 = (f[7] + f[8]) + (f[9] + f[10]) + (f[11] + f[12]);
+        const R d2 = (f[13] + f[14]) + (f[15] + f[16]) + (f[17] + f[18]);
+        drho = d0 + d1 + d2;
+        rho = rho0 + drho;
+        const R jx = (f[1] - f[2]) + (f[7] - f[8]) + (f[9] - f[10]) + (f[11] - f[12]) + (f[13] - f[14]);
+        const R jy = (f[3] - f[4]) + (f[7] - f[8]) + (f[10] - f[9]) + (f[15] - f[16]) + (f[17] - f[18]);
+        const R jz = (f[5] - f[6]) + (f[11] - f[12]) + (f[14] - f[13]) + (f[15] - f[16]) + (f[18] - f[17]);
+        const R ir = R(1) / rho;
+        u[0] = (jx + R(0.5) * F[0]) * ir;
+        u[1] = (jy + R(0.5) * F[1]) * ir;
+        u[2] = (jz + R(0.5) * F[2]) * ir;
+    }
+}
+
+// c_i . v for a direction with components in {-1,0,1}, in the order x, y, z.
+template <class R>
+__device__ __forceinline__ R cdot(int i, const R v[3]) {
+    R t = R(0);
+    bool first = true;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        const int c = cdir(i, a);
+        if (c != 0) {
+            if (first) {
+                t = c > 0 ? v[a] : -v[a];
+                first = false;
+            } else {
+                t = c > 0 ? t + v[a] : t - v[a];
+            }
+        }
+    }
+    return t;
+}
+
+// TRT collision with Guo forcing, Eqs. (lb), (lb-equilibrium), (guo), in place on f.
+// FP64 mode: feq_i = (w_i rho)(1 + 3 cu + 9/2 cu^2 - 3/2 u^2); shifted modes work on the
+// deviations with feq_i - w_i rho0 = w_i (drho + rho (3 cu + 9/2 cu^2 - 3/2 u^2)).
+template <class R, bool SH>
+__device__ __forceinline__ void collide(R (&f)[Q], R rho, R drho, const R u[3], const R F[3], const Phys<R> &ph) {
+    const R usq = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
+    const R uF = u[0] * F[0] + u[1] * F[1] + u[2] * F[2];
+    const R wp = ph.omega_p, wm = ph.omega_m;
+    // rest population
+    {
+        R feq0;
+        if constexpr (!SH)
+            feq0 = wgt<R>(0) * rho * (R(1) + R(3) * R(0) + R(4.5) * R(0) * R(0) - R(1.5) * usq);
+        else
+            feq0 = wgt<R>(0) * (drho - rho * (R(1.5) * usq));
+        const R D0 = wgt<R>(0) * (ph.A * R(0) + ph.B * (R(9) * R(0) * R(0) - R(3) * uF));
+        f[0] = f[0] - wp * (R(0.5) * (f[0] + f[0]) - R(0.5) * (feq0 + feq0)) - wm * R(0) + D0;
+    }
+#pragma unroll
+    for (int i = 1; i < Q; i += 2) {
+        const int ip = i + 1;
+        const R cu = cdot<R>(i, u);
+        const R cF = cdot<R>(i, F);
+        R fe_i, fe_o;
+        if constexpr (!SH) {
+            const R wr = wgt<R>(i) * rho;
+            fe_i = wr * (R(1) + R(3) * cu + R(4.5) * cu * cu - R(1.5) * usq);
+            fe_o = wr * (R(1) + R(3) * (-cu) + R(4.5) * (-cu) * (-cu) - R(1.5) * usq);
+        } else {
+            const R sym = R(4.5) * cu * cu - R(1.5) * usq;
+            fe_i = wgt<R>(i) * (drho + rho * (sym + R(3) * cu));
+            fe_o = wgt<R>(i) * (drho + rho * (sym - R(3) * cu));
+        }
+        const R Bt = ph.B * (R(9) * cu * cF - R(3) * uF);
+        const R Di = wgt<R>(i) * (ph.A * cF + Bt);
+        const R Do = wgt<R>(i) * (Bt - ph.A * cF);
+        const R fp = R(0.5) * (f[i] + f[ip]);
+        const R fm = R(0.5) * (f[i] - f[ip]);
+        const R ep = R(0.5) * (fe_i + fe_o);
+        const R em = R(0.5) * (fe_i - fe_o);
+        const R Pp = wp * (fp - ep);
+        const R Pm = wm * (fm - em);
+        const R fi = f[i] - Pp - Pm + Di;
+        const R fo = f[ip] - Pp + Pm + Do;
+        f[i] = fi;
+        f[ip] = fo;
+    }
+}
+
+// Finite-volume stress update of one fluid cell (Sec. "Discretization", "Stability
+// improvements"): velocity gradient by the central-point rule (boundary velocity as
+// the face value towards solid cells), donor-cell flux on the D3Q7 faces with zero flux
+// across solid links, source Eq. (source) without the tau div u term, explicit Euler.
+template <class R>
+__device__ __forceinline__ void fv_cell(const Geo &g, const Phys<R> &ph, const Cell &cl, long long r,
+                                        const R *__restrict__ tau, const R *__restrict__ u,
+                                        const uint8_t *__restrict__ flag, const PartDev *parts, R out[6]) {
+    const long long np = g.np;
+    R tr[6], ur[3];
+#pragma unroll
+    for (int c = 0; c < 6; ++c) tr[c] = tau[c * np + r];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) ur[a] = u[a * np + r];
+    R G[3][3];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        const long long npl = cl.idx(k == 0, k == 1, k == 2);
+        const long long nmi = cl.idx(-(k == 0), -(k == 1), -(k == 2));
+        const int fp_ = flag[npl], fm_ = flag[nmi];
+        R ubp[3], ubm[3];
+        if (fp_ != FLAG_FLUID)
+            boundary_velocity<R>(g, ph, parts, fp_, cl.X(k == 0), cl.Y(k == 1), cl.Z(k == 2), ubp);
+        if (fm_ != FLAG_FLUID)
+            boundary_velocity<R>(g, ph, parts, fm_, cl.X(-(k == 0)), cl.Y(-(k == 1)), cl.Z(-(k == 2)), ubm);
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+            const R up = fp_ == FLAG_FLUID ? R(0.5) * (ur[j] + u[j * np + npl]) : ubp[j];
+            const R um = fm_ == FLAG_FLUID ? R(0.5) * (ur[j] + u[j * np + nmi]) : ubm[j];
+            G[k][j] = up - um;
+        }
+    }
+    R net[6] = {R(0), R(0), R(0), R(0), R(0), R(0)};
+    if (ph.flux_on) {
+#pragma unroll
+        for (int l = 0; l < 6; ++l) {
+            const int k = l >> 1;
+            const int s = (l & 1) ? -1 : 1;
+            const long long nb = cl.idx(k == 0 ? s : 0, k == 1 ? s : 0, k == 2 ? s : 0);
+            if (flag[nb] != FLAG_FLUID) continue;
+            const R vout = s > 0 ? ur[k] : -ur[k];
+            const R unk = u[k * np + nb];
+            const R vin = s > 0 ? -unk : unk;
+#pragma unroll
+            for (int c = 0; c < 6; ++c) {
+                const R Jo = vout > R(0) ? vout * tr[c] : R(0);
+                const R Ji = vin > R(0) ? vin * tau[c * np + nb] : R(0);
+                net[c] = net[c] + (Jo - Ji);
+            }
+        }
+    }
+#pragma unroll
+    for (int c = 0; c < 6; ++c) {
+        R S = R(0);
+        if (ph.src_on) {
+            const int i = comp_i(c), j = comp_j(c);
+            R a = R(0), b = R(0);
+#pragma unroll
+            for (int k = 0; k < 3; ++k) a = a + tr[comp(i, k)] * G[k][j];
+#pragma unroll
+            for (int k = 0; k < 3; ++k) b = b + tr[comp(k, j)] * G[k][i];
+            S = a + b + ph.ep_l * (G[i][j] + G[j][i]) - ph.inv_l * tr[c];
+        }
+        out[c] = tr[c] - net[c] + S;
+    }
+}
+
+} // namespace lbve

@@ -1,0 +1,81 @@
+// lbve_launch.h -- internal interface between the host library (lbve_api.cu) and the
+// per-precision kernel translation units: parameter structs passed by value to the
+// kernels and a table of host-side launchers per PDF storage type.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stddef.h>
+#include <stdint.h>
+
+namespace lbve {
+
+constexpr int Q = 19;
+constexpr int FLAG_FLUID = 0;
+constexpr int FLAG_NOSLIP = 1;
+constexpr int FLAG_WALL0 = 2;
+constexpr int MAX_WALL = 16;
+constexpr int FLAG_PART0 = 64;
+constexpr int MAX_PART = 64;
+
+struct Geo {
+    int nx, ny, nz;
+    int per[3];
+    long long n;  // nx*ny*nz
+    long long np; // stride between the arrays of one field (n rounded up to 64)
+};
+
+template <class R>
+struct Phys {
+    R omega_p, omega_m;
+    R A, B;        // 3 (1 - omega-/2) and 1 - omega+/2 of the forcing term
+    R ep_l, inv_l; // eta_p / lambda_p and 1 / lambda_p
+    R g[3];
+    R rho0;        // shift base of the stored deviations (0 in FP64 mode)
+    R scale, inv_scale;
+    int flux_on, src_on;
+    R wall_vel[MAX_WALL][3];
+};
+
+// FP64 rigid-sphere state used by the particle kernels.
+struct PartDev {
+    double X[3], v[3], w[3];
+    double R, rho_p, m, I;
+    double Fext[3], Text[3];
+    double Fme[3], Tme[3];
+    double dP[3], dL[3];
+};
+
+// Device buffers of one solve.
+struct DevState {
+    Geo g;
+    Phys<double> ph;  // converted to the kernel's real type by the launchers
+    void *f;          // 19 * np PDF storage elements
+    void *tau[2];     // 6 * np reals each (ping-pong)
+    void *u;          // 3 * np reals
+    uint8_t *flag;    // np bytes
+    PartDev *parts;   // MAX_PART entries
+    int cur;          // index of tau^t in tau[]
+    int block_x;      // threads per block along x
+};
+
+struct KernelTable {
+    int prec;          // lbve_pdf_prec
+    size_t pdf_bytes;  // bytes per stored PDF
+    size_t real_bytes; // bytes per stress / velocity value
+    cudaError_t (*init)(const DevState &, const double *rho, const double *u, const double *tau, cudaStream_t);
+    cudaError_t (*lb)(const DevState &, int parity, cudaStream_t);
+    cudaError_t (*fv)(const DevState &, cudaStream_t);
+    cudaError_t (*momentum_exchange)(const DevState &, int parity, const long long *links, int nlinks,
+                                     double *contrib, cudaStream_t);
+    cudaError_t (*read)(const DevState &, int parity, double *rho, double *u, double *tau, cudaStream_t);
+    cudaError_t (*pdfs_io)(const DevState &, int parity, double *io, int write, cudaStream_t);
+    cudaError_t (*reduce)(const DevState &, int parity, double *partial, long long *nblocks, cudaStream_t);
+    cudaError_t (*probe)(const DevState &, int parity, const long long *cells, int count, double *out, cudaStream_t);
+};
+
+const KernelTable *table_f64();
+const KernelTable *table_f32();
+const KernelTable *table_f16();
+const KernelTable *table_bf16();
+
+} // namespace lbve

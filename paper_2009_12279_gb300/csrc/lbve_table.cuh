@@ -1,0 +1,126 @@
+// lbve_table.cuh -- host-side launchers of the step kernels for one PDF storage type,
+// collected in a KernelTable.  Included once per storage type by the precision TUs.
+#pragma once
+
+#include "lbve_kernels.cuh"
+
+namespace lbve {
+
+template <class R>
+inline Phys<R> convert_phys(const Phys<double> &p) {
+    Phys<R> o;
+    o.omega_p = (R)p.omega_p;
+    o.omega_m = (R)p.omega_m;
+    o.A = (R)p.A;
+    o.B = (R)p.B;
+    o.ep_l = (R)p.ep_l;
+    o.inv_l = (R)p.inv_l;
+    for (int k = 0; k < 3; ++k) o.g[k] = (R)p.g[k];
+    o.rho0 = (R)p.rho0;
+    o.scale = (R)p.scale;
+    o.inv_scale = (R)p.inv_scale;
+    o.flux_on = p.flux_on;
+    o.src_on = p.src_on;
+    for (int c = 0; c < MAX_WALL; ++c)
+        for (int k = 0; k < 3; ++k) o.wall_vel[c][k] = (R)p.wall_vel[c][k];
+    return o;
+}
+
+template <class S>
+struct Launch {
+    using R = typename Store<S>::R;
+
+    static KArgs<S> args(const DevState &d) {
+        KArgs<S> a;
+        a.g = d.g;
+        a.ph = convert_phys<R>(d.ph);
+        a.f = (S *)d.f;
+        a.tau = (const R *)d.tau[d.cur];
+        a.tau_out = (R *)d.tau[d.cur ^ 1];
+        a.u = (R *)d.u;
+        a.flag = d.flag;
+        a.parts = d.parts;
+        return a;
+    }
+    static dim3 grid3(const DevState &d) { return dim3((unsigned)((d.g.nx + d.block_x - 1) / d.block_x), d.g.ny, d.g.nz); }
+
+    static cudaError_t init(const DevState &d, const double *rho, const double *u, const double *tau, cudaStream_t s) {
+        KArgs<S> a = args(d);
+        const unsigned nb = (unsigned)((d.g.n + 255) / 256);
+        k_init<S><<<nb, 256, 0, s>>>(a, rho, u, tau, (R *)d.tau[d.cur]);
+        return cudaGetLastError();
+    }
+    static cudaError_t lb(const DevState &d, int parity, cudaStream_t s) {
+        KArgs<S> a = args(d);
+        if (parity == 0)
+            k_lb<S, 0><<<grid3(d), d.block_x, 0, s>>>(a);
+        else
+            k_lb<S, 1><<<grid3(d), d.block_x, 0, s>>>(a);
+        return cudaGetLastError();
+    }
+    static cudaError_t fv(const DevState &d, cudaStream_t s) {
+        KArgs<S> a = args(d);
+        k_fv<S><<<grid3(d), d.block_x, 0, s>>>(a);
+        return cudaGetLastError();
+    }
+    static cudaError_t momentum_exchange(const DevState &d, int parity, const long long *links, int nlinks,
+                                         double *contrib, cudaStream_t s) {
+        if (nlinks <= 0) return cudaSuccess;
+        KArgs<S> a = args(d);
+        const unsigned nb = (unsigned)((nlinks + 127) / 128);
+        if (parity == 0)
+            k_momentum_exchange<S, 0><<<nb, 128, 0, s>>>(a, links, nlinks, contrib);
+        else
+            k_momentum_exchange<S, 1><<<nb, 128, 0, s>>>(a, links, nlinks, contrib);
+        return cudaGetLastError();
+    }
+    static cudaError_t read(const DevState &d, int parity, double *rho, double *u, double *tau, cudaStream_t s) {
+        KArgs<S> a = args(d);
+        if (parity == 0)
+            k_read<S, 0><<<grid3(d), d.block_x, 0, s>>>(a, rho, u, tau);
+        else
+            k_read<S, 1><<<grid3(d), d.block_x, 0, s>>>(a, rho, u, tau);
+        return cudaGetLastError();
+    }
+    static cudaError_t pdfs_io(const DevState &d, int parity, double *io, int write, cudaStream_t s) {
+        KArgs<S> a = args(d);
+        if (parity == 0)
+            k_pdfs_io<S, 0><<<grid3(d), d.block_x, 0, s>>>(a, io, write);
+        else
+            k_pdfs_io<S, 1><<<grid3(d), d.block_x, 0, s>>>(a, io, write);
+        return cudaGetLastError();
+    }
+    static cudaError_t reduce(const DevState &d, int parity, double *partial, long long *nblocks, cudaStream_t s) {
+        KArgs<S> a = args(d);
+        dim3 g(grid3(d).x, d.g.ny, d.g.nz);
+        // the reduction kernel needs exactly 256 threads per block
+        g.x = (unsigned)((d.g.nx + 255) / 256);
+        *nblocks = (long long)g.x * g.y * g.z;
+        if (!partial) return cudaSuccess;
+        if (parity == 0)
+            k_reduce<S, 0><<<g, 256, 0, s>>>(a, partial);
+        else
+            k_reduce<S, 1><<<g, 256, 0, s>>>(a, partial);
+        return cudaGetLastError();
+    }
+
+    static cudaError_t probe(const DevState &d, int parity, const long long *cells, int count, double *out,
+                             cudaStream_t s) {
+        if (count <= 0) return cudaSuccess;
+        KArgs<S> a = args(d);
+        const unsigned nb = (unsigned)((count + 127) / 128);
+        if (parity == 0)
+            k_probe<S, 0><<<nb, 128, 0, s>>>(a, cells, count, out);
+        else
+            k_probe<S, 1><<<nb, 128, 0, s>>>(a, cells, count, out);
+        return cudaGetLastError();
+    }
+
+    static const KernelTable *table(int prec) {
+        static const KernelTable t = {prec, sizeof(S), sizeof(R), &init,   &lb,     &fv,
+                                      &momentum_exchange, &read, &pdfs_io, &reduce, &probe};
+        return &t;
+    }
+};
+
+} // namespace lbve

@@ -1,0 +1,283 @@
+"""Thin ctypes binding of the C ABI in include/lbve.h (argument marshalling only).
+
+Every step of the method runs in the CUDA kernels of liblbve.so; this module only
+converts numpy arrays and Python numbers into the ABI's plain pointers and sizes.
+If the library is missing it raises: there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes as ct
+import os
+import threading
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "liblbve.so")
+
+F64, F32, F16_SHIFTED, BF16_SHIFTED = 0, 1, 2, 3
+PRECISIONS = {"f64": F64, "f32": F32, "f16": F16_SHIFTED, "bf16": BF16_SHIFTED}
+FV_FLUX, FV_SOURCE = 1, 2
+SCHED_AUTO, SCHED_SPLIT, SCHED_FUSED = 0, 1, 2
+FLAG_FLUID, FLAG_NOSLIP, FLAG_WALL0, FLAG_PARTICLE0 = 0, 1, 2, 64
+KERNEL_KINDS = ["lb", "fv", "fused", "momentum_exchange", "particle", "", "", ""]
+STATUS = ["LBVE_OK", "LBVE_EINVAL", "LBVE_ENOMEM", "LBVE_ECUDA", "LBVE_EUNSTABLE", "LBVE_ETIMEOUT", "LBVE_ESTATE"]
+
+# every entry point declared in include/lbve.h
+EXPORTS = [
+    "lbve_default_params", "lbve_device_bytes", "lbve_create", "lbve_create_with_allocator", "lbve_destroy",
+    "lbve_set_geometry", "lbve_init_fields", "lbve_init_fields_device", "lbve_probe", "lbve_add_particle", "lbve_step", "lbve_read_fields",
+    "lbve_read_fields_device", "lbve_read_pdfs", "lbve_write_pdfs", "lbve_read_particle", "lbve_read_body_forces",
+    "lbve_reduce", "lbve_set_kernel_timing", "lbve_read_kernel_times", "lbve_time", "lbve_synchronize", "lbve_last_error", "lbve_status_string",
+]
+
+
+class LbveError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        self.status = status
+        name = STATUS[status] if 0 <= status < len(STATUS) else str(status)
+        super().__init__(f"{name}: {msg}")
+
+
+class Params(ct.Structure):
+    _fields_ = [
+        ("nx", ct.c_int), ("ny", ct.c_int), ("nz", ct.c_int),
+        ("periodic", ct.c_int * 3),
+        ("eta", ct.c_double), ("beta", ct.c_double), ("lambda_p", ct.c_double), ("rho0", ct.c_double),
+        ("body_force", ct.c_double * 3),
+        ("magic", ct.c_double),
+        ("pdf_prec", ct.c_int), ("pdf_scale_log2", ct.c_int), ("fv_terms", ct.c_int),
+        ("schedule", ct.c_int), ("block_x", ct.c_int),
+    ]
+
+
+ALLOC_FN = ct.CFUNCTYPE(ct.c_void_p, ct.c_size_t, ct.c_void_p, ct.c_void_p)
+FREE_FN = ct.CFUNCTYPE(None, ct.c_void_p, ct.c_size_t, ct.c_void_p, ct.c_void_p)
+
+_lock = threading.Lock()
+_lib = None
+
+
+def load(path: str | None = None):
+    """Load liblbve.so (raises if it has not been built)."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        p = path or os.environ.get("LBVE_LIB") or LIB_PATH
+        if not os.path.exists(p):
+            raise RuntimeError(f"CUDA library {p} is missing; build it with paper_2009_12279_gb300.build.build()")
+        L = ct.CDLL(p)
+        vp, dp = ct.c_void_p, ct.POINTER(ct.c_double)
+        L.lbve_default_params.argtypes = [ct.POINTER(Params)]
+        L.lbve_device_bytes.argtypes = [ct.POINTER(Params)]
+        L.lbve_device_bytes.restype = ct.c_size_t
+        L.lbve_create.argtypes = [ct.POINTER(Params), vp, ct.POINTER(vp)]
+        L.lbve_create_with_allocator.argtypes = [ct.POINTER(Params), vp, ALLOC_FN, FREE_FN, vp, ct.POINTER(vp)]
+        L.lbve_destroy.argtypes = [vp]
+        L.lbve_set_geometry.argtypes = [vp, vp, dp, ct.c_int]
+        L.lbve_init_fields.argtypes = [vp, vp, vp, vp]
+        L.lbve_init_fields_device.argtypes = [vp, vp, vp, vp]
+        L.lbve_probe.argtypes = [vp, vp, ct.c_int, dp]
+        L.lbve_add_particle.argtypes = [vp, dp, ct.c_double, ct.c_double, dp, dp, dp, dp, ct.POINTER(ct.c_int)]
+        L.lbve_step.argtypes = [vp, ct.c_int]
+        L.lbve_read_fields.argtypes = [vp, vp, vp, vp, vp]
+        L.lbve_read_fields_device.argtypes = [vp, vp, vp, vp]
+        L.lbve_read_pdfs.argtypes = [vp, vp]
+        L.lbve_write_pdfs.argtypes = [vp, vp]
+        L.lbve_read_particle.argtypes = [vp, ct.c_int, dp]
+        L.lbve_read_body_forces.argtypes = [vp, dp]
+        L.lbve_reduce.argtypes = [vp, dp]
+        L.lbve_set_kernel_timing.argtypes = [vp, ct.c_int]
+        L.lbve_read_kernel_times.argtypes = [vp, dp, ct.POINTER(ct.c_longlong)]
+        L.lbve_time.argtypes = [vp]
+        L.lbve_time.restype = ct.c_longlong
+        L.lbve_synchronize.argtypes = [vp]
+        L.lbve_last_error.argtypes = [vp]
+        L.lbve_last_error.restype = ct.c_char_p
+        L.lbve_status_string.argtypes = [ct.c_int]
+        L.lbve_status_string.restype = ct.c_char_p
+        _lib = L
+        return L
+
+
+def _dp(a):
+    return a.ctypes.data_as(ct.POINTER(ct.c_double))
+
+
+def _vec3(v):
+    return np.ascontiguousarray(np.asarray(v if v is not None else (0.0, 0.0, 0.0), dtype=np.float64).reshape(3))
+
+
+def default_params() -> Params:
+    p = Params()
+    load().lbve_default_params(ct.byref(p))
+    return p
+
+
+def make_params(shape, *, periodic=(1, 1, 1), eta=1.0 / 6.0, beta=0.5, lambda_p=1000.0, rho0=1.0,
+                body_force=(0.0, 0.0, 0.0), magic=3.0 / 16.0, precision="f32", pdf_scale_log2=-1,
+                fv_terms=FV_FLUX | FV_SOURCE, schedule=SCHED_AUTO, block_x=0) -> Params:
+    p = default_params()
+    p.nx, p.ny, p.nz = (int(v) for v in shape)
+    for a in range(3):
+        p.periodic[a] = int(periodic[a])
+        p.body_force[a] = float(body_force[a])
+    p.eta, p.beta, p.lambda_p, p.rho0, p.magic = float(eta), float(beta), float(lambda_p), float(rho0), float(magic)
+    p.pdf_prec = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
+    p.pdf_scale_log2, p.fv_terms, p.schedule, p.block_x = int(pdf_scale_log2), int(fv_terms), int(schedule), int(block_x)
+    return p
+
+
+def device_bytes(params: Params) -> int:
+    return int(load().lbve_device_bytes(ct.byref(params)))
+
+
+class Solver:
+    """One solve on the current CUDA device.  Host arrays are numpy, shape (..., nz, ny, nx)."""
+
+    def __init__(self, shape=None, *, params: Params | None = None, stream: int | None = None,
+                 allocator=None, **kw):
+        self._L = load()
+        self.params = params if params is not None else make_params(shape, **kw)
+        self.shape = (self.params.nx, self.params.ny, self.params.nz)
+        self.n = self.shape[0] * self.shape[1] * self.shape[2]
+        h = ct.c_void_p()
+        s = ct.c_void_p(stream or 0)
+        self._cb = None
+        if allocator is not None:
+            alloc, free = allocator
+            self._cb = (ALLOC_FN(lambda b, st, u: alloc(int(b), st) or 0),
+                        FREE_FN(lambda ptr, b, st, u: free(ptr, int(b), st)))
+            rc = self._L.lbve_create_with_allocator(ct.byref(self.params), s, self._cb[0], self._cb[1], None, ct.byref(h))
+        else:
+            rc = self._L.lbve_create(ct.byref(self.params), s, ct.byref(h))
+        if rc != 0:
+            raise LbveError(rc, self._L.lbve_last_error(None).decode())
+        self._h = h
+
+    # -- plumbing -------------------------------------------------------------
+    def _check(self, rc):
+        if rc != 0:
+            raise LbveError(rc, self._L.lbve_last_error(self._h).decode())
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._L.lbve_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def _grid(self, k=None):
+        nx, ny, nz = self.shape
+        return (nz, ny, nx) if k is None else (k, nz, ny, nx)
+
+    # -- API ------------------------------------------------------------------
+    def set_geometry(self, flags, wall_vel=()):
+        fl = np.ascontiguousarray(flags, dtype=np.uint8).reshape(self._grid())
+        wv = np.ascontiguousarray(np.asarray(wall_vel, dtype=np.float64).reshape(-1, 3)) if len(wall_vel) else None
+        self._check(self._L.lbve_set_geometry(self._h, fl.ctypes.data, _dp(wv) if wv is not None else None,
+                                              0 if wv is None else wv.shape[0]))
+
+    def init_fields(self, rho=None, u=None, tau=None):
+        keep = []
+
+        def ptr(a, k):
+            if a is None:
+                return None
+            a = np.ascontiguousarray(a, dtype=np.float64).reshape(self._grid(k))
+            keep.append(a)
+            return a.ctypes.data
+
+        self._check(self._L.lbve_init_fields(self._h, ptr(rho, None), ptr(u, 3), ptr(tau, 6)))
+
+    def init_fields_ptr(self, rho_ptr, u_ptr, tau_ptr):
+        """Initial fields from host pointers (e.g. pinned buffers); each may be 0."""
+        self._check(self._L.lbve_init_fields(self._h, rho_ptr or None, u_ptr or None, tau_ptr or None))
+
+    def init_fields_device(self, rho_ptr=0, u_ptr=0, tau_ptr=0):
+        """Initial fields from device pointers (FP64), e.g. torch tensors' data_ptr()."""
+        self._check(self._L.lbve_init_fields_device(self._h, rho_ptr or None, u_ptr or None, tau_ptr or None))
+
+    def probe(self, cells) -> np.ndarray:
+        """(count, 29): f_0..f_18, rho, u_x, u_y, u_z, tau_xx..tau_yz of the listed cells."""
+        idx = np.ascontiguousarray(np.asarray(cells, dtype=np.int64).reshape(-1))
+        out = np.zeros((idx.size, 29))
+        self._check(self._L.lbve_probe(self._h, idx.ctypes.data, int(idx.size), _dp(out)))
+        return out
+
+    def add_particle(self, X, R, rho_p, v=None, w=None, Fext=None, Text=None) -> int:
+        pid = ct.c_int(-1)
+        self._check(self._L.lbve_add_particle(self._h, _dp(_vec3(X)), float(R), float(rho_p), _dp(_vec3(v)),
+                                              _dp(_vec3(w)), _dp(_vec3(Fext)), _dp(_vec3(Text)), ct.byref(pid)))
+        return pid.value
+
+    def step(self, n: int = 1):
+        self._check(self._L.lbve_step(self._h, int(n)))
+
+    def synchronize(self):
+        self._check(self._L.lbve_synchronize(self._h))
+
+    @property
+    def time(self) -> int:
+        return int(self._L.lbve_time(self._h))
+
+    def read_fields(self):
+        rho = np.zeros(self._grid())
+        u = np.zeros(self._grid(3))
+        tau = np.zeros(self._grid(6))
+        flags = np.zeros(self._grid(), dtype=np.uint8)
+        self._check(self._L.lbve_read_fields(self._h, rho.ctypes.data, u.ctypes.data, tau.ctypes.data, flags.ctypes.data))
+        return rho, u, tau, flags
+
+    def read_fields_ptr(self, rho_ptr, u_ptr, tau_ptr, flags_ptr=0):
+        self._check(self._L.lbve_read_fields(self._h, rho_ptr or None, u_ptr or None, tau_ptr or None, flags_ptr or None))
+
+    def read_fields_device(self, rho_ptr, u_ptr, tau_ptr):
+        self._check(self._L.lbve_read_fields_device(self._h, rho_ptr or None, u_ptr or None, tau_ptr or None))
+
+    def read_pdfs(self) -> np.ndarray:
+        f = np.zeros(self._grid(19))
+        self._check(self._L.lbve_read_pdfs(self._h, f.ctypes.data))
+        return f
+
+    def write_pdfs(self, f):
+        f = np.ascontiguousarray(f, dtype=np.float64).reshape(self._grid(19))
+        self._check(self._L.lbve_write_pdfs(self._h, f.ctypes.data))
+
+    def read_particle(self, pid=0) -> dict:
+        o = np.zeros(24)
+        self._check(self._L.lbve_read_particle(self._h, int(pid), _dp(o)))
+        return {"X": o[0:3].copy(), "v": o[3:6].copy(), "w": o[6:9].copy(), "F": o[9:12].copy(),
+                "T": o[12:15].copy(), "dP": o[15:18].copy(), "dL": o[18:21].copy(),
+                "m": o[21], "I": o[22], "R": o[23]}
+
+    def body_forces(self) -> np.ndarray:
+        o = np.zeros((256, 3))
+        self._check(self._L.lbve_read_body_forces(self._h, _dp(o)))
+        return o
+
+    def set_kernel_timing(self, enable: bool = True):
+        self._check(self._L.lbve_set_kernel_timing(self._h, int(bool(enable))))
+
+    def kernel_times(self) -> dict:
+        """{kind: (total_ms, launches)} of the kernels launched while timing was on."""
+        ms = np.zeros(8)
+        cnt = (ct.c_longlong * 8)()
+        self._check(self._L.lbve_read_kernel_times(self._h, _dp(ms), cnt))
+        return {k: (float(ms[i]), int(cnt[i])) for i, k in enumerate(KERNEL_KINDS) if k and cnt[i] > 0}
+
+    def reduce(self) -> dict:
+        o = np.zeros(6)
+        self._check(self._L.lbve_reduce(self._h, _dp(o)))
+        return {"mass": o[0], "momentum": o[1:4].copy(), "fluid_cells": int(o[4]), "bad": bool(o[5] > 0)}

@@ -1,0 +1,117 @@
+"""Seeded synthetic inputs shaped like the paper's workloads (geometry, initial fields).
+
+These generators hold none of the method's arithmetic: they only build flag fields,
+random initial velocities and stresses, and the parameter sets of the benchmark
+configurations.  Both the CUDA library and the CPU oracle are fed from here.
+Arrays use the (…, nz, ny, nx) layout of the C ABI (x fastest).
+"""
+from __future__ import annotations
+
+import math
+
+import numpy as np
+
+FLUID, NOSLIP, WALL0 = 0, 1, 2
+
+
+def channel_flags(shape, wall_axis=1, top_flag=NOSLIP, bottom_flag=NOSLIP):
+    """Channel with solid first and last layers along wall_axis (0=x, 1=y, 2=z)."""
+    nx, ny, nz = shape
+    fl = np.zeros((nz, ny, nx), np.uint8)
+    ax = 2 - wall_axis
+    idx = [slice(None)] * 3
+    idx[ax] = 0
+    fl[tuple(idx)] = bottom_flag
+    idx[ax] = -1
+    fl[tuple(idx)] = top_flag
+    return fl
+
+
+def sphere_mask(shape, centre, radius):
+    """Cells whose centre (integer coordinates) lies within radius of centre."""
+    nx, ny, nz = shape
+    z, y, x = np.meshgrid(np.arange(nz), np.arange(ny), np.arange(nx), indexing="ij")
+    return ((x - centre[0]) ** 2 + (y - centre[1]) ** 2 + (z - centre[2]) ** 2) <= radius * radius
+
+
+def random_obstacles(shape, fraction, seed):
+    """Seeded Bernoulli(fraction) no-slip obstacles."""
+    nx, ny, nz = shape
+    rng = np.random.default_rng(seed)
+    return (rng.random((nz, ny, nx)) < fraction).astype(np.uint8)
+
+
+def random_velocity(shape, amplitude, seed):
+    """u ~ U(-amplitude, amplitude) per component and cell."""
+    nx, ny, nz = shape
+    rng = np.random.default_rng(seed)
+    return rng.uniform(-amplitude, amplitude, (3, nz, ny, nx))
+
+
+def random_stress(shape, amplitude, seed):
+    nx, ny, nz = shape
+    rng = np.random.default_rng(seed)
+    return amplitude * rng.standard_normal((6, nz, ny, nx))
+
+
+# ---------------------------------------------------------------------------------
+# the benchmark configurations
+# ---------------------------------------------------------------------------------
+def config_channel(nx=4, ny=32, nz=4):
+    """Plain method, FP64: periodic channel with walls at y=0 and y=ny-1, g=1e-6 along x,
+    rho0=1, eta=1/6, beta=0.5, lambda=3000, zero initial velocity and stress."""
+    return {
+        "shape": (nx, ny, nz),
+        "params": dict(periodic=(1, 0, 1), eta=1.0 / 6.0, beta=0.5, lambda_p=3000.0, rho0=1.0,
+                       body_force=(1e-6, 0.0, 0.0)),
+        "flags": channel_flags((nx, ny, nz), 1),
+        "wall_vel": (),
+        "steps": 20000,
+    }
+
+
+def duct_centreline_factor(aspect=1.0, terms=60):
+    """u_c = factor * g H^2 / eta for a square duct of side H (textbook Fourier series)."""
+    s = 0.0
+    for n in range(1, 2 * terms, 2):
+        s += (-1) ** ((n - 1) // 2) / n ** 3 * (1.0 - 1.0 / math.cosh(n * math.pi * aspect / 2.0))
+    return 4.0 / math.pi ** 3 * s / 1.0
+
+
+def config_sphere_duct(n=128, radius=12.0, beta=0.5, wi=0.5, g=5e-6, eta=1.0):
+    """Fixed complex boundary: n^3 box periodic in x, no-slip walls in y and z, a fixed
+    sphere (wall class 0, zero velocity) at the centre, body force g along x.  lambda is
+    set from Wi = lambda u_ref / R with u_ref the empty-duct centreline velocity."""
+    shape = (n, n, n)
+    fl = np.zeros((n, n, n), np.uint8)
+    fl[:, 0, :] = NOSLIP
+    fl[:, -1, :] = NOSLIP
+    fl[0, :, :] = NOSLIP
+    fl[-1, :, :] = NOSLIP
+    c = (n - 1) / 2.0
+    fl[sphere_mask(shape, (c, c, c), radius)] = WALL0
+    H = n - 2.0
+    u_ref = duct_centreline_factor() * g * H * H / eta
+    lam = wi * radius / u_ref
+    return {
+        "shape": shape,
+        "params": dict(periodic=(1, 0, 0), eta=eta, beta=beta, lambda_p=lam, rho0=1.0, body_force=(g, 0.0, 0.0)),
+        "flags": fl,
+        "wall_vel": [(0.0, 0.0, 0.0)],
+        "steps": 50000,
+        "u_ref": u_ref,
+    }
+
+
+def config_throughput(n=512, seed=0, obstacle_fraction=0.01, beta=0.5, lam=1000.0):
+    """Throughput, single large domain: n^3 periodic box, 1 % seeded Bernoulli obstacles,
+    u ~ U(-1e-3, 1e-3), zero stress, beta=0.5, lambda=1000, eta=1/6."""
+    shape = (n, n, n)
+    return {
+        "shape": shape,
+        "params": dict(periodic=(1, 1, 1), eta=1.0 / 6.0, beta=beta, lambda_p=lam, rho0=1.0,
+                       body_force=(0.0, 0.0, 0.0)),
+        "flags_fn": lambda: random_obstacles(shape, obstacle_fraction, seed),
+        "u_fn": lambda: random_velocity(shape, 1e-3, seed + 1),
+        "steps": 1000,
+    }

@@ -1,0 +1,185 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 oracle.
+
+FP64 storage must match to relative L2 <= 1e-12 after up to 1000 steps, FP32 storage
+to <= 1e-5; FP16/BF16 shifted storage errors are measured and bounded loosely.
+"""
+import numpy as np
+import pytest
+
+from gpu_helpers import TOL_F32, TOL_F64, compare, pair, require_gpu
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _gpu():
+    require_gpu()
+
+
+def _channel_case():
+    from paper_2009_12279_gb300 import workloads
+
+    cfg = workloads.config_channel()
+    return cfg["shape"], cfg["params"], cfg["flags"]
+
+
+def _obstacle_case(shape=(37, 20, 18), seed=3):
+    """Ragged x extent, walls in y (bottom no-slip, top a moving wall class), a tracked
+    obstacle class, random no-slip obstacles, random initial u and tau, body force."""
+    from paper_2009_12279_gb300 import workloads
+
+    nx, ny, nz = shape
+    fl = workloads.channel_flags(shape, 1, top_flag=workloads.WALL0 + 1)
+    rng = np.random.default_rng(seed)
+    fl[(rng.random((nz, ny, nx)) < 0.03) & (fl == 0)] = workloads.NOSLIP
+    fl[5:9, 6:10, 10:15] = workloads.WALL0
+    wall = [(0.0, 0.0, 0.0), (2e-3, 0.0, -1e-3)]
+    u0 = workloads.random_velocity(shape, 2e-3, seed + 1) * (fl == 0)
+    t0 = workloads.random_stress(shape, 1e-5, seed + 2) * (fl == 0)
+    rho0 = 1.0 + 1e-3 * np.random.default_rng(seed + 3).standard_normal((nz, ny, nx))
+    prm = dict(periodic=(1, 0, 1), eta=1.0 / 6.0, beta=0.6, lambda_p=150.0, body_force=(1e-5, 0.0, 3e-6))
+    return shape, prm, fl, wall, rho0, u0, t0
+
+
+def test_fp64_channel_1000_steps():
+    shape, prm, fl = _channel_case()
+    g, o = pair(shape, prm, fl, precision="f64")
+    g.step(1000)
+    o.step(1000)
+    e = compare(g, o)
+    assert max(e["f"], e["u"], e["tau"]) <= TOL_F64, e
+    assert e["rho"] <= 1e-14
+
+
+@pytest.mark.parametrize("block_x", [32, 64, 128])
+def test_fp64_obstacles_moving_wall_body_forces(block_x):
+    shape, prm, fl, wall, rho0, u0, t0 = _obstacle_case()
+    g, o = pair(shape, prm, fl, wall, rho=rho0, u=u0, tau=t0, precision="f64", block_x=block_x)
+    for k in range(4):
+        g.step(75 if k else 76)
+        o.step(75 if k else 76)
+    assert g.time == o.time == 301
+    e = compare(g, o)
+    assert max(e["f"], e["u"], e["tau"]) <= TOL_F64, e
+    bg, bo = g.body_forces(), o.body_forces()
+    for fl_v in (2, 3):
+        assert np.linalg.norm(bg[fl_v] - bo[fl_v]) <= TOL_F64 * np.linalg.norm(bo[fl_v]), (fl_v, bg[fl_v], bo[fl_v])
+    assert np.abs(bo[2]).max() > 0
+
+
+def test_fp64_is_bitwise_repeatable_across_block_sizes():
+    shape, prm, fl, wall, rho0, u0, t0 = _obstacle_case((33, 12, 10))
+    outs = []
+    for bx in (32, 256):
+        g, _ = pair(shape, prm, fl, wall, rho=rho0, u=u0, tau=t0, precision="f64", block_x=bx)
+        g.step(57)
+        outs.append(g.read_pdfs())
+    assert np.array_equal(outs[0], outs[1])
+
+
+def test_fp32_channel_1000_steps():
+    shape, prm, fl = _channel_case()
+    g, o = pair(shape, prm, fl, precision="f32")
+    g.step(1000)
+    o.step(1000)
+    e = compare(g, o)
+    assert max(e["u"], e["tau"]) <= TOL_F32, e
+
+
+def test_fp32_obstacles_1000_steps():
+    shape, prm, fl, wall, rho0, u0, t0 = _obstacle_case()
+    g, o = pair(shape, prm, fl, wall, rho=rho0, u=u0, tau=t0, precision="f32")
+    g.step(1000)
+    o.step(1000)
+    e = compare(g, o)
+    assert max(e["u"], e["tau"]) <= TOL_F32, e
+    bg, bo = g.body_forces(), o.body_forces()
+    assert np.linalg.norm(bg[2] - bo[2]) <= 1e-4 * np.linalg.norm(bo[2])
+
+
+@pytest.mark.parametrize("precision,bound", [("f16", 5e-2), ("bf16", 2e-1)])
+def test_reduced_precision_error_is_reported(precision, bound, capsys):
+    shape, prm, fl, wall, rho0, u0, t0 = _obstacle_case()
+    g, o = pair(shape, prm, fl, wall, rho=rho0, u=u0, tau=t0, precision=precision)
+    g.step(1000)
+    o.step(1000)
+    e = compare(g, o)
+    with capsys.disabled():
+        print(f"\n[{precision}] rel L2 vs FP64 oracle after 1000 steps: u {e['u']:.3e} tau {e['tau']:.3e}")
+    assert np.isfinite([e["u"], e["tau"]]).all()
+    assert max(e["u"], e["tau"]) <= bound, e
+
+
+# ---------------------------------------------------------------------------------
+# edge and degenerate cases
+# ---------------------------------------------------------------------------------
+def test_zero_steps_is_a_no_op():
+    shape, prm, fl = _channel_case()
+    g, o = pair(shape, prm, fl, precision="f64")
+    g.step(0)
+    assert g.time == 0
+    e = compare(g, o)
+    assert e["f"] == 0.0
+
+
+def test_single_cell_periodic_domain():
+    prm = dict(periodic=(1, 1, 1), eta=0.3, beta=0.4, lambda_p=50.0, body_force=(1e-4, -2e-4, 5e-5))
+    u0 = np.array([1e-3, 2e-3, -1e-3]).reshape(3, 1, 1, 1)
+    g, o = pair((1, 1, 1), prm, u=u0, precision="f64")
+    g.step(25)
+    o.step(25)
+    e = compare(g, o)
+    assert max(e["f"], e["u"]) <= TOL_F64, e
+
+
+def test_isolated_fluid_cell_and_all_solid_domain():
+    prm = dict(periodic=(1, 1, 1), eta=1.0 / 6.0, beta=0.5, lambda_p=100.0, body_force=(1e-5, 0.0, 0.0))
+    fl = np.ones((3, 3, 3), np.uint8)
+    fl[1, 1, 1] = 0
+    g, o = pair((3, 3, 3), prm, fl, precision="f64")
+    g.step(40)
+    o.step(40)
+    e = compare(g, o)
+    assert max(e["f"], e["u"]) <= TOL_F64, e
+    solid = np.ones((4, 4, 4), np.uint8)
+    g2, _ = pair((4, 4, 4), prm, solid, precision="f32")
+    g2.step(5)
+    r = g2.reduce()
+    assert r["fluid_cells"] == 0 and not r["bad"]
+
+
+def test_newtonian_limit_beta_zero():
+    shape, prm, fl = _channel_case()
+    prm = dict(prm, beta=0.0, lambda_p=0.0)
+    g, o = pair(shape, prm, fl, precision="f64")
+    g.step(500)
+    o.step(500)
+    e = compare(g, o)
+    assert max(e["f"], e["u"]) <= TOL_F64 and e["tau"] == 0.0, e
+
+
+def test_invalid_geometry_is_rejected():
+    from paper_2009_12279_gb300 import LbveError, Solver
+
+    g = Solver((6, 6, 6), periodic=(1, 0, 1), precision="f32")
+    with pytest.raises(LbveError):
+        g.set_geometry(np.zeros((6, 6, 6), np.uint8))  # fluid in the outer y layers
+    bad = np.zeros((6, 6, 6), np.uint8)
+    bad[:, 0], bad[:, -1] = 1, 1
+    bad[2, 2, 2] = 9  # undeclared wall class
+    with pytest.raises(LbveError):
+        g.set_geometry(bad)
+
+
+def test_mass_conservation_fp32_reduction():
+    from paper_2009_12279_gb300 import Solver, workloads
+
+    shape = (40, 24, 16)
+    fl = workloads.random_obstacles(shape, 0.02, 5)
+    g = Solver(shape, precision="f32", beta=0.5, lambda_p=300.0)
+    g.set_geometry(fl)
+    g.init_fields(u=workloads.random_velocity(shape, 1e-3, 6))
+    m0 = g.reduce()["mass"]
+    g.step(300)
+    r = g.reduce()
+    assert abs(r["mass"] - m0) / m0 < 1e-7 and not r["bad"]
