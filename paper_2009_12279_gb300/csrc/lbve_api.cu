@@ -160,6 +160,7 @@ void set_phys(lbve_ctx *c) {
     ph.inv_l = p.lambda_p > 0.0 ? 1.0 / p.lambda_p : 0.0;
     for (int k = 0; k < 3; ++k) ph.g[k] = p.body_force[k];
     ph.rho0 = p.pdf_prec == LBVE_F64 ? 0.0 : p.rho0;
+    ph.rho_ref = p.rho0;
     int k = p.pdf_scale_log2;
     if (k < 0) k = p.pdf_prec == LBVE_F16_SHIFTED ? 15 : 0;
     if (p.pdf_prec == LBVE_F64) k = 0;
@@ -229,35 +230,47 @@ __global__ void k_final_sum(const double *__restrict__ partial, long long nblock
     if (threadIdx.x < 6) out[threadIdx.x] = sh[threadIdx.x][0];
 }
 
-// Host-side list of links (fluid cell, direction into a wall-class cell), in cell order
-// then direction order, grouped by flag value (stable), with the segment boundaries.
+// Host-side list of links (fluid cell r, direction i with r + c_i a wall-class cell),
+// ordered by flag value, then cell, then direction (the order of a plain cell loop
+// within each body).  Built from the wall-class cells, so its cost is O(wall cells).
 void build_wall_links(const lbve_ctx *c, std::vector<long long> &links, std::vector<int> &seg,
                       std::vector<int> &seg_flag) {
+    static const int CX[Q] = {0, 1, -1, 0, 0, 0, 0, 1, -1, 1, -1, 1, -1, 1, -1, 0, 0, 0, 0};
+    static const int CY[Q] = {0, 0, 0, 1, -1, 0, 0, 1, -1, -1, 1, 0, 0, 0, 0, 1, -1, 1, -1};
+    static const int CZ[Q] = {0, 0, 0, 0, 0, 1, -1, 0, 0, 0, 0, 1, -1, -1, 1, 1, -1, -1, 1};
     const int nx = c->p.nx, ny = c->p.ny, nz = c->p.nz;
     const std::vector<uint8_t> &fl = c->flags_host;
-    std::vector<std::vector<long long>> by_flag(256);
-    for (int z = 0; z < nz; ++z)
-        for (int y = 0; y < ny; ++y)
-            for (int x = 0; x < nx; ++x) {
-                const long long r = x + (long long)nx * (y + (long long)ny * z);
-                if (fl[r] != FLAG_FLUID) continue;
-                for (int i = 1; i < Q; ++i) {
-                    static const int CX[Q] = {0, 1, -1, 0, 0, 0, 0, 1, -1, 1, -1, 1, -1, 1, -1, 0, 0, 0, 0};
-                    static const int CY[Q] = {0, 0, 0, 1, -1, 0, 0, 1, -1, -1, 1, 0, 0, 0, 0, 1, -1, 1, -1};
-                    static const int CZ[Q] = {0, 0, 0, 0, 0, 1, -1, 0, 0, 0, 0, 1, -1, -1, 1, 1, -1, -1, 1};
-                    const int xq = (x + CX[i] + nx) % nx, yq = (y + CY[i] + ny) % ny, zq = (z + CZ[i] + nz) % nz;
-                    const uint8_t f = fl[xq + (long long)nx * (yq + (long long)ny * zq)];
-                    if (f >= FLAG_WALL0 && f < FLAG_WALL0 + MAX_WALL) by_flag[f].push_back((r << 5) | i);
-                }
+    const long long n = (long long)nx * ny * nz;
+    std::vector<std::pair<int, long long>> tmp;  // (flag, (r << 5) | i)
+    for (long long rw = 0; rw < n; ++rw) {
+        const uint8_t f = fl[rw];
+        if (f < FLAG_WALL0 || f >= FLAG_WALL0 + MAX_WALL) continue;
+        const int x = (int)(rw % nx), y = (int)((rw / nx) % ny), z = (int)(rw / ((long long)nx * ny));
+        for (int i = 1; i < Q; ++i) {
+            // fluid cell r with r + c_i = rw
+            int xq = x - CX[i], yq = y - CY[i], zq = z - CZ[i];
+            if (xq < 0 || xq >= nx || yq < 0 || yq >= ny || zq < 0 || zq >= nz) {
+                if (!c->p.periodic[0] && (xq < 0 || xq >= nx)) continue;
+                if (!c->p.periodic[1] && (yq < 0 || yq >= ny)) continue;
+                if (!c->p.periodic[2] && (zq < 0 || zq >= nz)) continue;
+                xq = (xq + nx) % nx;
+                yq = (yq + ny) % ny;
+                zq = (zq + nz) % nz;
             }
+            const long long r = xq + (long long)nx * (yq + (long long)ny * zq);
+            if (fl[r] == FLAG_FLUID) tmp.push_back({(int)f, (r << 5) | i});
+        }
+    }
+    std::sort(tmp.begin(), tmp.end());
     links.clear();
     seg.clear();
     seg_flag.clear();
-    for (int f = 0; f < 256; ++f) {
-        if (by_flag[f].empty()) continue;
-        seg.push_back((int)links.size());
-        seg_flag.push_back(f);
-        links.insert(links.end(), by_flag[f].begin(), by_flag[f].end());
+    for (size_t k = 0; k < tmp.size(); ++k) {
+        if (k == 0 || tmp[k].first != tmp[k - 1].first) {
+            seg.push_back((int)links.size());
+            seg_flag.push_back(tmp[k].first);
+        }
+        links.push_back(tmp[k].second);
     }
     seg.push_back((int)links.size());
 }
@@ -342,7 +355,7 @@ lbve_status create_impl(const lbve_params *p, void *stream, lbve_alloc_fn alloc,
     if (e == cudaSuccess) e = cudaMemsetAsync(c->d.tau[1], 0, (size_t)6 * np * c->kt->real_bytes, c->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(c->d.parts, 0, sizeof(PartDev) * MAX_PART, c->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(c->body_F, 0, sizeof(double) * 256 * 3, c->stream);
-    if (e == cudaSuccess) e = c->kt->init(c->d, nullptr, nullptr, nullptr, c->stream);
+    if (e == cudaSuccess) e = c->kt->init(c->d, nullptr, nullptr, nullptr, 0, g.n, g.n, c->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
     if (e != cudaSuccess) {
         g_create_error = std::string("initialisation failed: ") + cudaGetErrorString(e);
@@ -392,14 +405,16 @@ cudaError_t harvest_times(lbve_ctx *c) {
     return cudaSuccess;
 }
 
-// Stage a host array to a temporary device buffer.
-lbve_status stage(lbve_ctx *c, const void *host, size_t bytes, void **dev) {
-    *dev = nullptr;
-    if (!host) return LBVE_OK;
-    *dev = dev_alloc(c, bytes);
-    if (!*dev) return fail(c, LBVE_ENOMEM, "staging allocation failed");
-    CK(cudaMemcpyAsync(*dev, host, bytes, cudaMemcpyHostToDevice, c->stream), "stage copy");
-    return LBVE_OK;
+// Host <-> device transfers of the FP64 fields go through a bounded staging buffer in
+// slabs of whole z-planes (10 doubles per cell: rho, u, tau).
+constexpr size_t kStagingBytes = size_t(256) << 20;
+
+int slab_planes(const lbve_ctx *c) {
+    const long long plane = (long long)c->p.nx * c->p.ny;
+    long long k = (long long)(kStagingBytes / (sizeof(double) * 10 * (size_t)plane));
+    if (k < 1) k = 1;
+    if (k > c->p.nz) k = c->p.nz;
+    return (int)k;
 }
 
 } // namespace
@@ -463,19 +478,30 @@ lbve_status lbve_set_geometry(lbve_ctx *c, const uint8_t *flags, const double *w
     if (n_wall < 0 || n_wall > MAX_WALL || (n_wall > 0 && !wall_vel))
         return fail(c, LBVE_EINVAL, "n_wall must be in [0, 16] with wall_vel given");
     const int nx = c->p.nx, ny = c->p.ny, nz = c->p.nz;
+    bool ok[256] = {false};
+    ok[FLAG_FLUID] = ok[FLAG_NOSLIP] = true;
+    for (int k = 0; k < n_wall; ++k) ok[FLAG_WALL0 + k] = true;
     for (long long r = 0; r < c->d.g.n; ++r) {
-        const uint8_t f = flags[r];
-        if (f >= FLAG_WALL0 + n_wall && f != FLAG_FLUID && f != FLAG_NOSLIP) {
+        if (!ok[flags[r]]) {
             char b[128];
-            std::snprintf(b, sizeof b, "flag %d at cell %lld is not fluid, no-slip or a declared wall class", (int)f, r);
+            std::snprintf(b, sizeof b, "flag %d at cell %lld is not fluid, no-slip or a declared wall class",
+                          (int)flags[r], r);
             return fail(c, LBVE_EINVAL, b);
         }
-        if (f == FLAG_FLUID) {
-            const int x = (int)(r % nx), y = (int)((r / nx) % ny), z = (int)(r / ((long long)nx * ny));
-            const int q[3] = {x, y, z}, nn[3] = {nx, ny, nz};
-            for (int a = 0; a < 3; ++a)
-                if (!c->p.periodic[a] && (q[a] == 0 || q[a] == nn[a] - 1))
-                    return fail(c, LBVE_EINVAL, "fluid cell in the outer layer of a non-periodic direction");
+    }
+    // a non-periodic direction needs non-fluid first and last layers
+    const int nn[3] = {nx, ny, nz};
+    for (int a = 0; a < 3; ++a) {
+        if (c->p.periodic[a]) continue;
+        for (int side = 0; side < 2; ++side) {
+            const int q = side ? nn[a] - 1 : 0;
+            const int b1 = a == 0 ? ny : nx, b2 = a == 2 ? ny : nz;
+            for (int j = 0; j < b2; ++j)
+                for (int i = 0; i < b1; ++i) {
+                    const int x = a == 0 ? q : i, y = a == 1 ? q : (a == 0 ? i : j), z = a == 2 ? q : j;
+                    if (flags[x + (long long)nx * (y + (long long)ny * z)] == FLAG_FLUID)
+                        return fail(c, LBVE_EINVAL, "fluid cell in the outer layer of a non-periodic direction");
+                }
         }
     }
     for (int k = 0; k < MAX_WALL; ++k)
@@ -493,18 +519,29 @@ lbve_status lbve_set_geometry(lbve_ctx *c, const uint8_t *flags, const double *w
 
 lbve_status lbve_init_fields(lbve_ctx *c, const double *rho, const double *u, const double *tau) {
     if (!c) return LBVE_EINVAL;
-    const long long n = c->d.g.n;
-    void *drho, *du, *dtau;
-    lbve_status s;
-    if ((s = stage(c, rho, sizeof(double) * n, &drho)) != LBVE_OK) return s;
-    if ((s = stage(c, u, sizeof(double) * 3 * n, &du)) != LBVE_OK) return s;
-    if ((s = stage(c, tau, sizeof(double) * 6 * n, &dtau)) != LBVE_OK) return s;
+    const long long n = c->d.g.n, plane = (long long)c->p.nx * c->p.ny;
+    const int zs = slab_planes(c);
+    const long long cap = plane * zs;
+    double *st = (double *)dev_alloc(c, sizeof(double) * 10 * (size_t)cap);
+    if (!st) return fail(c, LBVE_ENOMEM, "staging allocation failed");
     c->d.cur = 0;
-    CK(c->kt->init(c->d, (const double *)drho, (const double *)du, (const double *)dtau, c->stream), "init kernel");
+    for (int z0 = 0; z0 < c->p.nz; z0 += zs) {
+        const int z1 = std::min(c->p.nz, z0 + zs);
+        const long long r0 = (long long)z0 * plane, cnt = (long long)(z1 - z0) * plane;
+        double *srho = st, *su = st + cnt, *stau = st + 4 * cnt;
+        if (rho) CK(cudaMemcpyAsync(srho, rho + r0, sizeof(double) * cnt, cudaMemcpyHostToDevice, c->stream), "init copy");
+        for (int k = 0; u && k < 3; ++k)
+            CK(cudaMemcpyAsync(su + k * cnt, u + k * n + r0, sizeof(double) * cnt, cudaMemcpyHostToDevice, c->stream),
+               "init copy");
+        for (int k = 0; tau && k < 6; ++k)
+            CK(cudaMemcpyAsync(stau + k * cnt, tau + k * n + r0, sizeof(double) * cnt, cudaMemcpyHostToDevice,
+                               c->stream),
+               "init copy");
+        CK(c->kt->init(c->d, rho ? srho : nullptr, u ? su : nullptr, tau ? stau : nullptr, r0, cnt, cnt, c->stream),
+           "init kernel");
+    }
     CK(cudaStreamSynchronize(c->stream), "init sync");
-    dev_free(c, drho);
-    dev_free(c, du);
-    dev_free(c, dtau);
+    dev_free(c, st);
     c->t = 0;
     return LBVE_OK;
 }
@@ -512,7 +549,7 @@ lbve_status lbve_init_fields(lbve_ctx *c, const double *rho, const double *u, co
 lbve_status lbve_init_fields_device(lbve_ctx *c, const double *rho, const double *u, const double *tau) {
     if (!c) return LBVE_EINVAL;
     c->d.cur = 0;
-    CK(c->kt->init(c->d, rho, u, tau, c->stream), "init kernel");
+    CK(c->kt->init(c->d, rho, u, tau, 0, c->d.g.n, c->d.g.n, c->stream), "init kernel");
     c->t = 0;
     return LBVE_OK;
 }
@@ -574,28 +611,39 @@ lbve_status lbve_step(lbve_ctx *c, int nsteps) {
 
 lbve_status lbve_read_fields_device(lbve_ctx *c, double *rho, double *u, double *tau) {
     if (!c) return LBVE_EINVAL;
-    CK(c->kt->read(c->d, (int)(c->t & 1), rho, u, tau, c->stream), "read kernel");
+    CK(c->kt->read(c->d, (int)(c->t & 1), rho, u, tau, 0, c->p.nz, c->d.g.n, c->stream), "read kernel");
     return LBVE_OK;
 }
 
 lbve_status lbve_read_fields(lbve_ctx *c, double *rho, double *u, double *tau, uint8_t *flags) {
     if (!c) return LBVE_EINVAL;
-    const long long n = c->d.g.n;
-    double *d = nullptr;
-    const size_t bytes = sizeof(double) * 10 * n;
+    const long long n = c->d.g.n, plane = (long long)c->p.nx * c->p.ny;
     if (rho || u || tau) {
-        d = (double *)dev_alloc(c, bytes);
-        if (!d) return fail(c, LBVE_ENOMEM, "read staging allocation failed");
-        CK(c->kt->read(c->d, (int)(c->t & 1), rho ? d : nullptr, u ? d + n : nullptr, tau ? d + 4 * n : nullptr,
-                       c->stream),
-           "read kernel");
-        if (rho) CK(cudaMemcpyAsync(rho, d, sizeof(double) * n, cudaMemcpyDeviceToHost, c->stream), "read rho");
-        if (u) CK(cudaMemcpyAsync(u, d + n, sizeof(double) * 3 * n, cudaMemcpyDeviceToHost, c->stream), "read u");
-        if (tau) CK(cudaMemcpyAsync(tau, d + 4 * n, sizeof(double) * 6 * n, cudaMemcpyDeviceToHost, c->stream), "read tau");
+        const int zs = slab_planes(c);
+        const long long cap = plane * zs;
+        double *st = (double *)dev_alloc(c, sizeof(double) * 10 * (size_t)cap);
+        if (!st) return fail(c, LBVE_ENOMEM, "read staging allocation failed");
+        for (int z0 = 0; z0 < c->p.nz; z0 += zs) {
+            const int z1 = std::min(c->p.nz, z0 + zs);
+            const long long r0 = (long long)z0 * plane, cnt = (long long)(z1 - z0) * plane;
+            double *srho = st, *su = st + cnt, *stau = st + 4 * cnt;
+            CK(c->kt->read(c->d, (int)(c->t & 1), rho ? srho : nullptr, u ? su : nullptr, tau ? stau : nullptr, z0, z1,
+                           cnt, c->stream),
+               "read kernel");
+            if (rho) CK(cudaMemcpyAsync(rho + r0, srho, sizeof(double) * cnt, cudaMemcpyDeviceToHost, c->stream), "read rho");
+            for (int k = 0; u && k < 3; ++k)
+                CK(cudaMemcpyAsync(u + k * n + r0, su + k * cnt, sizeof(double) * cnt, cudaMemcpyDeviceToHost, c->stream),
+                   "read u");
+            for (int k = 0; tau && k < 6; ++k)
+                CK(cudaMemcpyAsync(tau + k * n + r0, stau + k * cnt, sizeof(double) * cnt, cudaMemcpyDeviceToHost,
+                                   c->stream),
+                   "read tau");
+        }
+        CK(cudaStreamSynchronize(c->stream), "read sync");
+        dev_free(c, st);
     }
     if (flags) CK(cudaMemcpyAsync(flags, c->d.flag, (size_t)n, cudaMemcpyDeviceToHost, c->stream), "read flags");
     CK(cudaStreamSynchronize(c->stream), "read sync");
-    dev_free(c, d);
     return LBVE_OK;
 }
 

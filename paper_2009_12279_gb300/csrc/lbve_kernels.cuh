@@ -214,17 +214,20 @@ __global__ void __launch_bounds__(128) k_momentum_exchange(KArgs<S> a, const lon
 // initialisation, read-back and reductions
 // ---------------------------------------------------------------------------------
 
-// f = f^eq(rho, u) of Eq. (lb-equilibrium) in the even-step layout; tau copied.
+// f = f^eq(rho, u) of Eq. (lb-equilibrium) in the even-step layout; tau copied.  Works on
+// the cells r0 .. r0+count-1; the inputs hold those cells with leading dimension ld.
 template <class S>
 __global__ void k_init(KArgs<S> a, const double *__restrict__ rho_in, const double *__restrict__ u_in,
-                       const double *__restrict__ tau_in, typename Store<S>::R *__restrict__ tau_dst) {
+                       const double *__restrict__ tau_in, typename Store<S>::R *__restrict__ tau_dst, long long r0,
+                       long long count, long long ld) {
     using R = typename Store<S>::R;
-    const long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (r >= a.g.n) return;
-    const double rho = rho_in ? rho_in[r] : (double)a.ph.rho0;
+    const long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= count) return;
+    const long long r = r0 + k;
+    const double rho = rho_in ? rho_in[k] : (double)a.ph.rho_ref;
     double u[3] = {0.0, 0.0, 0.0};
     if (u_in)
-        for (int k = 0; k < 3; ++k) u[k] = u_in[k * a.g.n + r];
+        for (int j = 0; j < 3; ++j) u[j] = u_in[j * ld + k];
     const double usq = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
@@ -238,26 +241,27 @@ __global__ void k_init(KArgs<S> a, const double *__restrict__ rho_in, const doub
         }
         Store<S>::st(a.f + (long long)i * a.g.np + r, (R)v, a.ph.scale);
     }
-    for (int c = 0; c < 6; ++c) tau_dst[c * a.g.np + r] = tau_in ? (R)tau_in[c * a.g.n + r] : R(0);
+    for (int c = 0; c < 6; ++c) tau_dst[c * a.g.np + r] = tau_in ? (R)tau_in[c * ld + k] : R(0);
 }
 
-// rho, physical u and tau of every cell (0 in non-fluid cells), FP64 outputs of n cells.
+// rho, physical u and tau of the cells in z-planes z0.. (grid z extent), 0 in non-fluid
+// cells; FP64 outputs indexed from the slab's first cell r0 with leading dimension ld.
 template <class S, int PAR>
 __global__ void k_read(KArgs<S> a, double *__restrict__ rho_out, double *__restrict__ u_out,
-                       double *__restrict__ tau_out) {
+                       double *__restrict__ tau_out, int z0, long long ld) {
     using R = typename Store<S>::R;
     constexpr bool SH = Store<S>::shifted;
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
     if (x >= a.g.nx) return;
-    const Cell cl(a.g, x, blockIdx.y, blockIdx.z);
+    const Cell cl(a.g, x, blockIdx.y, blockIdx.z + z0);
     const long long r = cl.self();
-    const long long n = a.g.n;
+    const long long k = r - (long long)z0 * a.g.nx * a.g.ny;
     if (a.flag[r] != FLAG_FLUID) {
-        if (rho_out) rho_out[r] = 0.0;
-        for (int k = 0; k < 3; ++k)
-            if (u_out) u_out[k * n + r] = 0.0;
+        if (rho_out) rho_out[k] = 0.0;
+        for (int j = 0; j < 3; ++j)
+            if (u_out) u_out[j * ld + k] = 0.0;
         for (int c = 0; c < 6; ++c)
-            if (tau_out) tau_out[c * n + r] = 0.0;
+            if (tau_out) tau_out[c * ld + k] = 0.0;
         return;
     }
     R f[Q];
@@ -265,13 +269,13 @@ __global__ void k_read(KArgs<S> a, double *__restrict__ rho_out, double *__restr
     R Fp[3], F[3], u[3], rho, drho;
     polymer_force<R>(a.g, cl, r, a.tau, a.flag, Fp);
 #pragma unroll
-    for (int k = 0; k < 3; ++k) F[k] = a.ph.g[k] + Fp[k];
+    for (int j = 0; j < 3; ++j) F[j] = a.ph.g[j] + Fp[j];
     moments<R, SH>(f, F, a.ph.rho0, rho, drho, u);
-    if (rho_out) rho_out[r] = SH ? (double)a.ph.rho0 + (double)drho : (double)rho;
-    for (int k = 0; k < 3; ++k)
-        if (u_out) u_out[k * n + r] = (double)u[k];
+    if (rho_out) rho_out[k] = SH ? (double)a.ph.rho0 + (double)drho : (double)rho;
+    for (int j = 0; j < 3; ++j)
+        if (u_out) u_out[j * ld + k] = (double)u[j];
     for (int c = 0; c < 6; ++c)
-        if (tau_out) tau_out[c * n + r] = (double)a.tau[c * a.g.np + r];
+        if (tau_out) tau_out[c * ld + k] = (double)a.tau[c * a.g.np + r];
 }
 
 // PDFs of every cell to / from unshifted FP64 in the plain (pre-collision) layout.

@@ -31,6 +31,7 @@ struct Phys {
     R ep_l, inv_l; // eta_p / lambda_p and 1 / lambda_p
     R g[3];
     R rho0;        // shift base of the stored deviations (0 in FP64 mode)
+    R rho_ref;     // reference density rho0 of the solve (all modes)
     R scale, inv_scale;
     int flux_on, src_on;
     R wall_vel[MAX_WALL][3];
@@ -62,12 +63,14 @@ struct KernelTable {
     int prec;          // lbve_pdf_prec
     size_t pdf_bytes;  // bytes per stored PDF
     size_t real_bytes; // bytes per stress / velocity value
-    cudaError_t (*init)(const DevState &, const double *rho, const double *u, const double *tau, cudaStream_t);
+    cudaError_t (*init)(const DevState &, const double *rho, const double *u, const double *tau, long long r0,
+                        long long count, long long ld, cudaStream_t);
     cudaError_t (*lb)(const DevState &, int parity, cudaStream_t);
     cudaError_t (*fv)(const DevState &, cudaStream_t);
     cudaError_t (*momentum_exchange)(const DevState &, int parity, const long long *links, int nlinks,
                                      double *contrib, cudaStream_t);
-    cudaError_t (*read)(const DevState &, int parity, double *rho, double *u, double *tau, cudaStream_t);
+    cudaError_t (*read)(const DevState &, int parity, double *rho, double *u, double *tau, int z0, int z1,
+                        long long ld, cudaStream_t);
     cudaError_t (*pdfs_io)(const DevState &, int parity, double *io, int write, cudaStream_t);
     cudaError_t (*reduce)(const DevState &, int parity, double *partial, long long *nblocks, cudaStream_t);
     cudaError_t (*probe)(const DevState &, int parity, const long long *cells, int count, double *out, cudaStream_t);

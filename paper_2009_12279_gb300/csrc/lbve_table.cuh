@@ -17,6 +17,7 @@ inline Phys<R> convert_phys(const Phys<double> &p) {
     o.inv_l = (R)p.inv_l;
     for (int k = 0; k < 3; ++k) o.g[k] = (R)p.g[k];
     o.rho0 = (R)p.rho0;
+    o.rho_ref = (R)p.rho_ref;
     o.scale = (R)p.scale;
     o.inv_scale = (R)p.inv_scale;
     o.flux_on = p.flux_on;
@@ -44,10 +45,12 @@ struct Launch {
     }
     static dim3 grid3(const DevState &d) { return dim3((unsigned)((d.g.nx + d.block_x - 1) / d.block_x), d.g.ny, d.g.nz); }
 
-    static cudaError_t init(const DevState &d, const double *rho, const double *u, const double *tau, cudaStream_t s) {
+    static cudaError_t init(const DevState &d, const double *rho, const double *u, const double *tau, long long r0,
+                            long long count, long long ld, cudaStream_t s) {
+        if (count <= 0) return cudaSuccess;
         KArgs<S> a = args(d);
-        const unsigned nb = (unsigned)((d.g.n + 255) / 256);
-        k_init<S><<<nb, 256, 0, s>>>(a, rho, u, tau, (R *)d.tau[d.cur]);
+        const unsigned nb = (unsigned)((count + 255) / 256);
+        k_init<S><<<nb, 256, 0, s>>>(a, rho, u, tau, (R *)d.tau[d.cur], r0, count, ld);
         return cudaGetLastError();
     }
     static cudaError_t lb(const DevState &d, int parity, cudaStream_t s) {
@@ -74,12 +77,16 @@ struct Launch {
             k_momentum_exchange<S, 1><<<nb, 128, 0, s>>>(a, links, nlinks, contrib);
         return cudaGetLastError();
     }
-    static cudaError_t read(const DevState &d, int parity, double *rho, double *u, double *tau, cudaStream_t s) {
+    static cudaError_t read(const DevState &d, int parity, double *rho, double *u, double *tau, int z0, int z1,
+                            long long ld, cudaStream_t s) {
+        if (z1 <= z0) return cudaSuccess;
         KArgs<S> a = args(d);
+        dim3 g = grid3(d);
+        g.z = (unsigned)(z1 - z0);
         if (parity == 0)
-            k_read<S, 0><<<grid3(d), d.block_x, 0, s>>>(a, rho, u, tau);
+            k_read<S, 0><<<g, d.block_x, 0, s>>>(a, rho, u, tau, z0, ld);
         else
-            k_read<S, 1><<<grid3(d), d.block_x, 0, s>>>(a, rho, u, tau);
+            k_read<S, 1><<<g, d.block_x, 0, s>>>(a, rho, u, tau, z0, ld);
         return cudaGetLastError();
     }
     static cudaError_t pdfs_io(const DevState &d, int parity, double *io, int write, cudaStream_t s) {
