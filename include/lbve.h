@@ -196,6 +196,44 @@ lbve_status lbve_reduce(lbve_ctx *ctx, double out[6]);
 lbve_status lbve_set_kernel_timing(lbve_ctx *ctx, int enable);
 lbve_status lbve_read_kernel_times(lbve_ctx *ctx, double ms[LBVE_KT_COUNT], long long launches[LBVE_KT_COUNT]);
 
+/*
+ * Time steps on caller-owned device buffers, allocating no device memory.
+ *
+ * The paper has no counterpart: this serves callers that cannot call cudaMalloc, such
+ * as code that runs inside a framework which owns all device memory through its own
+ * pool, or a host that forbids allocation after start-up.  Such a caller keeps the
+ * state in its own buffers and this call advances it with the split-schedule kernels.
+ * The one intermediate the kernels need (the velocity field passed from the
+ * stream-collide kernel to the stress kernel) lives in a fixed file-scope device array
+ * of 3 * LBVE_NOALLOC_MAX_CELLS doubles (12 MiB), which every GPU that loads the library
+ * holds until the process exits.
+ *
+ * Buffers (device, caller-owned, same layouts as a context uses internally), with
+ * n = nx*ny*nz and np = n rounded up to a multiple of 64:
+ *   f      19 * np PDF storage elements of p->pdf_prec: FP64 stores f_i itself; the
+ *          reduced modes store (f_i - w_i rho0) * 2^k (k = 15 for FP16 by default,
+ *          else 0; see pdf_scale_log2), w = 1/3, 1/18 (1..6), 1/36 (7..18).  At even t0
+ *          slot i of cell r holds f_i(r) (the plain layout); at odd t0 the in-place
+ *          (AA) layout of an odd step, i.e. the state after an odd number of steps.
+ *   tau_a  6 * np stress values (FP64 in FP64 mode, else FP32) at time t0;
+ *   tau_b  6 * np values of scratch for the other stress time level; after the call
+ *          the stress at t0 + nsteps is in tau_a if nsteps is even, else in tau_b;
+ *   flags  n bytes: 0 fluid, 1 no-slip, LBVE_FLAG_WALL0 + k wall class k < n_wall
+ *          (velocities in wall_vel, host, 3 doubles each); particle flags act as
+ *          resting walls.  Momentum-exchange forces are not computed by this call.
+ * Validation: EINVAL for bad parameters, NULL buffers or more than
+ * LBVE_NOALLOC_MAX_CELLS cells.  The first call on each device (with that device
+ * current) looks up the address of the static array; make that first call before any
+ * stream capture.  Every call shares the array, which keeps the last call's contents;
+ * nothing in it needs to start at zero.  Calls that overlap on the GPU (other streams,
+ * other threads) race on it: serialise them.  Enqueues the kernels on cuda_stream and
+ * returns without synchronising.  Errors are described by lbve_noalloc_last_error().
+ */
+#define LBVE_NOALLOC_MAX_CELLS (1 << 19)
+lbve_status lbve_step_noalloc(const lbve_params *p, void *f, void *tau_a, void *tau_b, const uint8_t *flags,
+                              const double *wall_vel, int n_wall, long long t0, int nsteps, void *cuda_stream);
+const char *lbve_noalloc_last_error(void);
+
 /* Steps done since the last lbve_init_fields. */
 long long lbve_time(const lbve_ctx *ctx);
 lbve_status lbve_synchronize(lbve_ctx *ctx);

@@ -23,6 +23,7 @@ UNITS = {
     "lbve_api.cu": [],
     "lbve_f64.cu": ["--fmad=false"],
     "lbve_f32.cu": [],
+    "lbve_noalloc.cu": [],
 }
 
 

@@ -14,6 +14,7 @@
 #include <vector>
 
 #include "../../include/lbve.h"
+#include "lbve_host.h"
 #include "lbve_launch.h"
 
 using namespace lbve;
@@ -142,9 +143,11 @@ void dev_free(lbve_ctx *c, void *ptr) {
     }
 }
 
-void set_phys(lbve_ctx *c) {
-    const lbve_params &p = c->p;
-    Phys<double> &ph = c->d.ph;
+void set_phys(lbve_ctx *c) { lbve::fill_phys(c->p, c->d.ph); }
+
+} // namespace
+
+void lbve::fill_phys(const lbve_params &p, Phys<double> &ph) {
     std::memset(&ph, 0, sizeof(ph));
     // TRT rates from the viscosity (Sec. "Lattice Boltzmann"): rates, magic product.
     const double eta_n = (1.0 - p.beta) * p.eta;
@@ -170,6 +173,16 @@ void set_phys(lbve_ctx *c) {
     ph.flux_on = (terms & LBVE_FV_FLUX) != 0;
     ph.src_on = (terms & LBVE_FV_SOURCE) != 0;
 }
+
+bool lbve::params_valid(const lbve_params *p, std::string &why) { return valid_params(p, why); }
+
+int lbve::default_block_x(const lbve_params &p) {
+    int bx = p.block_x > 0 ? p.block_x : 128;
+    while (bx > 32 && bx / 2 >= p.nx) bx /= 2;
+    return bx;
+}
+
+namespace {
 
 // ---------------------------------------------------------------------------------
 // small kernels that do not depend on the storage type
@@ -328,9 +341,7 @@ lbve_status create_impl(const lbve_params *p, void *stream, lbve_alloc_fn alloc,
     for (int k = 0; k < 3; ++k) g.per[k] = p->periodic[k] ? 1 : 0;
     g.n = (long long)p->nx * p->ny * p->nz;
     g.np = padded(g.n);
-    int bx = p->block_x > 0 ? p->block_x : 128;
-    while (bx > 32 && bx / 2 >= p->nx) bx /= 2;
-    c->d.block_x = bx;
+    c->d.block_x = lbve::default_block_x(*p);
     set_phys(c);
     const long long np = g.np;
     c->d.f = dev_alloc(c, (size_t)Q * np * c->kt->pdf_bytes);

@@ -28,7 +28,7 @@ EXPORTS = [
     "lbve_default_params", "lbve_device_bytes", "lbve_create", "lbve_create_with_allocator", "lbve_destroy",
     "lbve_set_geometry", "lbve_init_fields", "lbve_init_fields_device", "lbve_probe", "lbve_add_particle", "lbve_step", "lbve_read_fields",
     "lbve_read_fields_device", "lbve_read_pdfs", "lbve_write_pdfs", "lbve_read_particle", "lbve_read_body_forces",
-    "lbve_reduce", "lbve_set_kernel_timing", "lbve_read_kernel_times", "lbve_time", "lbve_synchronize", "lbve_last_error", "lbve_status_string",
+    "lbve_reduce", "lbve_step_noalloc", "lbve_noalloc_last_error", "lbve_set_kernel_timing", "lbve_read_kernel_times", "lbve_time", "lbve_synchronize", "lbve_last_error", "lbve_status_string",
 ]
 
 
@@ -88,6 +88,9 @@ def load(path: str | None = None):
         L.lbve_read_particle.argtypes = [vp, ct.c_int, dp]
         L.lbve_read_body_forces.argtypes = [vp, dp]
         L.lbve_reduce.argtypes = [vp, dp]
+        L.lbve_step_noalloc.argtypes = [ct.POINTER(Params), vp, vp, vp, vp, dp, ct.c_int, ct.c_longlong, ct.c_int, vp]
+        L.lbve_noalloc_last_error.argtypes = []
+        L.lbve_noalloc_last_error.restype = ct.c_char_p
         L.lbve_set_kernel_timing.argtypes = [vp, ct.c_int]
         L.lbve_read_kernel_times.argtypes = [vp, dp, ct.POINTER(ct.c_longlong)]
         L.lbve_time.argtypes = [vp]
@@ -127,6 +130,20 @@ def make_params(shape, *, periodic=(1, 1, 1), eta=1.0 / 6.0, beta=0.5, lambda_p=
     p.pdf_prec = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
     p.pdf_scale_log2, p.fv_terms, p.schedule, p.block_x = int(pdf_scale_log2), int(fv_terms), int(schedule), int(block_x)
     return p
+
+
+NOALLOC_MAX_CELLS = 1 << 19
+
+
+def step_noalloc(params: Params, f_ptr, tau_a_ptr, tau_b_ptr, flags_ptr, wall_vel=(), t0=0, nsteps=1, stream=0):
+    """Advance caller-owned device buffers (raw pointers) without device allocation."""
+    L = load()
+    wv = np.ascontiguousarray(np.asarray(wall_vel, dtype=np.float64).reshape(-1, 3)) if len(wall_vel) else None
+    rc = L.lbve_step_noalloc(ct.byref(params), f_ptr, tau_a_ptr, tau_b_ptr, flags_ptr,
+                             _dp(wv) if wv is not None else None, 0 if wv is None else wv.shape[0],
+                             int(t0), int(nsteps), ct.c_void_p(stream or 0))
+    if rc != 0:
+        raise LbveError(rc, L.lbve_noalloc_last_error().decode())
 
 
 def device_bytes(params: Params) -> int:
