@@ -171,6 +171,10 @@ lbve_status lbve_write_pdfs(lbve_ctx *ctx, const double *f);
  * Non-fluid cells read f as stored and rho = u = tau = 0.  Synchronises the stream. */
 lbve_status lbve_probe(lbve_ctx *ctx, const int64_t *cells, int count, double *out);
 
+/* Fill/drain totals since creation: out[0..5] stress dropped because a destroyed cell
+ * had no fluid neighbour, [6] cells destroyed, [7] cells created. */
+lbve_status lbve_read_conversions(lbve_ctx *ctx, double out[8]);
+
 /* Particle state: out[0..2] X, [3..5] v, [6..8] w, [9..11] momentum-exchange force
  * and [12..14] torque of the last step, [15..17] fill/drain impulse dP and [18..20]
  * angular impulse dL of the last step, [21] m, [22] I, [23] R. */

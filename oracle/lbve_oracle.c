@@ -284,7 +284,7 @@ void orc_polymer_force_field(orc_state *s, double *Fp) {
 /* Steps 1-2: F = g + F^p and u = (j + F/2)/rho for every fluid cell. */
 static void macroscopic(orc_state *s) {
     long n = s->n;
-#pragma omp parallel for schedule(static)
+#pragma omp parallel for schedule(static) if (n >= 32768)
     for (long r = 0; r < n; ++r) {
         if (!is_fluid(s, r)) {
             s->rho[r] = 0.0;
@@ -317,7 +317,7 @@ static void fv_update(orc_state *s, const double *u, const double *tau, double *
     long n = s->n;
     int flux_on = (s->p.fv_terms & ORC_FV_FLUX) != 0;
     int src_on = (s->p.fv_terms & ORC_FV_SOURCE) != 0;
-#pragma omp parallel for schedule(static)
+#pragma omp parallel for schedule(static) if (n >= 32768)
     for (long r = 0; r < n; ++r) {
         if (!is_fluid(s, r)) {
             for (int c = 0; c < 6; ++c) taun[(long)c * n + r] = 0.0;
@@ -532,7 +532,7 @@ static void one_step(orc_state *s) {
     /* 3: tau^{t+1} from tau^t and u^t */
     fv_update(s, s->u, s->tau, s->taun);
     /* 4: collision (in place: f becomes the post-collision f*) */
-#pragma omp parallel for schedule(static)
+#pragma omp parallel for schedule(static) if (n >= 32768)
     for (long r = 0; r < n; ++r) {
         if (!is_fluid(s, r)) continue;
         double f[19], fs[19], u[3], F[3];
@@ -545,7 +545,7 @@ static void one_step(orc_state *s) {
         for (int i = 0; i < 19; ++i) s->f[(long)i * n + r] = fs[i];
     }
     /* 5: push streaming; a link into a solid cell bounces back with Eq. (ubb) */
-#pragma omp parallel for schedule(static)
+#pragma omp parallel for schedule(static) if (n >= 32768)
     for (long r = 0; r < n; ++r) {
         if (!is_fluid(s, r)) continue;
         for (int i = 0; i < 19; ++i) {

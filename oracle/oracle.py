@@ -7,6 +7,7 @@ CPU-baseline leg may import this module.  It shares no code with the CUDA path.
 from __future__ import annotations
 
 import ctypes as ct
+import fcntl
 import os
 import subprocess
 import threading
@@ -24,12 +25,26 @@ _lock = threading.Lock()
 _lib = None
 
 
+def _fresh() -> bool:
+    return os.path.exists(LIB) and os.path.getmtime(LIB) >= max(
+        os.path.getmtime(SRC), os.path.getmtime(os.path.join(HERE, "lbve_oracle.h")))
+
+
 def build(force: bool = False) -> str:
     """Compile the oracle with gcc (FP contraction off so that a*b+c is never fused)."""
-    if not force and os.path.exists(LIB) and os.path.getmtime(LIB) >= max(
-        os.path.getmtime(SRC), os.path.getmtime(os.path.join(HERE, "lbve_oracle.h"))
-    ):
+    if not force and _fresh():
         return LIB
+    with open(LIB + ".lock", "w") as lk:
+        fcntl.flock(lk, fcntl.LOCK_EX)
+        try:
+            if not force and _fresh():
+                return LIB
+            return _compile()
+        finally:
+            fcntl.flock(lk, fcntl.LOCK_UN)
+
+
+def _compile() -> str:
     tmp = LIB + f".tmp{os.getpid()}"
     cmd = ["gcc", "-O2", "-std=gnu11", "-fPIC", "-shared", "-ffp-contract=off", "-fopenmp",
            SRC, "-o", tmp, "-lm"]

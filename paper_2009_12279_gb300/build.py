@@ -6,6 +6,7 @@ contraction off so its expressions round exactly as written.
 from __future__ import annotations
 
 import concurrent.futures as cf
+import fcntl
 import os
 import shutil
 import subprocess
@@ -39,10 +40,26 @@ def _sources_mtime() -> float:
     return max(os.path.getmtime(p) for p in paths)
 
 
+def _fresh() -> bool:
+    return os.path.exists(LIB) and os.path.getmtime(LIB) >= _sources_mtime()
+
+
 def build(force: bool = False, verbose: bool = False) -> str:
-    if not force and os.path.exists(LIB) and os.path.getmtime(LIB) >= _sources_mtime():
+    if not force and _fresh():
         return LIB
     os.makedirs(BUILD, exist_ok=True)
+    # one builder at a time (parallel test workers may all ask for the library)
+    with open(os.path.join(BUILD, ".lock"), "w") as lk:
+        fcntl.flock(lk, fcntl.LOCK_EX)
+        try:
+            if not force and _fresh():
+                return LIB
+            return _build(verbose)
+        finally:
+            fcntl.flock(lk, fcntl.LOCK_UN)
+
+
+def _build(verbose: bool) -> str:
     cc = nvcc()
 
     def compile_unit(name):

@@ -30,14 +30,23 @@ struct lbve_ctx {
     long long t = 0;
     std::string err;
     std::vector<std::pair<void *, size_t>> blocks;
-    // boundary links into tracked bodies (wall classes >= 2 and particles)
+    // boundary links into tracked bodies, one segment per body:
+    // [wall-class links (host-built) | particle 0 capacity | particle 1 capacity | ...]
+    std::vector<long long> wall_links;
+    std::vector<int> wall_seg_begin, wall_seg_count, wall_seg_flag;
     long long *links = nullptr;  // device, capacity links_cap
-    int nlinks = 0;
     size_t links_cap = 0;
     double *contrib = nullptr;   // device, 8 doubles per link
-    int *seg = nullptr;          // device, segment begin per body (nbody + 1)
-    int nbody = 0;
-    int *seg_flag = nullptr;     // device, flag value per body segment
+    int *seg_begin = nullptr;    // device, kMaxBodies each
+    int *seg_count = nullptr;
+    int *seg_flag = nullptr;
+    int nbody = 0, max_seg_len = 0;
+    int *part_cap = nullptr;     // device, link capacity per particle
+    std::vector<int> part_cap_host;
+    uint8_t *pkind = nullptr, *pnf = nullptr;  // fill/drain scratch (largest particle box)
+    double *pdelta = nullptr;
+    size_t pscratch_cells = 0;
+    double *pdiag = nullptr;     // device: dropped stress (6), destroyed, created
     double *body_F = nullptr;    // device, 256 x 3 forces of the last step
     double *red = nullptr;       // device reduction scratch
     size_t red_cap = 0;
@@ -191,12 +200,12 @@ namespace {
 // Sum the momentum-exchange contributions of each body segment in link order.  FP64
 // parity mode uses one thread per body (the sequential order of a plain loop); the
 // reduced modes use a fixed-shape block reduction.  Deterministic in both cases.
-__global__ void k_body_reduce(const double *__restrict__ contrib, const int *__restrict__ seg,
-                              const int *__restrict__ seg_flag, int nbody, double *__restrict__ body_F,
-                              PartDev *__restrict__ parts) {
+__global__ void k_body_reduce(const double *__restrict__ contrib, const int *__restrict__ seg_begin,
+                              const int *__restrict__ seg_count, const int *__restrict__ seg_flag, int nbody,
+                              double *__restrict__ body_F, PartDev *__restrict__ parts) {
     const int b = blockIdx.x;
     if (b >= nbody) return;
-    const int beg = seg[b], end = seg[b + 1];
+    const int beg = seg_begin[b], end = seg_begin[b] + seg_count[b];
     __shared__ double sh[6][256];
     double acc[6] = {0, 0, 0, 0, 0, 0};
     const int T = blockDim.x;
@@ -246,8 +255,9 @@ __global__ void k_final_sum(const double *__restrict__ partial, long long nblock
 // Host-side list of links (fluid cell r, direction i with r + c_i a wall-class cell),
 // ordered by flag value, then cell, then direction (the order of a plain cell loop
 // within each body).  Built from the wall-class cells, so its cost is O(wall cells).
-void build_wall_links(const lbve_ctx *c, std::vector<long long> &links, std::vector<int> &seg,
-                      std::vector<int> &seg_flag) {
+void build_wall_links(lbve_ctx *c) {
+    std::vector<long long> &links = c->wall_links;
+    std::vector<int> &seg = c->wall_seg_begin, &seg_flag = c->wall_seg_flag, &seg_count = c->wall_seg_count;
     static const int CX[Q] = {0, 1, -1, 0, 0, 0, 0, 1, -1, 1, -1, 1, -1, 1, -1, 0, 0, 0, 0};
     static const int CY[Q] = {0, 0, 0, 1, -1, 0, 0, 1, -1, -1, 1, 0, 0, 0, 0, 1, -1, 1, -1};
     static const int CZ[Q] = {0, 0, 0, 0, 0, 1, -1, 0, 0, 0, 0, 1, -1, -1, 1, 1, -1, -1, 1};
@@ -278,41 +288,68 @@ void build_wall_links(const lbve_ctx *c, std::vector<long long> &links, std::vec
     links.clear();
     seg.clear();
     seg_flag.clear();
+    seg_count.clear();
     for (size_t k = 0; k < tmp.size(); ++k) {
         if (k == 0 || tmp[k].first != tmp[k - 1].first) {
             seg.push_back((int)links.size());
             seg_flag.push_back(tmp[k].first);
+            seg_count.push_back(0);
         }
         links.push_back(tmp[k].second);
+        seg_count.back()++;
     }
-    seg.push_back((int)links.size());
 }
 
-lbve_status upload_links(lbve_ctx *c, const std::vector<long long> &links, const std::vector<int> &seg,
-                         const std::vector<int> &seg_flag) {
-    if (links.size() > c->links_cap) {
+constexpr int kMaxBodies = 128;
+
+// Lay out the link array (wall links, then one fixed-capacity segment per particle),
+// upload the wall links and the segment tables, and build the particles' links.
+lbve_status layout_links(lbve_ctx *c) {
+    size_t total = c->wall_links.size();
+    for (int cap : c->part_cap_host) total += (size_t)cap;
+    if (total > c->links_cap) {
         dev_free(c, c->links);
         dev_free(c, c->contrib);
         c->links = nullptr;
         c->contrib = nullptr;
-        const size_t cap = std::max<size_t>(links.size(), 1024);
+        const size_t cap = std::max<size_t>(total, 1024);
         c->links = (long long *)dev_alloc(c, cap * sizeof(long long));
         c->contrib = (double *)dev_alloc(c, cap * 8 * sizeof(double));
         if (!c->links || !c->contrib) return fail(c, LBVE_ENOMEM, "link list allocation failed");
         c->links_cap = cap;
     }
-    if (!links.empty())
-        CK(cudaMemcpyAsync(c->links, links.data(), links.size() * sizeof(long long), cudaMemcpyHostToDevice, c->stream),
+    if (!c->wall_links.empty())
+        CK(cudaMemcpyAsync(c->links, c->wall_links.data(), c->wall_links.size() * sizeof(long long),
+                           cudaMemcpyHostToDevice, c->stream),
            "upload links");
-    c->nlinks = (int)links.size();
-    c->nbody = (int)seg_flag.size();
-    if (c->nbody > 0) {
-        CK(cudaMemcpyAsync(c->seg, seg.data(), seg.size() * sizeof(int), cudaMemcpyHostToDevice, c->stream), "upload seg");
-        CK(cudaMemcpyAsync(c->seg_flag, seg_flag.data(), seg_flag.size() * sizeof(int), cudaMemcpyHostToDevice,
-                           c->stream),
-           "upload seg flags");
+    std::vector<int> beg(c->wall_seg_begin), cnt(c->wall_seg_count), flg(c->wall_seg_flag);
+    int off = (int)c->wall_links.size();
+    int mx = 0;
+    for (int v : cnt) mx = std::max(mx, v);
+    for (int p = 0; p < c->nparts; ++p) {
+        beg.push_back(off);
+        cnt.push_back(0);
+        flg.push_back(FLAG_PART0 + p);
+        off += c->part_cap_host[p];
+        mx = std::max(mx, c->part_cap_host[p]);
     }
-    CK(cudaStreamSynchronize(c->stream), "upload sync");
+    c->nbody = (int)beg.size();
+    c->max_seg_len = mx;
+    if (c->nbody > kMaxBodies) return fail(c, LBVE_EINVAL, "too many tracked bodies");
+    if (c->nbody > 0) {
+        CK(cudaMemcpyAsync(c->seg_begin, beg.data(), beg.size() * sizeof(int), cudaMemcpyHostToDevice, c->stream), "seg");
+        CK(cudaMemcpyAsync(c->seg_count, cnt.data(), cnt.size() * sizeof(int), cudaMemcpyHostToDevice, c->stream), "seg");
+        CK(cudaMemcpyAsync(c->seg_flag, flg.data(), flg.size() * sizeof(int), cudaMemcpyHostToDevice, c->stream), "seg");
+    }
+    if (c->nparts > 0) {
+        CK(cudaMemcpyAsync(c->part_cap, c->part_cap_host.data(), sizeof(int) * c->nparts, cudaMemcpyHostToDevice,
+                           c->stream),
+           "part cap");
+        CK(c->kt->particle_links(c->d, c->nparts, c->links, c->seg_begin, c->seg_count, (int)c->wall_seg_begin.size(),
+                                 c->part_cap, c->stream),
+           "particle links");
+    }
+    CK(cudaStreamSynchronize(c->stream), "links sync");
     return LBVE_OK;
 }
 
@@ -350,11 +387,15 @@ lbve_status create_impl(const lbve_params *p, void *stream, lbve_alloc_fn alloc,
     c->d.u = dev_alloc(c, (size_t)3 * np * c->kt->real_bytes);
     c->d.flag = (uint8_t *)dev_alloc(c, (size_t)np);
     c->d.parts = (PartDev *)dev_alloc(c, sizeof(PartDev) * MAX_PART);
-    c->seg = (int *)dev_alloc(c, sizeof(int) * 257);
-    c->seg_flag = (int *)dev_alloc(c, sizeof(int) * 256);
+    c->seg_begin = (int *)dev_alloc(c, sizeof(int) * kMaxBodies);
+    c->seg_count = (int *)dev_alloc(c, sizeof(int) * kMaxBodies);
+    c->seg_flag = (int *)dev_alloc(c, sizeof(int) * kMaxBodies);
+    c->part_cap = (int *)dev_alloc(c, sizeof(int) * MAX_PART);
+    c->pdiag = (double *)dev_alloc(c, sizeof(double) * 8);
     c->body_F = (double *)dev_alloc(c, sizeof(double) * 256 * 3);
     c->red_out = (double *)dev_alloc(c, sizeof(double) * 8);
-    if (!c->d.f || !c->d.tau[0] || !c->d.tau[1] || !c->d.u || !c->d.flag || !c->d.parts || !c->seg || !c->seg_flag ||
+    if (!c->d.f || !c->d.tau[0] || !c->d.tau[1] || !c->d.u || !c->d.flag || !c->d.parts || !c->seg_begin || !c->seg_count ||
+        !c->seg_flag || !c->part_cap || !c->pdiag ||
         !c->body_F || !c->red_out) {
         g_create_error = "device allocation failed";
         lbve_destroy(c);
@@ -366,6 +407,7 @@ lbve_status create_impl(const lbve_params *p, void *stream, lbve_alloc_fn alloc,
     if (e == cudaSuccess) e = cudaMemsetAsync(c->d.tau[1], 0, (size_t)6 * np * c->kt->real_bytes, c->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(c->d.parts, 0, sizeof(PartDev) * MAX_PART, c->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(c->body_F, 0, sizeof(double) * 256 * 3, c->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(c->pdiag, 0, sizeof(double) * 8, c->stream);
     if (e == cudaSuccess) e = c->kt->init(c->d, nullptr, nullptr, nullptr, 0, g.n, g.n, c->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
     if (e != cudaSuccess) {
@@ -519,10 +561,8 @@ lbve_status lbve_set_geometry(lbve_ctx *c, const uint8_t *flags, const double *w
         for (int a = 0; a < 3; ++a) c->d.ph.wall_vel[k][a] = k < n_wall ? wall_vel[3 * k + a] : 0.0;
     std::memcpy(c->flags_host.data(), flags, (size_t)c->d.g.n);
     CK(cudaMemcpyAsync(c->d.flag, flags, (size_t)c->d.g.n, cudaMemcpyHostToDevice, c->stream), "upload flags");
-    std::vector<long long> links;
-    std::vector<int> seg, seg_flag;
-    build_wall_links(c, links, seg, seg_flag);
-    lbve_status s = upload_links(c, links, seg, seg_flag);
+    build_wall_links(c);
+    lbve_status s = layout_links(c);
     if (s != LBVE_OK) return s;
     c->geometry_set = true;
     return LBVE_OK;
@@ -590,7 +630,58 @@ lbve_status lbve_probe(lbve_ctx *c, const int64_t *cells, int count, double *out
 lbve_status lbve_add_particle(lbve_ctx *c, const double X[3], double R, double rho_p, const double v[3],
                               const double w[3], const double Fext[3], const double Text[3], int *id) {
     if (!c) return LBVE_EINVAL;
-    return fail(c, LBVE_ESTATE, "moving particles are not available in this build");
+    if (!X) return fail(c, LBVE_EINVAL, "X is NULL");
+    if (!(R > 0.0) || !(rho_p > 0.0)) return fail(c, LBVE_EINVAL, "radius and density must be > 0");
+    if (c->nparts >= MAX_PART) return fail(c, LBVE_ESTATE, "too many particles");
+    const int nn[3] = {c->p.nx, c->p.ny, c->p.nz};
+    for (int a = 0; a < 3; ++a) {
+        if (!std::isfinite(X[a])) return fail(c, LBVE_EINVAL, "X must be finite");
+        if (2.0 * R + 6.0 > nn[a]) return fail(c, LBVE_EINVAL, "particle too large for the domain");
+    }
+    PartDev P;
+    std::memset(&P, 0, sizeof(P));
+    for (int a = 0; a < 3; ++a) {
+        P.X[a] = X[a];
+        P.v[a] = v ? v[a] : 0.0;
+        P.w[a] = w ? w[a] : 0.0;
+        P.Fext[a] = Fext ? Fext[a] : 0.0;
+        P.Text[a] = Text ? Text[a] : 0.0;
+    }
+    P.R = R;
+    P.rho_p = rho_p;
+    P.m = rho_p * (4.0 / 3.0) * M_PI * R * R * R;
+    P.I = 0.4 * P.m * R * R;
+    const int p = c->nparts;
+    // scratch for fill/drain (box with margin 3) and the link capacity (box with margin 2)
+    const long long side3 = particle_box_side(R, 3), side2 = particle_box_side(R, 2);
+    const size_t cells3 = (size_t)(side3 * side3 * side3);
+    if (cells3 > c->pscratch_cells) {
+        dev_free(c, c->pkind);
+        dev_free(c, c->pnf);
+        dev_free(c, c->pdelta);
+        c->pkind = (uint8_t *)dev_alloc(c, cells3);
+        c->pnf = (uint8_t *)dev_alloc(c, cells3);
+        c->pdelta = (double *)dev_alloc(c, sizeof(double) * 6 * cells3);
+        if (!c->pkind || !c->pnf || !c->pdelta) return fail(c, LBVE_ENOMEM, "particle scratch allocation failed");
+        CK(cudaMemsetAsync(c->pnf, 0, cells3, c->stream), "scratch clear");
+        c->pscratch_cells = cells3;
+    }
+    CK(cudaMemcpyAsync(c->d.parts + p, &P, sizeof(P), cudaMemcpyHostToDevice, c->stream), "upload particle");
+    CK(c->kt->voxelise(c->d, p, c->stream), "voxelise");
+    c->parts_host[p] = P;
+    c->nparts++;
+    c->part_cap_host.push_back((int)(18 * side2 * side2 * side2));
+    lbve_status s = layout_links(c);
+    if (s != LBVE_OK) return s;
+    if (id) *id = p;
+    return LBVE_OK;
+}
+
+lbve_status lbve_read_conversions(lbve_ctx *c, double out[8]) {
+    if (!c || !out) return c ? fail(c, LBVE_EINVAL, "out is NULL") : LBVE_EINVAL;
+    CK(cudaMemcpyAsync(out, c->pdiag, sizeof(double) * 8, cudaMemcpyDeviceToHost, c->stream), "read diag");
+    CK(cudaStreamSynchronize(c->stream), "read diag sync");
+    return LBVE_OK;
 }
 
 lbve_status lbve_step(lbve_ctx *c, int nsteps) {
@@ -598,12 +689,14 @@ lbve_status lbve_step(lbve_ctx *c, int nsteps) {
     if (nsteps < 0) return fail(c, LBVE_EINVAL, "nsteps must be >= 0");
     for (int s = 0; s < nsteps; ++s) {
         const int parity = (int)(c->t & 1);
-        if (c->nlinks > 0) {
+        if (c->nbody > 0) {
             CK(timed_begin(c, LBVE_KT_ME), "timing");
-            CK(c->kt->momentum_exchange(c->d, parity, c->links, c->nlinks, c->contrib, c->stream), "momentum exchange");
+            CK(c->kt->momentum_exchange(c->d, parity, c->links, c->seg_begin, c->seg_count, c->nbody, c->max_seg_len,
+                                        c->contrib, c->stream),
+               "momentum exchange");
             const int threads = c->p.pdf_prec == LBVE_F64 ? 1 : 256;
-            k_body_reduce<<<c->nbody, threads, 0, c->stream>>>(c->contrib, c->seg, c->seg_flag, c->nbody, c->body_F,
-                                                               c->d.parts);
+            k_body_reduce<<<c->nbody, threads, 0, c->stream>>>(c->contrib, c->seg_begin, c->seg_count, c->seg_flag,
+                                                               c->nbody, c->body_F, c->d.parts);
             CK(cudaGetLastError(), "body reduce");
             CK(timed_end(c), "timing");
         }
@@ -613,9 +706,19 @@ lbve_status lbve_step(lbve_ctx *c, int nsteps) {
         CK(timed_begin(c, LBVE_KT_FV), "timing");
         CK(c->kt->fv(c->d, c->stream), "fv kernel");
         CK(timed_end(c), "timing");
-        if (c->ev_used >= 4096) CK(harvest_times(c), "timing harvest");
         c->d.cur ^= 1;
+        if (c->nparts > 0) {
+            CK(timed_begin(c, LBVE_KT_PARTICLE), "timing");
+            CK(c->kt->particle_update(c->d, c->nparts, c->stream), "particle update");
+            CK(c->kt->fill_drain(c->d, parity ^ 1, c->nparts, c->pkind, c->pnf, c->pdelta, c->pdiag, c->stream),
+               "fill/drain");
+            CK(c->kt->particle_links(c->d, c->nparts, c->links, c->seg_begin, c->seg_count,
+                                     (int)c->wall_seg_begin.size(), c->part_cap, c->stream),
+               "particle links");
+            CK(timed_end(c), "timing");
+        }
         c->t++;
+        if (c->ev_used >= 4096) CK(harvest_times(c), "timing harvest");
     }
     return LBVE_OK;
 }

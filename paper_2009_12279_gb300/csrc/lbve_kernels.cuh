@@ -128,14 +128,11 @@ __global__ void __launch_bounds__(256) k_fv(KArgs<S> a) {
 // its torque about the owning particle.  Runs before k_lb on the same f^t and repeats
 // the cell's collision, so f*_i is exactly the value k_lb streams.
 // ---------------------------------------------------------------------------------
+// Momentum-exchange contribution of one link (code = r << 5 | i) into contrib[8].
 template <class S, int PAR>
-__global__ void __launch_bounds__(128) k_momentum_exchange(KArgs<S> a, const long long *__restrict__ links, int nlinks,
-                                                           double *__restrict__ contrib) {
+__device__ __forceinline__ void me_link(const KArgs<S> &a, long long code, double *__restrict__ o) {
     using R = typename Store<S>::R;
     constexpr bool SH = Store<S>::shifted;
-    const int l = blockIdx.x * blockDim.x + threadIdx.x;
-    if (l >= nlinks) return;
-    const long long code = links[l];
     const int i = (int)(code & 31);
     const long long r = code >> 5;
     const int x = (int)(r % a.g.nx), y = (int)((r / a.g.nx) % a.g.ny), z = (int)(r / ((long long)a.g.nx * a.g.ny));
@@ -148,7 +145,7 @@ __global__ void __launch_bounds__(128) k_momentum_exchange(KArgs<S> a, const lon
     for (int k = 0; k < 3; ++k) F[k] = a.ph.g[k] + Fp[k];
     moments<R, SH>(f, F, a.ph.rho0, rho, drho, u);
     collide<R, SH>(f, rho, drho, u, F, a.ph);
-    // f*_i as a full population (the stored deviation plus w_i rho0 in shifted modes)
+    // f*_i (a full population: the stored deviation plus w_i rho0 in shifted modes)
     R fsi = R(0);
     int ci[3] = {0, 0, 0};
 #pragma unroll
@@ -179,7 +176,7 @@ __global__ void __launch_bounds__(128) k_momentum_exchange(KArgs<S> a, const lon
             }
         }
     }
-    R wi = i < 7 ? wgt<R>(1) : wgt<R>(7);
+    const R wi = i < 7 ? wgt<R>(1) : wgt<R>(7);
     const R X = R(6) * wi * rho * cub;
     double m;
     if constexpr (SH)
@@ -200,7 +197,6 @@ __global__ void __launch_bounds__(128) k_momentum_exchange(KArgs<S> a, const lon
         T[1] = d[2] * Fl[0] - d[0] * Fl[2];
         T[2] = d[0] * Fl[1] - d[1] * Fl[0];
     }
-    double *o = contrib + (long long)l * 8;
     o[0] = Fl[0];
     o[1] = Fl[1];
     o[2] = Fl[2];
@@ -208,6 +204,404 @@ __global__ void __launch_bounds__(128) k_momentum_exchange(KArgs<S> a, const lon
     o[4] = T[1];
     o[5] = T[2];
     o[6] = (double)fl;
+}
+
+// Momentum exchange over link segments (one segment per tracked body, blockIdx.y):
+// link l of segment b is links[seg_begin[b] + l] for l < seg_count[b].
+template <class S, int PAR>
+__global__ void __launch_bounds__(128) k_momentum_exchange(KArgs<S> a, const long long *__restrict__ links,
+                                                           const int *__restrict__ seg_begin,
+                                                           const int *__restrict__ seg_count,
+                                                           double *__restrict__ contrib) {
+    const int b = blockIdx.y;
+    const int l = blockIdx.x * blockDim.x + threadIdx.x;
+    if (l >= seg_count[b]) return;
+    const long long at = (long long)seg_begin[b] + l;
+    me_link<S, PAR>(a, links[at], contrib + at * 8);
+}
+
+// ---------------------------------------------------------------------------------
+// moving particles (Sec. "Moving boundaries")
+// ---------------------------------------------------------------------------------
+struct BBox {
+    int lo[3], ext[3];
+    __host__ __device__ long long cells() const { return (long long)ext[0] * ext[1] * ext[2]; }
+};
+
+// Cells within R + margin of the particle centre (whole domain along a periodic side
+// the box would wrap onto itself; clamped to the domain along a closed side).
+__host__ __device__ inline BBox particle_bbox(const Geo &g, const double X[3], double R, int margin) {
+    BBox b;
+    const int nn[3] = {g.nx, g.ny, g.nz};
+    for (int k = 0; k < 3; ++k) {
+        int lo = (int)floor(X[k] - R) - margin;
+        int hi = (int)ceil(X[k] + R) + margin;
+        if (!g.per[k]) {
+            lo = lo < 0 ? 0 : lo;
+            hi = hi > nn[k] - 1 ? nn[k] - 1 : hi;
+        }
+        int ext = hi - lo + 1;
+        if (ext > nn[k]) {
+            lo = 0;
+            ext = nn[k];
+        }
+        if (ext < 0) ext = 0;
+        b.lo[k] = lo;
+        b.ext[k] = ext;
+    }
+    return b;
+}
+
+__host__ __device__ inline int bbox_capacity_side(double R, int margin) { return 2 * (int)ceil(R) + 2 * margin + 3; }
+
+__device__ __forceinline__ int wrapc(int v, int n) { return ((v % n) + n) % n; }
+
+__device__ __forceinline__ long long bbox_cell(const Geo &g, const BBox &b, long long k, int &x, int &y, int &z) {
+    const int ix = (int)(k % b.ext[0]);
+    const int iy = (int)((k / b.ext[0]) % b.ext[1]);
+    const int iz = (int)(k / ((long long)b.ext[0] * b.ext[1]));
+    x = wrapc(b.lo[0] + ix, g.nx);
+    y = wrapc(b.lo[1] + iy, g.ny);
+    z = wrapc(b.lo[2] + iz, g.nz);
+    return (long long)x + (long long)g.nx * (y + (long long)g.ny * z);
+}
+
+// index of global cell (x, y, z) inside the box, or -1
+__device__ __forceinline__ long long bbox_index(const Geo &g, const BBox &b, int x, int y, int z) {
+    const int q[3] = {x, y, z}, nn[3] = {g.nx, g.ny, g.nz};
+    int o[3];
+    for (int k = 0; k < 3; ++k) {
+        int d = q[k] - b.lo[k];
+        if (g.per[k]) d = wrapc(d, nn[k]);
+        if (d < 0 || d >= b.ext[k]) return -1;
+        o[k] = d;
+    }
+    return (long long)o[0] + (long long)b.ext[0] * (o[1] + (long long)b.ext[1] * o[2]);
+}
+
+__device__ __forceinline__ void min_image(const Geo &g, const double X[3], int x, int y, int z, double d[3]) {
+    const double q[3] = {(double)x, (double)y, (double)z};
+    const int nn[3] = {g.nx, g.ny, g.nz};
+    for (int k = 0; k < 3; ++k) {
+        d[k] = q[k] - X[k];
+        if (g.per[k]) d[k] -= (double)nn[k] * floor(d[k] / (double)nn[k] + 0.5);
+    }
+}
+
+// Initial placement: covered fluid cells become particle cells, their stress is zeroed.
+template <class S>
+__global__ void k_voxelise(KArgs<S> a, PartDev *__restrict__ parts, int p, uint8_t *__restrict__ flag,
+                           typename Store<S>::R *__restrict__ tau0, typename Store<S>::R *__restrict__ tau1) {
+    using R = typename Store<S>::R;
+    const PartDev &P = parts[p];
+    const BBox b = particle_bbox(a.g, P.X, P.R, 1);
+    for (long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x; k < b.cells(); k += (long long)gridDim.x * blockDim.x) {
+        int x, y, z;
+        const long long r = bbox_cell(a.g, b, k, x, y, z);
+        if (flag[r] != FLAG_FLUID) continue;
+        double d[3];
+        min_image(a.g, P.X, x, y, z, d);
+        if (d[0] * d[0] + d[1] * d[1] + d[2] * d[2] <= P.R * P.R) {
+            flag[r] = (uint8_t)(FLAG_PART0 + p);
+            for (int c = 0; c < 6; ++c) {
+                tau0[c * a.g.np + r] = R(0);
+                tau1[c * a.g.np + r] = R(0);
+            }
+        }
+    }
+}
+
+// Symplectic Euler (Sec. "Moving boundaries"): velocities with the momentum-exchange
+// force and torque of this step plus the external ones, then the position with the new
+// velocity.  One thread per particle, FP64.
+template <class S>
+__global__ void k_particle_update(PartDev *__restrict__ parts, int nparts) {
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= nparts) return;
+    PartDev &P = parts[p];
+    for (int k = 0; k < 3; ++k) {
+        P.v[k] += (P.Fme[k] + P.Fext[k]) / P.m;
+        P.w[k] += (P.Tme[k] + P.Text[k]) / P.I;
+        P.X[k] += P.v[k];
+    }
+}
+
+// Boundary links of each particle (one block per particle): every (fluid cell r,
+// direction i) with r + c_i covered by the particle, in cell order then direction
+// order, compacted with a block-wide prefix sum so the order is deterministic.
+template <class S>
+__global__ void __launch_bounds__(256) k_particle_links(Geo g, const PartDev *__restrict__ parts,
+                                                        const uint8_t *__restrict__ flag,
+                                                        long long *__restrict__ links,
+                                                        const int *__restrict__ seg_begin, int *__restrict__ seg_count,
+                                                        int first_seg, const int *__restrict__ capacity) {
+    const int p = blockIdx.x;
+    const PartDev &P = parts[p];
+    const BBox b = particle_bbox(g, P.X, P.R, 2);
+    const long long nc = b.cells();
+    const int seg = first_seg + p;
+    long long *out = links + seg_begin[seg];
+    const int cap = capacity[p];
+    __shared__ int scan[256];
+    __shared__ int base;
+    if (threadIdx.x == 0) base = 0;
+    __syncthreads();
+    for (long long k0 = 0; k0 < nc; k0 += blockDim.x) {
+        const long long k = k0 + threadIdx.x;
+        unsigned mask = 0;
+        long long r = 0;
+        if (k < nc) {
+            int x, y, z;
+            r = bbox_cell(g, b, k, x, y, z);
+            if (flag[r] == FLAG_FLUID) {
+                const Cell cl(g, x, y, z);
+                for (int i = 1; i < Q; ++i) {
+                    if (!g.per[0] && (x + cx(i) < 0 || x + cx(i) >= g.nx)) continue;
+                    if (!g.per[1] && (y + cy(i) < 0 || y + cy(i) >= g.ny)) continue;
+                    if (!g.per[2] && (z + cz(i) < 0 || z + cz(i) >= g.nz)) continue;
+                    if (flag[cl.idx(cx(i), cy(i), cz(i))] == FLAG_PART0 + p) mask |= 1u << i;
+                }
+            }
+        }
+        const int cnt = __popc(mask);
+        scan[threadIdx.x] = cnt;
+        __syncthreads();
+        // inclusive Hillis-Steele scan over the block
+        for (int off = 1; off < (int)blockDim.x; off <<= 1) {
+            const int v = (int)threadIdx.x >= off ? scan[threadIdx.x - off] : 0;
+            __syncthreads();
+            scan[threadIdx.x] += v;
+            __syncthreads();
+        }
+        int pos = base + scan[threadIdx.x] - cnt;
+        for (int i = 1; i < Q; ++i)
+            if (mask & (1u << i)) {
+                if (pos < cap) out[pos] = (r << 5) | i;
+                pos++;
+            }
+        __syncthreads();
+        if (threadIdx.x == blockDim.x - 1) base += scan[threadIdx.x];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) seg_count[seg] = base < cap ? base : cap;
+}
+
+// Fill/drain after re-voxelisation at the particles' new positions (one block, the
+// particles one after another).  f is the state at time t+1 in the layout PAR reads.
+// kind: 0 other, 1 fluid before and after, 2 destroyed (fluid -> particle),
+// 3 created (particle -> fluid).  All stress moves use the pre-conversion stress:
+//   destroyed d: each of its N_f stable D3Q7 neighbours gains tau(d)/N_f;
+//   created c:   tau(c) = sum of its stable neighbours' tau / (N_f + 1), each of
+//                them gives up tau(c)/N_f;
+// the deleted / created momentum goes to the particle as an impulse at the cell.
+template <class S, int PAR>
+__global__ void __launch_bounds__(512) k_fill_drain(KArgs<S> a, PartDev *__restrict__ parts, int nparts,
+                                                    uint8_t *__restrict__ flag, typename Store<S>::R *__restrict__ tau,
+                                                    uint8_t *__restrict__ kind, uint8_t *__restrict__ nf_arr,
+                                                    double *__restrict__ delta, double *__restrict__ diag) {
+    using R = typename Store<S>::R;
+    constexpr bool SH = Store<S>::shifted;
+    const long long np = a.g.np;
+    auto kind_of = [&](const BBox &b, int x, int y, int z) -> int {
+        const long long k = bbox_index(a.g, b, x, y, z);
+        if (k >= 0) return kind[k];
+        return flag[(long long)x + (long long)a.g.nx * (y + (long long)a.g.ny * z)] == FLAG_FLUID ? 1 : 0;
+    };
+    for (int p = 0; p < nparts; ++p) {
+        PartDev &P = parts[p];
+        const BBox b = particle_bbox(a.g, P.X, P.R, 3);
+        const long long nc = b.cells();
+        // A: classify
+        for (long long k = threadIdx.x; k < nc; k += blockDim.x) {
+            int x, y, z;
+            const long long r = bbox_cell(a.g, b, k, x, y, z);
+            const int old = flag[r];
+            int kd = 0;
+            if (old == FLAG_FLUID || old == FLAG_PART0 + p) {
+                double d[3];
+                min_image(a.g, P.X, x, y, z, d);
+                const bool inside = d[0] * d[0] + d[1] * d[1] + d[2] * d[2] <= P.R * P.R;
+                if (old == FLAG_FLUID) kd = inside ? 2 : 1;
+                else kd = inside ? 0 : 3;
+            }
+            kind[k] = (uint8_t)kd;
+        }
+        __syncthreads();
+        // B: N_f of converted cells, new stress of created cells
+        for (long long k = threadIdx.x; k < nc; k += blockDim.x) {
+            const int kd = kind[k];
+            if (kd != 2 && kd != 3) continue;
+            int x, y, z;
+            bbox_cell(a.g, b, k, x, y, z);
+            const Cell cl(a.g, x, y, z);
+            int nf = 0;
+            double sum[6] = {0, 0, 0, 0, 0, 0};
+            for (int l = 0; l < 6; ++l) {
+                const int ax = l >> 1, s = (l & 1) ? -1 : 1;
+                const int xq = cl.X(ax == 0 ? s : 0), yq = cl.Y(ax == 1 ? s : 0), zq = cl.Z(ax == 2 ? s : 0);
+                if (!a.g.per[ax]) {
+                    const int q = ax == 0 ? x + s : (ax == 1 ? y + s : z + s);
+                    const int nn = ax == 0 ? a.g.nx : (ax == 1 ? a.g.ny : a.g.nz);
+                    if (q < 0 || q >= nn) continue;
+                }
+                if (kind_of(b, xq, yq, zq) != 1) continue;
+                nf++;
+                const long long nb = (long long)xq + (long long)a.g.nx * (yq + (long long)a.g.ny * zq);
+                for (int c = 0; c < 6; ++c) sum[c] += (double)tau[c * np + nb];
+            }
+            nf_arr[k] = (uint8_t)nf;
+            if (kd == 3)
+                for (int c = 0; c < 6; ++c) delta[c * nc + k] = sum[c] / (double)(nf + 1);
+        }
+        __syncthreads();
+        // C: stress gathered by each stable cell from its converted D3Q7 neighbours
+        for (long long k = threadIdx.x; k < nc; k += blockDim.x) {
+            if (kind[k] != 1) continue;
+            int x, y, z;
+            bbox_cell(a.g, b, k, x, y, z);
+            const Cell cl(a.g, x, y, z);
+            double acc[6] = {0, 0, 0, 0, 0, 0};
+            bool touched = false;
+            for (int l = 0; l < 6; ++l) {
+                const int ax = l >> 1, s = (l & 1) ? -1 : 1;
+                if (!a.g.per[ax]) {
+                    const int q = ax == 0 ? x + s : (ax == 1 ? y + s : z + s);
+                    const int nn = ax == 0 ? a.g.nx : (ax == 1 ? a.g.ny : a.g.nz);
+                    if (q < 0 || q >= nn) continue;
+                }
+                const int xq = cl.X(ax == 0 ? s : 0), yq = cl.Y(ax == 1 ? s : 0), zq = cl.Z(ax == 2 ? s : 0);
+                const long long kb = bbox_index(a.g, b, xq, yq, zq);
+                if (kb < 0) continue;
+                const int kd = kind[kb];
+                if (kd == 2) {
+                    const long long nb = (long long)xq + (long long)a.g.nx * (yq + (long long)a.g.ny * zq);
+                    for (int c = 0; c < 6; ++c) acc[c] += (double)tau[c * np + nb] / (double)nf_arr[kb];
+                    touched = true;
+                } else if (kd == 3) {
+                    for (int c = 0; c < 6; ++c) acc[c] -= delta[c * nc + kb] / (double)nf_arr[kb];
+                    touched = true;
+                }
+            }
+            if (touched) {
+                nf_arr[k] = 255;  // marks a stable cell whose stress changes
+                for (int c = 0; c < 6; ++c) delta[c * nc + k] = acc[c];
+            }
+        }
+        __syncthreads();
+        // D: impulses (sequential, cell order: destroyed cells, then created cells) and
+        // the populations of created cells
+        if (threadIdx.x == 0) {
+            double dP[3] = {0, 0, 0}, dL[3] = {0, 0, 0};
+            for (long long k = 0; k < nc; ++k) {
+                if (kind[k] != 2) continue;
+                int x, y, z;
+                const long long r = bbox_cell(a.g, b, k, x, y, z);
+                const Cell cl(a.g, x, y, z);
+                R f[Q];
+                load_pdfs<S, PAR>(a, cl, r, f);
+                double Pm[3] = {0, 0, 0};
+                for (int c3 = 0; c3 < 3; ++c3)
+                    for (int i = 0; i < Q; ++i) {
+                        const double fi = (double)f[i] + (SH ? wgt<double>(i) * (double)a.ph.rho0 : 0.0);
+                        Pm[c3] += fi * (double)cdir(i, c3);
+                    }
+                double d[3];
+                min_image(a.g, P.X, x, y, z, d);
+                dP[0] += Pm[0];
+                dP[1] += Pm[1];
+                dP[2] += Pm[2];
+                dL[0] += d[1] * Pm[2] - d[2] * Pm[1];
+                dL[1] += d[2] * Pm[0] - d[0] * Pm[2];
+                dL[2] += d[0] * Pm[1] - d[1] * Pm[0];
+                if (nf_arr[k] == 0)
+                    for (int c = 0; c < 6; ++c) diag[c] += (double)tau[c * np + r];
+                diag[6] += 1.0;
+            }
+            for (long long k = 0; k < nc; ++k) {
+                if (kind[k] != 3) continue;
+                int x, y, z;
+                const long long r = bbox_cell(a.g, b, k, x, y, z);
+                const Cell cl(a.g, x, y, z);
+                double rsum = 0.0;
+                int cnt = 0;
+                for (int i = 1; i < Q; ++i) {
+                    if (!a.g.per[0] && (x + cx(i) < 0 || x + cx(i) >= a.g.nx)) continue;
+                    if (!a.g.per[1] && (y + cy(i) < 0 || y + cy(i) >= a.g.ny)) continue;
+                    if (!a.g.per[2] && (z + cz(i) < 0 || z + cz(i) >= a.g.nz)) continue;
+                    const int xq = cl.X(cx(i)), yq = cl.Y(cy(i)), zq = cl.Z(cz(i));
+                    if (kind_of(b, xq, yq, zq) != 1) continue;
+                    const long long nb = (long long)xq + (long long)a.g.nx * (yq + (long long)a.g.ny * zq);
+                    const Cell cn(a.g, xq, yq, zq);
+                    R fn[Q];
+                    load_pdfs<S, PAR>(a, cn, nb, fn);
+                    double rn = 0.0;
+                    for (int j = 0; j < Q; ++j) rn += (double)fn[j] + (SH ? wgt<double>(j) * (double)a.ph.rho0 : 0.0);
+                    rsum += rn;
+                    cnt++;
+                }
+                const double rho_bar = cnt > 0 ? rsum / (double)cnt : (double)a.ph.rho_ref;
+                double d[3], ub[3];
+                min_image(a.g, P.X, x, y, z, d);
+                const double wxd[3] = {P.w[1] * d[2] - P.w[2] * d[1], P.w[2] * d[0] - P.w[0] * d[2],
+                                       P.w[0] * d[1] - P.w[1] * d[0]};
+                for (int c3 = 0; c3 < 3; ++c3) ub[c3] = P.v[c3] + wxd[c3];
+                const double usq = ub[0] * ub[0] + ub[1] * ub[1] + ub[2] * ub[2];
+                double feq[Q];
+                for (int i = 0; i < Q; ++i) {
+                    const double cu = cx(i) * ub[0] + cy(i) * ub[1] + cz(i) * ub[2];
+                    feq[i] = wgt<double>(i) * rho_bar * (1.0 + 3.0 * cu + 4.5 * cu * cu - 1.5 * usq);
+                }
+                for (int i = 0; i < Q; ++i) {
+                    S *dst = PAR == 0 ? a.f + (long long)i * np + r
+                                      : a.f + (long long)copp(i) * np + cl.idx(-cx(i), -cy(i), -cz(i));
+                    const double v = SH ? feq[i] - wgt<double>(i) * (double)a.ph.rho0 : feq[i];
+                    Store<S>::st(dst, (R)v, a.ph.scale);
+                }
+                double Pm[3] = {0, 0, 0};
+                for (int c3 = 0; c3 < 3; ++c3)
+                    for (int i = 0; i < Q; ++i) Pm[c3] += feq[i] * (double)cdir(i, c3);
+                dP[0] -= Pm[0];
+                dP[1] -= Pm[1];
+                dP[2] -= Pm[2];
+                dL[0] -= d[1] * Pm[2] - d[2] * Pm[1];
+                dL[1] -= d[2] * Pm[0] - d[0] * Pm[2];
+                dL[2] -= d[0] * Pm[1] - d[1] * Pm[0];
+                diag[7] += 1.0;
+            }
+            for (int c3 = 0; c3 < 3; ++c3) {
+                P.dP[c3] = dP[c3];
+                P.dL[c3] = dL[c3];
+            }
+        }
+        __syncthreads();
+        // E: apply the stress moves and the new flags
+        for (long long k = threadIdx.x; k < nc; k += blockDim.x) {
+            const int kd = kind[k];
+            if (kd == 0) continue;
+            int x, y, z;
+            const long long r = bbox_cell(a.g, b, k, x, y, z);
+            if (kd == 1) {
+                if (nf_arr[k] == 255)
+                    for (int c = 0; c < 6; ++c) tau[c * np + r] = (R)((double)tau[c * np + r] + delta[c * nc + k]);
+            } else if (kd == 3) {
+                for (int c = 0; c < 6; ++c) tau[c * np + r] = (R)delta[c * nc + k];
+                flag[r] = FLAG_FLUID;
+            } else {
+                for (int c = 0; c < 6; ++c) tau[c * np + r] = R(0);
+                flag[r] = (uint8_t)(FLAG_PART0 + p);
+            }
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            for (int c3 = 0; c3 < 3; ++c3) {
+                P.v[c3] += P.dP[c3] / P.m;
+                P.w[c3] += P.dL[c3] / P.I;
+            }
+        }
+        // clear the stable-cell marks for the next particle / step
+        for (long long k = threadIdx.x; k < nc; k += blockDim.x) nf_arr[k] = 0;
+        __syncthreads();
+    }
 }
 
 // ---------------------------------------------------------------------------------

@@ -67,14 +67,27 @@ struct KernelTable {
                         long long count, long long ld, cudaStream_t);
     cudaError_t (*lb)(const DevState &, int parity, cudaStream_t);
     cudaError_t (*fv)(const DevState &, cudaStream_t);
-    cudaError_t (*momentum_exchange)(const DevState &, int parity, const long long *links, int nlinks,
-                                     double *contrib, cudaStream_t);
+    cudaError_t (*momentum_exchange)(const DevState &, int parity, const long long *links, const int *seg_begin,
+                                     const int *seg_count, int nseg, int max_len, double *contrib, cudaStream_t);
+    cudaError_t (*voxelise)(const DevState &, int p, cudaStream_t);
+    cudaError_t (*particle_update)(const DevState &, int nparts, cudaStream_t);
+    cudaError_t (*particle_links)(const DevState &, int nparts, long long *links, const int *seg_begin, int *seg_count,
+                                  int first_seg, const int *capacity, cudaStream_t);
+    cudaError_t (*fill_drain)(const DevState &, int parity, int nparts, uint8_t *kind, uint8_t *nf, double *delta,
+                              double *diag, cudaStream_t);
     cudaError_t (*read)(const DevState &, int parity, double *rho, double *u, double *tau, int z0, int z1,
                         long long ld, cudaStream_t);
     cudaError_t (*pdfs_io)(const DevState &, int parity, double *io, int write, cudaStream_t);
     cudaError_t (*reduce)(const DevState &, int parity, double *partial, long long *nblocks, cudaStream_t);
     cudaError_t (*probe)(const DevState &, int parity, const long long *cells, int count, double *out, cudaStream_t);
 };
+
+// Bounding-box side used to size the per-particle scratch (cells within R + margin).
+inline int particle_box_side(double R, int margin) {
+    int c = (int)R;
+    if ((double)c < R) ++c;
+    return 2 * c + 2 * margin + 3;
+}
 
 const KernelTable *table_f64();
 const KernelTable *table_f32();

@@ -66,15 +66,43 @@ struct Launch {
         k_fv<S><<<grid3(d), d.block_x, 0, s>>>(a);
         return cudaGetLastError();
     }
-    static cudaError_t momentum_exchange(const DevState &d, int parity, const long long *links, int nlinks,
-                                         double *contrib, cudaStream_t s) {
-        if (nlinks <= 0) return cudaSuccess;
+    static cudaError_t momentum_exchange(const DevState &d, int parity, const long long *links, const int *seg_begin,
+                                         const int *seg_count, int nseg, int max_len, double *contrib, cudaStream_t s) {
+        if (nseg <= 0 || max_len <= 0) return cudaSuccess;
         KArgs<S> a = args(d);
-        const unsigned nb = (unsigned)((nlinks + 127) / 128);
+        const dim3 g((unsigned)((max_len + 127) / 128), (unsigned)nseg);
         if (parity == 0)
-            k_momentum_exchange<S, 0><<<nb, 128, 0, s>>>(a, links, nlinks, contrib);
+            k_momentum_exchange<S, 0><<<g, 128, 0, s>>>(a, links, seg_begin, seg_count, contrib);
         else
-            k_momentum_exchange<S, 1><<<nb, 128, 0, s>>>(a, links, nlinks, contrib);
+            k_momentum_exchange<S, 1><<<g, 128, 0, s>>>(a, links, seg_begin, seg_count, contrib);
+        return cudaGetLastError();
+    }
+    static cudaError_t voxelise(const DevState &d, int p, cudaStream_t s) {
+        KArgs<S> a = args(d);
+        k_voxelise<S><<<64, 256, 0, s>>>(a, d.parts, p, d.flag, (R *)d.tau[0], (R *)d.tau[1]);
+        return cudaGetLastError();
+    }
+    static cudaError_t particle_update(const DevState &d, int nparts, cudaStream_t s) {
+        if (nparts <= 0) return cudaSuccess;
+        k_particle_update<S><<<1, 64, 0, s>>>(d.parts, nparts);
+        return cudaGetLastError();
+    }
+    static cudaError_t particle_links(const DevState &d, int nparts, long long *links, const int *seg_begin,
+                                      int *seg_count, int first_seg, const int *capacity, cudaStream_t s) {
+        if (nparts <= 0) return cudaSuccess;
+        k_particle_links<S><<<nparts, 256, 0, s>>>(d.g, d.parts, d.flag, links, seg_begin, seg_count, first_seg,
+                                                   capacity);
+        return cudaGetLastError();
+    }
+    static cudaError_t fill_drain(const DevState &d, int parity, int nparts, uint8_t *kind, uint8_t *nf, double *delta,
+                                  double *diag, cudaStream_t s) {
+        if (nparts <= 0) return cudaSuccess;
+        KArgs<S> a = args(d);
+        R *tau = (R *)d.tau[d.cur];
+        if (parity == 0)
+            k_fill_drain<S, 0><<<1, 512, 0, s>>>(a, d.parts, nparts, d.flag, tau, kind, nf, delta, diag);
+        else
+            k_fill_drain<S, 1><<<1, 512, 0, s>>>(a, d.parts, nparts, d.flag, tau, kind, nf, delta, diag);
         return cudaGetLastError();
     }
     static cudaError_t read(const DevState &d, int parity, double *rho, double *u, double *tau, int z0, int z1,
@@ -124,8 +152,10 @@ struct Launch {
     }
 
     static const KernelTable *table(int prec) {
-        static const KernelTable t = {prec, sizeof(S), sizeof(R), &init,   &lb,     &fv,
-                                      &momentum_exchange, &read, &pdfs_io, &reduce, &probe};
+        static const KernelTable t = {prec,           sizeof(S),        sizeof(R),   &init,
+                                      &lb,            &fv,              &momentum_exchange, &voxelise,
+                                      &particle_update, &particle_links, &fill_drain, &read,
+                                      &pdfs_io,       &reduce,          &probe};
         return &t;
     }
 };

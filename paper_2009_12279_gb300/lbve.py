@@ -27,7 +27,7 @@ STATUS = ["LBVE_OK", "LBVE_EINVAL", "LBVE_ENOMEM", "LBVE_ECUDA", "LBVE_EUNSTABLE
 EXPORTS = [
     "lbve_default_params", "lbve_device_bytes", "lbve_create", "lbve_create_with_allocator", "lbve_destroy",
     "lbve_set_geometry", "lbve_init_fields", "lbve_init_fields_device", "lbve_probe", "lbve_add_particle", "lbve_step", "lbve_read_fields",
-    "lbve_read_fields_device", "lbve_read_pdfs", "lbve_write_pdfs", "lbve_read_particle", "lbve_read_body_forces",
+    "lbve_read_fields_device", "lbve_read_pdfs", "lbve_write_pdfs", "lbve_read_particle", "lbve_read_conversions", "lbve_read_body_forces",
     "lbve_reduce", "lbve_step_noalloc", "lbve_noalloc_last_error", "lbve_set_kernel_timing", "lbve_read_kernel_times", "lbve_time", "lbve_synchronize", "lbve_last_error", "lbve_status_string",
 ]
 
@@ -87,6 +87,7 @@ def load(path: str | None = None):
         L.lbve_write_pdfs.argtypes = [vp, vp]
         L.lbve_read_particle.argtypes = [vp, ct.c_int, dp]
         L.lbve_read_body_forces.argtypes = [vp, dp]
+        L.lbve_read_conversions.argtypes = [vp, dp]
         L.lbve_reduce.argtypes = [vp, dp]
         L.lbve_step_noalloc.argtypes = [ct.POINTER(Params), vp, vp, vp, vp, dp, ct.c_int, ct.c_longlong, ct.c_int, vp]
         L.lbve_noalloc_last_error.argtypes = []
@@ -278,6 +279,11 @@ class Solver:
         return {"X": o[0:3].copy(), "v": o[3:6].copy(), "w": o[6:9].copy(), "F": o[9:12].copy(),
                 "T": o[12:15].copy(), "dP": o[15:18].copy(), "dL": o[18:21].copy(),
                 "m": o[21], "I": o[22], "R": o[23]}
+
+    def conversions(self) -> dict:
+        o = np.zeros(8)
+        self._check(self._L.lbve_read_conversions(self._h, _dp(o)))
+        return {"dropped_tau": o[:6].copy(), "destroyed": int(o[6]), "created": int(o[7])}
 
     def body_forces(self) -> np.ndarray:
         o = np.zeros((256, 3))
