@@ -207,10 +207,11 @@ lbve_status lbve_read_kernel_times(lbve_ctx *ctx, double ms[LBVE_KT_COUNT], long
  * as code that runs inside a framework which owns all device memory through its own
  * pool, or a host that forbids allocation after start-up.  Such a caller keeps the
  * state in its own buffers and this call advances it with the split-schedule kernels.
- * The one intermediate the kernels need (the velocity field passed from the
- * stream-collide kernel to the stress kernel) lives in a fixed file-scope device array
- * of 3 * LBVE_NOALLOC_MAX_CELLS doubles (12 MiB), which every GPU that loads the library
- * holds until the process exits.
+ * The intermediates the kernels need (the velocity field passed from the stream-collide
+ * kernel to the stress kernel, and the per-cell neighbour masks derived from the flags
+ * at the start of every call) live in fixed file-scope device arrays of
+ * 3 * LBVE_NOALLOC_MAX_CELLS doubles and LBVE_NOALLOC_MAX_CELLS 32-bit words (14 MiB in
+ * all), which every GPU that loads the library holds until the process exits.
  *
  * Buffers (device, caller-owned, same layouts as a context uses internally), with
  * n = nx*ny*nz and np = n rounded up to a multiple of 64:

@@ -112,6 +112,7 @@ bool valid_params(const lbve_params *p, std::string &why) {
     if (!p) return why = "params is NULL", false;
     if (p->nx < 1 || p->ny < 1 || p->nz < 1) return why = "grid dimensions must be >= 1", false;
     if (p->ny > 65535 || p->nz > 65535) return why = "ny and nz must be <= 65535", false;
+    if ((long long)p->nx * p->ny * p->nz > 2147483647LL) return why = "grids are limited to 2^31 - 1 cells", false;
     if (!(p->eta > 0.0)) return why = "eta must be > 0", false;
     if (!(p->beta >= 0.0 && p->beta < 1.0)) return why = "beta must be in [0, 1)", false;
     if (!(p->rho0 > 0.0)) return why = "rho0 must be > 0", false;
@@ -384,7 +385,10 @@ lbve_status create_impl(const lbve_params *p, void *stream, lbve_alloc_fn alloc,
     c->d.f = dev_alloc(c, (size_t)Q * np * c->kt->pdf_bytes);
     c->d.tau[0] = dev_alloc(c, (size_t)6 * np * c->kt->real_bytes);
     c->d.tau[1] = dev_alloc(c, (size_t)6 * np * c->kt->real_bytes);
-    c->d.u = dev_alloc(c, (size_t)3 * np * c->kt->real_bytes);
+    c->d.u[0] = dev_alloc(c, (size_t)3 * np * c->kt->real_bytes);
+    c->d.u[1] = dev_alloc(c, (size_t)3 * np * c->kt->real_bytes);
+    c->d.ucur = 0;
+    c->d.mask = (uint32_t *)dev_alloc(c, (size_t)np * sizeof(uint32_t));
     c->d.flag = (uint8_t *)dev_alloc(c, (size_t)np);
     c->d.parts = (PartDev *)dev_alloc(c, sizeof(PartDev) * MAX_PART);
     c->seg_begin = (int *)dev_alloc(c, sizeof(int) * kMaxBodies);
@@ -394,7 +398,7 @@ lbve_status create_impl(const lbve_params *p, void *stream, lbve_alloc_fn alloc,
     c->pdiag = (double *)dev_alloc(c, sizeof(double) * 8);
     c->body_F = (double *)dev_alloc(c, sizeof(double) * 256 * 3);
     c->red_out = (double *)dev_alloc(c, sizeof(double) * 8);
-    if (!c->d.f || !c->d.tau[0] || !c->d.tau[1] || !c->d.u || !c->d.flag || !c->d.parts || !c->seg_begin || !c->seg_count ||
+    if (!c->d.f || !c->d.tau[0] || !c->d.tau[1] || !c->d.u[0] || !c->d.u[1] || !c->d.mask || !c->d.flag || !c->d.parts || !c->seg_begin || !c->seg_count ||
         !c->seg_flag || !c->part_cap || !c->pdiag ||
         !c->body_F || !c->red_out) {
         g_create_error = "device allocation failed";
@@ -403,7 +407,9 @@ lbve_status create_impl(const lbve_params *p, void *stream, lbve_alloc_fn alloc,
     }
     c->flags_host.assign((size_t)g.n, 0);
     cudaError_t e = cudaMemsetAsync(c->d.flag, 0, (size_t)np, c->stream);
-    if (e == cudaSuccess) e = cudaMemsetAsync(c->d.u, 0, (size_t)3 * np * c->kt->real_bytes, c->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(c->d.u[0], 0, (size_t)3 * np * c->kt->real_bytes, c->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(c->d.u[1], 0, (size_t)3 * np * c->kt->real_bytes, c->stream);
+    if (e == cudaSuccess) e = c->kt->build_mask(c->d, 0, 0, 0, g.nx, g.ny, g.nz, c->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(c->d.tau[1], 0, (size_t)6 * np * c->kt->real_bytes, c->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(c->d.parts, 0, sizeof(PartDev) * MAX_PART, c->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(c->body_F, 0, sizeof(double) * 256 * 3, c->stream);
@@ -496,7 +502,7 @@ size_t lbve_device_bytes(const lbve_params *p) {
     if (!valid_params(p, why)) return 0;
     const long long np = padded((long long)p->nx * p->ny * p->nz);
     const size_t pb = pdf_bytes_of(p->pdf_prec), rb = real_bytes_of(p->pdf_prec);
-    return (size_t)np * (Q * pb + 15 * rb + 1) + sizeof(PartDev) * MAX_PART + 32768;
+    return (size_t)np * (Q * pb + 18 * rb + 1 + 4) + sizeof(PartDev) * MAX_PART + 32768;
 }
 
 lbve_status lbve_create(const lbve_params *p, void *cuda_stream, lbve_ctx **out) {
@@ -561,6 +567,7 @@ lbve_status lbve_set_geometry(lbve_ctx *c, const uint8_t *flags, const double *w
         for (int a = 0; a < 3; ++a) c->d.ph.wall_vel[k][a] = k < n_wall ? wall_vel[3 * k + a] : 0.0;
     std::memcpy(c->flags_host.data(), flags, (size_t)c->d.g.n);
     CK(cudaMemcpyAsync(c->d.flag, flags, (size_t)c->d.g.n, cudaMemcpyHostToDevice, c->stream), "upload flags");
+    CK(c->kt->build_mask(c->d, 0, 0, 0, c->p.nx, c->p.ny, c->p.nz, c->stream), "neighbour masks");
     build_wall_links(c);
     lbve_status s = layout_links(c);
     if (s != LBVE_OK) return s;
@@ -667,7 +674,7 @@ lbve_status lbve_add_particle(lbve_ctx *c, const double X[3], double R, double r
         c->pscratch_cells = cells3;
     }
     CK(cudaMemcpyAsync(c->d.parts + p, &P, sizeof(P), cudaMemcpyHostToDevice, c->stream), "upload particle");
-    CK(c->kt->voxelise(c->d, p, c->stream), "voxelise");
+    CK(c->kt->voxelise(c->d, p, P, c->stream), "voxelise");
     c->parts_host[p] = P;
     c->nparts++;
     c->part_cap_host.push_back((int)(18 * side2 * side2 * side2));
@@ -684,9 +691,52 @@ lbve_status lbve_read_conversions(lbve_ctx *c, double out[8]) {
     return LBVE_OK;
 }
 
+// z-planes per block of the fused kernel: enough blocks for several waves over the
+// SMs, at least 8 planes so the two recomputed halo planes stay a small overhead.
+int fused_zchunk(const lbve_ctx *c) {
+    const long long tiles = (long long)((c->p.nx + 31) / 32) * ((c->p.ny + 7) / 8);
+    int dev = 0, sms = 148;
+    if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const long long want = 12LL * 3 * sms;  // ~12 waves of 3 resident blocks per SM
+    long long chunks = (want + tiles - 1) / tiles;
+    long long zc = (c->p.nz + chunks - 1) / chunks;
+    if (zc < 8) zc = 8;
+    if (zc > c->p.nz) zc = c->p.nz;
+    return (int)zc;
+}
+
+bool use_fused(const lbve_ctx *c, int nsteps) {
+    if (c->p.schedule == LBVE_SCHED_SPLIT) return false;
+    if (c->nbody > 0 || c->nparts > 0) return false;  // forces / fill-drain need the split order
+    return nsteps >= 2;
+}
+
 lbve_status lbve_step(lbve_ctx *c, int nsteps) {
     if (!c) return LBVE_EINVAL;
     if (nsteps < 0) return fail(c, LBVE_EINVAL, "nsteps must be >= 0");
+    if (use_fused(c, nsteps)) {
+        // stream-collide of the first step, fused (stress of step t-1 + stream-collide of
+        // step t) for the others, stress update of the last step
+        const int zc = fused_zchunk(c);
+        CK(timed_begin(c, LBVE_KT_LB), "timing");
+        CK(c->kt->lb(c->d, (int)(c->t & 1), c->stream), "lb kernel");
+        CK(timed_end(c), "timing");
+        c->t++;
+        for (int s = 1; s < nsteps; ++s) {
+            CK(timed_begin(c, LBVE_KT_FUSED), "timing");
+            CK(c->kt->fused(c->d, (int)(c->t & 1), zc, c->stream), "fused kernel");
+            CK(timed_end(c), "timing");
+            c->d.cur ^= 1;
+            c->d.ucur ^= 1;
+            c->t++;
+            if (c->ev_used >= 4096) CK(harvest_times(c), "timing harvest");
+        }
+        CK(timed_begin(c, LBVE_KT_FV), "timing");
+        CK(c->kt->fv(c->d, c->stream), "fv kernel");
+        CK(timed_end(c), "timing");
+        c->d.cur ^= 1;
+        return LBVE_OK;
+    }
     for (int s = 0; s < nsteps; ++s) {
         const int parity = (int)(c->t & 1);
         if (c->nbody > 0) {

@@ -99,10 +99,12 @@ struct Store<__nv_bfloat16> {
     }
 };
 
+// Coordinates of one cell and its periodically wrapped neighbours; cell indices are
+// 32-bit (grids are limited to 2^31 cells).
 struct Cell {
     int x, y, z;
     int xm, xp, ym, yp, zm, zp;
-    long long nx, nxy;
+    unsigned nx, nxy;
     __device__ __forceinline__ Cell(const Geo &g, int x_, int y_, int z_) : x(x_), y(y_), z(z_) {
         xm = x == 0 ? g.nx - 1 : x - 1;
         xp = x == g.nx - 1 ? 0 : x + 1;
@@ -110,17 +112,21 @@ struct Cell {
         yp = y == g.ny - 1 ? 0 : y + 1;
         zm = z == 0 ? g.nz - 1 : z - 1;
         zp = z == g.nz - 1 ? 0 : z + 1;
-        nx = g.nx;
-        nxy = (long long)g.nx * g.ny;
+        nx = (unsigned)g.nx;
+        nxy = (unsigned)g.nx * (unsigned)g.ny;
     }
     __device__ __forceinline__ int X(int d) const { return d == 0 ? x : (d > 0 ? xp : xm); }
     __device__ __forceinline__ int Y(int d) const { return d == 0 ? y : (d > 0 ? yp : ym); }
     __device__ __forceinline__ int Z(int d) const { return d == 0 ? z : (d > 0 ? zp : zm); }
-    __device__ __forceinline__ long long idx(int dx, int dy, int dz) const {
-        return (long long)X(dx) + nx * Y(dy) + nxy * Z(dz);
+    __device__ __forceinline__ unsigned idx(int dx, int dy, int dz) const {
+        return (unsigned)X(dx) + nx * (unsigned)Y(dy) + nxy * (unsigned)Z(dz);
     }
-    __device__ __forceinline__ long long self() const { return (long long)x + nx * y + nxy * z; }
+    __device__ __forceinline__ unsigned self() const { return (unsigned)x + nx * (unsigned)y + nxy * (unsigned)z; }
 };
+
+// Neighbour mask of a cell: bit 0 set if the cell is not fluid, bit i (1..18) set if the
+// neighbour r + c_i is not fluid.  Faces of the D3Q7 set are directions 1..6.
+__device__ __forceinline__ bool nb_solid(uint32_t m, int i) { return (m >> i) & 1u; }
 
 // Boundary velocity u_b of the solid cell (xq, yq, zq) with flag fl: zero for a no-slip
 // wall, the class velocity for a moving wall (Eq. (ubb)), v + w x (r_b - X) with the
@@ -151,19 +157,40 @@ __device__ __forceinline__ void boundary_velocity(const Geo &g, const Phys<R> &p
     }
 }
 
+// Boundary velocity with the common no-slip case inline and the moving-wall / particle
+// cases out of line (they are rare and would otherwise bloat every caller).
+template <class R>
+__device__ __noinline__ void boundary_velocity_slow(const Geo &g, const Phys<R> &ph, const PartDev *parts, int fl,
+                                                    int xq, int yq, int zq, R *ub) {
+    R t[3];
+    boundary_velocity<R>(g, ph, parts, fl, xq, yq, zq, t);
+    ub[0] = t[0];
+    ub[1] = t[1];
+    ub[2] = t[2];
+}
+
+template <class R>
+__device__ __forceinline__ void boundary_velocity_fast(const Geo &g, const Phys<R> &ph, const PartDev *parts, int fl,
+                                                       int xq, int yq, int zq, R ub[3]) {
+    if (fl == FLAG_NOSLIP) {
+        ub[0] = R(0);
+        ub[1] = R(0);
+        ub[2] = R(0);
+    } else {
+        boundary_velocity_slow<R>(g, ph, parts, fl, xq, yq, zq, ub);
+    }
+}
+
 // --------------------------------------------------------------------------------
 // local operators
 // --------------------------------------------------------------------------------
 
 // Polymer force Eq. (force) on the D3Q7 faces (A_0 = 1): F_j = sum_faces s tau_kj(face),
 // face value by Eq. (interpolation), or tau(r) towards a solid cell (Eq. (extrapolation)).
-template <class R>
-__device__ __forceinline__ void polymer_force(const Geo &g, const Cell &cl, long long r, const R *__restrict__ tau,
-                                              const uint8_t *__restrict__ flag, R Fp[3]) {
-    const long long np = g.np;
-    R tr[6];
-#pragma unroll
-    for (int c = 0; c < 6; ++c) tr[c] = tau[c * np + r];
+// tn(l, c) returns component c of the stress of the face-l neighbour (l = 0..5 for
+// +x, -x, +y, -y, +z, -z); it is only called for fluid neighbours.
+template <class R, class TauNb>
+__device__ __forceinline__ void polymer_force_core(const R (&tr)[6], uint32_t mask, const TauNb &tn, R Fp[3]) {
     Fp[0] = R(0);
     Fp[1] = R(0);
     Fp[2] = R(0);
@@ -171,18 +198,32 @@ __device__ __forceinline__ void polymer_force(const Geo &g, const Cell &cl, long
     for (int l = 0; l < 6; ++l) {
         const int k = l >> 1;
         const int s = (l & 1) ? -1 : 1;
-        const long long nb = cl.idx(k == 0 ? s : 0, k == 1 ? s : 0, k == 2 ? s : 0);
-        const bool fl = flag[nb] == FLAG_FLUID;
+        const bool fl = !nb_solid(mask, l + 1);
 #pragma unroll
         for (int j = 0; j < 3; ++j) {
             const int c = comp(k, j);
-            const R tf = fl ? R(0.5) * (tr[c] + tau[c * np + nb]) : tr[c];
+            const R tf = fl ? R(0.5) * (tr[c] + tn(l, c)) : tr[c];
             if (s > 0)
                 Fp[j] = Fp[j] + tf;
             else
                 Fp[j] = Fp[j] - tf;
         }
     }
+}
+
+// Same with the stress read from global memory.
+template <class R>
+__device__ __forceinline__ void polymer_force(const Geo &g, const Cell &cl, unsigned r, uint32_t mask,
+                                              const R *__restrict__ tau, R Fp[3]) {
+    const size_t np = (size_t)g.np;
+    R tr[6];
+#pragma unroll
+    for (int c = 0; c < 6; ++c) tr[c] = tau[c * np + r];
+    auto tn = [&](int l, int c) -> R {
+        const int k = l >> 1, s = (l & 1) ? -1 : 1;
+        return tau[c * np + cl.idx(k == 0 ? s : 0, k == 1 ? s : 0, k == 2 ? s : 0)];
+    };
+    polymer_force_core<R>(tr, mask, tn, Fp);
 }
 
 // Macroscopic moments, Eq. (macroscopic-velocity).  FP64 mode sums in direction order;
@@ -246,103 +287,137 @@ __device__ __forceinline__ R cdot(int i, const R v[3]) {
 }
 
 // TRT collision with Guo forcing, Eqs. (lb), (lb-equilibrium), (guo), in place on f.
-// FP64 mode: feq_i = (w_i rho)(1 + 3 cu + 9/2 cu^2 - 3/2 u^2); shifted modes work on the
-// deviations with feq_i - w_i rho0 = w_i (drho + rho (3 cu + 9/2 cu^2 - 3/2 u^2)).
+// FP64 mode: feq_i = (w_i rho)(1 + 3 cu + 9/2 cu^2 - 3/2 u^2), each population evaluated
+// as the plain statement of the equations orders it.  Shifted modes work on the
+// deviations, with feq_i - w_i rho0 = w_i (drho + rho (3 cu + 9/2 cu^2 - 3/2 u^2)), and
+// fold the pair (i, -i) algebraically:
+//   f*_{+-i} = f_{+-i} - P -+ M,
+//   P = omega+/2 (f_i + f_-i) - omega+ w_i (drho + rho (9/2 cu^2 - 3/2 u^2)) - w_i B (9 cu cF - 3 u.F)
+//   M = omega-/2 (f_i - f_-i) - w_i (3 omega- rho cu + A cF).
 template <class R, bool SH>
 __device__ __forceinline__ void collide(R (&f)[Q], R rho, R drho, const R u[3], const R F[3], const Phys<R> &ph) {
     const R usq = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
     const R uF = u[0] * F[0] + u[1] * F[1] + u[2] * F[2];
     const R wp = ph.omega_p, wm = ph.omega_m;
-    // rest population
-    {
-        R feq0;
-        if constexpr (!SH)
-            feq0 = wgt<R>(0) * rho * (R(1) + R(3) * R(0) + R(4.5) * R(0) * R(0) - R(1.5) * usq);
-        else
-            feq0 = wgt<R>(0) * (drho - rho * (R(1.5) * usq));
-        const R D0 = wgt<R>(0) * (ph.A * R(0) + ph.B * (R(9) * R(0) * R(0) - R(3) * uF));
-        f[0] = f[0] - wp * (R(0.5) * (f[0] + f[0]) - R(0.5) * (feq0 + feq0)) - wm * R(0) + D0;
-    }
-#pragma unroll
-    for (int i = 1; i < Q; i += 2) {
-        const int ip = i + 1;
-        const R cu = cdot<R>(i, u);
-        const R cF = cdot<R>(i, F);
-        R fe_i, fe_o;
-        if constexpr (!SH) {
-            const R wr = wgt<R>(i) * rho;
-            fe_i = wr * (R(1) + R(3) * cu + R(4.5) * cu * cu - R(1.5) * usq);
-            fe_o = wr * (R(1) + R(3) * (-cu) + R(4.5) * (-cu) * (-cu) - R(1.5) * usq);
-        } else {
-            const R sym = R(4.5) * cu * cu - R(1.5) * usq;
-            fe_i = wgt<R>(i) * (drho + rho * (sym + R(3) * cu));
-            fe_o = wgt<R>(i) * (drho + rho * (sym - R(3) * cu));
+    if constexpr (!SH) {
+        {
+            const R feq0 = wgt<R>(0) * rho * (R(1) + R(3) * R(0) + R(4.5) * R(0) * R(0) - R(1.5) * usq);
+            const R D0 = wgt<R>(0) * (ph.A * R(0) + ph.B * (R(9) * R(0) * R(0) - R(3) * uF));
+            f[0] = f[0] - wp * (R(0.5) * (f[0] + f[0]) - R(0.5) * (feq0 + feq0)) - wm * R(0) + D0;
         }
-        const R Bt = ph.B * (R(9) * cu * cF - R(3) * uF);
-        const R Di = wgt<R>(i) * (ph.A * cF + Bt);
-        const R Do = wgt<R>(i) * (Bt - ph.A * cF);
-        const R fp = R(0.5) * (f[i] + f[ip]);
-        const R fm = R(0.5) * (f[i] - f[ip]);
-        const R ep = R(0.5) * (fe_i + fe_o);
-        const R em = R(0.5) * (fe_i - fe_o);
-        const R Pp = wp * (fp - ep);
-        const R Pm = wm * (fm - em);
-        const R fi = f[i] - Pp - Pm + Di;
-        const R fo = f[ip] - Pp + Pm + Do;
-        f[i] = fi;
-        f[ip] = fo;
+#pragma unroll
+        for (int i = 1; i < Q; i += 2) {
+            const int ip = i + 1;
+            const R cu = cdot<R>(i, u);
+            const R cF = cdot<R>(i, F);
+            const R wr = wgt<R>(i) * rho;
+            const R fe_i = wr * (R(1) + R(3) * cu + R(4.5) * cu * cu - R(1.5) * usq);
+            const R fe_o = wr * (R(1) + R(3) * (-cu) + R(4.5) * (-cu) * (-cu) - R(1.5) * usq);
+            const R Bt = ph.B * (R(9) * cu * cF - R(3) * uF);
+            const R Di = wgt<R>(i) * (ph.A * cF + Bt);
+            const R Do = wgt<R>(i) * (Bt - ph.A * cF);
+            const R fp = R(0.5) * (f[i] + f[ip]);
+            const R fm = R(0.5) * (f[i] - f[ip]);
+            const R ep = R(0.5) * (fe_i + fe_o);
+            const R em = R(0.5) * (fe_i - fe_o);
+            const R Pp = wp * (fp - ep);
+            const R Pm = wm * (fm - em);
+            const R fi = f[i] - Pp - Pm + Di;
+            const R fo = f[ip] - Pp + Pm + Do;
+            f[i] = fi;
+            f[ip] = fo;
+        }
+    } else {
+        const R hp = R(0.5) * wp, hm = R(0.5) * wm;
+        const R q = R(1.5) * usq;
+        const R k3 = R(3) * wm * rho;
+        const R u3F = R(3) * uF;
+        // rest population: feq0 - w0 rho0 = w0 (drho - rho q), forcing w0 B (-3 u.F)
+        f[0] = f[0] - wp * (f[0] - wgt<R>(0) * (drho - rho * q)) - wgt<R>(0) * ph.B * u3F;
+#pragma unroll
+        for (int i = 1; i < Q; i += 2) {
+            const int ip = i + 1;
+            const R w = wgt<R>(i);
+            const R cu = cdot<R>(i, u);
+            const R cF = cdot<R>(i, F);
+            const R sym = drho + rho * (R(4.5) * cu * cu - q);
+            const R x9 = R(9) * cu * cF - u3F;
+            const R P = hp * (f[i] + f[ip]) - (wp * w) * sym - (w * ph.B) * x9;
+            const R M = hm * (f[i] - f[ip]) - w * (k3 * cu + ph.A * cF);
+            const R fi = f[i] - P - M;
+            const R fo = f[ip] - P + M;
+            f[i] = fi;
+            f[ip] = fo;
+        }
     }
 }
 
 // Finite-volume stress update of one fluid cell (Sec. "Discretization", "Stability
-// improvements"): velocity gradient by the central-point rule (boundary velocity as
-// the face value towards solid cells), donor-cell flux on the D3Q7 faces with zero flux
+// improvements"): velocity gradient by the central-point rule (boundary velocity as the
+// face value towards solid cells), donor-cell flux on the D3Q7 faces with zero flux
 // across solid links, source Eq. (source) without the tau div u term, explicit Euler.
-template <class R>
-__device__ __forceinline__ void fv_cell(const Geo &g, const Phys<R> &ph, const Cell &cl, long long r,
-                                        const R *__restrict__ tau, const R *__restrict__ u,
-                                        const uint8_t *__restrict__ flag, const PartDev *parts, R out[6]) {
-    const long long np = g.np;
-    R tr[6], ur[3];
+// nb.u(l, k), nb.tau(l, c): velocity / stress of the face-l neighbour (fluid only);
+// nb.ub(l, out): boundary velocity of a solid face-l neighbour.
+// FP64 mode keeps the face-by-face order of the plain statement; shifted modes gather
+// the outflow as (sum of outgoing face velocities) * tau(r).
+template <class R, bool SH, class Nb>
+__device__ __forceinline__ void fv_core(const Phys<R> &ph, const R (&tr)[6], const R (&ur)[3], uint32_t mask,
+                                        const Nb &nb, R out[6]) {
+    R un[6][3];
 #pragma unroll
-    for (int c = 0; c < 6; ++c) tr[c] = tau[c * np + r];
+    for (int l = 0; l < 6; ++l) {
+        if (!nb_solid(mask, l + 1)) {
 #pragma unroll
-    for (int a = 0; a < 3; ++a) ur[a] = u[a * np + r];
+            for (int j = 0; j < 3; ++j) un[l][j] = nb.u(l, j);
+        } else {
+            nb.ub(l, un[l]);
+        }
+    }
     R G[3][3];
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
-        const long long npl = cl.idx(k == 0, k == 1, k == 2);
-        const long long nmi = cl.idx(-(k == 0), -(k == 1), -(k == 2));
-        const int fp_ = flag[npl], fm_ = flag[nmi];
-        R ubp[3], ubm[3];
-        if (fp_ != FLAG_FLUID)
-            boundary_velocity<R>(g, ph, parts, fp_, cl.X(k == 0), cl.Y(k == 1), cl.Z(k == 2), ubp);
-        if (fm_ != FLAG_FLUID)
-            boundary_velocity<R>(g, ph, parts, fm_, cl.X(-(k == 0)), cl.Y(-(k == 1)), cl.Z(-(k == 2)), ubm);
+        const bool fp_ = !nb_solid(mask, 2 * k + 1), fm_ = !nb_solid(mask, 2 * k + 2);
 #pragma unroll
         for (int j = 0; j < 3; ++j) {
-            const R up = fp_ == FLAG_FLUID ? R(0.5) * (ur[j] + u[j * np + npl]) : ubp[j];
-            const R um = fm_ == FLAG_FLUID ? R(0.5) * (ur[j] + u[j * np + nmi]) : ubm[j];
+            const R up = fp_ ? R(0.5) * (ur[j] + un[2 * k][j]) : un[2 * k][j];
+            const R um = fm_ ? R(0.5) * (ur[j] + un[2 * k + 1][j]) : un[2 * k + 1][j];
             G[k][j] = up - um;
         }
     }
     R net[6] = {R(0), R(0), R(0), R(0), R(0), R(0)};
     if (ph.flux_on) {
+        if constexpr (!SH) {
 #pragma unroll
-        for (int l = 0; l < 6; ++l) {
-            const int k = l >> 1;
-            const int s = (l & 1) ? -1 : 1;
-            const long long nb = cl.idx(k == 0 ? s : 0, k == 1 ? s : 0, k == 2 ? s : 0);
-            if (flag[nb] != FLAG_FLUID) continue;
-            const R vout = s > 0 ? ur[k] : -ur[k];
-            const R unk = u[k * np + nb];
-            const R vin = s > 0 ? -unk : unk;
+            for (int l = 0; l < 6; ++l) {
+                const int k = l >> 1;
+                const int s = (l & 1) ? -1 : 1;
+                if (nb_solid(mask, l + 1)) continue;
+                const R vout = s > 0 ? ur[k] : -ur[k];
+                const R vin = s > 0 ? -un[l][k] : un[l][k];
 #pragma unroll
-            for (int c = 0; c < 6; ++c) {
-                const R Jo = vout > R(0) ? vout * tr[c] : R(0);
-                const R Ji = vin > R(0) ? vin * tau[c * np + nb] : R(0);
-                net[c] = net[c] + (Jo - Ji);
+                for (int c = 0; c < 6; ++c) {
+                    const R Jo = vout > R(0) ? vout * tr[c] : R(0);
+                    const R Ji = vin > R(0) ? vin * nb.tau(l, c) : R(0);
+                    net[c] = net[c] + (Jo - Ji);
+                }
             }
+        } else {
+            R aout = R(0);
+            R inflow[6] = {R(0), R(0), R(0), R(0), R(0), R(0)};
+#pragma unroll
+            for (int l = 0; l < 6; ++l) {
+                const int k = l >> 1;
+                const int s = (l & 1) ? -1 : 1;
+                if (nb_solid(mask, l + 1)) continue;
+                const R vout = s > 0 ? ur[k] : -ur[k];
+                const R vin = s > 0 ? -un[l][k] : un[l][k];
+                aout += vout > R(0) ? vout : R(0);
+                const R b = vin > R(0) ? vin : R(0);
+#pragma unroll
+                for (int c = 0; c < 6; ++c) inflow[c] += b * nb.tau(l, c);
+            }
+#pragma unroll
+            for (int c = 0; c < 6; ++c) net[c] = aout * tr[c] - inflow[c];
         }
     }
 #pragma unroll

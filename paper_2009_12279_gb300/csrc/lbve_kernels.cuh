@@ -21,105 +21,423 @@ struct KArgs {
     Geo g;
     Phys<R> ph;
     S *f;
-    const R *tau;   // tau^t
-    R *tau_out;     // tau^{t+1}
-    R *u;           // u^t (written by k_lb, read by k_fv)
+    const R *tau;     // stress at the time level read
+    R *tau_out;       // stress at the next time level
+    const R *u_in;    // velocity read by the stress update
+    R *u_out;         // velocity written by the stream-collide
     const uint8_t *flag;
+    const uint32_t *mask;
     const PartDev *parts;
 };
 
 // Load f_i^t of cell r from its AA location for the given parity.
 template <class S, int PAR>
-__device__ __forceinline__ void load_pdfs(const KArgs<S> &a, const Cell &cl, long long r,
+__device__ __forceinline__ void load_pdfs(const KArgs<S> &a, const Cell &cl, unsigned r,
                                           typename Store<S>::R (&f)[Q]) {
     using R = typename Store<S>::R;
-    const long long np = a.g.np;
+    const size_t np = (size_t)a.g.np;
     const R inv = a.ph.inv_scale;
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
-        const S *p = PAR == 0 ? a.f + (long long)i * np + r
-                              : a.f + (long long)copp(i) * np + cl.idx(-cx(i), -cy(i), -cz(i));
+        const S *p = PAR == 0 ? a.f + i * np + r : a.f + copp(i) * np + cl.idx(-cx(i), -cy(i), -cz(i));
         f[i] = Store<S>::ld(p, inv);
     }
+}
+
+// 6 w_i rho c_i . u_b of a link into a moving wall or particle cell (out of line: rare).
+template <class R>
+__device__ __noinline__ R moving_wall_term(const Geo &g, const Phys<R> &ph, const PartDev *parts, int fl, int xq,
+                                           int yq, int zq, int i, R rho) {
+    R ub[3];
+    boundary_velocity<R>(g, ph, parts, fl, xq, yq, zq, ub);
+    R cub = R(0);
+    bool first = true;
+    for (int k = 0; k < 3; ++k) {
+        const int c = k == 0 ? cx(i) : (k == 1 ? cy(i) : cz(i));
+        if (c != 0) {
+            if (first) {
+                cub = c > 0 ? ub[k] : -ub[k];
+                first = false;
+            } else {
+                cub = c > 0 ? cub + ub[k] : cub - ub[k];
+            }
+        }
+    }
+    const R w = i < 7 ? wgt<R>(1) : wgt<R>(7);
+    return R(6) * w * rho * cub;
 }
 
 // Store post-collision f*_i with AA addressing; links into solid cells bounce back with
 // the moving-wall term of Eq. (ubb): f_-i(r, t+1) = f*_i(r) - 6 w_i rho c_i . u_b.
 template <class S, int PAR>
-__device__ __forceinline__ void store_pdfs(const KArgs<S> &a, const Cell &cl, long long r,
+__device__ __forceinline__ void store_pdfs(const KArgs<S> &a, const Cell &cl, unsigned r, uint32_t mask,
                                            const typename Store<S>::R (&fs)[Q], typename Store<S>::R rho) {
     using R = typename Store<S>::R;
-    const long long np = a.g.np;
+    const size_t np = (size_t)a.g.np;
     const R sc = a.ph.scale;
+    Store<S>::st(a.f + r, fs[0], sc);
 #pragma unroll
-    for (int i = 0; i < Q; ++i) {
-        if (i == 0) {
-            Store<S>::st(a.f + r, fs[0], sc);
-            continue;
-        }
-        const long long nb = cl.idx(cx(i), cy(i), cz(i));
-        const int fl = a.flag[nb];
-        if (fl == FLAG_FLUID) {
-            S *p = PAR == 0 ? a.f + (long long)copp(i) * np + r : a.f + (long long)i * np + nb;
+    for (int i = 1; i < Q; ++i) {
+        const unsigned nb = cl.idx(cx(i), cy(i), cz(i));
+        if (!nb_solid(mask, i)) {
+            S *p = PAR == 0 ? a.f + copp(i) * np + r : a.f + i * np + nb;
             Store<S>::st(p, fs[i], sc);
         } else {
             R X = R(0);
-            if (fl != FLAG_NOSLIP) {
-                R ub[3];
-                boundary_velocity<R>(a.g, a.ph, a.parts, fl, cl.X(cx(i)), cl.Y(cy(i)), cl.Z(cz(i)), ub);
-                X = R(6) * wgt<R>(i) * rho * cdot<R>(i, ub);
-            }
-            S *p = PAR == 0 ? a.f + (long long)i * np + nb : a.f + (long long)copp(i) * np + r;
+            const int fl = a.flag[nb];
+            if (fl != FLAG_NOSLIP) X = moving_wall_term<R>(a.g, a.ph, a.parts, fl, cl.X(cx(i)), cl.Y(cy(i)), cl.Z(cz(i)), i, rho);
+            S *p = PAR == 0 ? a.f + i * np + nb : a.f + copp(i) * np + r;
             Store<S>::st(p, fs[i] - X, sc);
         }
     }
 }
 
-// LB half of the step for one fluid cell: F = g + F^p(tau^t), moments, u^t written out,
-// TRT collision with forcing, AA streaming with bounce-back.
-template <class S, int PAR>
-__device__ __forceinline__ void lb_cell(const KArgs<S> &a, const Cell &cl, long long r) {
+// LB half of the step for one fluid cell, given its own stress tr and an accessor tn for
+// its face neighbours' stress (tau^t): F = g + F^p, moments, u^t written out, TRT
+// collision with forcing, AA streaming with bounce-back.
+template <class S, int PAR, class TauNb>
+__device__ __forceinline__ void lb_core(const KArgs<S> &a, const Cell &cl, unsigned r, uint32_t mask,
+                                        const typename Store<S>::R (&tr)[6], const TauNb &tn) {
     using R = typename Store<S>::R;
     constexpr bool SH = Store<S>::shifted;
     R f[Q];
     load_pdfs<S, PAR>(a, cl, r, f);
     R Fp[3], F[3], u[3], rho, drho;
-    polymer_force<R>(a.g, cl, r, a.tau, a.flag, Fp);
+    polymer_force_core<R>(tr, mask, tn, Fp);
 #pragma unroll
     for (int k = 0; k < 3; ++k) F[k] = a.ph.g[k] + Fp[k];
     moments<R, SH>(f, F, a.ph.rho0, rho, drho, u);
+    const size_t np = (size_t)a.g.np;
 #pragma unroll
-    for (int k = 0; k < 3; ++k) a.u[k * a.g.np + r] = u[k];
+    for (int k = 0; k < 3; ++k) a.u_out[k * np + r] = u[k];
     collide<R, SH>(f, rho, drho, u, F, a.ph);
-    store_pdfs<S, PAR>(a, cl, r, f, rho);
+    store_pdfs<S, PAR>(a, cl, r, mask, f, rho);
 }
+
+// Velocity / stress / boundary-velocity accessors of the face neighbours in global memory.
+template <class R>
+struct GlobalNb {
+    const Geo &g;
+    const Phys<R> &ph;
+    const Cell &cl;
+    const R *tau;
+    const R *u;
+    const uint8_t *flag;
+    const PartDev *parts;
+    __device__ __forceinline__ unsigned at(int l) const {
+        const int k = l >> 1, s = (l & 1) ? -1 : 1;
+        return cl.idx(k == 0 ? s : 0, k == 1 ? s : 0, k == 2 ? s : 0);
+    }
+    __device__ __forceinline__ R u_(int l, int j) const { return u[j * (size_t)g.np + at(l)]; }
+    __device__ __forceinline__ R tau_(int l, int c) const { return tau[c * (size_t)g.np + at(l)]; }
+    __device__ __forceinline__ void ub_(int l, R out[3]) const {
+        const int k = l >> 1, s = (l & 1) ? -1 : 1;
+        const int dx = k == 0 ? s : 0, dy = k == 1 ? s : 0, dz = k == 2 ? s : 0;
+        boundary_velocity_fast<R>(g, ph, parts, flag[at(l)], cl.X(dx), cl.Y(dy), cl.Z(dz), out);
+    }
+};
+template <class R>
+struct NbAdapter {  // gives GlobalNb the u / tau / ub interface fv_core expects
+    const GlobalNb<R> &n;
+    __device__ __forceinline__ R u(int l, int j) const { return n.u_(l, j); }
+    __device__ __forceinline__ R tau(int l, int c) const { return n.tau_(l, c); }
+    __device__ __forceinline__ void ub(int l, R out[3]) const { n.ub_(l, out); }
+};
 
 template <class S, int PAR>
 __global__ void __launch_bounds__(256) k_lb(KArgs<S> a) {
+    using R = typename Store<S>::R;
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
     if (x >= a.g.nx) return;
     const Cell cl(a.g, x, blockIdx.y, blockIdx.z);
-    const long long r = cl.self();
-    if (a.flag[r] != FLAG_FLUID) return;
-    lb_cell<S, PAR>(a, cl, r);
+    const unsigned r = cl.self();
+    const uint32_t m = a.mask[r];
+    if (m & 1u) return;
+    const size_t np = (size_t)a.g.np;
+    R tr[6];
+#pragma unroll
+    for (int c = 0; c < 6; ++c) tr[c] = a.tau[c * np + r];
+    auto tn = [&](int l, int c) -> R {
+        const int k = l >> 1, s = (l & 1) ? -1 : 1;
+        return a.tau[c * np + cl.idx(k == 0 ? s : 0, k == 1 ? s : 0, k == 2 ? s : 0)];
+    };
+    lb_core<S, PAR>(a, cl, r, m, tr, tn);
 }
 
 template <class S>
 __global__ void __launch_bounds__(256) k_fv(KArgs<S> a) {
     using R = typename Store<S>::R;
+    constexpr bool SH = Store<S>::shifted;
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
     if (x >= a.g.nx) return;
     const Cell cl(a.g, x, blockIdx.y, blockIdx.z);
-    const long long r = cl.self();
+    const unsigned r = cl.self();
+    const size_t np = (size_t)a.g.np;
+    const uint32_t m = a.mask[r];
     R out[6];
-    if (a.flag[r] != FLAG_FLUID) {
+    if (m & 1u) {
 #pragma unroll
-        for (int c = 0; c < 6; ++c) a.tau_out[c * a.g.np + r] = R(0);
+        for (int c = 0; c < 6; ++c) a.tau_out[c * np + r] = R(0);
         return;
     }
-    fv_cell<R>(a.g, a.ph, cl, r, a.tau, a.u, a.flag, a.parts, out);
+    R tr[6], ur[3];
 #pragma unroll
-    for (int c = 0; c < 6; ++c) a.tau_out[c * a.g.np + r] = out[c];
+    for (int c = 0; c < 6; ++c) tr[c] = a.tau[c * np + r];
+#pragma unroll
+    for (int j = 0; j < 3; ++j) ur[j] = a.u_in[j * np + r];
+    const GlobalNb<R> gn{a.g, a.ph, cl, a.tau, a.u_in, a.flag, a.parts};
+    const NbAdapter<R> nb{gn};
+    fv_core<R, SH>(a.ph, tr, ur, m, nb, out);
+#pragma unroll
+    for (int c = 0; c < 6; ++c) a.tau_out[c * np + r] = out[c];
+}
+
+// Neighbour masks of the cells in a box (whole grid: lo = 0, ext = n) from the flags.
+// A neighbour outside a closed side counts as solid.
+__device__ __forceinline__ uint32_t cell_mask(const Geo &g, const uint8_t *__restrict__ flag, int x, int y, int z) {
+    const Cell cl(g, x, y, z);
+    uint32_t m = flag[cl.self()] != FLAG_FLUID ? 1u : 0u;
+#pragma unroll
+    for (int i = 1; i < Q; ++i) {
+        const bool out = (!g.per[0] && (x + cx(i) < 0 || x + cx(i) >= g.nx)) ||
+                         (!g.per[1] && (y + cy(i) < 0 || y + cy(i) >= g.ny)) ||
+                         (!g.per[2] && (z + cz(i) < 0 || z + cz(i) >= g.nz));
+        if (out || flag[cl.idx(cx(i), cy(i), cz(i))] != FLAG_FLUID) m |= 1u << i;
+    }
+    return m;
+}
+
+template <class S>
+__global__ void k_build_mask(Geo g, const uint8_t *__restrict__ flag, uint32_t *__restrict__ mask, int lx, int ly,
+                             int lz, int ex, int ey, int ez) {
+    const long long cells = (long long)ex * ey * ez;
+    for (long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x; k < cells;
+         k += (long long)gridDim.x * blockDim.x) {
+        const int ix = (int)(k % ex), iy = (int)((k / ex) % ey), iz = (int)(k / ((long long)ex * ey));
+        const int x = ((lx + ix) % g.nx + g.nx) % g.nx;
+        const int y = ((ly + iy) % g.ny + g.ny) % g.ny;
+        const int z = ((lz + iz) % g.nz + g.nz) % g.nz;
+        mask[(unsigned)x + (unsigned)g.nx * ((unsigned)y + (unsigned)g.ny * (unsigned)z)] = cell_mask(g, flag, x, y, z);
+    }
+}
+
+// ---------------------------------------------------------------------------------
+// fused schedule: one kernel per step t does the stress update of step t-1 (tau^t from
+// tau^{t-1}, u^{t-1}) and the LB half of step t, marching along z through an x-y tile.
+// tau^{t-1} and u^{t-1} planes are staged in shared memory with cp.async (two planes
+// ahead), tau^t is kept for three planes so the polymer force of plane z reads its
+// face neighbours from shared memory, and only the tile's own cells are written out.
+// ---------------------------------------------------------------------------------
+constexpr int FT_X = 32, FT_Y = 8;
+constexpr int H2X = FT_X + 4, H2Y = FT_Y + 4, NH2 = H2X * H2Y;  // staged inputs
+constexpr int H1X = FT_X + 2, H1Y = FT_Y + 2, NH1 = H1X * H1Y;  // tau^t and masks
+
+template <class R>
+struct FusedSmem {
+    R in_tau[3][6][NH2];
+    R in_u[3][3][NH2];
+    R tnew[3][6][NH1];
+    uint32_t mask[4][NH1];
+};
+
+struct FusedWork {
+    int tiles_x, tiles_y, zchunk, nzchunks;
+};
+
+__device__ __forceinline__ void cp_async4(void *dst, const void *src) {
+    const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(d), "l"(src));
+}
+__device__ __forceinline__ void cp_async8(void *dst, const void *src) {
+    const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(d), "l"(src));
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
+
+template <class R>
+__device__ __forceinline__ void cp_async_real(R *dst, const R *src) {
+    if constexpr (sizeof(R) == 8)
+        cp_async8(dst, src);
+    else
+        cp_async4(dst, src);
+}
+
+// wrapped coordinate along a side, or -1 outside a closed side
+__device__ __forceinline__ int side_coord(int q, int n, int per) {
+    if (q >= 0 && q < n) return q;
+    if (!per) return -1;
+    return ((q % n) + n) % n;
+}
+
+__device__ __forceinline__ int ring3(int z) { return ((z % 3) + 3) % 3; }
+__device__ __forceinline__ int ring4(int z) { return ((z % 4) + 4) % 4; }
+
+// Smem neighbour accessor of the fused stress update (the staged planes zz-1, zz, zz+1).
+template <class S>
+struct SmemNb {
+    using R = typename Store<S>::R;
+    const FusedSmem<R> &sm;
+    const KArgs<S> &a;
+    int sc, sd, su, c2, xg, yg, zg;
+    __device__ __forceinline__ int slot(int l) const { return l == 4 ? su : (l == 5 ? sd : sc); }
+    __device__ __forceinline__ int cell(int l) const {
+        return l == 0 ? c2 + 1 : l == 1 ? c2 - 1 : l == 2 ? c2 + H2X : l == 3 ? c2 - H2X : c2;
+    }
+    __device__ __forceinline__ R u(int l, int j) const { return sm.in_u[slot(l)][j][cell(l)]; }
+    __device__ __forceinline__ R tau(int l, int c) const { return sm.in_tau[slot(l)][c][cell(l)]; }
+    __device__ __forceinline__ void ub(int l, R o[3]) const {
+        const int k = l >> 1, s = (l & 1) ? -1 : 1;
+        int xq = xg + (k == 0 ? s : 0), yq = yg + (k == 1 ? s : 0), zq = zg + (k == 2 ? s : 0);
+        xq = xq < 0 ? xq + a.g.nx : (xq >= a.g.nx ? xq - a.g.nx : xq);
+        yq = yq < 0 ? yq + a.g.ny : (yq >= a.g.ny ? yq - a.g.ny : yq);
+        zq = zq < 0 ? zq + a.g.nz : (zq >= a.g.nz ? zq - a.g.nz : zq);
+        const int fl = a.flag[(unsigned)xq + (unsigned)a.g.nx * ((unsigned)yq + (unsigned)a.g.ny * (unsigned)zq)];
+        boundary_velocity_fast<R>(a.g, a.ph, a.parts, fl, xq, yq, zq, o);
+    }
+};
+
+template <class S, int PAR>
+__global__ void __launch_bounds__(FT_X * FT_Y, sizeof(typename Store<S>::R) == 8 ? 1 : 3) k_fused(KArgs<S> a, FusedWork w) {
+    using R = typename Store<S>::R;
+    constexpr bool SH = Store<S>::shifted;
+    constexpr int NT = FT_X * FT_Y;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    FusedSmem<R> &sm = *reinterpret_cast<FusedSmem<R> *>(smem_raw);
+    const int tid = threadIdx.x;
+    const int item = blockIdx.x;
+    const int tx = item % w.tiles_x;
+    const int ty = (item / w.tiles_x) % w.tiles_y;
+    const int zc = item / (w.tiles_x * w.tiles_y);
+    const int x0 = tx * FT_X, y0 = ty * FT_Y;
+    const int z0 = zc * w.zchunk;
+    const int z1 = min(a.g.nz, z0 + w.zchunk);
+    const size_t np = (size_t)a.g.np;
+    const unsigned nx = (unsigned)a.g.nx, nxy = (unsigned)a.g.nx * (unsigned)a.g.ny;
+
+    // in-plane offsets of the cells this thread stages (H2: tid, tid + NT; H1: the same)
+    // and of its own stress-update cells; -1 marks a cell outside a closed side
+    int off2[2], off1[2];
+#pragma unroll
+    for (int q = 0; q < 2; ++q) {
+        const int k2 = tid + q * NT;
+        off2[q] = -1;
+        if (k2 < NH2) {
+            const int xg = side_coord(x0 - 2 + k2 % H2X, a.g.nx, a.g.per[0]);
+            const int yg = side_coord(y0 - 2 + k2 / H2X, a.g.ny, a.g.per[1]);
+            if (xg >= 0 && yg >= 0) off2[q] = xg + (int)nx * yg;
+        }
+        const int k1 = tid + q * NT;
+        off1[q] = -1;
+        if (k1 < NH1) {
+            const int xg = side_coord(x0 - 1 + k1 % H1X, a.g.nx, a.g.per[0]);
+            const int yg = side_coord(y0 - 1 + k1 / H1X, a.g.ny, a.g.per[1]);
+            if (xg >= 0 && yg >= 0) off1[q] = xg + (int)nx * yg;
+        }
+    }
+
+    // stage tau^{t-1}, u^{t-1} (H2 region) and neighbour masks (H1 region) of plane zz
+    auto stage = [&](int zz) {
+        const int zg = side_coord(zz, a.g.nz, a.g.per[2]);
+        const int s3 = ring3(zz), s4 = ring4(zz);
+#pragma unroll
+        for (int q = 0; q < 2; ++q) {
+            const int k2 = tid + q * NT;
+            if (k2 < NH2) {
+                if (off2[q] < 0 || zg < 0) {
+#pragma unroll
+                    for (int c = 0; c < 6; ++c) sm.in_tau[s3][c][k2] = R(0);
+#pragma unroll
+                    for (int j = 0; j < 3; ++j) sm.in_u[s3][j][k2] = R(0);
+                } else {
+                    const unsigned r = (unsigned)off2[q] + nxy * (unsigned)zg;
+#pragma unroll
+                    for (int c = 0; c < 6; ++c) cp_async_real<R>(&sm.in_tau[s3][c][k2], a.tau + c * np + r);
+#pragma unroll
+                    for (int j = 0; j < 3; ++j) cp_async_real<R>(&sm.in_u[s3][j][k2], a.u_in + j * np + r);
+                }
+            }
+            const int k1 = tid + q * NT;
+            if (k1 < NH1) {
+                if (off1[q] < 0 || zg < 0)
+                    sm.mask[s4][k1] = 0xffffffffu;
+                else
+                    cp_async4(&sm.mask[s4][k1], a.mask + ((unsigned)off1[q] + nxy * (unsigned)zg));
+            }
+        }
+        cp_async_commit();
+    };
+
+    const int ti = tid % FT_X, tj = tid / FT_X;
+    const int x = x0 + ti, y = y0 + tj;
+    const int kc = (ti + 1) + (tj + 1) * H1X;  // the thread's own cell in H1 coordinates
+    const bool own_xy = x < a.g.nx && y < a.g.ny;
+
+#pragma unroll 1
+    for (int zz = z0 - 2; zz <= z0; ++zz) stage(zz);
+
+    // plane zf: stress update tau^t (H1 region), then stream-collide of plane zf - 1
+#pragma unroll 1
+    for (int zf = z0 - 1; zf <= z1; ++zf) {
+        cp_async_wait_all();
+        __syncthreads();
+        {
+            const int sc = ring3(zf), sd = ring3(zf - 1), su = ring3(zf + 1), s4 = ring4(zf);
+            const int zg = side_coord(zf, a.g.nz, a.g.per[2]);
+            const bool own_plane = zf >= z0 && zf < z1;
+#pragma unroll 1
+            for (int k = tid; k < NH1; k += NT) {
+                const int hi = k % H1X, hj = k / H1X;
+                const uint32_t m = sm.mask[s4][k];
+                R out[6];
+                if (m & 1u) {
+#pragma unroll
+                    for (int c = 0; c < 6; ++c) out[c] = R(0);
+                } else {
+                    const int c2 = (hi + 1) + (hj + 1) * H2X;
+                    R tr[6], ur[3];
+#pragma unroll
+                    for (int c = 0; c < 6; ++c) tr[c] = sm.in_tau[sc][c][c2];
+#pragma unroll
+                    for (int j = 0; j < 3; ++j) ur[j] = sm.in_u[sc][j][c2];
+                    const int xg = side_coord(x0 - 1 + hi, a.g.nx, a.g.per[0]);
+                    const int yg = side_coord(y0 - 1 + hj, a.g.ny, a.g.per[1]);
+                    const SmemNb<S> nb{sm, a, sc, sd, su, c2, xg, yg, zg};
+                    fv_core<R, SH>(a.ph, tr, ur, m, nb, out);
+                }
+#pragma unroll
+                for (int c = 0; c < 6; ++c) sm.tnew[sc][c][k] = out[c];
+                if (own_plane && hi >= 1 && hi <= FT_X && hj >= 1 && hj <= FT_Y) {
+                    const int xo = x0 + hi - 1, yo = y0 + hj - 1;
+                    if (xo < a.g.nx && yo < a.g.ny) {
+                        const unsigned r = (unsigned)xo + nx * (unsigned)yo + nxy * (unsigned)zf;
+#pragma unroll
+                        for (int c = 0; c < 6; ++c) a.tau_out[c * np + r] = out[c];
+                    }
+                }
+            }
+        }
+        __syncthreads();
+        if (zf + 2 <= z1 + 1) stage(zf + 2);
+        const int z = zf - 1;
+        if (z >= z0 && own_xy) {
+            const uint32_t m = sm.mask[ring4(z)][kc];
+            if (!(m & 1u)) {
+                const int sc = ring3(z), sd = ring3(z - 1), su = ring3(z + 1);
+                R tr[6];
+#pragma unroll
+                for (int c = 0; c < 6; ++c) tr[c] = sm.tnew[sc][c][kc];
+                auto tn = [&](int l, int c) -> R {
+                    const int slot = l == 4 ? su : (l == 5 ? sd : sc);
+                    const int cell = l == 0 ? kc + 1 : l == 1 ? kc - 1 : l == 2 ? kc + H1X : l == 3 ? kc - H1X : kc;
+                    return sm.tnew[slot][c][cell];
+                };
+                const Cell cl(a.g, x, y, z);
+                lb_core<S, PAR>(a, cl, cl.self(), m, tr, tn);
+            }
+        }
+    }
+    cp_async_wait_all();
 }
 
 // ---------------------------------------------------------------------------------
@@ -134,13 +452,13 @@ __device__ __forceinline__ void me_link(const KArgs<S> &a, long long code, doubl
     using R = typename Store<S>::R;
     constexpr bool SH = Store<S>::shifted;
     const int i = (int)(code & 31);
-    const long long r = code >> 5;
-    const int x = (int)(r % a.g.nx), y = (int)((r / a.g.nx) % a.g.ny), z = (int)(r / ((long long)a.g.nx * a.g.ny));
+    const unsigned r = (unsigned)(code >> 5);
+    const int x = (int)(r % a.g.nx), y = (int)((r / a.g.nx) % a.g.ny), z = (int)(r / ((unsigned)a.g.nx * a.g.ny));
     const Cell cl(a.g, x, y, z);
     R f[Q];
     load_pdfs<S, PAR>(a, cl, r, f);
     R Fp[3], F[3], u[3], rho, drho;
-    polymer_force<R>(a.g, cl, r, a.tau, a.flag, Fp);
+    polymer_force<R>(a.g, cl, r, a.mask[r], a.tau, Fp);
 #pragma unroll
     for (int k = 0; k < 3; ++k) F[k] = a.ph.g[k] + Fp[k];
     moments<R, SH>(f, F, a.ph.rho0, rho, drho, u);
@@ -396,7 +714,8 @@ __global__ void __launch_bounds__(256) k_particle_links(Geo g, const PartDev *__
 // the deleted / created momentum goes to the particle as an impulse at the cell.
 template <class S, int PAR>
 __global__ void __launch_bounds__(512) k_fill_drain(KArgs<S> a, PartDev *__restrict__ parts, int nparts,
-                                                    uint8_t *__restrict__ flag, typename Store<S>::R *__restrict__ tau,
+                                                    uint8_t *__restrict__ flag, uint32_t *__restrict__ mask,
+                                                    typename Store<S>::R *__restrict__ tau,
                                                     uint8_t *__restrict__ kind, uint8_t *__restrict__ nf_arr,
                                                     double *__restrict__ delta, double *__restrict__ diag) {
     using R = typename Store<S>::R;
@@ -495,7 +814,7 @@ __global__ void __launch_bounds__(512) k_fill_drain(KArgs<S> a, PartDev *__restr
             for (long long k = 0; k < nc; ++k) {
                 if (kind[k] != 2) continue;
                 int x, y, z;
-                const long long r = bbox_cell(a.g, b, k, x, y, z);
+                const unsigned r = (unsigned)bbox_cell(a.g, b, k, x, y, z);
                 const Cell cl(a.g, x, y, z);
                 R f[Q];
                 load_pdfs<S, PAR>(a, cl, r, f);
@@ -530,7 +849,7 @@ __global__ void __launch_bounds__(512) k_fill_drain(KArgs<S> a, PartDev *__restr
                     if (!a.g.per[2] && (z + cz(i) < 0 || z + cz(i) >= a.g.nz)) continue;
                     const int xq = cl.X(cx(i)), yq = cl.Y(cy(i)), zq = cl.Z(cz(i));
                     if (kind_of(b, xq, yq, zq) != 1) continue;
-                    const long long nb = (long long)xq + (long long)a.g.nx * (yq + (long long)a.g.ny * zq);
+                    const unsigned nb = (unsigned)xq + (unsigned)a.g.nx * ((unsigned)yq + (unsigned)a.g.ny * (unsigned)zq);
                     const Cell cn(a.g, xq, yq, zq);
                     R fn[Q];
                     load_pdfs<S, PAR>(a, cn, nb, fn);
@@ -592,6 +911,12 @@ __global__ void __launch_bounds__(512) k_fill_drain(KArgs<S> a, PartDev *__restr
             }
         }
         __syncthreads();
+        // F: neighbour masks of every cell in the box (covers all cells whose masks change)
+        for (long long k = threadIdx.x; k < nc; k += blockDim.x) {
+            int x, y, z;
+            const long long r = bbox_cell(a.g, b, k, x, y, z);
+            mask[r] = cell_mask(a.g, flag, x, y, z);
+        }
         if (threadIdx.x == 0) {
             for (int c3 = 0; c3 < 3; ++c3) {
                 P.v[c3] += P.dP[c3] / P.m;
@@ -648,8 +973,8 @@ __global__ void k_read(KArgs<S> a, double *__restrict__ rho_out, double *__restr
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
     if (x >= a.g.nx) return;
     const Cell cl(a.g, x, blockIdx.y, blockIdx.z + z0);
-    const long long r = cl.self();
-    const long long k = r - (long long)z0 * a.g.nx * a.g.ny;
+    const unsigned r = cl.self();
+    const long long k = (long long)r - (long long)z0 * a.g.nx * a.g.ny;
     if (a.flag[r] != FLAG_FLUID) {
         if (rho_out) rho_out[k] = 0.0;
         for (int j = 0; j < 3; ++j)
@@ -661,7 +986,7 @@ __global__ void k_read(KArgs<S> a, double *__restrict__ rho_out, double *__restr
     R f[Q];
     load_pdfs<S, PAR>(a, cl, r, f);
     R Fp[3], F[3], u[3], rho, drho;
-    polymer_force<R>(a.g, cl, r, a.tau, a.flag, Fp);
+    polymer_force<R>(a.g, cl, r, a.mask[r], a.tau, Fp);
 #pragma unroll
     for (int j = 0; j < 3; ++j) F[j] = a.ph.g[j] + Fp[j];
     moments<R, SH>(f, F, a.ph.rho0, rho, drho, u);
@@ -678,7 +1003,7 @@ __global__ void k_pdfs_io(KArgs<S> a, double *__restrict__ io, int write) {
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
     if (x >= a.g.nx) return;
     const Cell cl(a.g, x, blockIdx.y, blockIdx.z);
-    const long long r = cl.self();
+    const unsigned r = cl.self();
     const long long np = a.g.np, n = a.g.n;
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
@@ -699,8 +1024,8 @@ __global__ void k_probe(KArgs<S> a, const long long *__restrict__ cells, int cou
     constexpr bool SH = Store<S>::shifted;
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= count) return;
-    const long long r = cells[k];
-    const int x = (int)(r % a.g.nx), y = (int)((r / a.g.nx) % a.g.ny), z = (int)(r / ((long long)a.g.nx * a.g.ny));
+    const unsigned r = (unsigned)cells[k];
+    const int x = (int)(r % a.g.nx), y = (int)((r / a.g.nx) % a.g.ny), z = (int)(r / ((unsigned)a.g.nx * a.g.ny));
     const Cell cl(a.g, x, y, z);
     R f[Q];
     load_pdfs<S, PAR>(a, cl, r, f);
@@ -709,7 +1034,7 @@ __global__ void k_probe(KArgs<S> a, const long long *__restrict__ cells, int cou
     for (int j = 19; j < 29; ++j) o[j] = 0.0;
     if (a.flag[r] != FLAG_FLUID) return;
     R Fp[3], F[3], u[3], rho, drho;
-    polymer_force<R>(a.g, cl, r, a.tau, a.flag, Fp);
+    polymer_force<R>(a.g, cl, r, a.mask[r], a.tau, Fp);
     for (int j = 0; j < 3; ++j) F[j] = a.ph.g[j] + Fp[j];
     moments<R, SH>(f, F, a.ph.rho0, rho, drho, u);
     o[19] = SH ? (double)a.ph.rho0 + (double)drho : (double)rho;
@@ -724,7 +1049,7 @@ __global__ void __launch_bounds__(256) k_reduce(KArgs<S> a, double *__restrict__
     double v[6] = {0, 0, 0, 0, 0, 0};
     if (x < a.g.nx) {
         const Cell cl(a.g, x, blockIdx.y, blockIdx.z);
-        const long long r = cl.self();
+        const unsigned r = cl.self();
         if (a.flag[r] == FLAG_FLUID) {
             typename Store<S>::R f[Q];
             load_pdfs<S, PAR>(a, cl, r, f);

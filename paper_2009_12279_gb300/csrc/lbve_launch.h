@@ -52,7 +52,9 @@ struct DevState {
     Phys<double> ph;  // converted to the kernel's real type by the launchers
     void *f;          // 19 * np PDF storage elements
     void *tau[2];     // 6 * np reals each (ping-pong)
-    void *u;          // 3 * np reals
+    void *u[2];       // 3 * np reals each (velocity of the last stream-collide, ping-pong)
+    int ucur;         // index of the velocity written by the last stream-collide
+    uint32_t *mask;   // np neighbour masks
     uint8_t *flag;    // np bytes
     PartDev *parts;   // MAX_PART entries
     int cur;          // index of tau^t in tau[]
@@ -69,7 +71,7 @@ struct KernelTable {
     cudaError_t (*fv)(const DevState &, cudaStream_t);
     cudaError_t (*momentum_exchange)(const DevState &, int parity, const long long *links, const int *seg_begin,
                                      const int *seg_count, int nseg, int max_len, double *contrib, cudaStream_t);
-    cudaError_t (*voxelise)(const DevState &, int p, cudaStream_t);
+    cudaError_t (*voxelise)(const DevState &, int p, const PartDev &host, cudaStream_t);
     cudaError_t (*particle_update)(const DevState &, int nparts, cudaStream_t);
     cudaError_t (*particle_links)(const DevState &, int nparts, long long *links, const int *seg_begin, int *seg_count,
                                   int first_seg, const int *capacity, cudaStream_t);
@@ -80,6 +82,8 @@ struct KernelTable {
     cudaError_t (*pdfs_io)(const DevState &, int parity, double *io, int write, cudaStream_t);
     cudaError_t (*reduce)(const DevState &, int parity, double *partial, long long *nblocks, cudaStream_t);
     cudaError_t (*probe)(const DevState &, int parity, const long long *cells, int count, double *out, cudaStream_t);
+    cudaError_t (*build_mask)(const DevState &, int lx, int ly, int lz, int ex, int ey, int ez, cudaStream_t);
+    cudaError_t (*fused)(const DevState &, int parity, int zchunk, cudaStream_t);
 };
 
 // Bounding-box side used to size the per-particle scratch (cells within R + margin).

@@ -20,8 +20,10 @@ namespace {
 // Largest grid (cells) the static scratch serves: 3 velocity components of up to 8 bytes.
 constexpr long long kNoallocMaxCells = LBVE_NOALLOC_MAX_CELLS;
 
-// The velocity scratch.  Every GPU that loads the library holds it until exit.
+// The velocity scratch and the neighbour masks derived from the caller's flags.  Every
+// GPU that loads the library holds them until exit.
 static __device__ __align__(256) double g_noalloc_u[3 * kNoallocMaxCells];
+static __device__ __align__(256) uint32_t g_noalloc_mask[kNoallocMaxCells];
 // Zero-valued particle table: a particle flag in the caller's field then acts as a
 // resting wall instead of dereferencing a missing table.
 static __device__ __align__(256) PartDev g_noalloc_parts[MAX_PART];
@@ -30,6 +32,7 @@ constexpr int kMaxDevices = 128;
 std::mutex g_mu;
 void *g_u_addr[kMaxDevices] = {nullptr};
 void *g_parts_addr[kMaxDevices] = {nullptr};
+void *g_mask_addr[kMaxDevices] = {nullptr};
 thread_local std::string g_err;
 
 lbve_status fail(lbve_status s, const std::string &m) {
@@ -71,7 +74,7 @@ lbve_status lbve_step_noalloc(const lbve_params *p, void *f, void *tau_a, void *
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return fail(LBVE_ECUDA, std::string("cudaGetDevice: ") + cudaGetErrorString(e));
     if (dev < 0 || dev >= kMaxDevices) return fail(LBVE_EINVAL, "device index out of range");
-    void *u_scratch, *parts;
+    void *u_scratch, *parts, *mask;
     {
         // once per device, with that device current: the device address of the arrays
         std::lock_guard<std::mutex> lk(g_mu);
@@ -81,11 +84,16 @@ lbve_status lbve_step_noalloc(const lbve_params *p, void *f, void *tau_a, void *
             if (e != cudaSuccess) return fail(LBVE_ECUDA, std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e));
             e = cudaGetSymbolAddress(&b, g_noalloc_parts);
             if (e != cudaSuccess) return fail(LBVE_ECUDA, std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e));
+            void *m = nullptr;
+            e = cudaGetSymbolAddress(&m, g_noalloc_mask);
+            if (e != cudaSuccess) return fail(LBVE_ECUDA, std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e));
             g_parts_addr[dev] = b;
+            g_mask_addr[dev] = m;
             g_u_addr[dev] = a;
         }
         u_scratch = g_u_addr[dev];
         parts = g_parts_addr[dev];
+        mask = g_mask_addr[dev];
     }
     DevState d;
     d.g.nx = p->nx;
@@ -100,13 +108,17 @@ lbve_status lbve_step_noalloc(const lbve_params *p, void *f, void *tau_a, void *
     d.f = f;
     d.tau[0] = tau_a;
     d.tau[1] = tau_b;
-    d.u = u_scratch;  // fully written by the stream-collide kernel before the stress kernel reads it
+    d.u[0] = d.u[1] = u_scratch;  // fully written by the stream-collide kernel before the stress kernel reads it
+    d.ucur = 0;
+    d.mask = (uint32_t *)mask;     // rebuilt from the caller's flags below, before any step kernel
     d.flag = const_cast<uint8_t *>(flags);
     d.parts = (PartDev *)parts;
     d.cur = 0;
     d.block_x = default_block_x(*p);
     const KernelTable *kt = table_for(p->pdf_prec);
     cudaStream_t s = (cudaStream_t)cuda_stream;
+    e = kt->build_mask(d, 0, 0, 0, p->nx, p->ny, p->nz, s);
+    if (e != cudaSuccess) return fail(LBVE_ECUDA, std::string("mask kernel: ") + cudaGetErrorString(e));
     for (int k = 0; k < nsteps; ++k) {
         const int parity = (int)((t0 + k) & 1);
         e = kt->lb(d, parity, s);

@@ -2,6 +2,8 @@
 // collected in a KernelTable.  Included once per storage type by the precision TUs.
 #pragma once
 
+#include <algorithm>
+
 #include "lbve_kernels.cuh"
 
 namespace lbve {
@@ -31,15 +33,19 @@ template <class S>
 struct Launch {
     using R = typename Store<S>::R;
 
-    static KArgs<S> args(const DevState &d) {
+    // split schedule: the stream-collide writes u[ucur] and the stress update reads it;
+    // fused schedule: the stress update reads u[ucur], the stream-collide writes u[ucur^1].
+    static KArgs<S> args(const DevState &d, bool fused = false) {
         KArgs<S> a;
         a.g = d.g;
         a.ph = convert_phys<R>(d.ph);
         a.f = (S *)d.f;
         a.tau = (const R *)d.tau[d.cur];
         a.tau_out = (R *)d.tau[d.cur ^ 1];
-        a.u = (R *)d.u;
+        a.u_in = (const R *)d.u[d.ucur];
+        a.u_out = (R *)d.u[fused ? d.ucur ^ 1 : d.ucur];
         a.flag = d.flag;
+        a.mask = d.mask;
         a.parts = d.parts;
         return a;
     }
@@ -77,10 +83,14 @@ struct Launch {
             k_momentum_exchange<S, 1><<<g, 128, 0, s>>>(a, links, seg_begin, seg_count, contrib);
         return cudaGetLastError();
     }
-    static cudaError_t voxelise(const DevState &d, int p, cudaStream_t s) {
+    static cudaError_t build_mask(const DevState &d, int lx, int ly, int lz, int ex, int ey, int ez, cudaStream_t s);
+    static cudaError_t voxelise(const DevState &d, int p, const PartDev &host, cudaStream_t s) {
         KArgs<S> a = args(d);
         k_voxelise<S><<<64, 256, 0, s>>>(a, d.parts, p, d.flag, (R *)d.tau[0], (R *)d.tau[1]);
-        return cudaGetLastError();
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+        const BBox b = particle_bbox(d.g, host.X, host.R, 3);
+        return build_mask(d, b.lo[0], b.lo[1], b.lo[2], b.ext[0], b.ext[1], b.ext[2], s);
     }
     static cudaError_t particle_update(const DevState &d, int nparts, cudaStream_t s) {
         if (nparts <= 0) return cudaSuccess;
@@ -100,9 +110,39 @@ struct Launch {
         KArgs<S> a = args(d);
         R *tau = (R *)d.tau[d.cur];
         if (parity == 0)
-            k_fill_drain<S, 0><<<1, 512, 0, s>>>(a, d.parts, nparts, d.flag, tau, kind, nf, delta, diag);
+            k_fill_drain<S, 0><<<1, 512, 0, s>>>(a, d.parts, nparts, d.flag, d.mask, tau, kind, nf, delta, diag);
         else
-            k_fill_drain<S, 1><<<1, 512, 0, s>>>(a, d.parts, nparts, d.flag, tau, kind, nf, delta, diag);
+            k_fill_drain<S, 1><<<1, 512, 0, s>>>(a, d.parts, nparts, d.flag, d.mask, tau, kind, nf, delta, diag);
+        return cudaGetLastError();
+    }
+    static cudaError_t build_mask_impl(const DevState &d, int lx, int ly, int lz, int ex, int ey, int ez,
+                                       cudaStream_t s) {
+        const long long cells = (long long)ex * ey * ez;
+        if (cells <= 0) return cudaSuccess;
+        const unsigned nb = (unsigned)std::min<long long>((cells + 255) / 256, 65535);
+        k_build_mask<S><<<nb, 256, 0, s>>>(d.g, d.flag, d.mask, lx, ly, lz, ex, ey, ez);
+        return cudaGetLastError();
+    }
+    static cudaError_t fused(const DevState &d, int parity, int zchunk, cudaStream_t s) {
+        KArgs<S> a = args(d, true);
+        FusedWork w;
+        w.tiles_x = (d.g.nx + FT_X - 1) / FT_X;
+        w.tiles_y = (d.g.ny + FT_Y - 1) / FT_Y;
+        w.zchunk = zchunk;
+        w.nzchunks = (d.g.nz + zchunk - 1) / zchunk;
+        const size_t sm = sizeof(FusedSmem<R>);
+        static bool configured[2] = {false, false};
+        if (!configured[parity]) {
+            cudaError_t e = parity == 0 ? cudaFuncSetAttribute(k_fused<S, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm)
+                                        : cudaFuncSetAttribute(k_fused<S, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+            if (e != cudaSuccess) return e;
+            configured[parity] = true;
+        }
+        const unsigned nblk = (unsigned)w.tiles_x * w.tiles_y * w.nzchunks;
+        if (parity == 0)
+            k_fused<S, 0><<<nblk, FT_X * FT_Y, sm, s>>>(a, w);
+        else
+            k_fused<S, 1><<<nblk, FT_X * FT_Y, sm, s>>>(a, w);
         return cudaGetLastError();
     }
     static cudaError_t read(const DevState &d, int parity, double *rho, double *u, double *tau, int z0, int z1,
@@ -151,13 +191,22 @@ struct Launch {
         return cudaGetLastError();
     }
 
-    static const KernelTable *table(int prec) {
+    static const KernelTable *table(int prec);
+};
+
+template <class S>
+cudaError_t Launch<S>::build_mask(const DevState &d, int lx, int ly, int lz, int ex, int ey, int ez, cudaStream_t s) {
+    return build_mask_impl(d, lx, ly, lz, ex, ey, ez, s);
+}
+
+template <class S>
+const KernelTable *Launch<S>::table(int prec) {
         static const KernelTable t = {prec,           sizeof(S),        sizeof(R),   &init,
                                       &lb,            &fv,              &momentum_exchange, &voxelise,
                                       &particle_update, &particle_links, &fill_drain, &read,
-                                      &pdfs_io,       &reduce,          &probe};
+                                      &pdfs_io,       &reduce,          &probe,      &build_mask,
+                                      &fused};
         return &t;
-    }
-};
+}
 
 } // namespace lbve

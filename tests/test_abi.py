@@ -53,7 +53,9 @@ def test_default_params_and_memory_estimate(lib):
     p16 = lbve.make_params((512, 512, 512), precision="f16")
     b32, b16 = lbve.device_bytes(p32), lbve.device_bytes(p16)
     n = 512 ** 3
-    assert 19 * 4 * n + 15 * 4 * n <= b32 <= 19 * 4 * n + 15 * 4 * n + n + 10 ** 7
+    # PDFs + stress ping-pong + velocity ping-pong + flags + neighbour masks
+    per_cell = 19 * 4 + 12 * 4 + 6 * 4 + 1 + 4
+    assert per_cell * n <= b32 <= per_cell * n + 10 ** 7
     assert b16 < b32
 
 
