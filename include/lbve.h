@@ -88,7 +88,8 @@ typedef struct {
     int pdf_scale_log2;  /* storage scale 2^k of the shifted PDFs; -1 selects the default */
     int fv_terms;        /* LBVE_FV_* bits; 0 selects both */
     int schedule;        /* LBVE_SCHED_* */
-    int block_x;         /* threads per block along x; 0 selects the tuned default */
+    int block_x;         /* per-cell kernels: threads per block along x (32, 64 or 128; blocks
+                            hold 128 threads); 0 selects the default */
 } lbve_params;
 
 /* Optional device allocator (e.g. a framework's caching allocator).  alloc returns a

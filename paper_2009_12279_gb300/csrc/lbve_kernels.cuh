@@ -15,6 +15,13 @@
 
 namespace lbve {
 
+// 128-thread stream-collide blocks, at least 8 resident per SM (64 registers per thread):
+// without the cap the odd-parity kernel keeps all 37 neighbour addresses live and
+// drops to ~10 % occupancy.
+#ifndef LBVE_LB_MIN_BLOCKS
+#define LBVE_LB_MIN_BLOCKS 8
+#endif
+
 template <class S>
 struct KArgs {
     using R = typename Store<S>::R;
@@ -144,12 +151,20 @@ struct NbAdapter {  // gives GlobalNb the u / tau / ub interface fv_core expects
     __device__ __forceinline__ void ub(int l, R out[3]) const { n.ub_(l, out); }
 };
 
+// Launch shape of the per-cell kernels: blockDim (bx, by), grid (nx/bx, ny/by, nz).
+__device__ __forceinline__ bool cell_of_thread(const Geo &g, int &x, int &y, int &z) {
+    x = blockIdx.x * blockDim.x + threadIdx.x;
+    y = blockIdx.y * blockDim.y + threadIdx.y;
+    z = blockIdx.z;
+    return x < g.nx && y < g.ny;
+}
+
 template <class S, int PAR>
-__global__ void __launch_bounds__(256) k_lb(KArgs<S> a) {
+__global__ void __launch_bounds__(128, LBVE_LB_MIN_BLOCKS) k_lb(KArgs<S> a) {
     using R = typename Store<S>::R;
-    const int x = blockIdx.x * blockDim.x + threadIdx.x;
-    if (x >= a.g.nx) return;
-    const Cell cl(a.g, x, blockIdx.y, blockIdx.z);
+    int x, y, z;
+    if (!cell_of_thread(a.g, x, y, z)) return;
+    const Cell cl(a.g, x, y, z);
     const unsigned r = cl.self();
     const uint32_t m = a.mask[r];
     if (m & 1u) return;
@@ -165,12 +180,12 @@ __global__ void __launch_bounds__(256) k_lb(KArgs<S> a) {
 }
 
 template <class S>
-__global__ void __launch_bounds__(256) k_fv(KArgs<S> a) {
+__global__ void __launch_bounds__(128) k_fv(KArgs<S> a) {
     using R = typename Store<S>::R;
     constexpr bool SH = Store<S>::shifted;
-    const int x = blockIdx.x * blockDim.x + threadIdx.x;
-    if (x >= a.g.nx) return;
-    const Cell cl(a.g, x, blockIdx.y, blockIdx.z);
+    int x, y, z;
+    if (!cell_of_thread(a.g, x, y, z)) return;
+    const Cell cl(a.g, x, y, z);
     const unsigned r = cl.self();
     const size_t np = (size_t)a.g.np;
     const uint32_t m = a.mask[r];
@@ -436,6 +451,133 @@ __global__ void __launch_bounds__(FT_X * FT_Y, sizeof(typename Store<S>::R) == 8
                 lb_core<S, PAR>(a, cl, cl.self(), m, tr, tn);
             }
         }
+    }
+    cp_async_wait_all();
+}
+
+// ---------------------------------------------------------------------------------
+// stress update, z-marching: a block owns a 32 x 8 column of cells and walks a chunk of
+// z-planes; tau^t and u^t of the planes z-1 .. z+2 (with a one-cell x-y halo) sit in a
+// four-plane shared-memory ring filled with cp.async one plane ahead, so every stencil
+// read of the update comes from shared memory.
+// ---------------------------------------------------------------------------------
+constexpr int FV_X = 32, FV_Y = 8;
+constexpr int FVH_X = FV_X + 2, FVH_Y = FV_Y + 2, FVH_N = FVH_X * FVH_Y;
+
+template <class R>
+struct FvSmem {
+    R tau[4][6][FVH_N];
+    R u[4][3][FVH_N];
+};
+
+template <class S>
+struct FvSmemNb {
+    using R = typename Store<S>::R;
+    const FvSmem<R> &sm;
+    const KArgs<S> &a;
+    int sc, sd, su, c, xg, yg, zg;
+    __device__ __forceinline__ int slot(int l) const { return l == 4 ? su : (l == 5 ? sd : sc); }
+    __device__ __forceinline__ int cell(int l) const {
+        return l == 0 ? c + 1 : l == 1 ? c - 1 : l == 2 ? c + FVH_X : l == 3 ? c - FVH_X : c;
+    }
+    __device__ __forceinline__ R u(int l, int j) const { return sm.u[slot(l)][j][cell(l)]; }
+    __device__ __forceinline__ R tau(int l, int cc) const { return sm.tau[slot(l)][cc][cell(l)]; }
+    __device__ __forceinline__ void ub(int l, R o[3]) const {
+        const int k = l >> 1, s = (l & 1) ? -1 : 1;
+        int xq = xg + (k == 0 ? s : 0), yq = yg + (k == 1 ? s : 0), zq = zg + (k == 2 ? s : 0);
+        xq = xq < 0 ? xq + a.g.nx : (xq >= a.g.nx ? xq - a.g.nx : xq);
+        yq = yq < 0 ? yq + a.g.ny : (yq >= a.g.ny ? yq - a.g.ny : yq);
+        zq = zq < 0 ? zq + a.g.nz : (zq >= a.g.nz ? zq - a.g.nz : zq);
+        const int fl = a.flag[(unsigned)xq + (unsigned)a.g.nx * ((unsigned)yq + (unsigned)a.g.ny * (unsigned)zq)];
+        boundary_velocity_fast<R>(a.g, a.ph, a.parts, fl, xq, yq, zq, o);
+    }
+};
+
+template <class S>
+__global__ void __launch_bounds__(FV_X * FV_Y, sizeof(typename Store<S>::R) == 8 ? 2 : 4) k_fv_tiled(KArgs<S> a, int zchunk) {
+    using R = typename Store<S>::R;
+    constexpr bool SH = Store<S>::shifted;
+    constexpr int NT = FV_X * FV_Y;
+    extern __shared__ __align__(16) unsigned char fv_smem_raw[];
+    FvSmem<R> &sm = *reinterpret_cast<FvSmem<R> *>(fv_smem_raw);
+    const int tid = threadIdx.x;
+    const int tiles_x = (a.g.nx + FV_X - 1) / FV_X, tiles_y = (a.g.ny + FV_Y - 1) / FV_Y;
+    const int item = blockIdx.x;
+    const int tx = item % tiles_x, ty = (item / tiles_x) % tiles_y, zc = item / (tiles_x * tiles_y);
+    const int x0 = tx * FV_X, y0 = ty * FV_Y;
+    const int z0 = zc * zchunk, z1 = min(a.g.nz, z0 + zchunk);
+    const size_t np = (size_t)a.g.np;
+    const unsigned nx = (unsigned)a.g.nx, nxy = (unsigned)a.g.nx * (unsigned)a.g.ny;
+    int off[2];
+#pragma unroll
+    for (int q = 0; q < 2; ++q) {
+        const int k = tid + q * NT;
+        off[q] = -1;
+        if (k < FVH_N) {
+            const int xg = side_coord(x0 - 1 + k % FVH_X, a.g.nx, a.g.per[0]);
+            const int yg = side_coord(y0 - 1 + k / FVH_X, a.g.ny, a.g.per[1]);
+            if (xg >= 0 && yg >= 0) off[q] = xg + (int)nx * yg;
+        }
+    }
+    auto stage = [&](int zz) {
+        const int zg = side_coord(zz, a.g.nz, a.g.per[2]);
+        const int s4 = ring4(zz);
+#pragma unroll
+        for (int q = 0; q < 2; ++q) {
+            const int k = tid + q * NT;
+            if (k >= FVH_N) continue;
+            if (off[q] < 0 || zg < 0) {
+#pragma unroll
+                for (int c = 0; c < 6; ++c) sm.tau[s4][c][k] = R(0);
+#pragma unroll
+                for (int j = 0; j < 3; ++j) sm.u[s4][j][k] = R(0);
+            } else {
+                const unsigned r = (unsigned)off[q] + nxy * (unsigned)zg;
+#pragma unroll
+                for (int c = 0; c < 6; ++c) cp_async_real<R>(&sm.tau[s4][c][k], a.tau + c * np + r);
+#pragma unroll
+                for (int j = 0; j < 3; ++j) cp_async_real<R>(&sm.u[s4][j][k], a.u_in + j * np + r);
+            }
+        }
+        cp_async_commit();
+    };
+    const int ti = tid % FV_X, tj = tid / FV_X;
+    const int x = x0 + ti, y = y0 + tj;
+    const int kc = (ti + 1) + (tj + 1) * FVH_X;
+    const bool own = x < a.g.nx && y < a.g.ny;
+    stage(z0 - 1);
+    stage(z0);
+    stage(z0 + 1);
+#pragma unroll 1
+    for (int z = z0; z < z1; ++z) {
+        // plane z + 2 is fetched while plane z is updated (an empty group keeps the count)
+        if (z + 2 <= z1)
+            stage(z + 2);
+        else
+            cp_async_commit();
+        asm volatile("cp.async.wait_group 1;\n" ::: "memory");
+        __syncthreads();
+        if (own) {
+            const unsigned r = (unsigned)x + nx * (unsigned)y + nxy * (unsigned)z;
+            const uint32_t m = a.mask[r];
+            R out[6];
+            if (m & 1u) {
+#pragma unroll
+                for (int c = 0; c < 6; ++c) out[c] = R(0);
+            } else {
+                const int sc = ring4(z), sd = ring4(z - 1), su = ring4(z + 1);
+                R tr[6], ur[3];
+#pragma unroll
+                for (int c = 0; c < 6; ++c) tr[c] = sm.tau[sc][c][kc];
+#pragma unroll
+                for (int j = 0; j < 3; ++j) ur[j] = sm.u[sc][j][kc];
+                const FvSmemNb<S> nb{sm, a, sc, sd, su, kc, x, y, z};
+                fv_core<R, SH>(a.ph, tr, ur, m, nb, out);
+            }
+#pragma unroll
+            for (int c = 0; c < 6; ++c) a.tau_out[c * np + r] = out[c];
+        }
+        __syncthreads();  // the next stage overwrites the slot of plane z - 1
     }
     cp_async_wait_all();
 }

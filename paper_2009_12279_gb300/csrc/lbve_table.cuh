@@ -49,6 +49,12 @@ struct Launch {
         a.parts = d.parts;
         return a;
     }
+    // per-cell kernels: blocks of block_x x (128 / block_x) threads
+    static dim3 block2(const DevState &d) { return dim3((unsigned)d.block_x, (unsigned)(128 / d.block_x)); }
+    static dim3 grid2(const DevState &d) {
+        const dim3 b = block2(d);
+        return dim3((unsigned)((d.g.nx + b.x - 1) / b.x), (unsigned)((d.g.ny + b.y - 1) / b.y), (unsigned)d.g.nz);
+    }
     static dim3 grid3(const DevState &d) { return dim3((unsigned)((d.g.nx + d.block_x - 1) / d.block_x), d.g.ny, d.g.nz); }
 
     static cudaError_t init(const DevState &d, const double *rho, const double *u, const double *tau, long long r0,
@@ -62,14 +68,36 @@ struct Launch {
     static cudaError_t lb(const DevState &d, int parity, cudaStream_t s) {
         KArgs<S> a = args(d);
         if (parity == 0)
-            k_lb<S, 0><<<grid3(d), d.block_x, 0, s>>>(a);
+            k_lb<S, 0><<<grid2(d), block2(d), 0, s>>>(a);
         else
-            k_lb<S, 1><<<grid3(d), d.block_x, 0, s>>>(a);
+            k_lb<S, 1><<<grid2(d), block2(d), 0, s>>>(a);
         return cudaGetLastError();
+    }
+    // z-planes per block of the z-marching stress update (enough blocks for ~16 waves)
+    static int fv_zchunk(const DevState &d) {
+        const long long tiles = (long long)((d.g.nx + FV_X - 1) / FV_X) * ((d.g.ny + FV_Y - 1) / FV_Y);
+        int dev = 0, sms = 148;
+        if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        const long long want = 16LL * 4 * sms;
+        const long long chunks = (want + tiles - 1) / tiles;
+        long long zc = (d.g.nz + chunks - 1) / chunks;
+        if (zc < 16) zc = 16;
+        if (zc > d.g.nz) zc = d.g.nz;
+        return (int)zc;
     }
     static cudaError_t fv(const DevState &d, cudaStream_t s) {
         KArgs<S> a = args(d);
-        k_fv<S><<<grid3(d), d.block_x, 0, s>>>(a);
+        const int zc = fv_zchunk(d);
+        const int tiles = ((d.g.nx + FV_X - 1) / FV_X) * ((d.g.ny + FV_Y - 1) / FV_Y);
+        const unsigned nblk = (unsigned)(tiles * ((d.g.nz + zc - 1) / zc));
+        const size_t sm = sizeof(FvSmem<R>);
+        static bool configured = false;
+        if (!configured) {
+            cudaError_t e = cudaFuncSetAttribute(k_fv_tiled<S>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+            if (e != cudaSuccess) return e;
+            configured = true;
+        }
+        k_fv_tiled<S><<<nblk, FV_X * FV_Y, sm, s>>>(a, zc);
         return cudaGetLastError();
     }
     static cudaError_t momentum_exchange(const DevState &d, int parity, const long long *links, const int *seg_begin,
