@@ -240,6 +240,44 @@ lbve_status lbve_step_noalloc(const lbve_params *p, void *f, void *tau_a, void *
                               const double *wall_vel, int n_wall, long long t0, int nsteps, void *cuda_stream);
 const char *lbve_noalloc_last_error(void);
 
+/*
+ * Residual of a solve (steady-state test): out[0] = |u - u_prev| / |u| (L2 over fluid
+ * cells, FP64 with a fixed-shape reduction, so the value does not depend on what else
+ * runs), where u is the velocity of the last completed step and u_prev the one seen by
+ * the previous call (zero at the first call); out[1] = |u|.  The first call allocates
+ * the snapshot buffer.  Synchronises the stream.
+ */
+lbve_status lbve_residual(lbve_ctx *ctx, double out[2]);
+
+/*
+ * Pools: resident solves that advance together.  lbve_pool_step runs each time step as
+ * one persistent stream-collide kernel and one persistent stress kernel over a packed
+ * list of (solve, block) work items, plus the per-solve momentum-exchange and particle
+ * kernels; each cell is computed exactly as in lbve_step, so a solve's result does not
+ * depend on the other members.  Members must share the pool's PDF precision and stream.
+ * Admission is checked against the pool's device-memory budget (lbve_device_bytes of
+ * the member's parameters); the pool never owns or frees member contexts.
+ * With graphs enabled (default) the launch sequence of a step call is captured into a
+ * CUDA graph and replayed while the membership and step count are unchanged (not on
+ * the legacy default stream, which cannot be captured: there the kernels launch
+ * directly).
+ */
+typedef struct lbve_pool lbve_pool;
+lbve_status lbve_pool_create(int pdf_prec, size_t budget_bytes, void *cuda_stream, lbve_pool **out);
+lbve_status lbve_pool_destroy(lbve_pool *pool);
+/* 1 if a solve with these parameters fits the remaining budget, else 0. */
+int lbve_pool_fits(const lbve_pool *pool, const lbve_params *p);
+/* Errors: ENOMEM (over budget), ESTATE (precision or stream differ, already a member). */
+lbve_status lbve_pool_admit(lbve_pool *pool, lbve_ctx *ctx);
+lbve_status lbve_pool_remove(lbve_pool *pool, lbve_ctx *ctx);
+lbve_status lbve_pool_step(lbve_pool *pool, int nsteps);
+/* Residuals of all members in admission order: 2 doubles each as in lbve_residual. */
+lbve_status lbve_pool_residuals(lbve_pool *pool, double *out);
+int lbve_pool_size(const lbve_pool *pool);
+size_t lbve_pool_bytes_in_use(const lbve_pool *pool);
+lbve_status lbve_pool_set_graphs(lbve_pool *pool, int enable);
+const char *lbve_pool_last_error(const lbve_pool *pool);
+
 /* Steps done since the last lbve_init_fields. */
 long long lbve_time(const lbve_ctx *ctx);
 lbve_status lbve_synchronize(lbve_ctx *ctx);

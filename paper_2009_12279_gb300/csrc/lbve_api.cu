@@ -62,6 +62,10 @@ struct lbve_ctx {
     size_t ev_used = 0;
     double kt_ms[LBVE_KT_COUNT] = {0};
     long long kt_count[LBVE_KT_COUNT] = {0};
+    // steady-state residual
+    void *usnap = nullptr;
+    double *res_partial = nullptr;
+    lbve_pool *pool = nullptr;
 };
 
 namespace {
@@ -522,6 +526,7 @@ lbve_status lbve_create_with_allocator(const lbve_params *p, void *cuda_stream, 
 
 lbve_status lbve_destroy(lbve_ctx *c) {
     if (!c) return LBVE_EINVAL;
+    if (c->pool) lbve_pool_remove(c->pool, c);
     cudaStreamSynchronize(c->stream);
     for (auto &ev : c->ev_pool) {
         cudaEventDestroy(ev.first);
@@ -536,6 +541,7 @@ lbve_status lbve_set_geometry(lbve_ctx *c, const uint8_t *flags, const double *w
     if (!c) return LBVE_EINVAL;
     if (!flags) return fail(c, LBVE_EINVAL, "flags is NULL");
     if (c->nparts > 0) return fail(c, LBVE_ESTATE, "geometry must be set before particles are added");
+    if (c->pool) return fail(c, LBVE_ESTATE, "geometry cannot change while the solve is in a pool");
     if (n_wall < 0 || n_wall > MAX_WALL || (n_wall > 0 && !wall_vel))
         return fail(c, LBVE_EINVAL, "n_wall must be in [0, 16] with wall_vel given");
     const int nx = c->p.nx, ny = c->p.ny, nz = c->p.nz;
@@ -579,6 +585,7 @@ lbve_status lbve_set_geometry(lbve_ctx *c, const uint8_t *flags, const double *w
 
 lbve_status lbve_init_fields(lbve_ctx *c, const double *rho, const double *u, const double *tau) {
     if (!c) return LBVE_EINVAL;
+    if (c->pool) return fail(c, LBVE_ESTATE, "fields cannot be reset while the solve is in a pool");
     const long long n = c->d.g.n, plane = (long long)c->p.nx * c->p.ny;
     const int zs = slab_planes(c);
     const long long cap = plane * zs;
@@ -608,6 +615,7 @@ lbve_status lbve_init_fields(lbve_ctx *c, const double *rho, const double *u, co
 
 lbve_status lbve_init_fields_device(lbve_ctx *c, const double *rho, const double *u, const double *tau) {
     if (!c) return LBVE_EINVAL;
+    if (c->pool) return fail(c, LBVE_ESTATE, "fields cannot be reset while the solve is in a pool");
     c->d.cur = 0;
     CK(c->kt->init(c->d, rho, u, tau, 0, c->d.g.n, c->d.g.n, c->stream), "init kernel");
     c->t = 0;
@@ -642,6 +650,7 @@ lbve_status lbve_add_particle(lbve_ctx *c, const double X[3], double R, double r
     if (!X) return fail(c, LBVE_EINVAL, "X is NULL");
     if (!(R > 0.0) || !(rho_p > 0.0)) return fail(c, LBVE_EINVAL, "radius and density must be > 0");
     if (c->nparts >= MAX_PART) return fail(c, LBVE_ESTATE, "too many particles");
+    if (c->pool) return fail(c, LBVE_ESTATE, "particles cannot be added while the solve is in a pool");
     const int nn[3] = {c->p.nx, c->p.ny, c->p.nz};
     for (int a = 0; a < 3; ++a) {
         if (!std::isfinite(X[a])) return fail(c, LBVE_EINVAL, "X must be finite");
@@ -717,6 +726,7 @@ bool use_fused(const lbve_ctx *c, int nsteps) {
 lbve_status lbve_step(lbve_ctx *c, int nsteps) {
     if (!c) return LBVE_EINVAL;
     if (nsteps < 0) return fail(c, LBVE_EINVAL, "nsteps must be >= 0");
+    if (c->pool) return fail(c, LBVE_ESTATE, "a pool member advances through lbve_pool_step");
     if (use_fused(c, nsteps)) {
         // stream-collide of the first step, fused (stress of step t-1 + stream-collide of
         // step t) for the others, stress update of the last step
@@ -905,6 +915,48 @@ lbve_status lbve_read_kernel_times(lbve_ctx *c, double ms[LBVE_KT_COUNT], long l
     return LBVE_OK;
 }
 
+// Fixed reduction shape of a solve's residual (depends only on its size).
+static int residual_blocks(const lbve_ctx *c) {
+    long long b = (c->d.g.n + 255) / 256;
+    return (int)(b > 1024 ? 1024 : (b < 1 ? 1 : b));
+}
+
+static lbve_status residual_enqueue(lbve_ctx *c) {
+    const int nb = residual_blocks(c);
+    if (!c->usnap) {
+        c->usnap = dev_alloc(c, (size_t)3 * c->d.g.np * c->kt->real_bytes);
+        c->res_partial = (double *)dev_alloc(c, sizeof(double) * 2 * 1024);
+        if (!c->usnap || !c->res_partial) return fail(c, LBVE_ENOMEM, "residual buffers");
+        CK(cudaMemsetAsync(c->usnap, 0, (size_t)3 * c->d.g.np * c->kt->real_bytes, c->stream), "residual clear");
+    }
+    CK(c->kt->residual(c->d, c->usnap, c->res_partial, nb, c->stream), "residual kernel");
+    return LBVE_OK;
+}
+
+static void residual_finish(const lbve_ctx *c, const double *partial, double out[2]) {
+    double d2 = 0.0, u2 = 0.0;
+    const int nb = residual_blocks(c);
+    for (int b = 0; b < nb; ++b) {
+        d2 += partial[2 * b];
+        u2 += partial[2 * b + 1];
+    }
+    out[1] = std::sqrt(u2);
+    out[0] = u2 > 0.0 ? std::sqrt(d2) / out[1] : (d2 > 0.0 ? INFINITY : 0.0);
+}
+
+lbve_status lbve_residual(lbve_ctx *c, double out[2]) {
+    if (!c || !out) return c ? fail(c, LBVE_EINVAL, "out is NULL") : LBVE_EINVAL;
+    lbve_status s = residual_enqueue(c);
+    if (s != LBVE_OK) return s;
+    std::vector<double> h(2 * 1024);
+    CK(cudaMemcpyAsync(h.data(), c->res_partial, sizeof(double) * 2 * residual_blocks(c), cudaMemcpyDeviceToHost,
+                       c->stream),
+       "residual copy");
+    CK(cudaStreamSynchronize(c->stream), "residual sync");
+    residual_finish(c, h.data(), out);
+    return LBVE_OK;
+}
+
 long long lbve_time(const lbve_ctx *c) { return c ? c->t : -1; }
 
 lbve_status lbve_synchronize(lbve_ctx *c) {
@@ -918,5 +970,266 @@ const char *lbve_last_error(const lbve_ctx *c) { return c ? c->err.c_str() : g_c
 const char *lbve_status_string(lbve_status s) {
     return (s >= 0 && s <= LBVE_ESTATE) ? kStatusNames[s] : "LBVE_UNKNOWN";
 }
+
+} // extern "C"
+
+// ---------------------------------------------------------------------------------
+// pools: resident solves stepped together by the batched persistent kernels
+// ---------------------------------------------------------------------------------
+struct lbve_pool {
+    int prec = 0;
+    size_t budget = 0, in_use = 0;
+    cudaStream_t stream = nullptr;
+    const KernelTable *kt = nullptr;
+    std::vector<lbve_ctx *> members;
+    std::vector<size_t> member_bytes;
+    std::string err;
+    // packed work list, built from the members' state when the membership changes; a step
+    // k after the build swaps the stress ping-pong and the AA parity k times
+    void *entries[2] = {nullptr, nullptr};
+    size_t entries_cap = 0;
+    int total_lb = 0, total_fv = 0;
+    int grid_lb = 0, grid_fv = 0;
+    bool dirty = true;
+    long long steps_since_build = 0;
+    // residual staging
+    double *res_dev = nullptr;
+    size_t res_cap = 0;
+    // CUDA graphs, one per call parity
+    bool use_graphs = true;
+    cudaGraphExec_t graph[2] = {nullptr, nullptr};
+    int graph_steps[2] = {0, 0};
+};
+
+namespace {
+
+lbve_status pfail(lbve_pool *P, lbve_status s, const std::string &m) {
+    if (P) P->err = m;
+    return s;
+}
+
+#define PCK(call, where)                                                                           \
+    do {                                                                                           \
+        cudaError_t e_ = (call);                                                                   \
+        if (e_ != cudaSuccess) return pfail(P, LBVE_ECUDA, std::string(where) + ": " + cudaGetErrorString(e_)); \
+    } while (0)
+
+void drop_graphs(lbve_pool *P) {
+    for (int k = 0; k < 2; ++k) {
+        if (P->graph[k]) cudaGraphExecDestroy(P->graph[k]);
+        P->graph[k] = nullptr;
+        P->graph_steps[k] = 0;
+    }
+}
+
+// Entries for the two parities of the call (state after an even / odd number of steps
+// since the build), uploaded once per membership change.
+lbve_status build_entries(lbve_pool *P) {
+    const size_t eb = P->kt->batch_entry_bytes;
+    const size_t n = P->members.size();
+    if (n > P->entries_cap) {
+        for (int k = 0; k < 2; ++k) {
+            if (P->entries[k]) cudaFree(P->entries[k]);
+            P->entries[k] = nullptr;
+            PCK(cudaMalloc(&P->entries[k], eb * std::max<size_t>(n, 16)), "pool entries");
+        }
+        P->entries_cap = std::max<size_t>(n, 16);
+    }
+    std::vector<unsigned char> host(eb * std::max<size_t>(n, 1));
+    for (int q = 0; q < 1; ++q) {
+        int lb_first = 0, fv_first = 0;
+        for (size_t m = 0; m < n; ++m) {
+            const lbve_ctx *c = P->members[m];
+            const DevState d = c->d;
+            const int parity = (int)(c->t & 1);
+            int lbi = 0, fvi = 0;
+            P->kt->fill_entry(d, parity, lb_first, fv_first, 0, host.data() + eb * m, &lbi, &fvi);
+            lb_first += lbi;
+            fv_first += fvi;
+        }
+        P->total_lb = lb_first;
+        P->total_fv = fv_first;
+        if (n) PCK(cudaMemcpyAsync(P->entries[q], host.data(), eb * n, cudaMemcpyHostToDevice, P->stream), "upload entries");
+    }
+    PCK(cudaStreamSynchronize(P->stream), "entries sync");
+    if (!P->grid_lb) P->grid_lb = P->kt->batched_grid(0);
+    if (!P->grid_fv) P->grid_fv = P->kt->batched_grid(1);
+    P->dirty = false;
+    P->steps_since_build = 0;
+    drop_graphs(P);
+    return LBVE_OK;
+}
+
+// Enqueue nsteps steps of every member on the pool stream (graph-capturable).
+lbve_status enqueue_steps(lbve_pool *P, int q, int nsteps) {
+    const int n = (int)P->members.size();
+    for (int k = 0; k < nsteps; ++k) {
+        const int kk = q + k;  // steps since the entries were built (they encode that state)
+        for (lbve_ctx *c : P->members) {
+            if (c->nbody == 0) continue;
+            DevState d = c->d;    // the member's state at the start of this call
+            if (k & 1) d.cur ^= 1;
+            const int parity = (int)((c->t + k) & 1);
+            PCK(c->kt->momentum_exchange(d, parity, c->links, c->seg_begin, c->seg_count, c->nbody, c->max_seg_len,
+                                         c->contrib, P->stream),
+                "pool momentum exchange");
+            const int threads = c->p.pdf_prec == LBVE_F64 ? 1 : 256;
+            k_body_reduce<<<c->nbody, threads, 0, P->stream>>>(c->contrib, c->seg_begin, c->seg_count, c->seg_flag,
+                                                               c->nbody, c->body_F, d.parts);
+            PCK(cudaGetLastError(), "pool body reduce");
+        }
+        PCK(P->kt->lb_batched(P->entries[0], n, P->total_lb, kk, P->grid_lb, P->stream), "batched lb");
+        PCK(P->kt->fv_batched(P->entries[0], n, P->total_fv, kk, P->grid_fv, P->stream), "batched fv");
+        for (lbve_ctx *c : P->members) {
+            if (c->nparts == 0) continue;
+            DevState d = c->d;
+            if ((k + 1) & 1) d.cur ^= 1;  // after the stress swap of this step
+            const int parity_next = (int)((c->t + k + 1) & 1);
+            PCK(c->kt->particle_update(d, c->nparts, P->stream), "pool particle update");
+            PCK(c->kt->fill_drain(d, parity_next, c->nparts, c->pkind, c->pnf, c->pdelta, c->pdiag, P->stream),
+                "pool fill/drain");
+            PCK(c->kt->particle_links(d, c->nparts, c->links, c->seg_begin, c->seg_count,
+                                      (int)c->wall_seg_begin.size(), c->part_cap, P->stream),
+                "pool particle links");
+        }
+    }
+    return LBVE_OK;
+}
+
+} // namespace
+
+extern "C" {
+
+lbve_status lbve_pool_create(int pdf_prec, size_t budget_bytes, void *cuda_stream, lbve_pool **out) {
+    if (!out) return LBVE_EINVAL;
+    *out = nullptr;
+    const KernelTable *kt = table_for(pdf_prec);
+    if (!kt) return LBVE_EINVAL;
+    lbve_pool *P = new (std::nothrow) lbve_pool();
+    if (!P) return LBVE_ENOMEM;
+    P->prec = pdf_prec;
+    P->budget = budget_bytes;
+    P->stream = (cudaStream_t)cuda_stream;
+    P->kt = kt;
+    *out = P;
+    return LBVE_OK;
+}
+
+lbve_status lbve_pool_destroy(lbve_pool *P) {
+    if (!P) return LBVE_EINVAL;
+    cudaStreamSynchronize(P->stream);
+    drop_graphs(P);
+    for (int k = 0; k < 2; ++k)
+        if (P->entries[k]) cudaFree(P->entries[k]);
+    if (P->res_dev) cudaFree(P->res_dev);
+    for (lbve_ctx *c : P->members) c->pool = nullptr;
+    delete P;
+    return LBVE_OK;
+}
+
+int lbve_pool_fits(const lbve_pool *P, const lbve_params *p) {
+    if (!P || !p) return 0;
+    const size_t b = lbve_device_bytes(p);
+    return b > 0 && P->in_use + b <= P->budget ? 1 : 0;
+}
+
+lbve_status lbve_pool_admit(lbve_pool *P, lbve_ctx *c) {
+    if (!P || !c) return LBVE_EINVAL;
+    if (c->pool) return pfail(P, LBVE_ESTATE, "context already belongs to a pool");
+    if (c->p.pdf_prec != P->prec) return pfail(P, LBVE_ESTATE, "precision differs from the pool's");
+    if (c->stream != P->stream) return pfail(P, LBVE_ESTATE, "stream differs from the pool's");
+    const size_t b = lbve_device_bytes(&c->p);
+    if (P->in_use + b > P->budget) return pfail(P, LBVE_ENOMEM, "device-memory budget exhausted");
+    P->members.push_back(c);
+    P->member_bytes.push_back(b);
+    P->in_use += b;
+    c->pool = P;
+    P->dirty = true;
+    return LBVE_OK;
+}
+
+lbve_status lbve_pool_remove(lbve_pool *P, lbve_ctx *c) {
+    if (!P || !c) return LBVE_EINVAL;
+    for (size_t k = 0; k < P->members.size(); ++k) {
+        if (P->members[k] != c) continue;
+        cudaStreamSynchronize(P->stream);
+        P->in_use -= P->member_bytes[k];
+        P->members.erase(P->members.begin() + (long)k);
+        P->member_bytes.erase(P->member_bytes.begin() + (long)k);
+        c->pool = nullptr;
+        P->dirty = true;
+        return LBVE_OK;
+    }
+    return pfail(P, LBVE_EINVAL, "not a member");
+}
+
+lbve_status lbve_pool_step(lbve_pool *P, int nsteps) {
+    if (!P) return LBVE_EINVAL;
+    if (nsteps < 0) return pfail(P, LBVE_EINVAL, "nsteps must be >= 0");
+    if (nsteps == 0 || P->members.empty()) return LBVE_OK;
+    if (P->dirty) {
+        lbve_status s = build_entries(P);
+        if (s != LBVE_OK) return s;
+    }
+    const int q = (int)(P->steps_since_build & 1);
+    // the legacy default stream cannot be captured: launch directly there
+    const bool graphs = P->use_graphs && (uintptr_t)P->stream > 1;
+    if (graphs) {
+        if (!P->graph[q] || P->graph_steps[q] != nsteps) {
+            if (P->graph[q]) cudaGraphExecDestroy(P->graph[q]);
+            P->graph[q] = nullptr;
+            cudaGraph_t g;
+            PCK(cudaStreamBeginCapture(P->stream, cudaStreamCaptureModeThreadLocal), "begin capture");
+            lbve_status s = enqueue_steps(P, q, nsteps);
+            cudaError_t e = cudaStreamEndCapture(P->stream, &g);
+            if (s != LBVE_OK) return s;
+            PCK(e, "end capture");
+            PCK(cudaGraphInstantiate(&P->graph[q], g, 0), "graph instantiate");
+            cudaGraphDestroy(g);
+            P->graph_steps[q] = nsteps;
+        }
+        PCK(cudaGraphLaunch(P->graph[q], P->stream), "graph launch");
+    } else {
+        lbve_status s = enqueue_steps(P, q, nsteps);
+        if (s != LBVE_OK) return s;
+    }
+    for (lbve_ctx *c : P->members) {
+        c->t += nsteps;
+        if (nsteps & 1) c->d.cur ^= 1;
+    }
+    P->steps_since_build += nsteps;
+    return LBVE_OK;
+}
+
+lbve_status lbve_pool_residuals(lbve_pool *P, double *out) {
+    if (!P || !out) return P ? pfail(P, LBVE_EINVAL, "out is NULL") : LBVE_EINVAL;
+    const size_t n = P->members.size();
+    if (n == 0) return LBVE_OK;
+    for (lbve_ctx *c : P->members) {
+        lbve_status s = residual_enqueue(c);
+        if (s != LBVE_OK) return pfail(P, s, c->err);
+    }
+    std::vector<double> h(2 * 1024);
+    for (size_t m = 0; m < n; ++m) {
+        lbve_ctx *c = P->members[m];
+        PCK(cudaMemcpyAsync(h.data(), c->res_partial, sizeof(double) * 2 * residual_blocks(c), cudaMemcpyDeviceToHost,
+                            P->stream),
+            "residual copy");
+        PCK(cudaStreamSynchronize(P->stream), "residual sync");
+        residual_finish(c, h.data(), out + 2 * m);
+    }
+    return LBVE_OK;
+}
+
+int lbve_pool_size(const lbve_pool *P) { return P ? (int)P->members.size() : 0; }
+size_t lbve_pool_bytes_in_use(const lbve_pool *P) { return P ? P->in_use : 0; }
+lbve_status lbve_pool_set_graphs(lbve_pool *P, int enable) {
+    if (!P) return LBVE_EINVAL;
+    cudaStreamSynchronize(P->stream);
+    P->use_graphs = enable != 0;
+    drop_graphs(P);
+    return LBVE_OK;
+}
+const char *lbve_pool_last_error(const lbve_pool *P) { return P ? P->err.c_str() : "NULL pool"; }
 
 } // extern "C"

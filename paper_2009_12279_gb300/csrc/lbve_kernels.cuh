@@ -159,11 +159,10 @@ __device__ __forceinline__ bool cell_of_thread(const Geo &g, int &x, int &y, int
     return x < g.nx && y < g.ny;
 }
 
+// Stream-collide of the fluid cell (x, y, z) with the stress stencil read from global memory.
 template <class S, int PAR>
-__global__ void __launch_bounds__(128, LBVE_LB_MIN_BLOCKS) k_lb(KArgs<S> a) {
+__device__ __forceinline__ void lb_cell_at(const KArgs<S> &a, int x, int y, int z) {
     using R = typename Store<S>::R;
-    int x, y, z;
-    if (!cell_of_thread(a.g, x, y, z)) return;
     const Cell cl(a.g, x, y, z);
     const unsigned r = cl.self();
     const uint32_t m = a.mask[r];
@@ -177,6 +176,13 @@ __global__ void __launch_bounds__(128, LBVE_LB_MIN_BLOCKS) k_lb(KArgs<S> a) {
         return a.tau[c * np + cl.idx(k == 0 ? s : 0, k == 1 ? s : 0, k == 2 ? s : 0)];
     };
     lb_core<S, PAR>(a, cl, r, m, tr, tn);
+}
+
+template <class S, int PAR>
+__global__ void __launch_bounds__(128, LBVE_LB_MIN_BLOCKS) k_lb(KArgs<S> a) {
+    int x, y, z;
+    if (!cell_of_thread(a.g, x, y, z)) return;
+    lb_cell_at<S, PAR>(a, x, y, z);
 }
 
 template <class S>
@@ -493,16 +499,14 @@ struct FvSmemNb {
     }
 };
 
+// Stress update of work item `item` (x-y tile, z-chunk) of one solve.
 template <class S>
-__global__ void __launch_bounds__(FV_X * FV_Y, sizeof(typename Store<S>::R) == 8 ? 2 : 4) k_fv_tiled(KArgs<S> a, int zchunk) {
+__device__ __forceinline__ void fv_tile(const KArgs<S> &a, FvSmem<typename Store<S>::R> &sm, int item, int zchunk) {
     using R = typename Store<S>::R;
     constexpr bool SH = Store<S>::shifted;
     constexpr int NT = FV_X * FV_Y;
-    extern __shared__ __align__(16) unsigned char fv_smem_raw[];
-    FvSmem<R> &sm = *reinterpret_cast<FvSmem<R> *>(fv_smem_raw);
     const int tid = threadIdx.x;
     const int tiles_x = (a.g.nx + FV_X - 1) / FV_X, tiles_y = (a.g.ny + FV_Y - 1) / FV_Y;
-    const int item = blockIdx.x;
     const int tx = item % tiles_x, ty = (item / tiles_x) % tiles_y, zc = item / (tiles_x * tiles_y);
     const int x0 = tx * FV_X, y0 = ty * FV_Y;
     const int z0 = zc * zchunk, z1 = min(a.g.nz, z0 + zchunk);
@@ -580,6 +584,146 @@ __global__ void __launch_bounds__(FV_X * FV_Y, sizeof(typename Store<S>::R) == 8
         __syncthreads();  // the next stage overwrites the slot of plane z - 1
     }
     cp_async_wait_all();
+}
+
+template <class S>
+__global__ void __launch_bounds__(FV_X * FV_Y, sizeof(typename Store<S>::R) == 8 ? 2 : 4) k_fv_tiled(KArgs<S> a, int zchunk) {
+    using R = typename Store<S>::R;
+    extern __shared__ __align__(16) unsigned char fv_smem_raw[];
+    FvSmem<R> &sm = *reinterpret_cast<FvSmem<R> *>(fv_smem_raw);
+    fv_tile<S>(a, sm, blockIdx.x, zchunk);
+}
+
+// ---------------------------------------------------------------------------------
+// batched schedule: the resident solves of a pool advance together.  Each kernel is a
+// persistent grid over a packed list of work items (solve, block); a block reads the
+// solve's descriptor into shared memory and runs the same per-cell code as the
+// single-solve kernels, so every cell's arithmetic is the same alone and in the mix.
+// ---------------------------------------------------------------------------------
+constexpr int BLB_X = 32, BLB_Y = 4;  // cells per stream-collide work item
+
+template <class S>
+struct BatchEntry {
+    KArgs<S> a;      // at the first step of the launch sequence
+    int parity0;     // parity of that step
+    int lb_first, lb_items;
+    int fv_first, fv_items, fv_zchunk;
+};
+
+// the entry whose [first, first + items) range holds work item `it` (binary search)
+template <class S>
+__device__ __forceinline__ int batch_find(const BatchEntry<S> *__restrict__ e, int n, int it, bool fv) {
+    int lo = 0, hi = n - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        const int first = fv ? e[mid].fv_first : e[mid].lb_first;
+        if (first <= it)
+            lo = mid;
+        else
+            hi = mid - 1;
+    }
+    return lo;
+}
+
+// step k of a launch sequence flips the stress / velocity ping-pong and the AA parity
+template <class S>
+__device__ __forceinline__ void batch_args(KArgs<S> &a, const BatchEntry<S> &e, int k) {
+    a = e.a;
+    if (k & 1) {
+        const auto *t = a.tau;
+        a.tau = a.tau_out;
+        a.tau_out = const_cast<typename Store<S>::R *>(t);
+    }
+}
+
+template <class S>
+__global__ void __launch_bounds__(BLB_X * BLB_Y, LBVE_LB_MIN_BLOCKS) k_lb_batched(const BatchEntry<S> *__restrict__ e,
+                                                                                 int nsolves, int total, int k) {
+    __shared__ KArgs<S> sa;
+    __shared__ int s_parity, s_solve;
+    if (threadIdx.x == 0 && threadIdx.y == 0) s_solve = -1;
+    __syncthreads();
+    for (int it = blockIdx.x; it < total; it += gridDim.x) {
+        const int sv = batch_find<S>(e, nsolves, it, false);
+        if (sv != s_solve) {
+            __syncthreads();
+            if (threadIdx.x == 0 && threadIdx.y == 0) {
+                batch_args<S>(sa, e[sv], k);
+                s_parity = (e[sv].parity0 + k) & 1;
+                s_solve = sv;
+            }
+            __syncthreads();
+        }
+        const int local = it - e[sv].lb_first;
+        const int tiles_x = (sa.g.nx + BLB_X - 1) / BLB_X, tiles_y = (sa.g.ny + BLB_Y - 1) / BLB_Y;
+        const int bx = local % tiles_x, by = (local / tiles_x) % tiles_y, z = local / (tiles_x * tiles_y);
+        const int x = bx * BLB_X + threadIdx.x, y = by * BLB_Y + threadIdx.y;
+        if (x < sa.g.nx && y < sa.g.ny) {
+            if (s_parity == 0)
+                lb_cell_at<S, 0>(sa, x, y, z);
+            else
+                lb_cell_at<S, 1>(sa, x, y, z);
+        }
+    }
+}
+
+template <class S>
+__global__ void __launch_bounds__(FV_X * FV_Y, sizeof(typename Store<S>::R) == 8 ? 2 : 4) k_fv_batched(
+    const BatchEntry<S> *__restrict__ e, int nsolves, int total, int k) {
+    using R = typename Store<S>::R;
+    extern __shared__ __align__(16) unsigned char fv_smem_raw[];
+    FvSmem<R> &sm = *reinterpret_cast<FvSmem<R> *>(fv_smem_raw);
+    __shared__ KArgs<S> sa;
+    __shared__ int s_solve;
+    if (threadIdx.x == 0) s_solve = -1;
+    __syncthreads();
+    for (int it = blockIdx.x; it < total; it += gridDim.x) {
+        const int sv = batch_find<S>(e, nsolves, it, true);
+        if (sv != s_solve) {
+            __syncthreads();
+            if (threadIdx.x == 0) {
+                batch_args<S>(sa, e[sv], k);
+                s_solve = sv;
+            }
+            __syncthreads();
+        }
+        fv_tile<S>(sa, sm, it - e[sv].fv_first, e[sv].fv_zchunk);
+        __syncthreads();
+    }
+}
+
+// Residual of one solve: sums over fluid cells of |u - u_snap|^2 and |u|^2 (FP64,
+// fixed-shape block partials), then u_snap = u.
+template <class S>
+__global__ void __launch_bounds__(256) k_residual(Geo g, const uint32_t *__restrict__ mask,
+                                                  const typename Store<S>::R *__restrict__ u,
+                                                  typename Store<S>::R *__restrict__ usnap, double *__restrict__ partial) {
+    const size_t np = (size_t)g.np;
+    double d2 = 0.0, u2 = 0.0;
+    for (long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x; r < g.n; r += (long long)gridDim.x * blockDim.x) {
+        if (mask[r] & 1u) continue;
+        for (int j = 0; j < 3; ++j) {
+            const double v = (double)u[j * np + r], w = (double)usnap[j * np + r];
+            d2 += (v - w) * (v - w);
+            u2 += v * v;
+            usnap[j * np + r] = u[j * np + r];
+        }
+    }
+    __shared__ double sh[2][256];
+    sh[0][threadIdx.x] = d2;
+    sh[1][threadIdx.x] = u2;
+    __syncthreads();
+    for (int s = 128; s > 0; s >>= 1) {
+        if ((int)threadIdx.x < s) {
+            sh[0][threadIdx.x] += sh[0][threadIdx.x + s];
+            sh[1][threadIdx.x] += sh[1][threadIdx.x + s];
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        partial[2 * blockIdx.x] = sh[0][0];
+        partial[2 * blockIdx.x + 1] = sh[1][0];
+    }
 }
 
 // ---------------------------------------------------------------------------------

@@ -84,6 +84,14 @@ struct KernelTable {
     cudaError_t (*probe)(const DevState &, int parity, const long long *cells, int count, double *out, cudaStream_t);
     cudaError_t (*build_mask)(const DevState &, int lx, int ly, int lz, int ex, int ey, int ez, cudaStream_t);
     cudaError_t (*fused)(const DevState &, int parity, int zchunk, cudaStream_t);
+    // batched schedule (pools)
+    size_t batch_entry_bytes;
+    void (*fill_entry)(const DevState &, int parity, int lb_first, int fv_first, int fv_zchunk, void *entry,
+                       int *lb_items, int *fv_items);
+    cudaError_t (*lb_batched)(const void *entries, int n, int total, int k, int grid, cudaStream_t);
+    cudaError_t (*fv_batched)(const void *entries, int n, int total, int k, int grid, cudaStream_t);
+    int (*batched_grid)(int which);  // resident blocks for the persistent grids (0: LB, 1: FV)
+    cudaError_t (*residual)(const DevState &, void *usnap, double *partial, int nblocks, cudaStream_t);
 };
 
 // Bounding-box side used to size the per-particle scratch (cells within R + margin).

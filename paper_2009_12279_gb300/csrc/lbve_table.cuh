@@ -219,6 +219,57 @@ struct Launch {
         return cudaGetLastError();
     }
 
+    static void fill_entry(const DevState &d, int parity, int lb_first, int fv_first, int fv_zchunk, void *entry,
+                           int *lb_items, int *fv_items) {
+        BatchEntry<S> &e = *reinterpret_cast<BatchEntry<S> *>(entry);
+        e.a = args(d);
+        e.parity0 = parity;
+        e.lb_first = lb_first;
+        e.lb_items = ((d.g.nx + BLB_X - 1) / BLB_X) * ((d.g.ny + BLB_Y - 1) / BLB_Y) * d.g.nz;
+        e.fv_first = fv_first;
+        e.fv_zchunk = fv_zchunk > 0 ? fv_zchunk : fv_zchunk_of(d);
+        e.fv_items = ((d.g.nx + FV_X - 1) / FV_X) * ((d.g.ny + FV_Y - 1) / FV_Y) *
+                     ((d.g.nz + e.fv_zchunk - 1) / e.fv_zchunk);
+        *lb_items = e.lb_items;
+        *fv_items = e.fv_items;
+    }
+    static int fv_zchunk_of(const DevState &d) { return fv_zchunk(d); }
+    static cudaError_t lb_batched(const void *entries, int n, int total, int k, int grid, cudaStream_t s) {
+        if (total <= 0) return cudaSuccess;
+        k_lb_batched<S><<<grid, dim3(BLB_X, BLB_Y), 0, s>>>((const BatchEntry<S> *)entries, n, total, k);
+        return cudaGetLastError();
+    }
+    static cudaError_t fv_batched(const void *entries, int n, int total, int k, int grid, cudaStream_t s) {
+        if (total <= 0) return cudaSuccess;
+        const size_t sm = sizeof(FvSmem<R>);
+        static bool configured = false;
+        if (!configured) {
+            cudaError_t e = cudaFuncSetAttribute(k_fv_batched<S>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+            if (e != cudaSuccess) return e;
+            configured = true;
+        }
+        k_fv_batched<S><<<grid, FV_X * FV_Y, sm, s>>>((const BatchEntry<S> *)entries, n, total, k);
+        return cudaGetLastError();
+    }
+    static int batched_grid(int which) {
+        int dev = 0, sms = 148, per = 1;
+        if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        if (which == 0) {
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_lb_batched<S>, BLB_X * BLB_Y, 0);
+        } else {
+            const size_t sm = sizeof(FvSmem<R>);
+            cudaFuncSetAttribute(k_fv_batched<S>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_fv_batched<S>, FV_X * FV_Y, sm);
+        }
+        cudaGetLastError();
+        if (per < 1) per = 1;
+        return sms * per;
+    }
+    static cudaError_t residual(const DevState &d, void *usnap, double *partial, int nblocks, cudaStream_t s) {
+        k_residual<S><<<nblocks, 256, 0, s>>>(d.g, d.mask, (const R *)d.u[d.ucur], (R *)usnap, partial);
+        return cudaGetLastError();
+    }
+
     static const KernelTable *table(int prec);
 };
 
@@ -233,7 +284,8 @@ const KernelTable *Launch<S>::table(int prec) {
                                       &lb,            &fv,              &momentum_exchange, &voxelise,
                                       &particle_update, &particle_links, &fill_drain, &read,
                                       &pdfs_io,       &reduce,          &probe,      &build_mask,
-                                      &fused};
+                                      &fused,         sizeof(BatchEntry<S>), &fill_entry, &lb_batched,
+                                      &fv_batched,    &batched_grid,    &residual};
         return &t;
 }
 

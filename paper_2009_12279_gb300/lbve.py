@@ -28,7 +28,9 @@ EXPORTS = [
     "lbve_default_params", "lbve_device_bytes", "lbve_create", "lbve_create_with_allocator", "lbve_destroy",
     "lbve_set_geometry", "lbve_init_fields", "lbve_init_fields_device", "lbve_probe", "lbve_add_particle", "lbve_step", "lbve_read_fields",
     "lbve_read_fields_device", "lbve_read_pdfs", "lbve_write_pdfs", "lbve_read_particle", "lbve_read_conversions", "lbve_read_body_forces",
-    "lbve_reduce", "lbve_step_noalloc", "lbve_noalloc_last_error", "lbve_set_kernel_timing", "lbve_read_kernel_times", "lbve_time", "lbve_synchronize", "lbve_last_error", "lbve_status_string",
+    "lbve_reduce", "lbve_residual", "lbve_pool_create", "lbve_pool_destroy", "lbve_pool_fits", "lbve_pool_admit",
+    "lbve_pool_remove", "lbve_pool_step", "lbve_pool_residuals", "lbve_pool_size", "lbve_pool_bytes_in_use",
+    "lbve_pool_set_graphs", "lbve_pool_last_error", "lbve_step_noalloc", "lbve_noalloc_last_error", "lbve_set_kernel_timing", "lbve_read_kernel_times", "lbve_time", "lbve_synchronize", "lbve_last_error", "lbve_status_string",
 ]
 
 
@@ -89,6 +91,20 @@ def load(path: str | None = None):
         L.lbve_read_body_forces.argtypes = [vp, dp]
         L.lbve_read_conversions.argtypes = [vp, dp]
         L.lbve_reduce.argtypes = [vp, dp]
+        L.lbve_residual.argtypes = [vp, dp]
+        L.lbve_pool_create.argtypes = [ct.c_int, ct.c_size_t, vp, ct.POINTER(vp)]
+        L.lbve_pool_destroy.argtypes = [vp]
+        L.lbve_pool_fits.argtypes = [vp, ct.POINTER(Params)]
+        L.lbve_pool_admit.argtypes = [vp, vp]
+        L.lbve_pool_remove.argtypes = [vp, vp]
+        L.lbve_pool_step.argtypes = [vp, ct.c_int]
+        L.lbve_pool_residuals.argtypes = [vp, dp]
+        L.lbve_pool_size.argtypes = [vp]
+        L.lbve_pool_bytes_in_use.argtypes = [vp]
+        L.lbve_pool_bytes_in_use.restype = ct.c_size_t
+        L.lbve_pool_set_graphs.argtypes = [vp, ct.c_int]
+        L.lbve_pool_last_error.argtypes = [vp]
+        L.lbve_pool_last_error.restype = ct.c_char_p
         L.lbve_step_noalloc.argtypes = [ct.POINTER(Params), vp, vp, vp, vp, dp, ct.c_int, ct.c_longlong, ct.c_int, vp]
         L.lbve_noalloc_last_error.argtypes = []
         L.lbve_noalloc_last_error.restype = ct.c_char_p
@@ -300,7 +316,71 @@ class Solver:
         self._check(self._L.lbve_read_kernel_times(self._h, _dp(ms), cnt))
         return {k: (float(ms[i]), int(cnt[i])) for i, k in enumerate(KERNEL_KINDS) if k and cnt[i] > 0}
 
+    def residual(self) -> tuple:
+        """(|u - u_prev| / |u|, |u|) since the previous call (see lbve_residual)."""
+        o = np.zeros(2)
+        self._check(self._L.lbve_residual(self._h, _dp(o)))
+        return float(o[0]), float(o[1])
+
     def reduce(self) -> dict:
         o = np.zeros(6)
         self._check(self._L.lbve_reduce(self._h, _dp(o)))
         return {"mass": o[0], "momentum": o[1:4].copy(), "fluid_cells": int(o[4]), "bad": bool(o[5] > 0)}
+
+
+class Pool:
+    """Resident solves stepped together by the batched persistent kernels (lbve_pool_*)."""
+
+    def __init__(self, precision="bf16", budget_bytes=150 * 10**9, stream: int | None = None, graphs=True):
+        self._L = load()
+        self.precision = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
+        h = ct.c_void_p()
+        rc = self._L.lbve_pool_create(self.precision, int(budget_bytes), ct.c_void_p(stream or 0), ct.byref(h))
+        if rc != 0:
+            raise LbveError(rc, "pool creation failed")
+        self._h = h
+        self.members = []
+        if not graphs:
+            self._L.lbve_pool_set_graphs(self._h, 0)
+
+    def _check(self, rc):
+        if rc != 0:
+            raise LbveError(rc, self._L.lbve_pool_last_error(self._h).decode())
+
+    def fits(self, params: Params) -> bool:
+        return bool(self._L.lbve_pool_fits(self._h, ct.byref(params)))
+
+    def admit(self, solver: "Solver"):
+        self._check(self._L.lbve_pool_admit(self._h, solver._h))
+        self.members.append(solver)
+
+    def remove(self, solver: "Solver"):
+        self._check(self._L.lbve_pool_remove(self._h, solver._h))
+        self.members.remove(solver)
+
+    def step(self, n: int = 1):
+        self._check(self._L.lbve_pool_step(self._h, int(n)))
+
+    def residuals(self) -> np.ndarray:
+        o = np.zeros((max(len(self.members), 1), 2))
+        if self.members:
+            self._check(self._L.lbve_pool_residuals(self._h, _dp(o)))
+        return o[: len(self.members)]
+
+    @property
+    def bytes_in_use(self) -> int:
+        return int(self._L.lbve_pool_bytes_in_use(self._h))
+
+    def __len__(self):
+        return int(self._L.lbve_pool_size(self._h))
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._L.lbve_pool_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

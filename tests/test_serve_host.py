@@ -1,0 +1,182 @@
+"""Host-side checks of the serving scheduler (no GPU): request stream, admission against
+the budget, FIFO order, rejection, cancellation and eviction of unstable solves (faults
+injected on the host), and replica sharding over two gloo ranks."""
+import math
+import os
+
+import numpy as np
+import pytest
+
+from paper_2009_12279_gb300 import replicas, serve
+
+
+def test_request_stream_matches_the_serving_workload():
+    reqs = serve.make_requests(300, seed=5, mean_interarrival=0.01)
+    again = serve.make_requests(300, seed=5, mean_interarrival=0.01)
+    assert [r.shape for r in reqs] == [r.shape for r in again]
+    assert {r.kind for r in reqs} == set(serve.KINDS)
+    arr = [r.arrival for r in reqs]
+    assert all(b > a for a, b in zip(arr, arr[1:]))
+    for r in reqs:
+        nx, ny, nz = r.shape
+        assert 16 <= ny == nz <= 64 and ny <= nx <= 256 and nx * ny * nz <= 256 * 64 * 64
+        assert 0.1 <= r.params["beta"] <= 0.9
+        assert 10.0 <= r.params["lambda_p"] <= 1e5
+        assert 0 < r.max_steps <= 50000
+        fl = r.flags
+        for a, per in enumerate(r.params["periodic"]):
+            if not per:
+                assert (np.moveaxis(fl, 2 - a, 0)[0] != 0).all() and (np.moveaxis(fl, 2 - a, 0)[-1] != 0).all()
+    gaps = np.diff([0.0] + arr)
+    assert abs(gaps.mean() - 0.01) < 0.003  # exponential inter-arrival with the requested mean
+
+
+def test_percentiles():
+    v = list(range(1, 101))
+    assert serve.percentile(v, 50) == pytest.approx(50.5)
+    assert serve.percentile(v, 99) == pytest.approx(99.01)
+    assert math.isnan(serve.percentile([], 50))
+
+
+class FakeSolver:
+    def __init__(self, req):
+        self.req = req
+        self.closed = False
+
+    def close(self):
+        self.closed = True
+
+
+class FakePool:
+    """Budget bookkeeping like lbve_pool; residual r = 1/steps (converges), NaN for
+    requests marked unstable."""
+
+    def __init__(self, budget):
+        self.budget, self.used, self.members, self.steps = budget, 0, [], {}
+        self.peak = 0
+        self.admit_order = []
+
+    def fits(self, prm):
+        return self.used + prm <= self.budget
+
+    def admit(self, s):
+        self.used += s.req.bytes
+        assert self.used <= self.budget
+        self.peak = max(self.peak, self.used)
+        self.members.append(s)
+        self.steps[s.req.rid] = 0
+        self.admit_order.append(s.req.rid)
+
+    def remove(self, s):
+        self.members.remove(s)
+        self.used -= s.req.bytes
+
+    def step(self, n):
+        for s in self.members:
+            self.steps[s.req.rid] += n
+
+    def residuals(self):
+        out = []
+        for s in self.members:
+            k = self.steps[s.req.rid]
+            out.append((float("nan"), 1.0) if getattr(s.req, "unstable", False) else (100.0 / k ** 2, 1.0))
+        return np.array(out)
+
+    @property
+    def bytes_in_use(self):
+        return self.used
+
+    def close(self):
+        pass
+
+
+def _fake_requests(n, bytes_each, seed=1):
+    reqs = serve.make_requests(n, seed=seed, mean_interarrival=0.0, bases=(16,), elongations=(1,))
+    for r, b in zip(reqs, bytes_each):
+        r.bytes = b
+        r.arrival = 0.0
+        r.tol = 1e-6
+        r.max_steps = 10**6
+    return reqs
+
+
+def _server(budget):
+    pool = FakePool(budget)
+    srv = serve.Server(pool=pool, solver_factory=lambda req, prec, stream: FakeSolver(req),
+                       params_factory=lambda req, prec: req.bytes, check_every=100)
+    return srv, pool
+
+
+def test_admission_respects_budget_and_fifo():
+    reqs = _fake_requests(12, [30, 50, 20, 40, 10, 60, 25, 35, 15, 45, 5, 55])
+    srv, pool = _server(100)
+    results, _ = srv.run(reqs)
+    assert sorted(r.rid for r in results) == list(range(12))
+    assert all(r.status == "converged" for r in results)
+    assert pool.peak <= 100
+    assert pool.admit_order == sorted(pool.admit_order)  # FIFO
+
+
+def test_faults_injected_on_the_host():
+    reqs = _fake_requests(5, [10, 10, 500, 10, 10])
+    reqs[1].unstable = True        # a solve that blows up: evicted, the rest continue
+    reqs[3].cancel_at = 0.0        # a cancelled request
+    srv, pool = _server(100)       # request 2 can never fit: rejected, not waited for
+    results, _ = srv.run(reqs)
+    st = {r.rid: r.status for r in results}
+    assert st == {0: "converged", 1: "unstable", 2: "rejected", 3: "cancelled", 4: "converged"}
+    assert pool.used == 0
+
+
+def test_bad_request_is_rejected_without_stopping_the_server():
+    reqs = _fake_requests(3, [10, 10, 10])
+
+    def factory(req, prec, stream):
+        if req.rid == 1:
+            raise ValueError("invalid parameters")
+        return FakeSolver(req)
+
+    pool = FakePool(100)
+    srv = serve.Server(pool=pool, solver_factory=factory, params_factory=lambda r, p: r.bytes)
+    results, _ = srv.run(reqs)
+    assert {r.rid: r.status for r in results} == {0: "converged", 1: "rejected", 2: "converged"}
+
+
+def test_shard_covers_every_item_once():
+    items = list(range(37))
+    got = sorted(i for rank in range(4) for i in replicas.shard(items, rank, 4))
+    assert got == items
+    with pytest.raises(ValueError):
+        replicas.shard(items, 4, 4)
+
+
+def _gloo_worker(rank, world, port, out):
+    import torch.distributed as dist
+
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    mine = replicas.shard(list(range(10)), rank, world)
+    t, w = replicas.reduce_timing(dist, elapsed_s=1.0 + rank, work=float(len(mine)))
+    out.put((rank, t, w))
+    dist.barrier()
+    dist.destroy_process_group()
+
+
+def test_replica_timing_reduction_over_two_gloo_ranks():
+    import multiprocessing as mp
+    import socket
+
+    with socket.socket() as sk:
+        sk.bind(("127.0.0.1", 0))
+        port = sk.getsockname()[1]
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    procs = [ctx.Process(target=_gloo_worker, args=(r, 2, port, q)) for r in range(2)]
+    for p in procs:
+        p.start()
+    res = [q.get(timeout=120) for _ in procs]
+    for p in procs:
+        p.join(timeout=60)
+        assert p.exitcode == 0
+    for rank, t, w in res:
+        assert t == 2.0 and w == 10.0  # max of per-rank times, sum of per-rank work
