@@ -249,6 +249,79 @@ def time_e2e(n, prec, schedule, steps, torch, stream_obj):
             "finite": finite}
 
 
+def bench_serving(args, torch):
+    """Bounded sample of the serving workload: batched BF16 pool vs one-at-a-time FP32."""
+    import numpy as np
+
+    from paper_2009_12279_gb300 import serve
+
+    stream = torch.cuda.Stream()
+    kw = dict(max_steps_cap=args.serving_cap)
+    reqs0 = serve.make_requests(args.serving_requests, seed=0, mean_interarrival=0.0, **kw)
+    # throughput mode (all requests waiting at t = 0)
+    t0 = time.perf_counter()
+    solo, fsolo = serve.run_one_at_a_time(reqs0, precision="f32", stream=stream.cuda_stream, keep_fields=True)
+    torch.cuda.synchronize()
+    wall_solo = time.perf_counter() - t0
+    # batched FP32: bitwise the same results as one at a time (equal accuracy)
+    srv = serve.Server("f32", budget_bytes=int(args.serving_budget_gb * 1e9), stream=stream.cuda_stream)
+    t0 = time.perf_counter()
+    mix32, fmix32 = srv.run(reqs0, keep_fields=True)
+    torch.cuda.synchronize()
+    wall_mix32 = time.perf_counter() - t0
+    stats32 = dict(srv.stats)
+    srv.close()
+    same = all(all(np.array_equal(a, b) for a, b in zip(fsolo[r], fmix32[r])) for r in fsolo if r in fmix32)
+    srv = serve.Server("bf16", budget_bytes=int(args.serving_budget_gb * 1e9), stream=stream.cuda_stream)
+    t0 = time.perf_counter()
+    mix, fmix = srv.run(reqs0, keep_fields=True)
+    torch.cuda.synchronize()
+    wall_mix = time.perf_counter() - t0
+    peak = srv.peak_bytes
+    stats16 = dict(srv.stats)
+    srv.close()
+    # accuracy of the batched BF16 results against the FP32 one-at-a-time results
+    errs = []
+    for rid, fs in fsolo.items():
+        if rid in fmix:
+            u32, u16 = fs[1], fmix[rid][1]
+            errs.append(float(np.linalg.norm(u16 - u32) / max(np.linalg.norm(u32), 1e-300)))
+    # latency under Poisson arrivals at 0.8 x the batched service time per solve
+    mean_gap = 0.8 * wall_mix / max(len(reqs0), 1)
+    reqs = serve.make_requests(args.serving_requests, seed=0, mean_interarrival=mean_gap, **kw)
+    srv = serve.Server("bf16", budget_bytes=int(args.serving_budget_gb * 1e9), stream=stream.cuda_stream)
+    t0 = time.perf_counter()
+    lat_mix, _ = srv.run(reqs)
+    torch.cuda.synchronize()
+    wall_lat = time.perf_counter() - t0
+    srv.close()
+    t0 = time.perf_counter()
+    lat_solo, _ = serve.run_one_at_a_time(reqs, precision="f32", stream=stream.cuda_stream)
+    torch.cuda.synchronize()
+    wall_lat_solo = time.perf_counter() - t0
+    s_mix, s_solo = serve.summarize(lat_mix, wall_lat), serve.summarize(lat_solo, wall_lat_solo)
+    return {
+        "requests": len(reqs0), "step_cap": args.serving_cap, "stop": "residual 1e-6 per step or cap",
+        "batched_bf16": {"solves_per_s": len(mix) / wall_mix, "wall_s": wall_mix,
+                         "p50_latency_s": s_mix["p50_latency_s"], "p99_latency_s": s_mix["p99_latency_s"],
+                         "poisson_wall_s": wall_lat, "peak_device_bytes": peak, "phases": stats16,
+                         "mlups": serve.summarize(mix, wall_mix)["mlups"]},
+        "batched_f32": {"solves_per_s": len(mix32) / wall_mix32, "wall_s": wall_mix32,
+                        "bitwise_equal_to_one_at_a_time": bool(same), "phases": stats32,
+                        "mlups": serve.summarize(mix32, wall_mix32)["mlups"]},
+        "one_at_a_time_f32": {"solves_per_s": len(solo) / wall_solo, "wall_s": wall_solo,
+                              "p50_latency_s": s_solo["p50_latency_s"], "p99_latency_s": s_solo["p99_latency_s"],
+                              "poisson_wall_s": wall_lat_solo, "mlups": serve.summarize(solo, wall_solo)["mlups"]},
+        "speedup_solves_per_s": (len(mix) / wall_mix) / (len(solo) / wall_solo),
+        "mean_interarrival_s": mean_gap,
+        "bf16_vs_f32_u_rel_l2": {"median": float(np.median(errs)) if errs else None,
+                                 "max": float(np.max(errs)) if errs else None},
+        "statuses_bf16": {k: sum(r.status == k for r in mix) for k in ("converged", "capped", "unstable", "rejected")},
+        "statuses_f32": {k: sum(r.status == k for r in solo) for k in ("converged", "capped", "unstable", "rejected")},
+        "unstable_bf16": [(r.rid, r.kind) for r in mix if r.status == "unstable"],
+    }
+
+
 def run_ours(args):
     import torch
 
@@ -318,6 +391,9 @@ def run_ours(args):
             "gpu_launches": launches,
             "healthy": not health["bad"],
         }
+    serving = None
+    if rank == 0 and not args.no_serving:
+        serving = bench_serving(args, torch)
     e2e = None
     if not args.no_e2e:
         e2e = time_e2e(n, args.precisions[0], args.schedule, args.steps, torch, stream_obj)
@@ -341,6 +417,7 @@ def run_ours(args):
             "clocks": clocks,
             "e2e": e2e,
             "cpu_baseline": cpu,
+            "serving": serving,
             "modes": {p: {k: v for k, v in r.items() if k != "roofline"} | {"roofline_frac": r["roofline"]["frac"]}
                       for p, r in results.items()},
         }
@@ -375,6 +452,10 @@ def main():
     ap.add_argument("--schedule", choices=["auto", "split", "fused"], default="auto")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-serving", action="store_true")
+    ap.add_argument("--serving-requests", type=int, default=48)
+    ap.add_argument("--serving-cap", type=int, default=1000, help="step cap per solve in the serving sample")
+    ap.add_argument("--serving-budget-gb", type=float, default=150.0)
     args = ap.parse_args()
     args.precisions = [p.strip() for p in args.precisions.split(",") if p.strip()]
     if args.warmup < 3:

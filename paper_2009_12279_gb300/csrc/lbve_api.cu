@@ -45,6 +45,7 @@ struct lbve_ctx {
     std::vector<int> part_cap_host;
     uint8_t *pkind = nullptr, *pnf = nullptr;  // fill/drain scratch (largest particle box)
     double *pdelta = nullptr;
+    int *pconv = nullptr;
     size_t pscratch_cells = 0;
     double *pdiag = nullptr;     // device: dropped stress (6), destroyed, created
     double *body_F = nullptr;    // device, 256 x 3 forces of the last step
@@ -669,6 +670,7 @@ lbve_status lbve_add_particle(lbve_ctx *c, const double X[3], double R, double r
     P.rho_p = rho_p;
     P.m = rho_p * (4.0 / 3.0) * M_PI * R * R * R;
     P.I = 0.4 * P.m * R * R;
+    P.changed = 1;
     const int p = c->nparts;
     // scratch for fill/drain (box with margin 3) and the link capacity (box with margin 2)
     const long long side3 = particle_box_side(R, 3), side2 = particle_box_side(R, 2);
@@ -677,10 +679,13 @@ lbve_status lbve_add_particle(lbve_ctx *c, const double X[3], double R, double r
         dev_free(c, c->pkind);
         dev_free(c, c->pnf);
         dev_free(c, c->pdelta);
+        dev_free(c, c->pconv);
         c->pkind = (uint8_t *)dev_alloc(c, cells3);
         c->pnf = (uint8_t *)dev_alloc(c, cells3);
         c->pdelta = (double *)dev_alloc(c, sizeof(double) * 6 * cells3);
-        if (!c->pkind || !c->pnf || !c->pdelta) return fail(c, LBVE_ENOMEM, "particle scratch allocation failed");
+        c->pconv = (int *)dev_alloc(c, sizeof(int) * cells3);
+        if (!c->pkind || !c->pnf || !c->pdelta || !c->pconv)
+            return fail(c, LBVE_ENOMEM, "particle scratch allocation failed");
         CK(cudaMemsetAsync(c->pnf, 0, cells3, c->stream), "scratch clear");
         c->pscratch_cells = cells3;
     }
@@ -773,7 +778,7 @@ lbve_status lbve_step(lbve_ctx *c, int nsteps) {
         if (c->nparts > 0) {
             CK(timed_begin(c, LBVE_KT_PARTICLE), "timing");
             CK(c->kt->particle_update(c->d, c->nparts, c->stream), "particle update");
-            CK(c->kt->fill_drain(c->d, parity ^ 1, c->nparts, c->pkind, c->pnf, c->pdelta, c->pdiag, c->stream),
+            CK(c->kt->fill_drain(c->d, parity ^ 1, c->nparts, c->pkind, c->pnf, c->pdelta, c->pconv, c->pdiag, c->stream),
                "fill/drain");
             CK(c->kt->particle_links(c->d, c->nparts, c->links, c->seg_begin, c->seg_count,
                                      (int)c->wall_seg_begin.size(), c->part_cap, c->stream),
@@ -1086,7 +1091,7 @@ lbve_status enqueue_steps(lbve_pool *P, int q, int nsteps) {
             if ((k + 1) & 1) d.cur ^= 1;  // after the stress swap of this step
             const int parity_next = (int)((c->t + k + 1) & 1);
             PCK(c->kt->particle_update(d, c->nparts, P->stream), "pool particle update");
-            PCK(c->kt->fill_drain(d, parity_next, c->nparts, c->pkind, c->pnf, c->pdelta, c->pdiag, P->stream),
+            PCK(c->kt->fill_drain(d, parity_next, c->nparts, c->pkind, c->pnf, c->pdelta, c->pconv, c->pdiag, P->stream),
                 "pool fill/drain");
             PCK(c->kt->particle_links(d, c->nparts, c->links, c->seg_begin, c->seg_count,
                                       (int)c->wall_seg_begin.size(), c->part_cap, P->stream),

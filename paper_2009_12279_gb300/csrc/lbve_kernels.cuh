@@ -941,6 +941,7 @@ __global__ void __launch_bounds__(256) k_particle_links(Geo g, const PartDev *__
                                                         int first_seg, const int *__restrict__ capacity) {
     const int p = blockIdx.x;
     const PartDev &P = parts[p];
+    if (!P.changed) return;  // no cell converted since the last build: the links still hold
     const BBox b = particle_bbox(g, P.X, P.R, 2);
     const long long nc = b.cells();
     const int seg = first_seg + p;
@@ -1003,7 +1004,8 @@ __global__ void __launch_bounds__(512) k_fill_drain(KArgs<S> a, PartDev *__restr
                                                     uint8_t *__restrict__ flag, uint32_t *__restrict__ mask,
                                                     typename Store<S>::R *__restrict__ tau,
                                                     uint8_t *__restrict__ kind, uint8_t *__restrict__ nf_arr,
-                                                    double *__restrict__ delta, double *__restrict__ diag) {
+                                                    double *__restrict__ delta, int *__restrict__ conv,
+                                                    double *__restrict__ diag) {
     using R = typename Store<S>::R;
     constexpr bool SH = Store<S>::shifted;
     const long long np = a.g.np;
@@ -1017,6 +1019,7 @@ __global__ void __launch_bounds__(512) k_fill_drain(KArgs<S> a, PartDev *__restr
         const BBox b = particle_bbox(a.g, P.X, P.R, 3);
         const long long nc = b.cells();
         // A: classify
+        int any_local = 0;
         for (long long k = threadIdx.x; k < nc; k += blockDim.x) {
             int x, y, z;
             const long long r = bbox_cell(a.g, b, k, x, y, z);
@@ -1030,12 +1033,48 @@ __global__ void __launch_bounds__(512) k_fill_drain(KArgs<S> a, PartDev *__restr
                 else kd = inside ? 0 : 3;
             }
             kind[k] = (uint8_t)kd;
+            any_local |= (kd == 2 || kd == 3);
         }
+        if (!__syncthreads_or(any_local)) {
+            // nothing converts: no impulse, flags and links stay as they are
+            if (threadIdx.x == 0) {
+                for (int c3 = 0; c3 < 3; ++c3) P.dP[c3] = P.dL[c3] = 0.0;
+                P.changed = 0;
+            }
+            __syncthreads();
+            continue;
+        }
+        // A': ordered list of the converted cells (warp ballots + a scan over the warps)
+        __shared__ int s_wsum[32], s_base, s_total;
+        if (threadIdx.x == 0) s_base = 0;
         __syncthreads();
+        const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = (blockDim.x + 31) >> 5;
+        for (long long k0 = 0; k0 < nc; k0 += blockDim.x) {
+            const long long k = k0 + threadIdx.x;
+            const bool pred = k < nc && (kind[k] == 2 || kind[k] == 3);
+            const unsigned bal = __ballot_sync(0xffffffffu, pred);
+            if (lane == 0) s_wsum[warp] = __popc(bal);
+            __syncthreads();
+            if (threadIdx.x == 0) {
+                int acc = 0;
+                for (int w = 0; w < nwarp; ++w) {
+                    const int v = s_wsum[w];
+                    s_wsum[w] = acc;
+                    acc += v;
+                }
+                s_total = acc;
+            }
+            __syncthreads();
+            if (pred) conv[s_base + s_wsum[warp] + __popc(bal & ((1u << lane) - 1u))] = (int)k;
+            __syncthreads();
+            if (threadIdx.x == 0) s_base += s_total;
+            __syncthreads();
+        }
+        const int nconv = s_base;
         // B: N_f of converted cells, new stress of created cells
-        for (long long k = threadIdx.x; k < nc; k += blockDim.x) {
+        for (int q = threadIdx.x; q < nconv; q += blockDim.x) {
+            const long long k = conv[q];
             const int kd = kind[k];
-            if (kd != 2 && kd != 3) continue;
             int x, y, z;
             bbox_cell(a.g, b, k, x, y, z);
             const Cell cl(a.g, x, y, z);
@@ -1097,7 +1136,8 @@ __global__ void __launch_bounds__(512) k_fill_drain(KArgs<S> a, PartDev *__restr
         // the populations of created cells
         if (threadIdx.x == 0) {
             double dP[3] = {0, 0, 0}, dL[3] = {0, 0, 0};
-            for (long long k = 0; k < nc; ++k) {
+            for (int q = 0; q < nconv; ++q) {
+                const long long k = conv[q];
                 if (kind[k] != 2) continue;
                 int x, y, z;
                 const unsigned r = (unsigned)bbox_cell(a.g, b, k, x, y, z);
@@ -1122,7 +1162,8 @@ __global__ void __launch_bounds__(512) k_fill_drain(KArgs<S> a, PartDev *__restr
                     for (int c = 0; c < 6; ++c) diag[c] += (double)tau[c * np + r];
                 diag[6] += 1.0;
             }
-            for (long long k = 0; k < nc; ++k) {
+            for (int q = 0; q < nconv; ++q) {
+                const long long k = conv[q];
                 if (kind[k] != 3) continue;
                 int x, y, z;
                 const long long r = bbox_cell(a.g, b, k, x, y, z);
@@ -1197,13 +1238,24 @@ __global__ void __launch_bounds__(512) k_fill_drain(KArgs<S> a, PartDev *__restr
             }
         }
         __syncthreads();
-        // F: neighbour masks of every cell in the box (covers all cells whose masks change)
-        for (long long k = threadIdx.x; k < nc; k += blockDim.x) {
+        // F: neighbour masks of the converted cells and their neighbours (the only cells
+        // whose masks change; a cell reached twice gets the same value twice)
+        for (int e = threadIdx.x; e < nconv * Q; e += blockDim.x) {
+            const int q = e / Q, i = e - q * Q;
             int x, y, z;
-            const long long r = bbox_cell(a.g, b, k, x, y, z);
-            mask[r] = cell_mask(a.g, flag, x, y, z);
+            bbox_cell(a.g, b, conv[q], x, y, z);
+            int xq = x + cx(i), yq = y + cy(i), zq = z + cz(i);
+            if ((!a.g.per[0] && (xq < 0 || xq >= a.g.nx)) || (!a.g.per[1] && (yq < 0 || yq >= a.g.ny)) ||
+                (!a.g.per[2] && (zq < 0 || zq >= a.g.nz)))
+                continue;
+            xq = wrapc(xq, a.g.nx);
+            yq = wrapc(yq, a.g.ny);
+            zq = wrapc(zq, a.g.nz);
+            mask[(unsigned)xq + (unsigned)a.g.nx * ((unsigned)yq + (unsigned)a.g.ny * (unsigned)zq)] =
+                cell_mask(a.g, flag, xq, yq, zq);
         }
         if (threadIdx.x == 0) {
+            P.changed = 1;
             for (int c3 = 0; c3 < 3; ++c3) {
                 P.v[c3] += P.dP[c3] / P.m;
                 P.w[c3] += P.dL[c3] / P.I;

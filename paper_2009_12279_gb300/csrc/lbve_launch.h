@@ -44,6 +44,7 @@ struct PartDev {
     double Fext[3], Text[3];
     double Fme[3], Tme[3];
     double dP[3], dL[3];
+    int changed;  // 1 when the last fill/drain converted cells (links must be rebuilt)
 };
 
 // Device buffers of one solve.
@@ -76,7 +77,7 @@ struct KernelTable {
     cudaError_t (*particle_links)(const DevState &, int nparts, long long *links, const int *seg_begin, int *seg_count,
                                   int first_seg, const int *capacity, cudaStream_t);
     cudaError_t (*fill_drain)(const DevState &, int parity, int nparts, uint8_t *kind, uint8_t *nf, double *delta,
-                              double *diag, cudaStream_t);
+                              int *conv, double *diag, cudaStream_t);
     cudaError_t (*read)(const DevState &, int parity, double *rho, double *u, double *tau, int z0, int z1,
                         long long ld, cudaStream_t);
     cudaError_t (*pdfs_io)(const DevState &, int parity, double *io, int write, cudaStream_t);

@@ -133,14 +133,14 @@ struct Launch {
         return cudaGetLastError();
     }
     static cudaError_t fill_drain(const DevState &d, int parity, int nparts, uint8_t *kind, uint8_t *nf, double *delta,
-                                  double *diag, cudaStream_t s) {
+                                  int *conv, double *diag, cudaStream_t s) {
         if (nparts <= 0) return cudaSuccess;
         KArgs<S> a = args(d);
         R *tau = (R *)d.tau[d.cur];
         if (parity == 0)
-            k_fill_drain<S, 0><<<1, 512, 0, s>>>(a, d.parts, nparts, d.flag, d.mask, tau, kind, nf, delta, diag);
+            k_fill_drain<S, 0><<<1, 512, 0, s>>>(a, d.parts, nparts, d.flag, d.mask, tau, kind, nf, delta, conv, diag);
         else
-            k_fill_drain<S, 1><<<1, 512, 0, s>>>(a, d.parts, nparts, d.flag, d.mask, tau, kind, nf, delta, diag);
+            k_fill_drain<S, 1><<<1, 512, 0, s>>>(a, d.parts, nparts, d.flag, d.mask, tau, kind, nf, delta, conv, diag);
         return cudaGetLastError();
     }
     static cudaError_t build_mask_impl(const DevState &d, int lx, int ly, int lz, int ex, int ey, int ez,

@@ -88,15 +88,19 @@ def make_request(rid, rng, *, bases=(16, 32, 64), elongations=(1, 2, 4), eta=1.0
         lam = wi * R / u_ref
         params = dict(periodic=(1, 0, 0), eta=eta, beta=beta, body_force=(g, 0.0, 0.0))
     else:
+        # as in the paper's sedimenting-sphere runs, the Newtonian viscosity stays eta_n and
+        # the polymer adds eta_p = beta / (1 - beta) eta_n: the explicit particle coupling of
+        # a light sphere (rho_p = 1.2) is unstable once eta_n drops to ~1/30
         flags = np.ones((nz, ny, nx), np.uint8)
         flags[1:-1, 1:-1, 1:-1] = 0
         R = max(2.5, b / 8.0)
         rho_p = 1.2
-        F = (rho_p - 1.0) * (4.0 / 3.0) * math.pi * R ** 3 * g * 100.0
-        v_st = F / (6.0 * math.pi * eta * R)
+        eta_tot = eta / (1.0 - beta)
+        F = (rho_p - 1.0) * (4.0 / 3.0) * math.pi * R ** 3 * g  # net weight under gravity g
+        v_st = F / (6.0 * math.pi * eta_tot * R)
         lam = wi * R / v_st
         particle = dict(X=((nx - 1) / 2.0, (ny - 1) / 2.0, nz * 0.6), R=R, rho_p=rho_p, Fext=(0.0, 0.0, -F))
-        params = dict(periodic=(0, 0, 0), eta=eta, beta=beta, body_force=(0.0, 0.0, 0.0))
+        params = dict(periodic=(0, 0, 0), eta=eta_tot, beta=beta, body_force=(0.0, 0.0, 0.0))
     lam = float(min(max(lam, 10.0), 1e5))
     params["lambda_p"] = lam
     return Request(rid=rid, kind=kind, shape=shape, params=params, flags=flags, wall_vel=wall_vel,
@@ -165,6 +169,9 @@ class Server:
         self.clock = clock
         self.max_members = max_members
         self.peak_bytes = 0
+        # host-side time spent per phase (admission incl. context set-up, stepping incl.
+        # the residual read-back, retirement incl. read-out and release)
+        self.stats = {"admit_s": 0.0, "step_s": 0.0, "retire_s": 0.0, "steps": 0, "admitted": 0}
 
     def run(self, requests, keep_fields=False):
         """Serve the requests (sorted by arrival); returns (results, fields by rid)."""
@@ -186,6 +193,7 @@ class Server:
                     results.append(Result(req.rid, req.kind, int(np.prod(req.shape)), "cancelled", item[3], float("nan"),
                                           req.arrival, item[2], now()))
             # admission of arrived requests while the budget allows (FIFO)
+            ta = self.clock()
             while i < len(pending) and pending[i].arrival <= t and len(active) < self.max_members:
                 req = pending[i]
                 prm = self.params_factory(req, self.precision)
@@ -206,7 +214,9 @@ class Server:
                     i += 1
                     continue
                 active.append([req, s, now(), 0])
+                self.stats["admitted"] += 1
                 i += 1
+            self.stats["admit_s"] += self.clock() - ta
             self.peak_bytes = max(self.peak_bytes, self.pool.bytes_in_use)
             if not active:
                 if i < len(pending):
@@ -214,10 +224,14 @@ class Server:
                     if wait > 0:
                         time.sleep(min(wait, 0.05))
                 continue
+            ts = self.clock()
             self.pool.step(self.check_every)
             for item in active:
                 item[3] += self.check_every
             res = self.pool.residuals()
+            self.stats["step_s"] += self.clock() - ts
+            self.stats["steps"] += self.check_every
+            tr = self.clock()
             for item, (r, unorm) in zip(list(active), res):
                 req, s, adm, steps = item
                 per_step = r / self.check_every
@@ -236,6 +250,7 @@ class Server:
                     active.remove(item)
                     results.append(Result(req.rid, req.kind, int(np.prod(req.shape)), status, steps, float(per_step),
                                           req.arrival, adm, now()))
+            self.stats["retire_s"] += self.clock() - tr
         return results, fields
 
     def close(self):

@@ -21,6 +21,10 @@ def test_request_stream_matches_the_serving_workload():
         nx, ny, nz = r.shape
         assert 16 <= ny == nz <= 64 and ny <= nx <= 256 and nx * ny * nz <= 256 * 64 * 64
         assert 0.1 <= r.params["beta"] <= 0.9
+        eta_n = (1.0 - r.params["beta"]) * r.params["eta"]
+        assert eta_n >= 1.0 / 60.0 - 1e-12
+        if r.kind == "sedimenting":
+            assert abs(eta_n - 1.0 / 6.0) < 1e-12  # the paper's sphere runs keep eta_n
         assert 10.0 <= r.params["lambda_p"] <= 1e5
         assert 0 < r.max_steps <= 50000
         fl = r.flags
