@@ -76,6 +76,11 @@ __device__ __noinline__ R moving_wall_term(const Geo &g, const Phys<R> &ph, cons
 
 // Store post-collision f*_i with AA addressing; links into solid cells bounce back with
 // the moving-wall term of Eq. (ubb): f_-i(r, t+1) = f*_i(r) - 6 w_i rho c_i . u_b.
+// Every f*_i also goes to its normal destination, unconditionally: when r + c_i is
+// solid that slot belongs to the solid neighbour and is never read afterwards (even
+// step: slot -i of r holds f_i(r + c_i)), or is the one this thread itself read before
+// (odd step: slot i of r + c_i held the bounced population f_-i(r)).  The bounced value
+// is an extra store for the links into solid cells only.
 template <class S, int PAR>
 __device__ __forceinline__ void store_pdfs(const KArgs<S> &a, const Cell &cl, unsigned r, uint32_t mask,
                                            const typename Store<S>::R (&fs)[Q], typename Store<S>::R rho) {
@@ -85,11 +90,14 @@ __device__ __forceinline__ void store_pdfs(const KArgs<S> &a, const Cell &cl, un
     Store<S>::st(a.f + r, fs[0], sc);
 #pragma unroll
     for (int i = 1; i < Q; ++i) {
-        const unsigned nb = cl.idx(cx(i), cy(i), cz(i));
-        if (!nb_solid(mask, i)) {
-            S *p = PAR == 0 ? a.f + copp(i) * np + r : a.f + i * np + nb;
-            Store<S>::st(p, fs[i], sc);
-        } else {
+        S *p = PAR == 0 ? a.f + copp(i) * np + r : a.f + i * np + cl.idx(cx(i), cy(i), cz(i));
+        Store<S>::st(p, fs[i], sc);
+    }
+    if (mask & ~1u) {
+#pragma unroll
+        for (int i = 1; i < Q; ++i) {
+            if (!nb_solid(mask, i)) continue;
+            const unsigned nb = cl.idx(cx(i), cy(i), cz(i));
             R X = R(0);
             const int fl = a.flag[nb];
             if (fl != FLAG_NOSLIP) X = moving_wall_term<R>(a.g, a.ph, a.parts, fl, cl.X(cx(i)), cl.Y(cy(i)), cl.Z(cz(i)), i, rho);
