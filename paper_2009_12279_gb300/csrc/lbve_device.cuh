@@ -125,7 +125,10 @@ struct Cell {
 };
 
 // Neighbour mask of a cell: bit 0 set if the cell is not fluid, bit i (1..18) set if the
-// neighbour r + c_i is not fluid.  Faces of the D3Q7 set are directions 1..6.
+// neighbour r + c_i is not fluid, MASK_MOVING set if one of those neighbours is a wall
+// class or a particle cell (a boundary that may move, Eq. (ubb)) rather than a resting
+// no-slip wall.  Faces of the D3Q7 set are directions 1..6.
+constexpr uint32_t MASK_MOVING = 1u << 19;
 __device__ __forceinline__ bool nb_solid(uint32_t m, int i) { return (m >> i) & 1u; }
 
 // Boundary velocity u_b of the solid cell (xq, yq, zq) with flag fl: zero for a no-slip

@@ -21,6 +21,9 @@ namespace lbve {
 #ifndef LBVE_LB_MIN_BLOCKS
 #define LBVE_LB_MIN_BLOCKS 8
 #endif
+#ifndef LBVE_LB_MIN_BLOCKS_ODD
+#define LBVE_LB_MIN_BLOCKS_ODD LBVE_LB_MIN_BLOCKS
+#endif
 
 template <class S>
 struct KArgs {
@@ -87,22 +90,20 @@ __device__ __forceinline__ void store_pdfs(const KArgs<S> &a, const Cell &cl, un
     using R = typename Store<S>::R;
     const size_t np = (size_t)a.g.np;
     const R sc = a.ph.scale;
+    const bool moving = mask & MASK_MOVING;  // else every solid neighbour is a resting no-slip wall
     Store<S>::st(a.f + r, fs[0], sc);
 #pragma unroll
     for (int i = 1; i < Q; ++i) {
-        S *p = PAR == 0 ? a.f + copp(i) * np + r : a.f + i * np + cl.idx(cx(i), cy(i), cz(i));
-        Store<S>::st(p, fs[i], sc);
-    }
-    if (mask & ~1u) {
-#pragma unroll
-        for (int i = 1; i < Q; ++i) {
-            if (!nb_solid(mask, i)) continue;
-            const unsigned nb = cl.idx(cx(i), cy(i), cz(i));
+        const unsigned nb = cl.idx(cx(i), cy(i), cz(i));
+        Store<S>::st(PAR == 0 ? a.f + copp(i) * np + r : a.f + i * np + nb, fs[i], sc);
+        if (nb_solid(mask, i)) {
             R X = R(0);
-            const int fl = a.flag[nb];
-            if (fl != FLAG_NOSLIP) X = moving_wall_term<R>(a.g, a.ph, a.parts, fl, cl.X(cx(i)), cl.Y(cy(i)), cl.Z(cz(i)), i, rho);
-            S *p = PAR == 0 ? a.f + i * np + nb : a.f + copp(i) * np + r;
-            Store<S>::st(p, fs[i] - X, sc);
+            if (moving) {
+                const int fl = a.flag[nb];
+                if (fl != FLAG_NOSLIP)
+                    X = moving_wall_term<R>(a.g, a.ph, a.parts, fl, cl.X(cx(i)), cl.Y(cy(i)), cl.Z(cz(i)), i, rho);
+            }
+            Store<S>::st(PAR == 0 ? a.f + i * np + nb : a.f + copp(i) * np + r, fs[i] - X, sc);
         }
     }
 }
@@ -187,7 +188,7 @@ __device__ __forceinline__ void lb_cell_at(const KArgs<S> &a, int x, int y, int 
 }
 
 template <class S, int PAR>
-__global__ void __launch_bounds__(128, LBVE_LB_MIN_BLOCKS) k_lb(KArgs<S> a) {
+__global__ void __launch_bounds__(128, PAR ? LBVE_LB_MIN_BLOCKS_ODD : LBVE_LB_MIN_BLOCKS) k_lb(KArgs<S> a) {
     int x, y, z;
     if (!cell_of_thread(a.g, x, y, z)) return;
     lb_cell_at<S, PAR>(a, x, y, z);
@@ -231,7 +232,9 @@ __device__ __forceinline__ uint32_t cell_mask(const Geo &g, const uint8_t *__res
         const bool out = (!g.per[0] && (x + cx(i) < 0 || x + cx(i) >= g.nx)) ||
                          (!g.per[1] && (y + cy(i) < 0 || y + cy(i) >= g.ny)) ||
                          (!g.per[2] && (z + cz(i) < 0 || z + cz(i) >= g.nz));
-        if (out || flag[cl.idx(cx(i), cy(i), cz(i))] != FLAG_FLUID) m |= 1u << i;
+        const int fl = out ? FLAG_NOSLIP : flag[cl.idx(cx(i), cy(i), cz(i))];
+        if (fl != FLAG_FLUID) m |= 1u << i;
+        if (fl != FLAG_FLUID && fl != FLAG_NOSLIP) m |= MASK_MOVING;
     }
     return m;
 }
