@@ -163,15 +163,20 @@ __device__ __forceinline__ void boundary_velocity(const Geo &g, const Phys<R> &p
 // Boundary velocity with the common no-slip case inline and the moving-wall / particle
 // cases out of line (they are rare and would otherwise bloat every caller).
 template <class R>
-__device__ __noinline__ void boundary_velocity_slow(const Geo &g, const Phys<R> &ph, const PartDev *parts, int fl,
-                                                    int xq, int yq, int zq, R *ub) {
+struct Vec3 {
+    R x, y, z;
+};
+// Out-of-line wall-class / particle branch of boundary_velocity; the result comes back by
+// value so that callers keep their velocity arrays in registers.
+template <class R>
+__device__ __noinline__ Vec3<R> boundary_velocity_slow(const Geo &g, const Phys<R> &ph, const PartDev *parts, int fl,
+                                                       int xq, int yq, int zq) {
     R t[3];
     boundary_velocity<R>(g, ph, parts, fl, xq, yq, zq, t);
-    ub[0] = t[0];
-    ub[1] = t[1];
-    ub[2] = t[2];
+    return Vec3<R>{t[0], t[1], t[2]};
 }
 
+// boundary_velocity with the resting no-slip case inline.
 template <class R>
 __device__ __forceinline__ void boundary_velocity_fast(const Geo &g, const Phys<R> &ph, const PartDev *parts, int fl,
                                                        int xq, int yq, int zq, R ub[3]) {
@@ -180,7 +185,10 @@ __device__ __forceinline__ void boundary_velocity_fast(const Geo &g, const Phys<
         ub[1] = R(0);
         ub[2] = R(0);
     } else {
-        boundary_velocity_slow<R>(g, ph, parts, fl, xq, yq, zq, ub);
+        const Vec3<R> v = boundary_velocity_slow<R>(g, ph, parts, fl, xq, yq, zq);
+        ub[0] = v.x;
+        ub[1] = v.y;
+        ub[2] = v.z;
     }
 }
 
@@ -372,8 +380,11 @@ __device__ __forceinline__ void fv_core(const Phys<R> &ph, const R (&tr)[6], con
         if (!nb_solid(mask, l + 1)) {
 #pragma unroll
             for (int j = 0; j < 3; ++j) un[l][j] = nb.u(l, j);
-        } else {
+        } else if (mask & MASK_MOVING) {
             nb.ub(l, un[l]);
+        } else {  // a resting no-slip wall
+#pragma unroll
+            for (int j = 0; j < 3; ++j) un[l][j] = R(0);
         }
     }
     R G[3][3];

@@ -38,7 +38,20 @@ struct KArgs {
     const uint8_t *flag;
     const uint32_t *mask;
     const PartDev *parts;
+    // per-direction / per-component bases (f + i np, tau + c np, u_out + k np), so that an
+    // address is one multiply-add of a 32-bit cell index; set by link_dirs
+    S *fq[Q];
+    const R *tq[6];
+    R *uq[3];
 };
+
+template <class S>
+__host__ __device__ inline void link_dirs(KArgs<S> &a) {
+    const size_t np = (size_t)a.g.np;
+    for (int i = 0; i < Q; ++i) a.fq[i] = a.f + i * np;
+    for (int c = 0; c < 6; ++c) a.tq[c] = a.tau + c * np;
+    for (int k = 0; k < 3; ++k) a.uq[k] = a.u_out + k * np;
+}
 
 // Load f_i^t of cell r from its AA location for the given parity.
 template <class S, int PAR>
@@ -49,7 +62,7 @@ __device__ __forceinline__ void load_pdfs(const KArgs<S> &a, const Cell &cl, uns
     const R inv = a.ph.inv_scale;
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
-        const S *p = PAR == 0 ? a.f + i * np + r : a.f + copp(i) * np + cl.idx(-cx(i), -cy(i), -cz(i));
+        const S *p = PAR == 0 ? a.fq[i] + r : a.fq[copp(i)] + cl.idx(-cx(i), -cy(i), -cz(i));
         f[i] = Store<S>::ld(p, inv);
     }
 }
@@ -91,11 +104,11 @@ __device__ __forceinline__ void store_pdfs(const KArgs<S> &a, const Cell &cl, un
     const size_t np = (size_t)a.g.np;
     const R sc = a.ph.scale;
     const bool moving = mask & MASK_MOVING;  // else every solid neighbour is a resting no-slip wall
-    Store<S>::st(a.f + r, fs[0], sc);
+    Store<S>::st(a.fq[0] + r, fs[0], sc);
 #pragma unroll
     for (int i = 1; i < Q; ++i) {
         const unsigned nb = cl.idx(cx(i), cy(i), cz(i));
-        Store<S>::st(PAR == 0 ? a.f + copp(i) * np + r : a.f + i * np + nb, fs[i], sc);
+        Store<S>::st(PAR == 0 ? a.fq[copp(i)] + r : a.fq[i] + nb, fs[i], sc);
         if (nb_solid(mask, i)) {
             R X = R(0);
             if (moving) {
@@ -103,7 +116,7 @@ __device__ __forceinline__ void store_pdfs(const KArgs<S> &a, const Cell &cl, un
                 if (fl != FLAG_NOSLIP)
                     X = moving_wall_term<R>(a.g, a.ph, a.parts, fl, cl.X(cx(i)), cl.Y(cy(i)), cl.Z(cz(i)), i, rho);
             }
-            Store<S>::st(PAR == 0 ? a.f + i * np + nb : a.f + copp(i) * np + r, fs[i] - X, sc);
+            Store<S>::st(PAR == 0 ? a.fq[i] + nb : a.fq[copp(i)] + r, fs[i] - X, sc);
         }
     }
 }
@@ -125,7 +138,7 @@ __device__ __forceinline__ void lb_core(const KArgs<S> &a, const Cell &cl, unsig
     moments<R, SH>(f, F, a.ph.rho0, rho, drho, u);
     const size_t np = (size_t)a.g.np;
 #pragma unroll
-    for (int k = 0; k < 3; ++k) a.u_out[k * np + r] = u[k];
+    for (int k = 0; k < 3; ++k) a.uq[k][r] = u[k];
     collide<R, SH>(f, rho, drho, u, F, a.ph);
     store_pdfs<S, PAR>(a, cl, r, mask, f, rho);
 }
@@ -179,10 +192,10 @@ __device__ __forceinline__ void lb_cell_at(const KArgs<S> &a, int x, int y, int 
     const size_t np = (size_t)a.g.np;
     R tr[6];
 #pragma unroll
-    for (int c = 0; c < 6; ++c) tr[c] = a.tau[c * np + r];
+    for (int c = 0; c < 6; ++c) tr[c] = a.tq[c][r];
     auto tn = [&](int l, int c) -> R {
         const int k = l >> 1, s = (l & 1) ? -1 : 1;
-        return a.tau[c * np + cl.idx(k == 0 ? s : 0, k == 1 ? s : 0, k == 2 ? s : 0)];
+        return a.tq[c][cl.idx(k == 0 ? s : 0, k == 1 ? s : 0, k == 2 ? s : 0)];
     };
     lb_core<S, PAR>(a, cl, r, m, tr, tn);
 }
@@ -645,6 +658,7 @@ __device__ __forceinline__ void batch_args(KArgs<S> &a, const BatchEntry<S> &e, 
         a.tau = a.tau_out;
         a.tau_out = const_cast<typename Store<S>::R *>(t);
     }
+    link_dirs<S>(a);
 }
 
 template <class S>

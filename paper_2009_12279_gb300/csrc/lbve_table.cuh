@@ -47,6 +47,7 @@ struct Launch {
         a.flag = d.flag;
         a.mask = d.mask;
         a.parts = d.parts;
+        link_dirs<S>(a);
         return a;
     }
     // per-cell kernels: blocks of block_x x (128 / block_x) threads

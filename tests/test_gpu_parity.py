@@ -254,3 +254,38 @@ def test_fused_reduced_precision_matches_split(precision):
     for rho, u, tau, _ in res:
         assert rel_l2(u[:, fluid], uo[:, fluid]) <= tol
         assert rel_l2(tau[:, fluid], to[:, fluid]) <= tol
+
+
+# Ragged x and y tails of the 32 x 8 stress tiles and 32 x 4 stream-collide blocks with
+# 16-byte aligned rows, every periodicity, a 4-cell-wide domain
+@pytest.mark.parametrize("shape,periodic", [((36, 21, 19), (1, 1, 1)), ((44, 18, 27), (1, 0, 1)),
+                                            ((40, 10, 33), (0, 1, 0)), ((4, 6, 5), (1, 1, 1)),
+                                            ((68, 9, 12), (0, 0, 1))])
+def test_fp64_ragged_tiles_every_periodicity(shape, periodic):
+    prm, fl, u0, t0 = _fused_case(shape, periodic, 61)
+    g, o = pair(shape, prm, fl, u=u0, tau=t0, precision="f64")
+    for n in (1, 40, 59):
+        g.step(n)
+        o.step(n)
+    e = compare(g, o)
+    assert max(e["f"], e["u"], e["tau"]) <= TOL_F64, e
+
+
+def test_fp64_even_width_moving_wall_and_obstacle_class():
+    shape, prm, fl, wall, rho0, u0, t0 = _obstacle_case((44, 20, 18), seed=9)
+    g, o = pair(shape, prm, fl, wall, rho=rho0, u=u0, tau=t0, precision="f64")
+    g.step(150)
+    o.step(150)
+    e = compare(g, o)
+    assert max(e["f"], e["u"], e["tau"]) <= TOL_F64, e
+    bg, bo = g.body_forces(), o.body_forces()
+    assert np.linalg.norm(bg[2] - bo[2]) <= TOL_F64 * np.linalg.norm(bo[2])
+
+
+def test_fp32_even_width_obstacles_1000_steps():
+    shape, prm, fl, wall, rho0, u0, t0 = _obstacle_case((44, 20, 18), seed=5)
+    g, o = pair(shape, prm, fl, wall, rho=rho0, u=u0, tau=t0, precision="f32")
+    g.step(1000)
+    o.step(1000)
+    e = compare(g, o)
+    assert max(e["u"], e["tau"]) <= TOL_F32, e
