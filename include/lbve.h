@@ -50,7 +50,7 @@ typedef enum {
 } lbve_status;
 
 /* Storage precision of the PDFs (arithmetic is FP64 for LBVE_F64, else FP32).
- * All reduced modes store the deviation f_i - w_i rho0 (times 2^pdf_scale_log2). */
+ * All reduced modes store the deviation f_i - w_i rho0 (FP16: times 2^pdf_scale_log2). */
 typedef enum { LBVE_F64 = 0, LBVE_F32 = 1, LBVE_F16_SHIFTED = 2, LBVE_BF16_SHIFTED = 3 } lbve_pdf_prec;
 
 #define LBVE_FLAG_FLUID 0
@@ -85,7 +85,8 @@ typedef struct {
     double body_force[3];
     double magic;
     int pdf_prec;        /* lbve_pdf_prec */
-    int pdf_scale_log2;  /* storage scale 2^k of the shifted PDFs; -1 selects the default */
+    int pdf_scale_log2;  /* FP16 storage scale 2^k of the shifted PDFs (-1: k = 15); FP32
+                            and BF16 keep the FP32 exponent range and store unscaled */
     int fv_terms;        /* LBVE_FV_* bits; 0 selects both */
     int schedule;        /* LBVE_SCHED_* */
     int block_x;         /* per-cell kernels: threads per block along x (32, 64 or 128; blocks

@@ -180,9 +180,9 @@ void lbve::fill_phys(const lbve_params &p, Phys<double> &ph) {
     for (int k = 0; k < 3; ++k) ph.g[k] = p.body_force[k];
     ph.rho0 = p.pdf_prec == LBVE_F64 ? 0.0 : p.rho0;
     ph.rho_ref = p.rho0;
-    int k = p.pdf_scale_log2;
-    if (k < 0) k = p.pdf_prec == LBVE_F16_SHIFTED ? 15 : 0;
-    if (p.pdf_prec == LBVE_F64) k = 0;
+    // the storage scale only serves FP16 (5-bit exponent); FP32 and BF16 store unscaled
+    int k = p.pdf_scale_log2 < 0 ? 15 : p.pdf_scale_log2;
+    if (p.pdf_prec != LBVE_F16_SHIFTED) k = 0;
     ph.scale = std::ldexp(1.0, k);
     ph.inv_scale = std::ldexp(1.0, -k);
     const int terms = p.fv_terms == 0 ? (LBVE_FV_FLUX | LBVE_FV_SOURCE) : p.fv_terms;

@@ -77,8 +77,9 @@ template <>
 struct Store<float> {
     using R = float;
     static constexpr bool shifted = true;
-    __device__ static __forceinline__ float ld(const float *p, float inv) { return *p * inv; }
-    __device__ static __forceinline__ void st(float *p, float v, float sc) { *p = v * sc; }
+    // FP32 keeps its exponent range: stored unscaled (the scale argument is 1)
+    __device__ static __forceinline__ float ld(const float *p, float) { return *p; }
+    __device__ static __forceinline__ void st(float *p, float v, float) { *p = v; }
 };
 template <>
 struct Store<__half> {
@@ -91,12 +92,9 @@ template <>
 struct Store<__nv_bfloat16> {
     using R = float;
     static constexpr bool shifted = true;
-    __device__ static __forceinline__ float ld(const __nv_bfloat16 *p, float inv) {
-        return __bfloat162float(*p) * inv;
-    }
-    __device__ static __forceinline__ void st(__nv_bfloat16 *p, float v, float sc) {
-        *p = __float2bfloat16_rn(v * sc);
-    }
+    // BF16 has the FP32 exponent range: stored unscaled (the scale argument is 1)
+    __device__ static __forceinline__ float ld(const __nv_bfloat16 *p, float) { return __bfloat162float(*p); }
+    __device__ static __forceinline__ void st(__nv_bfloat16 *p, float v, float) { *p = __float2bfloat16_rn(v); }
 };
 
 // Coordinates of one cell and its periodically wrapped neighbours; cell indices are

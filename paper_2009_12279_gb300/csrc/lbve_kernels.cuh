@@ -21,6 +21,10 @@ namespace lbve {
 #ifndef LBVE_LB_MIN_BLOCKS
 #define LBVE_LB_MIN_BLOCKS 8
 #endif
+// 256-thread stress blocks, 3 resident per SM (80 registers: no spills at 4)
+#ifndef LBVE_FV_MIN_BLOCKS
+#define LBVE_FV_MIN_BLOCKS 3
+#endif
 #ifndef LBVE_LB_MIN_BLOCKS_ODD
 #define LBVE_LB_MIN_BLOCKS_ODD LBVE_LB_MIN_BLOCKS
 #endif
@@ -105,6 +109,16 @@ __device__ __forceinline__ void store_pdfs(const KArgs<S> &a, const Cell &cl, un
     const R sc = a.ph.scale;
     const bool moving = mask & MASK_MOVING;  // else every solid neighbour is a resting no-slip wall
     Store<S>::st(a.fq[0] + r, fs[0], sc);
+    if (!__any_sync(__activemask(), moving)) {
+        // no lane of the warp next to a moving boundary: bounce-back is a predicated store
+#pragma unroll
+        for (int i = 1; i < Q; ++i) {
+            const unsigned nb = cl.idx(cx(i), cy(i), cz(i));
+            Store<S>::st(PAR == 0 ? a.fq[copp(i)] + r : a.fq[i] + nb, fs[i], sc);
+            if (nb_solid(mask, i)) Store<S>::st(PAR == 0 ? a.fq[i] + nb : a.fq[copp(i)] + r, fs[i], sc);
+        }
+        return;
+    }
 #pragma unroll
     for (int i = 1; i < Q; ++i) {
         const unsigned nb = cl.idx(cx(i), cy(i), cz(i));
@@ -611,7 +625,7 @@ __device__ __forceinline__ void fv_tile(const KArgs<S> &a, FvSmem<typename Store
 }
 
 template <class S>
-__global__ void __launch_bounds__(FV_X * FV_Y, sizeof(typename Store<S>::R) == 8 ? 2 : 4) k_fv_tiled(KArgs<S> a, int zchunk) {
+__global__ void __launch_bounds__(FV_X * FV_Y, sizeof(typename Store<S>::R) == 8 ? 2 : LBVE_FV_MIN_BLOCKS) k_fv_tiled(KArgs<S> a, int zchunk) {
     using R = typename Store<S>::R;
     extern __shared__ __align__(16) unsigned char fv_smem_raw[];
     FvSmem<R> &sm = *reinterpret_cast<FvSmem<R> *>(fv_smem_raw);
@@ -693,7 +707,7 @@ __global__ void __launch_bounds__(BLB_X * BLB_Y, LBVE_LB_MIN_BLOCKS) k_lb_batche
 }
 
 template <class S>
-__global__ void __launch_bounds__(FV_X * FV_Y, sizeof(typename Store<S>::R) == 8 ? 2 : 4) k_fv_batched(
+__global__ void __launch_bounds__(FV_X * FV_Y, sizeof(typename Store<S>::R) == 8 ? 2 : LBVE_FV_MIN_BLOCKS) k_fv_batched(
     const BatchEntry<S> *__restrict__ e, int nsolves, int total, int k) {
     using R = typename Store<S>::R;
     extern __shared__ __align__(16) unsigned char fv_smem_raw[];

@@ -79,7 +79,7 @@ struct Launch {
         const long long tiles = (long long)((d.g.nx + FV_X - 1) / FV_X) * ((d.g.ny + FV_Y - 1) / FV_Y);
         int dev = 0, sms = 148;
         if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        const long long want = 16LL * 4 * sms;
+        const long long want = 16LL * LBVE_FV_MIN_BLOCKS * sms;  // ~16 waves of resident blocks
         const long long chunks = (want + tiles - 1) / tiles;
         long long zc = (d.g.nz + chunks - 1) / chunks;
         if (zc < 16) zc = 16;
