@@ -193,7 +193,7 @@ void lbve::fill_phys(const lbve_params &p, Phys<double> &ph) {
 bool lbve::params_valid(const lbve_params *p, std::string &why) { return valid_params(p, why); }
 
 int lbve::default_block_x(const lbve_params &p) {
-    int bx = p.block_x > 0 ? p.block_x : 32;
+    int bx = p.block_x > 0 ? p.block_x : 64;  // 64 x 2 measured ~1 % ahead of 32 x 4 at 512^3
     if (bx > 128) bx = 128;
     while (bx > 32 && bx / 2 >= p.nx) bx /= 2;
     return bx;

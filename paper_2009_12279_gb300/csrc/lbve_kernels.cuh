@@ -139,12 +139,11 @@ __device__ __forceinline__ void store_pdfs(const KArgs<S> &a, const Cell &cl, un
 // its face neighbours' stress (tau^t): F = g + F^p, moments, u^t written out, TRT
 // collision with forcing, AA streaming with bounce-back.
 template <class S, int PAR, class TauNb>
-__device__ __forceinline__ void lb_core(const KArgs<S> &a, const Cell &cl, unsigned r, uint32_t mask,
-                                        const typename Store<S>::R (&tr)[6], const TauNb &tn) {
+__device__ __forceinline__ void lb_core_f(const KArgs<S> &a, const Cell &cl, unsigned r, uint32_t mask,
+                                          const typename Store<S>::R (&tr)[6], const TauNb &tn,
+                                          typename Store<S>::R (&f)[Q]) {
     using R = typename Store<S>::R;
     constexpr bool SH = Store<S>::shifted;
-    R f[Q];
-    load_pdfs<S, PAR>(a, cl, r, f);
     R Fp[3], F[3], u[3], rho, drho;
     polymer_force_core<R>(tr, mask, tn, Fp);
 #pragma unroll
@@ -155,6 +154,13 @@ __device__ __forceinline__ void lb_core(const KArgs<S> &a, const Cell &cl, unsig
     for (int k = 0; k < 3; ++k) a.uq[k][r] = u[k];
     collide<R, SH>(f, rho, drho, u, F, a.ph);
     store_pdfs<S, PAR>(a, cl, r, mask, f, rho);
+}
+template <class S, int PAR, class TauNb>
+__device__ __forceinline__ void lb_core(const KArgs<S> &a, const Cell &cl, unsigned r, uint32_t mask,
+                                        const typename Store<S>::R (&tr)[6], const TauNb &tn) {
+    typename Store<S>::R f[Q];
+    load_pdfs<S, PAR>(a, cl, r, f);
+    lb_core_f<S, PAR>(a, cl, r, mask, tr, tn, f);
 }
 
 // Velocity / stress / boundary-velocity accessors of the face neighbours in global memory.
@@ -201,17 +207,19 @@ __device__ __forceinline__ void lb_cell_at(const KArgs<S> &a, int x, int y, int 
     using R = typename Store<S>::R;
     const Cell cl(a.g, x, y, z);
     const unsigned r = cl.self();
-    const uint32_t m = a.mask[r];
-    if (m & 1u) return;
-    const size_t np = (size_t)a.g.np;
-    R tr[6];
+    // the PDF and stress loads go out together with the mask (valid addresses for any
+    // cell), not one DRAM round trip after it
+    R f[Q], tr[6];
+    load_pdfs<S, PAR>(a, cl, r, f);
 #pragma unroll
     for (int c = 0; c < 6; ++c) tr[c] = a.tq[c][r];
+    const uint32_t m = a.mask[r];
+    if (m & 1u) return;
     auto tn = [&](int l, int c) -> R {
         const int k = l >> 1, s = (l & 1) ? -1 : 1;
         return a.tq[c][cl.idx(k == 0 ? s : 0, k == 1 ? s : 0, k == 2 ? s : 0)];
     };
-    lb_core<S, PAR>(a, cl, r, m, tr, tn);
+    lb_core_f<S, PAR>(a, cl, r, m, tr, tn, f);
 }
 
 template <class S, int PAR>
@@ -590,8 +598,12 @@ __device__ __forceinline__ void fv_tile(const KArgs<S> &a, FvSmem<typename Store
     stage(z0 - 1);
     stage(z0);
     stage(z0 + 1);
+    // the mask of the next plane is fetched one plane ahead
+    uint32_t m_next = own ? a.mask[(unsigned)x + nx * (unsigned)y + nxy * (unsigned)z0] : 1u;
 #pragma unroll 1
     for (int z = z0; z < z1; ++z) {
+        const uint32_t m = m_next;
+        if (own && z + 1 < z1) m_next = a.mask[(unsigned)x + nx * (unsigned)y + nxy * (unsigned)(z + 1)];
         // plane z + 2 is fetched while plane z is updated (an empty group keeps the count)
         if (z + 2 <= z1)
             stage(z + 2);
@@ -601,7 +613,6 @@ __device__ __forceinline__ void fv_tile(const KArgs<S> &a, FvSmem<typename Store
         __syncthreads();
         if (own) {
             const unsigned r = (unsigned)x + nx * (unsigned)y + nxy * (unsigned)z;
-            const uint32_t m = a.mask[r];
             R out[6];
             if (m & 1u) {
 #pragma unroll
