@@ -516,10 +516,18 @@ __global__ void __launch_bounds__(FT_X * FT_Y, sizeof(typename Store<S>::R) == 8
 constexpr int FV_X = 32, FV_Y = 8;
 constexpr int FVH_X = FV_X + 2, FVH_Y = FV_Y + 2, FVH_N = FVH_X * FVH_Y;
 
+// planes fetched beyond z + 1 while plane z is updated; the ring holds z - 1, z, z + 1
+// and those
+#ifndef LBVE_FV_AHEAD
+#define LBVE_FV_AHEAD 1
+#endif
+constexpr int FV_RING = LBVE_FV_AHEAD + 3;
+__device__ __forceinline__ int fv_slot(int z) { return ((z % FV_RING) + FV_RING) % FV_RING; }
+
 template <class R>
 struct FvSmem {
-    R tau[4][6][FVH_N];
-    R u[4][3][FVH_N];
+    R tau[FV_RING][6][FVH_N];
+    R u[FV_RING][3][FVH_N];
 };
 
 template <class S>
@@ -571,7 +579,7 @@ __device__ __forceinline__ void fv_tile(const KArgs<S> &a, FvSmem<typename Store
     }
     auto stage = [&](int zz) {
         const int zg = side_coord(zz, a.g.nz, a.g.per[2]);
-        const int s4 = ring4(zz);
+        const int s4 = fv_slot(zz);
 #pragma unroll
         for (int q = 0; q < 2; ++q) {
             const int k = tid + q * NT;
@@ -595,21 +603,22 @@ __device__ __forceinline__ void fv_tile(const KArgs<S> &a, FvSmem<typename Store
     const int x = x0 + ti, y = y0 + tj;
     const int kc = (ti + 1) + (tj + 1) * FVH_X;
     const bool own = x < a.g.nx && y < a.g.ny;
-    stage(z0 - 1);
-    stage(z0);
-    stage(z0 + 1);
+#pragma unroll
+    for (int q = -1; q <= LBVE_FV_AHEAD; ++q) stage(z0 + q);
     // the mask of the next plane is fetched one plane ahead
     uint32_t m_next = own ? a.mask[(unsigned)x + nx * (unsigned)y + nxy * (unsigned)z0] : 1u;
 #pragma unroll 1
     for (int z = z0; z < z1; ++z) {
         const uint32_t m = m_next;
         if (own && z + 1 < z1) m_next = a.mask[(unsigned)x + nx * (unsigned)y + nxy * (unsigned)(z + 1)];
-        // plane z + 2 is fetched while plane z is updated (an empty group keeps the count)
-        if (z + 2 <= z1)
-            stage(z + 2);
+        // plane z + 1 + AHEAD is fetched while plane z is updated (an empty group keeps
+        // the count); it goes to the slot of plane z - 2, free since the barrier that
+        // ended the previous plane; planes up to z + 1 have landed
+        if (z + 1 + LBVE_FV_AHEAD <= z1)
+            stage(z + 1 + LBVE_FV_AHEAD);
         else
             cp_async_commit();
-        asm volatile("cp.async.wait_group 1;\n" ::: "memory");
+        asm volatile("cp.async.wait_group %0;\n" ::"n"(LBVE_FV_AHEAD) : "memory");
         __syncthreads();
         if (own) {
             const unsigned r = (unsigned)x + nx * (unsigned)y + nxy * (unsigned)z;
@@ -618,7 +627,7 @@ __device__ __forceinline__ void fv_tile(const KArgs<S> &a, FvSmem<typename Store
 #pragma unroll
                 for (int c = 0; c < 6; ++c) out[c] = R(0);
             } else {
-                const int sc = ring4(z), sd = ring4(z - 1), su = ring4(z + 1);
+                const int sc = fv_slot(z), sd = fv_slot(z - 1), su = fv_slot(z + 1);
                 R tr[6], ur[3];
 #pragma unroll
                 for (int c = 0; c < 6; ++c) tr[c] = sm.tau[sc][c][kc];
