@@ -428,15 +428,32 @@ def run_ours(args):
     return 0
 
 
+# Sources whose kernels the traffic record was measured on; any change to them makes the
+# record stale (traffic is then reported as null until it is captured again).
+KERNEL_SOURCES = ("lbve_device.cuh", "lbve_kernels.cuh", "lbve_table.cuh", "lbve_launch.h")
+
+
+def kernel_sources_sha():
+    import hashlib
+
+    h = hashlib.sha256()
+    for name in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, "paper_2009_12279_gb300", "csrc", name), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()
+
+
 def load_traffic(prec, kernel, schedule):
-    """DRAM bytes per launch of the dominant kernel from the committed ncu summary, if the
-    summary matches this kernel build; else None."""
+    """DRAM bytes per launch of the dominant kernel from the committed ncu summary, if it
+    was captured on these kernel sources; else None."""
     path = os.path.join(ROOT, "profiles", "traffic.json")
     try:
         with open(path) as f:
             d = json.load(f)
-        rec = d.get(f"{kernel}:{prec}")
-        return rec["dram_bytes_per_launch_full_size"] if rec and rec.get("current", False) else None
+        rec = d.get("kernels", {}).get(f"{kernel}:{prec}")
+        if not rec or d.get("kernel_sources_sha256") != kernel_sources_sha():
+            return None
+        return rec["dram_bytes_per_launch_full_size"]
     except Exception:
         return None
 
