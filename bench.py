@@ -4,7 +4,7 @@
 Workload (default): the single-large-domain throughput case, a 512^3 periodic box with
 1 % seeded Bernoulli obstacles, u ~ U(-1e-3, 1e-3), zero stress, beta = 0.5,
 lambda = 1000, eta = 1/6.  One "step" is one time step of the whole coupled method over
-the whole domain.  The state (~18 GB in FP32 storage) is far larger than L2, so no
+the whole domain.  The state (~20 GB in FP32 storage) is far larger than L2, so no
 flush is needed between steps.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
