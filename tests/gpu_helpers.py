@@ -62,3 +62,29 @@ def compare(g, o, fluid=None):
         "u": rel_l2(ug[:, fluid], uo[:, fluid]),
         "tau": rel_l2(tg[:, fluid], to[:, fluid]),
     }
+
+
+def oracle_subbox_centre(params, flags_sub, u_sub, steps):
+    """The oracle's (19 PDFs, rho, u, tau) after `steps` steps at the centre of a periodic
+    sub-box (side 2M + 1, flags (z, y, x), u (3, z, y, x)) cut around one cell of a larger
+    periodic solve.  A cell depends only on cells within 2 per step, so for M > 2 steps the
+    centre equals that cell of the full solve."""
+    from oracle import oracle
+
+    side = flags_sub.shape[0]
+    M = side // 2
+    o = oracle.Oracle((side, side, side), **oracle_kwargs(params))
+    o.set_flags(flags_sub)
+    o.init_fields(u=u_sub)
+    o.step(steps)
+    rho, u, tau, fl = o.read_fields()
+    f = o.read_pdfs()
+    o.close()
+    c = M + side * (M + side * M)
+    out = np.zeros(29)
+    out[:19] = f.reshape(19, -1)[:, c]
+    if fl.reshape(-1)[c] == 0:
+        out[19] = rho.reshape(-1)[c]
+        out[20:23] = u.reshape(3, -1)[:, c]
+        out[23:29] = tau.reshape(6, -1)[:, c]
+    return out

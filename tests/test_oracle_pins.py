@@ -607,3 +607,56 @@ def test_created_cell_shares_uniform_stress_equally(oracle_mod):
                 assert np.allclose(tau1[(slice(None),) + nb], tau1[(slice(None),) + c], rtol=1e-14, atol=0)
                 checked += 1
     assert checked > 0
+
+
+def test_subbox_centre_equals_full_periodic_solve():
+    """Locality that the full-size GPU parity test relies on: after T steps the centre of a
+    periodic sub-box of side 2M + 1 (M = 2T + 2) cut around a cell equals that cell of the
+    full periodic solve, obstacles and wrap-around included."""
+    from gpu_helpers import oracle_kwargs, oracle_subbox_centre
+
+    from oracle import oracle
+    from paper_2009_12279_gb300 import workloads
+
+    n, T = 40, 3
+    M = 2 * T + 2
+    side = 2 * M + 1
+    cfg = workloads.config_throughput(n, obstacle_fraction=0.05)
+    cfg["params"]["body_force"] = (1e-5, -2e-6, 0.0)
+    flags = cfg["flags_fn"]()
+    u = workloads.random_velocity((n, n, n), 1e-3, 5)
+    tau = workloads.random_stress((n, n, n), 1e-5, 6)
+    full = oracle.Oracle((n, n, n), **oracle_kwargs(cfg["params"]))
+    full.set_flags(flags)
+    full.init_fields(u=u, tau=tau)
+    full.step(T)
+    _, uf, tf, _ = full.read_fields()
+    ff = full.read_pdfs()
+    rng = np.random.default_rng(3)
+    off = np.arange(-M, M + 1)
+    cells = [(0, 0, 0), (n - 1, 5, 0)] + [tuple(int(v) for v in rng.integers(0, n, 3)) for _ in range(6)]
+    for x, y, z in cells:
+        xi, yi, zi = (x + off) % n, (y + off) % n, (z + off) % n
+        o = oracle.Oracle((side, side, side), **oracle_kwargs(cfg["params"]))
+        o.set_flags(flags[np.ix_(zi, yi, xi)])
+        o.init_fields(u=u[:, zi][:, :, yi][:, :, :, xi], tau=tau[:, zi][:, :, yi][:, :, :, xi])
+        o.step(T)
+        c = M + side * (M + side * M)
+        r = x + n * (y + n * z)
+        assert np.array_equal(o.read_pdfs().reshape(19, -1)[:, c], ff.reshape(19, -1)[:, r])
+        _, uo, to, _ = o.read_fields()
+        assert np.array_equal(uo.reshape(3, -1)[:, c], uf.reshape(3, -1)[:, r])
+        assert np.array_equal(to.reshape(6, -1)[:, c], tf.reshape(6, -1)[:, r])
+        o.close()
+    # the helper the GPU test uses (zero initial stress) gives the same centre
+    x, y, z = 7, 33, 20
+    xi, yi, zi = (x + off) % n, (y + off) % n, (z + off) % n
+    full2 = oracle.Oracle((n, n, n), **oracle_kwargs(cfg["params"]))
+    full2.set_flags(flags)
+    full2.init_fields(u=u)
+    full2.step(T)
+    got = oracle_subbox_centre(cfg["params"], flags[np.ix_(zi, yi, xi)], u[:, zi][:, :, yi][:, :, :, xi], T)
+    r = x + n * (y + n * z)
+    assert np.array_equal(got[:19], full2.read_pdfs().reshape(19, -1)[:, r])
+    _, u2, _, _ = full2.read_fields()
+    assert np.array_equal(got[20:23], u2.reshape(3, -1)[:, r])
