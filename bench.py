@@ -29,6 +29,7 @@ sys.path.insert(0, ROOT)
 METRIC = "coupled LB+Oldroyd-B MLUPS (512^3 throughput workload)"
 UNIT = "MLUPS"
 HBM_FALLBACK_GBS = 6800.0
+HBM_NOMINAL_GBS = 8000.0  # GB300 HBM3e, nominal
 
 # Algorithmic bytes per cell update of the whole step: each PDF and stress value read
 # once and written once, plus the flag byte (FP32 stress in the reduced-precision modes).
@@ -137,7 +138,8 @@ def cores_used():
     return min(n, int(omp)) if omp else n
 
 
-def cpu_baseline(target_s=15.0, side=64):
+def oracle_rate(target_s, side):
+    """(MLUPS, steps, seconds) of the oracle on a side^3 sample, about target_s of work."""
     o = oracle_sample(side)
     t0 = time.perf_counter()
     o.step(1)
@@ -146,10 +148,26 @@ def cpu_baseline(target_s=15.0, side=64):
     t0 = time.perf_counter()
     o.step(steps)
     dt = time.perf_counter() - t0
-    mlups = side ** 3 * steps / dt / 1e6
-    return {"value": mlups, "unit": UNIT, "cores": cores_used(), "kind": "oracle",
-            "sample": f"{side}^3 periodic box of the same workload (1% obstacles, random u), {steps} steps, FP64, "
-                      f"{dt:.1f} s"}
+    return side ** 3 * steps / dt / 1e6, steps, dt
+
+
+def cpu_baseline(target_s=15.0, side=64):
+    mlups, steps, dt = oracle_rate(target_s, side)
+    out = {"value": mlups, "unit": UNIT, "cores": cores_used(), "kind": "oracle",
+           "sample": f"{side}^3 periodic box of the same workload (1% obstacles, random u), {steps} steps, FP64, "
+                     f"{dt:.1f} s"}
+    # the same oracle on one thread (a separate process with OMP_NUM_THREADS=1), 32^3 sample
+    code = ("import json, sys; sys.path.insert(0, %r); import bench; "
+            "print(json.dumps(bench.oracle_rate(5.0, 32)))" % ROOT)
+    env = dict(os.environ, OMP_NUM_THREADS="1")
+    try:
+        r = subprocess.run([sys.executable, "-c", code], env=env, capture_output=True, text=True, timeout=120)
+        m1, steps1, dt1 = json.loads(r.stdout.strip().splitlines()[-1])
+        out["single_thread"] = {"value": m1, "unit": UNIT, "cores": 1,
+                                "sample": f"32^3 box of the same workload, {steps1} steps, {dt1:.1f} s"}
+    except Exception as exc:  # reported, not fatal: the multi-core figure stands
+        out["single_thread"] = {"error": str(exc)[:200]}
+    return out
 
 
 def run_reference(args):
@@ -185,7 +203,10 @@ def build_solver(n, prec, schedule, stream, torch):
     cfg = workloads.config_throughput(n)
     sched = {"auto": lbve.SCHED_AUTO, "split": lbve.SCHED_SPLIT, "fused": lbve.SCHED_FUSED}[schedule]
     s = Solver(cfg["shape"], precision=prec, schedule=sched, stream=stream, **cfg["params"])
-    s.set_geometry(cfg["flags_fn"]())
+    flags = cfg["flags_fn"]()
+    cfg["fluid_cells"] = int((flags == 0).sum())
+    s.set_geometry(flags)
+    del flags
     # initial velocity drawn on the device (seeded) to keep host memory small
     g = torch.Generator(device="cuda")
     g.manual_seed(1)
@@ -373,6 +394,7 @@ def run_ours(args):
         ms_max = float(t.item())
         cells = n ** 3
         mlups = world * cells * args.steps / (ms_max * 1e-3) / 1e6
+        fluid_fraction = cfg["fluid_cells"] / cells
         dom = max(kt.items(), key=lambda kv: kv[1][0])
         kind, (kms, klaunch) = dom
         kb = kernel_bytes(kind, prec)
@@ -381,6 +403,8 @@ def run_ours(args):
         results[prec] = {
             "mlups": mlups, "ms_per_step": ms_max / args.steps,
             "step_roofline_frac": mlups * 1e6 * step_bytes(prec) / (peak * 1e9),
+            "step_roofline_frac_nominal": mlups * 1e6 * step_bytes(prec) / (HBM_NOMINAL_GBS * 1e9),
+            "fluid_mlups": mlups * fluid_fraction,
             "step_bytes_per_cell": step_bytes(prec),
             "kernels": {k: {"avg_ms": v[0] / max(v[1], 1), "launches": v[1],
                             "achieved_gbs": (kernel_bytes(k, prec) * cells * v[1] / (v[0] * 1e-3) / 1e9)
@@ -413,6 +437,8 @@ def run_ours(args):
                        "step_bytes_per_cell": main["step_bytes_per_cell"]},
             "roofline": main["roofline"],
             "step_roofline_frac": main["step_roofline_frac"],
+            "step_roofline_frac_nominal": main["step_roofline_frac_nominal"],
+            "fluid_mlups": main["fluid_mlups"],
             "gpu_launches": main["gpu_launches"],
             "clocks": clocks,
             "e2e": e2e,

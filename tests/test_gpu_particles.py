@@ -133,3 +133,52 @@ def test_add_particle_validation():
     assert pid == 0
     _, _, _, fl = s.read_fields()
     assert (fl == 64).sum() > 0
+
+
+def _three_spheres_case():
+    """Several moving spheres in one solve: a ragged box, walls in y (bottom resting, top a
+    moving lid class), periodic in x and z; the spheres differ in size, density and motion,
+    one of them straddles the periodic x boundary, none come within reach of another."""
+    from paper_2009_12279_gb300 import workloads
+
+    shape = (44, 22, 19)
+    fl = workloads.channel_flags(shape, 1, top_flag=workloads.WALL0)
+    prm = dict(periodic=(1, 0, 1), eta=1.0 / 6.0, beta=0.4, lambda_p=80.0, body_force=(2e-6, 0.0, 0.0))
+    u0 = workloads.random_velocity(shape, 1e-3, 31) * (fl == 0)
+    t0 = workloads.random_stress(shape, 1e-5, 32) * (fl == 0)
+    parts = [dict(X=(14.3, 10.4, 9.1), R=3.2, rho_p=1.3, v=(0.02, 0.004, -0.01), w=(1e-3, 0.0, -2e-3),
+                  Fext=(1e-3, 0.0, 0.0), Text=(0.0, 0.0, 1e-3)),
+             dict(X=(28.6, 11.2, 4.8), R=2.7, rho_p=2.0, v=(-0.015, -0.006, 0.012), w=(0.0, 2e-3, 0.0),
+                  Fext=(0.0, -1e-3, 0.0), Text=(0.0, 0.0, 0.0)),
+             dict(X=(43.2, 10.8, 13.3), R=3.0, rho_p=1.1, v=(0.025, 0.0, 0.006), w=(-1e-3, 1e-3, 1e-3),
+                  Fext=(0.0, 0.0, 5e-4), Text=(1e-3, 0.0, 0.0))]
+    return shape, prm, fl, u0, t0, parts
+
+
+@pytest.mark.parametrize("precision,tol", [("f64", TOL_F64), ("f32", TOL_F32)])
+def test_three_moving_spheres_parity(precision, tol):
+    shape, prm, fl, u0, t0, parts = _three_spheres_case()
+    wall = [(3e-3, 0.0, 1e-3)]
+    g, o = pair(shape, prm, fl, wall, precision=precision)
+    for p in parts:
+        assert _add(g, p) == _add(o, p)
+    flags0 = g.read_fields()[3]
+    assert (flags0[:, :, 0] == 66).any() and (flags0[:, :, -1] == 66).any()  # sphere 2 wraps in x
+    g.init_fields(u=u0, tau=t0)
+    o.init_fields(u=u0, tau=t0)
+    for _ in range(6):
+        g.step(25)
+        o.step(25)
+        for k in range(len(parts)):
+            pg, po = g.read_particle(k), o.read_particle(k)
+            assert _particle_err(pg, po) <= tol, (k, pg, po)
+    e = compare(g, o)
+    assert max(e["u"], e["tau"]) <= tol, e
+    if precision == "f64":
+        assert e["f"] <= tol
+    cg, co = g.conversions(), o.diag()
+    assert cg["created"] == co["created"] and cg["destroyed"] == co["destroyed"]
+    assert co["created"] > 15 and co["destroyed"] > 15
+    bg, bo = g.body_forces(), o.body_forces()
+    for k in [2] + [64 + p for p in range(len(parts))]:
+        assert np.linalg.norm(bg[k] - bo[k]) <= max(tol, 1e-9) * np.linalg.norm(bo[k]) * 10, (k, bg[k], bo[k])
