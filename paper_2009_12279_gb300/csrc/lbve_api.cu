@@ -217,11 +217,8 @@ __global__ void k_body_reduce(const double *__restrict__ contrib, const int *__r
     __shared__ double sh[6][256];
     double acc[6] = {0, 0, 0, 0, 0, 0};
     const int T = blockDim.x;
-    const int len = end - beg;
-    const int chunk = (len + T - 1) / T;
-    const int lo = beg + (int)threadIdx.x * chunk;
-    const int hi = min(end, lo + chunk);
-    for (int l = lo; l < hi; ++l)
+    // thread t sums links beg + t, beg + t + T, ... (coalesced; one thread: link order)
+    for (int l = beg + (int)threadIdx.x; l < end; l += T)
         for (int k = 0; k < 6; ++k) acc[k] += contrib[(long long)l * 8 + k];
     for (int k = 0; k < 6; ++k) sh[k][threadIdx.x] = acc[k];
     __syncthreads();
@@ -1004,6 +1001,13 @@ struct lbve_pool {
     bool use_graphs = true;
     cudaGraphExec_t graph[2] = {nullptr, nullptr};
     int graph_steps[2] = {0, 0};
+    // side streams: the members' small per-step kernels (momentum exchange, body sums,
+    // particle update, fill/drain, links) touch only their own buffers, so the chains of
+    // different members run side by side, forked from and joined back to the pool stream
+    static constexpr int kSide = 8;
+    cudaStream_t side[kSide] = {};
+    cudaEvent_t ev_fork = nullptr, ev_join[kSide] = {};
+    bool side_ready = false;
 };
 
 namespace {
@@ -1065,38 +1069,81 @@ lbve_status build_entries(lbve_pool *P) {
     return LBVE_OK;
 }
 
+lbve_status ensure_side_streams(lbve_pool *P) {
+    if (P->side_ready) return LBVE_OK;
+    PCK(cudaEventCreateWithFlags(&P->ev_fork, cudaEventDisableTiming), "side event");
+    for (int j = 0; j < lbve_pool::kSide; ++j) {
+        PCK(cudaStreamCreateWithFlags(&P->side[j], cudaStreamNonBlocking), "side stream");
+        PCK(cudaEventCreateWithFlags(&P->ev_join[j], cudaEventDisableTiming), "side event");
+    }
+    P->side_ready = true;
+    return LBVE_OK;
+}
+
+// Run body(member, stream) for every listed member: on the pool stream when there is one
+// member, else spread over the side streams between a fork and a join on the pool stream.
+template <class Body>
+lbve_status fan_out(lbve_pool *P, const std::vector<lbve_ctx *> &list, Body &&body) {
+    const int ns = std::min<int>(lbve_pool::kSide, (int)list.size());
+    if (ns <= 1 || !P->side_ready) {
+        for (lbve_ctx *c : list) {
+            lbve_status s = body(c, P->stream);
+            if (s != LBVE_OK) return s;
+        }
+        return LBVE_OK;
+    }
+    PCK(cudaEventRecord(P->ev_fork, P->stream), "fork");
+    for (int j = 0; j < ns; ++j) PCK(cudaStreamWaitEvent(P->side[j], P->ev_fork, 0), "fork wait");
+    for (size_t i = 0; i < list.size(); ++i) {
+        lbve_status s = body(list[i], P->side[i % ns]);
+        if (s != LBVE_OK) return s;
+    }
+    for (int j = 0; j < ns; ++j) {
+        PCK(cudaEventRecord(P->ev_join[j], P->side[j]), "join");
+        PCK(cudaStreamWaitEvent(P->stream, P->ev_join[j], 0), "join wait");
+    }
+    return LBVE_OK;
+}
+
 // Enqueue nsteps steps of every member on the pool stream (graph-capturable).
 lbve_status enqueue_steps(lbve_pool *P, int q, int nsteps) {
     const int n = (int)P->members.size();
+    std::vector<lbve_ctx *> with_bodies, with_parts;
+    for (lbve_ctx *c : P->members) {
+        if (c->nbody > 0) with_bodies.push_back(c);
+        if (c->nparts > 0) with_parts.push_back(c);
+    }
     for (int k = 0; k < nsteps; ++k) {
         const int kk = q + k;  // steps since the entries were built (they encode that state)
-        for (lbve_ctx *c : P->members) {
-            if (c->nbody == 0) continue;
-            DevState d = c->d;    // the member's state at the start of this call
+        lbve_status s = fan_out(P, with_bodies, [&](lbve_ctx *c, cudaStream_t st) -> lbve_status {
+            DevState d = c->d;  // the member's state at the start of this call
             if (k & 1) d.cur ^= 1;
             const int parity = (int)((c->t + k) & 1);
             PCK(c->kt->momentum_exchange(d, parity, c->links, c->seg_begin, c->seg_count, c->nbody, c->max_seg_len,
-                                         c->contrib, P->stream),
+                                         c->contrib, st),
                 "pool momentum exchange");
             const int threads = c->p.pdf_prec == LBVE_F64 ? 1 : 256;
-            k_body_reduce<<<c->nbody, threads, 0, P->stream>>>(c->contrib, c->seg_begin, c->seg_count, c->seg_flag,
-                                                               c->nbody, c->body_F, d.parts);
+            k_body_reduce<<<c->nbody, threads, 0, st>>>(c->contrib, c->seg_begin, c->seg_count, c->seg_flag, c->nbody,
+                                                        c->body_F, d.parts);
             PCK(cudaGetLastError(), "pool body reduce");
-        }
+            return LBVE_OK;
+        });
+        if (s != LBVE_OK) return s;
         PCK(P->kt->lb_batched(P->entries[0], n, P->total_lb, kk, P->grid_lb, P->stream), "batched lb");
         PCK(P->kt->fv_batched(P->entries[0], n, P->total_fv, kk, P->grid_fv, P->stream), "batched fv");
-        for (lbve_ctx *c : P->members) {
-            if (c->nparts == 0) continue;
+        s = fan_out(P, with_parts, [&](lbve_ctx *c, cudaStream_t st) -> lbve_status {
             DevState d = c->d;
             if ((k + 1) & 1) d.cur ^= 1;  // after the stress swap of this step
             const int parity_next = (int)((c->t + k + 1) & 1);
-            PCK(c->kt->particle_update(d, c->nparts, P->stream), "pool particle update");
-            PCK(c->kt->fill_drain(d, parity_next, c->nparts, c->pkind, c->pnf, c->pdelta, c->pconv, c->pdiag, P->stream),
+            PCK(c->kt->particle_update(d, c->nparts, st), "pool particle update");
+            PCK(c->kt->fill_drain(d, parity_next, c->nparts, c->pkind, c->pnf, c->pdelta, c->pconv, c->pdiag, st),
                 "pool fill/drain");
             PCK(c->kt->particle_links(d, c->nparts, c->links, c->seg_begin, c->seg_count,
-                                      (int)c->wall_seg_begin.size(), c->part_cap, P->stream),
+                                      (int)c->wall_seg_begin.size(), c->part_cap, st),
                 "pool particle links");
-        }
+            return LBVE_OK;
+        });
+        if (s != LBVE_OK) return s;
     }
     return LBVE_OK;
 }
@@ -1124,6 +1171,14 @@ lbve_status lbve_pool_destroy(lbve_pool *P) {
     if (!P) return LBVE_EINVAL;
     cudaStreamSynchronize(P->stream);
     drop_graphs(P);
+    if (P->side_ready) {
+        for (int j = 0; j < lbve_pool::kSide; ++j) {
+            cudaStreamSynchronize(P->side[j]);
+            cudaStreamDestroy(P->side[j]);
+            cudaEventDestroy(P->ev_join[j]);
+        }
+        cudaEventDestroy(P->ev_fork);
+    }
     for (int k = 0; k < 2; ++k)
         if (P->entries[k]) cudaFree(P->entries[k]);
     if (P->res_dev) cudaFree(P->res_dev);
@@ -1174,6 +1229,10 @@ lbve_status lbve_pool_step(lbve_pool *P, int nsteps) {
     if (nsteps == 0 || P->members.empty()) return LBVE_OK;
     if (P->dirty) {
         lbve_status s = build_entries(P);
+        if (s != LBVE_OK) return s;
+    }
+    {
+        lbve_status s = ensure_side_streams(P);
         if (s != LBVE_OK) return s;
     }
     const int q = (int)(P->steps_since_build & 1);
