@@ -25,6 +25,9 @@ namespace lbve {
 #ifndef LBVE_FV_MIN_BLOCKS
 #define LBVE_FV_MIN_BLOCKS 3
 #endif
+#ifndef LBVE_LBB_MIN_BLOCKS  // batched stream-collide (both parities in one kernel)
+#define LBVE_LBB_MIN_BLOCKS 8
+#endif
 #ifndef LBVE_LB_MIN_BLOCKS_ODD
 #define LBVE_LB_MIN_BLOCKS_ODD LBVE_LB_MIN_BLOCKS
 #endif
@@ -662,8 +665,9 @@ constexpr int BLB_X = 32, BLB_Y = 4;  // cells per stream-collide work item
 
 template <class S>
 struct BatchEntry {
-    KArgs<S> a;      // at the first step of the launch sequence
-    int parity0;     // parity of that step
+    KArgs<S> a[2];   // arguments for even / odd steps k of a launch sequence (k odd swaps
+                     // the stress / velocity ping-pong), pointers linked on the host
+    int parity0;     // AA parity at k = 0
     int lb_first, lb_items;
     int fv_first, fv_items, fv_zchunk;
 };
@@ -683,42 +687,41 @@ __device__ __forceinline__ int batch_find(const BatchEntry<S> *__restrict__ e, i
     return lo;
 }
 
-// step k of a launch sequence flips the stress / velocity ping-pong and the AA parity
+// Cooperative copy of a solve's arguments for step k into shared memory (all threads).
 template <class S>
-__device__ __forceinline__ void batch_args(KArgs<S> &a, const BatchEntry<S> &e, int k) {
-    a = e.a;
-    if (k & 1) {
-        const auto *t = a.tau;
-        a.tau = a.tau_out;
-        a.tau_out = const_cast<typename Store<S>::R *>(t);
-    }
-    link_dirs<S>(a);
+__device__ __forceinline__ void batch_load(KArgs<S> &sa, const BatchEntry<S> &e, int k, int tid, int nt) {
+    static_assert(sizeof(KArgs<S>) % 4 == 0, "argument block copied as words");
+    const int *src = reinterpret_cast<const int *>(&e.a[k & 1]);
+    int *dst = reinterpret_cast<int *>(&sa);
+    for (int w = tid; w < (int)(sizeof(KArgs<S>) / 4); w += nt) dst[w] = src[w];
 }
 
 template <class S>
-__global__ void __launch_bounds__(BLB_X * BLB_Y, LBVE_LB_MIN_BLOCKS) k_lb_batched(const BatchEntry<S> *__restrict__ e,
+__global__ void __launch_bounds__(BLB_X * BLB_Y, LBVE_LBB_MIN_BLOCKS) k_lb_batched(const BatchEntry<S> *__restrict__ e,
                                                                                  int nsolves, int total, int k) {
     __shared__ KArgs<S> sa;
-    __shared__ int s_parity, s_solve;
-    if (threadIdx.x == 0 && threadIdx.y == 0) s_solve = -1;
-    __syncthreads();
+    const int tid = threadIdx.x + BLB_X * threadIdx.y;
+    // items blockIdx.x, + gridDim.x, ...: the resident blocks sweep neighbouring tiles
+    // together (halos shared through L2); a block's items only increase, so its solve
+    // advances by a forward scan
+    if ((int)blockIdx.x >= total) return;
+    int sv = batch_find<S>(e, nsolves, blockIdx.x, false), end = -1, first = 0, parity = 0;
     for (int it = blockIdx.x; it < total; it += gridDim.x) {
-        const int sv = batch_find<S>(e, nsolves, it, false);
-        if (sv != s_solve) {
-            __syncthreads();
-            if (threadIdx.x == 0 && threadIdx.y == 0) {
-                batch_args<S>(sa, e[sv], k);
-                s_parity = (e[sv].parity0 + k) & 1;
-                s_solve = sv;
-            }
+        if (it >= end) {
+            while (it >= e[sv].lb_first + e[sv].lb_items) ++sv;
+            first = e[sv].lb_first;
+            end = first + e[sv].lb_items;
+            parity = (e[sv].parity0 + k) & 1;
+            __syncthreads();  // every thread is done with the previous solve's arguments
+            batch_load<S>(sa, e[sv], k, tid, BLB_X * BLB_Y);
             __syncthreads();
         }
-        const int local = it - e[sv].lb_first;
+        const int local = it - first;
         const int tiles_x = (sa.g.nx + BLB_X - 1) / BLB_X, tiles_y = (sa.g.ny + BLB_Y - 1) / BLB_Y;
         const int bx = local % tiles_x, by = (local / tiles_x) % tiles_y, z = local / (tiles_x * tiles_y);
         const int x = bx * BLB_X + threadIdx.x, y = by * BLB_Y + threadIdx.y;
         if (x < sa.g.nx && y < sa.g.ny) {
-            if (s_parity == 0)
+            if (parity == 0)
                 lb_cell_at<S, 0>(sa, x, y, z);
             else
                 lb_cell_at<S, 1>(sa, x, y, z);
@@ -733,20 +736,19 @@ __global__ void __launch_bounds__(FV_X * FV_Y, sizeof(typename Store<S>::R) == 8
     extern __shared__ __align__(16) unsigned char fv_smem_raw[];
     FvSmem<R> &sm = *reinterpret_cast<FvSmem<R> *>(fv_smem_raw);
     __shared__ KArgs<S> sa;
-    __shared__ int s_solve;
-    if (threadIdx.x == 0) s_solve = -1;
-    __syncthreads();
+    if ((int)blockIdx.x >= total) return;
+    int sv = batch_find<S>(e, nsolves, blockIdx.x, true), end = -1, first = 0, zchunk = 1;
     for (int it = blockIdx.x; it < total; it += gridDim.x) {
-        const int sv = batch_find<S>(e, nsolves, it, true);
-        if (sv != s_solve) {
+        if (it >= end) {
+            while (it >= e[sv].fv_first + e[sv].fv_items) ++sv;
+            first = e[sv].fv_first;
+            end = first + e[sv].fv_items;
+            zchunk = e[sv].fv_zchunk;
             __syncthreads();
-            if (threadIdx.x == 0) {
-                batch_args<S>(sa, e[sv], k);
-                s_solve = sv;
-            }
+            batch_load<S>(sa, e[sv], k, threadIdx.x, FV_X * FV_Y);
             __syncthreads();
         }
-        fv_tile<S>(sa, sm, it - e[sv].fv_first, e[sv].fv_zchunk);
+        fv_tile<S>(sa, sm, it - first, zchunk);
         __syncthreads();
     }
 }

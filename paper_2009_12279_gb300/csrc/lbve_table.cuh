@@ -223,7 +223,10 @@ struct Launch {
     static void fill_entry(const DevState &d, int parity, int lb_first, int fv_first, int fv_zchunk, void *entry,
                            int *lb_items, int *fv_items) {
         BatchEntry<S> &e = *reinterpret_cast<BatchEntry<S> *>(entry);
-        e.a = args(d);
+        e.a[0] = args(d);
+        DevState d1 = d;  // odd steps of a launch sequence: stress ping-pong swapped
+        d1.cur ^= 1;
+        e.a[1] = args(d1);
         e.parity0 = parity;
         e.lb_first = lb_first;
         e.lb_items = ((d.g.nx + BLB_X - 1) / BLB_X) * ((d.g.ny + BLB_Y - 1) / BLB_Y) * d.g.nz;
