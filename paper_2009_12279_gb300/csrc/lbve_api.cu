@@ -36,7 +36,8 @@ struct lbve_ctx {
     std::vector<int> wall_seg_begin, wall_seg_count, wall_seg_flag;
     long long *links = nullptr;  // device, capacity links_cap
     size_t links_cap = 0;
-    double *contrib = nullptr;   // device, 8 doubles per link
+    double *contrib = nullptr;   // device, 8 doubles per entry (per link, or per partial)
+    size_t contrib_cap = 0;      // entries
     int *seg_begin = nullptr;    // device, kMaxBodies each
     int *seg_count = nullptr;
     int *seg_flag = nullptr;
@@ -205,9 +206,9 @@ namespace {
 // small kernels that do not depend on the storage type
 // ---------------------------------------------------------------------------------
 
-// Sum the momentum-exchange contributions of each body segment in link order.  FP64
-// parity mode uses one thread per body (the sequential order of a plain loop); the
-// reduced modes use a fixed-shape block reduction.  Deterministic in both cases.
+// Sum the momentum-exchange contributions of each body segment in link order (FP64
+// parity mode, launched with one thread per body: the sequential order of a plain loop;
+// with more threads a fixed-shape block reduction).
 __global__ void k_body_reduce(const double *__restrict__ contrib, const int *__restrict__ seg_begin,
                               const int *__restrict__ seg_count, const int *__restrict__ seg_flag, int nbody,
                               double *__restrict__ body_F, PartDev *__restrict__ parts) {
@@ -238,6 +239,47 @@ __global__ void k_body_reduce(const double *__restrict__ contrib, const int *__r
             }
         }
     }
+}
+
+// Per-body sums of the reduced modes' momentum-exchange partials (gx per body, first
+// ceil(count / 128) used): warp w sums component w over partials lane, lane + 32, ...,
+// then a fixed shuffle tree.  Deterministic.
+__global__ void __launch_bounds__(192) k_body_partials(const double *__restrict__ part, int gx,
+                                                       const int *__restrict__ seg_count,
+                                                       const int *__restrict__ seg_flag, int nbody,
+                                                       double *__restrict__ body_F, PartDev *__restrict__ parts) {
+    const int b = blockIdx.x;
+    if (b >= nbody) return;
+    const int n = (seg_count[b] + 127) / 128;
+    const int w = (int)threadIdx.x >> 5, lane = (int)threadIdx.x & 31;
+    double acc = 0.0;
+    for (int j = lane; j < n; j += 32) acc += part[((long long)b * gx + j) * 8 + w];
+    for (int off = 16; off > 0; off >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, off);
+    __shared__ double tot[6];
+    if (lane == 0) tot[w] = acc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        const int fl = seg_flag[b];
+        for (int k = 0; k < 3; ++k) body_F[fl * 3 + k] = tot[k];
+        if (fl >= FLAG_PART0 && fl < FLAG_PART0 + MAX_PART) {
+            PartDev &P = parts[fl - FLAG_PART0];
+            for (int k = 0; k < 3; ++k) {
+                P.Fme[k] = tot[k];
+                P.Tme[k] = tot[3 + k];
+            }
+        }
+    }
+}
+
+// Launch the per-body force / torque sums of a context's momentum exchange.
+cudaError_t body_sums(const lbve_ctx *c, PartDev *parts, cudaStream_t st) {
+    if (c->p.pdf_prec == LBVE_F64)
+        k_body_reduce<<<c->nbody, 1, 0, st>>>(c->contrib, c->seg_begin, c->seg_count, c->seg_flag, c->nbody,
+                                              c->body_F, parts);
+    else
+        k_body_partials<<<c->nbody, 192, 0, st>>>(c->contrib, (c->max_seg_len + 127) / 128, c->seg_count,
+                                                  c->seg_flag, c->nbody, c->body_F, parts);
+    return cudaGetLastError();
 }
 
 __global__ void k_final_sum(const double *__restrict__ partial, long long nblocks, double *__restrict__ out) {
@@ -322,6 +364,7 @@ lbve_status layout_links(lbve_ctx *c) {
         c->contrib = (double *)dev_alloc(c, cap * 8 * sizeof(double));
         if (!c->links || !c->contrib) return fail(c, LBVE_ENOMEM, "link list allocation failed");
         c->links_cap = cap;
+        c->contrib_cap = cap;
     }
     if (!c->wall_links.empty())
         CK(cudaMemcpyAsync(c->links, c->wall_links.data(), c->wall_links.size() * sizeof(long long),
@@ -341,6 +384,14 @@ lbve_status layout_links(lbve_ctx *c) {
     c->nbody = (int)beg.size();
     c->max_seg_len = mx;
     if (c->nbody > kMaxBodies) return fail(c, LBVE_EINVAL, "too many tracked bodies");
+    // the reduced modes keep one partial per (body, block of 128 links) in contrib
+    const size_t parts_needed = (size_t)c->nbody * (size_t)((mx + 127) / 128);
+    if (parts_needed > c->contrib_cap) {
+        dev_free(c, c->contrib);
+        c->contrib = (double *)dev_alloc(c, parts_needed * 8 * sizeof(double));
+        if (!c->contrib) return fail(c, LBVE_ENOMEM, "momentum-exchange partials allocation failed");
+        c->contrib_cap = parts_needed;
+    }
     if (c->nbody > 0) {
         CK(cudaMemcpyAsync(c->seg_begin, beg.data(), beg.size() * sizeof(int), cudaMemcpyHostToDevice, c->stream), "seg");
         CK(cudaMemcpyAsync(c->seg_count, cnt.data(), cnt.size() * sizeof(int), cudaMemcpyHostToDevice, c->stream), "seg");
@@ -759,10 +810,7 @@ lbve_status lbve_step(lbve_ctx *c, int nsteps) {
             CK(c->kt->momentum_exchange(c->d, parity, c->links, c->seg_begin, c->seg_count, c->nbody, c->max_seg_len,
                                         c->contrib, c->stream),
                "momentum exchange");
-            const int threads = c->p.pdf_prec == LBVE_F64 ? 1 : 256;
-            k_body_reduce<<<c->nbody, threads, 0, c->stream>>>(c->contrib, c->seg_begin, c->seg_count, c->seg_flag,
-                                                               c->nbody, c->body_F, c->d.parts);
-            CK(cudaGetLastError(), "body reduce");
+            CK(body_sums(c, c->d.parts, c->stream), "body sums");
             CK(timed_end(c), "timing");
         }
         CK(timed_begin(c, LBVE_KT_LB), "timing");
@@ -1122,10 +1170,7 @@ lbve_status enqueue_steps(lbve_pool *P, int q, int nsteps) {
             PCK(c->kt->momentum_exchange(d, parity, c->links, c->seg_begin, c->seg_count, c->nbody, c->max_seg_len,
                                          c->contrib, st),
                 "pool momentum exchange");
-            const int threads = c->p.pdf_prec == LBVE_F64 ? 1 : 256;
-            k_body_reduce<<<c->nbody, threads, 0, st>>>(c->contrib, c->seg_begin, c->seg_count, c->seg_flag, c->nbody,
-                                                        c->body_F, d.parts);
-            PCK(cudaGetLastError(), "pool body reduce");
+            PCK(body_sums(c, d.parts, st), "pool body sums");
             return LBVE_OK;
         });
         if (s != LBVE_OK) return s;

@@ -885,6 +885,35 @@ __global__ void __launch_bounds__(128) k_momentum_exchange(KArgs<S> a, const lon
     me_link<S, PAR>(a, links[at], contrib + at * 8);
 }
 
+// Same with the links of a block summed inside the block (fixed tree order): one partial
+// of 6 doubles (stride 8) per (body, block) at part[(b * gridDim.x + block) * 8].  The
+// final per-body sum then reads ceil(count / 128) partials instead of every link.
+template <class S, int PAR>
+__global__ void __launch_bounds__(128) k_momentum_exchange_part(KArgs<S> a, const long long *__restrict__ links,
+                                                                const int *__restrict__ seg_begin,
+                                                                const int *__restrict__ seg_count,
+                                                                double *__restrict__ part) {
+    const int b = blockIdx.y;
+    const int cnt = seg_count[b];
+    if ((int)blockIdx.x * 128 >= cnt) return;  // the whole block is past this body's links
+    const int l = blockIdx.x * 128 + threadIdx.x;
+    double o[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    if (l < cnt) me_link<S, PAR>(a, links[(long long)seg_begin[b] + l], o);
+    __shared__ double sh[6][128];
+#pragma unroll
+    for (int k = 0; k < 6; ++k) sh[k][threadIdx.x] = o[k];
+    __syncthreads();
+    for (int s = 64; s > 0; s >>= 1) {
+        if ((int)threadIdx.x < s)
+#pragma unroll
+            for (int k = 0; k < 6; ++k) sh[k][threadIdx.x] += sh[k][threadIdx.x + s];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0)
+#pragma unroll
+        for (int k = 0; k < 6; ++k) part[((long long)b * gridDim.x + blockIdx.x) * 8 + k] = sh[k][0];
+}
+
 // ---------------------------------------------------------------------------------
 // moving particles (Sec. "Moving boundaries")
 // ---------------------------------------------------------------------------------

@@ -70,6 +70,8 @@ struct KernelTable {
                         long long count, long long ld, cudaStream_t);
     cudaError_t (*lb)(const DevState &, int parity, cudaStream_t);
     cudaError_t (*fv)(const DevState &, cudaStream_t);
+    // FP64: 8 doubles per link in contrib; shifted modes: 8 doubles per (segment, block of
+    // 128 links), ceil(max_len / 128) blocks per segment
     cudaError_t (*momentum_exchange)(const DevState &, int parity, const long long *links, const int *seg_begin,
                                      const int *seg_count, int nseg, int max_len, double *contrib, cudaStream_t);
     cudaError_t (*voxelise)(const DevState &, int p, const PartDev &host, cudaStream_t);

@@ -106,10 +106,19 @@ struct Launch {
         if (nseg <= 0 || max_len <= 0) return cudaSuccess;
         KArgs<S> a = args(d);
         const dim3 g((unsigned)((max_len + 127) / 128), (unsigned)nseg);
-        if (parity == 0)
-            k_momentum_exchange<S, 0><<<g, 128, 0, s>>>(a, links, seg_begin, seg_count, contrib);
-        else
-            k_momentum_exchange<S, 1><<<g, 128, 0, s>>>(a, links, seg_begin, seg_count, contrib);
+        if constexpr (Store<S>::shifted) {
+            // reduced modes: per-block partials (nseg x ceil(max_len / 128) of them)
+            if (parity == 0)
+                k_momentum_exchange_part<S, 0><<<g, 128, 0, s>>>(a, links, seg_begin, seg_count, contrib);
+            else
+                k_momentum_exchange_part<S, 1><<<g, 128, 0, s>>>(a, links, seg_begin, seg_count, contrib);
+        } else {
+            // FP64 parity mode: one contribution per link, summed in link order
+            if (parity == 0)
+                k_momentum_exchange<S, 0><<<g, 128, 0, s>>>(a, links, seg_begin, seg_count, contrib);
+            else
+                k_momentum_exchange<S, 1><<<g, 128, 0, s>>>(a, links, seg_begin, seg_count, contrib);
+        }
         return cudaGetLastError();
     }
     static cudaError_t build_mask(const DevState &d, int lx, int ly, int lz, int ex, int ey, int ez, cudaStream_t s);
