@@ -279,6 +279,44 @@ size_t lbve_pool_bytes_in_use(const lbve_pool *pool);
 lbve_status lbve_pool_set_graphs(lbve_pool *pool, int enable);
 const char *lbve_pool_last_error(const lbve_pool *pool);
 
+/*
+ * Schedule autotuning.  No launch shape changes a result (every cell runs the same
+ * arithmetic in whatever block it falls), so the tuner times candidate schedules on the
+ * solve's own steps: the solve advances by the steps measured.
+ *
+ * lbve_autotune (split schedule; LBVE_ESTATE for the fused schedule or a pool member):
+ * for every candidate -- stream-collide block width 32, 64 or 128 (up to the width nx
+ * needs) times stress z-planes per block at half, one and two times the default --
+ * `steps` untimed steps, then `steps` steps timed with CUDA events on the context's
+ * stream.  The
+ * fastest is kept for this context and recorded in a process-wide table keyed by
+ * (precision, nx, ny, nz); contexts created later with that key start from it (unless
+ * their params set block_x).  steps <= 0: apply a recorded choice only, measuring
+ * nothing.  out may be NULL.
+ */
+typedef struct {
+    int block_x;                 /* chosen stream-collide block width */
+    int fv_zchunk;               /* chosen stress z-planes per block */
+    int candidates;              /* schedules measured by this call */
+    long long steps_taken;       /* steps the context advanced */
+    double ms_per_step;          /* chosen schedule, as measured (0 if not measured) */
+    double ms_per_step_default;  /* the schedule before the call, as measured */
+} lbve_tuning;
+lbve_status lbve_autotune(lbve_ctx *ctx, int steps, lbve_tuning *out);
+
+/* Pool tile autotuning.  Members are grouped into classes by nx.  Class by class, in
+ * decreasing order of cells, the stream-collide tile width (16, 32, 64 or 128 cells of a
+ * 128-thread block, up to the width nx needs) and then the stress tile width (16, 32 or
+ * 64 cells of a 256-thread block; FP64: 32) are chosen by coordinate descent, each
+ * candidate timed over `steps` pool steps after two untimed calls of `steps` steps (which
+ * leave the step graphs of both call parities captured).  The choices are
+ * recorded per (precision, nx) and applied to contexts admitted to any pool later.  Every
+ * member advances by the steps measured.  The first max_classes classes are reported
+ * (arrays of max_classes entries, NULL allowed): nx, chosen tile widths; ms_before /
+ * ms_after: pool step time with the tiles before the call and with the choices. */
+lbve_status lbve_pool_autotune(lbve_pool *pool, int steps, int max_classes, int *n_classes, int *class_nx,
+                               int *lb_tx, int *fv_tx, double *ms_before, double *ms_after);
+
 /* Steps done since the last lbve_init_fields. */
 long long lbve_time(const lbve_ctx *ctx);
 lbve_status lbve_synchronize(lbve_ctx *ctx);

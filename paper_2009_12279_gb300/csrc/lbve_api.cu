@@ -6,9 +6,12 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <array>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <map>
+#include <mutex>
 #include <new>
 #include <string>
 #include <vector>
@@ -38,6 +41,7 @@ struct lbve_ctx {
     size_t links_cap = 0;
     double *contrib = nullptr;   // device, 8 doubles per entry (per link, or per partial)
     size_t contrib_cap = 0;      // entries
+    int lb_tx = 0, fv_tx = 0;    // tile widths in a pool's batched kernels (0: default by nx)
     int *seg_begin = nullptr;    // device, kMaxBodies each
     int *seg_count = nullptr;
     int *seg_flag = nullptr;
@@ -69,6 +73,32 @@ struct lbve_ctx {
     double *res_partial = nullptr;
     lbve_pool *pool = nullptr;
 };
+
+namespace {
+// Process-wide record of tuned schedules: single solves by (precision, nx, ny, nz) ->
+// (stream-collide block width, stress z-planes per block); pool tiles by (precision, nx)
+// -> (stream-collide tile width, stress tile width).
+std::mutex g_tune_mu;
+std::map<std::array<int, 4>, std::array<int, 2>> g_tuned_ctx;
+std::map<std::array<int, 2>, std::array<int, 2>> g_tuned_tiles;
+
+bool tuned_ctx(const lbve_params &p, int &bx, int &zc) {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    auto it = g_tuned_ctx.find({p.pdf_prec, p.nx, p.ny, p.nz});
+    if (it == g_tuned_ctx.end()) return false;
+    bx = it->second[0];
+    zc = it->second[1];
+    return true;
+}
+bool tuned_tiles(int prec, int nx, int &lb_tx, int &fv_tx) {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    auto it = g_tuned_tiles.find({prec, nx});
+    if (it == g_tuned_tiles.end()) return false;
+    lb_tx = it->second[0];
+    fv_tx = it->second[1];
+    return true;
+}
+} // namespace
 
 namespace {
 
@@ -435,6 +465,13 @@ lbve_status create_impl(const lbve_params *p, void *stream, lbve_alloc_fn alloc,
     g.n = (long long)p->nx * p->ny * p->nz;
     g.np = padded(g.n);
     c->d.block_x = lbve::default_block_x(*p);
+    if (p->block_x == 0) {  // a schedule tuned for this shape earlier in the process
+        int bx = 0, zc = 0;
+        if (tuned_ctx(*p, bx, zc)) {
+            c->d.block_x = bx;
+            c->d.fv_zchunk = zc;
+        }
+    }
     set_phys(c);
     const long long np = g.np;
     c->d.f = dev_alloc(c, (size_t)Q * np * c->kt->pdf_bytes);
@@ -1038,8 +1075,12 @@ struct lbve_pool {
     // k after the build swaps the stress ping-pong and the AA parity k times
     void *entries[2] = {nullptr, nullptr};
     size_t entries_cap = 0;
-    int total_lb = 0, total_fv = 0;
-    int grid_lb = 0, grid_fv = 0;
+    int total_lb = 0;
+    int grid_lb = 0;
+    struct FvGroup {
+        int tx, start, n, total, grid;  // stress tile width, first entry, entries, items, grid
+    };
+    std::vector<FvGroup> fv_groups;
     bool dirty = true;
     long long steps_since_build = 0;
     // residual staging
@@ -1092,25 +1133,38 @@ lbve_status build_entries(lbve_pool *P) {
         }
         P->entries_cap = std::max<size_t>(n, 16);
     }
+    // entries grouped by stress tile width (one stress launch per group); the stream-collide
+    // numbers its items over all entries
     std::vector<unsigned char> host(eb * std::max<size_t>(n, 1));
-    for (int q = 0; q < 1; ++q) {
-        int lb_first = 0, fv_first = 0;
+    P->fv_groups.clear();
+    int lb_first = 0;
+    size_t slot = 0;
+    for (int tx : {16, 32, 64}) {
+        lbve_pool::FvGroup grp{tx, (int)slot, 0, 0, 0};
+        int fv_first = 0;
         for (size_t m = 0; m < n; ++m) {
             const lbve_ctx *c = P->members[m];
-            const DevState d = c->d;
+            int lbe = 0, fve = 0;
+            P->kt->batch_tiles(c->d, c->lb_tx, c->fv_tx, &lbe, &fve);
+            if (fve != tx) continue;
             const int parity = (int)(c->t & 1);
             int lbi = 0, fvi = 0;
-            P->kt->fill_entry(d, parity, lb_first, fv_first, 0, host.data() + eb * m, &lbi, &fvi);
+            P->kt->fill_entry(c->d, parity, lb_first, fv_first, 0, lbe, fve, host.data() + eb * slot, &lbi, &fvi);
             lb_first += lbi;
             fv_first += fvi;
+            ++slot;
+            ++grp.n;
         }
-        P->total_lb = lb_first;
-        P->total_fv = fv_first;
-        if (n) PCK(cudaMemcpyAsync(P->entries[q], host.data(), eb * n, cudaMemcpyHostToDevice, P->stream), "upload entries");
+        if (grp.n == 0) continue;
+        grp.total = fv_first;
+        grp.grid = P->kt->batched_grid(tx);
+        P->fv_groups.push_back(grp);
     }
+    if (slot != n) return pfail(P, LBVE_ECUDA, "internal: stress tile of a member not covered");
+    P->total_lb = lb_first;
+    if (n) PCK(cudaMemcpyAsync(P->entries[0], host.data(), eb * n, cudaMemcpyHostToDevice, P->stream), "upload entries");
     PCK(cudaStreamSynchronize(P->stream), "entries sync");
     if (!P->grid_lb) P->grid_lb = P->kt->batched_grid(0);
-    if (!P->grid_fv) P->grid_fv = P->kt->batched_grid(1);
     P->dirty = false;
     P->steps_since_build = 0;
     drop_graphs(P);
@@ -1175,7 +1229,10 @@ lbve_status enqueue_steps(lbve_pool *P, int q, int nsteps) {
         });
         if (s != LBVE_OK) return s;
         PCK(P->kt->lb_batched(P->entries[0], n, P->total_lb, kk, P->grid_lb, P->stream), "batched lb");
-        PCK(P->kt->fv_batched(P->entries[0], n, P->total_fv, kk, P->grid_fv, P->stream), "batched fv");
+        for (const lbve_pool::FvGroup &grp : P->fv_groups)
+            PCK(P->kt->fv_batched((const unsigned char *)P->entries[0] + (size_t)grp.start * P->kt->batch_entry_bytes,
+                                  grp.n, grp.total, kk, grp.grid, grp.tx, P->stream),
+                "batched fv");
         s = fan_out(P, with_parts, [&](lbve_ctx *c, cudaStream_t st) -> lbve_status {
             DevState d = c->d;
             if ((k + 1) & 1) d.cur ^= 1;  // after the stress swap of this step
@@ -1245,6 +1302,7 @@ lbve_status lbve_pool_admit(lbve_pool *P, lbve_ctx *c) {
     if (c->stream != P->stream) return pfail(P, LBVE_ESTATE, "stream differs from the pool's");
     const size_t b = lbve_device_bytes(&c->p);
     if (P->in_use + b > P->budget) return pfail(P, LBVE_ENOMEM, "device-memory budget exhausted");
+    if (c->lb_tx == 0 && c->fv_tx == 0) tuned_tiles(P->prec, c->p.nx, c->lb_tx, c->fv_tx);
     P->members.push_back(c);
     P->member_bytes.push_back(b);
     P->in_use += b;
@@ -1340,5 +1398,196 @@ lbve_status lbve_pool_set_graphs(lbve_pool *P, int enable) {
     return LBVE_OK;
 }
 const char *lbve_pool_last_error(const lbve_pool *P) { return P ? P->err.c_str() : "NULL pool"; }
+
+} // extern "C"
+
+// ---------------------------------------------------------------------------------
+// schedule autotuning (launch shapes only: results do not depend on them)
+// ---------------------------------------------------------------------------------
+namespace {
+
+// Device milliseconds per step of `steps` steps on the stream, after `warm` untimed calls
+// of `steps` steps (a pool captures one graph per call parity: two warm calls leave both
+// captured, so no capture falls in the timed call).
+template <class StepFn>
+lbve_status time_steps(cudaStream_t st, int steps, int warm, StepFn &&step, double &ms, std::string &err) {
+    for (int w = 0; w < warm; ++w) {
+        lbve_status s = step(steps);
+        if (s != LBVE_OK) return s;
+    }
+    lbve_status s = LBVE_OK;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
+        if (e0) cudaEventDestroy(e0);
+        cudaGetLastError();
+        err = "event creation failed";
+        return LBVE_ECUDA;
+    }
+    cudaEventRecord(e0, st);
+    s = step(steps);
+    cudaEventRecord(e1, st);
+    float t = 0.f;
+    cudaError_t e = cudaEventSynchronize(e1);
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&t, e0, e1);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (s != LBVE_OK) return s;
+    if (e != cudaSuccess) {
+        err = std::string("autotune timing: ") + cudaGetErrorString(e);
+        return LBVE_ECUDA;
+    }
+    ms = (double)t / steps;
+    return LBVE_OK;
+}
+
+int pow2_at_least(int v) {
+    int p = 1;
+    while (p < v) p <<= 1;
+    return p;
+}
+
+} // namespace
+
+extern "C" {
+
+lbve_status lbve_autotune(lbve_ctx *c, int steps, lbve_tuning *out) {
+    if (!c) return LBVE_EINVAL;
+    if (c->pool) return fail(c, LBVE_ESTATE, "a pool member is tuned through its pool");
+    if (c->p.schedule == LBVE_SCHED_FUSED) return fail(c, LBVE_ESTATE, "autotuning covers the split schedule");
+    lbve_tuning r{};
+    const long long t0 = c->t;
+    int bx = 0, zc = 0;
+    if (steps <= 0 || tuned_ctx(c->p, bx, zc)) {
+        if (tuned_ctx(c->p, bx, zc)) {
+            c->d.block_x = bx;
+            c->d.fv_zchunk = zc;
+        }
+        r.block_x = c->d.block_x;
+        r.fv_zchunk = c->kt->fv_zchunk_of(c->d);
+        if (out) *out = r;
+        return LBVE_OK;
+    }
+    auto step = [&](int n) { return lbve_step(c, n); };
+    const int bx0 = c->d.block_x, zc0 = c->d.fv_zchunk;
+    DevState probe = c->d;
+    probe.fv_zchunk = 0;
+    const int h = c->kt->fv_zchunk_of(probe);
+    std::vector<int> bxs, zcs;
+    for (int b : {32, 64, 128})
+        if (b == 32 || b / 2 < c->p.nx) bxs.push_back(b);
+    for (int z : {std::max(4, h / 2), h, std::min(c->p.nz, 2 * h)})
+        if (std::find(zcs.begin(), zcs.end(), z) == zcs.end()) zcs.push_back(z);
+    double ms0 = 0.0;
+    lbve_status s = time_steps(c->stream, steps, 1, step, ms0, c->err);
+    if (s != LBVE_OK) return s;
+    double best = ms0;
+    int best_bx = bx0, best_zc = zc0 > 0 ? zc0 : h;
+    int count = 1;
+    for (int b : bxs) {
+        for (int z : zcs) {
+            if (b == bx0 && z == (zc0 > 0 ? zc0 : h)) continue;  // the starting schedule, measured above
+            c->d.block_x = b;
+            c->d.fv_zchunk = z;
+            double ms = 0.0;
+            s = time_steps(c->stream, steps, 1, step, ms, c->err);
+            if (s != LBVE_OK) return s;
+            ++count;
+            if (ms < best) {
+                best = ms;
+                best_bx = b;
+                best_zc = z;
+            }
+        }
+    }
+    c->d.block_x = best_bx;
+    c->d.fv_zchunk = best_zc;
+    {
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        g_tuned_ctx[{c->p.pdf_prec, c->p.nx, c->p.ny, c->p.nz}] = {best_bx, best_zc};
+    }
+    r.block_x = best_bx;
+    r.fv_zchunk = best_zc;
+    r.candidates = count;
+    r.steps_taken = c->t - t0;
+    r.ms_per_step = best;
+    r.ms_per_step_default = ms0;
+    if (out) *out = r;
+    return LBVE_OK;
+}
+
+lbve_status lbve_pool_autotune(lbve_pool *P, int steps, int max_classes, int *n_classes, int *class_nx, int *lb_tx,
+                               int *fv_tx, double *ms_before, double *ms_after) {
+    if (!P) return LBVE_EINVAL;
+    if (steps <= 0) return pfail(P, LBVE_EINVAL, "steps must be > 0");
+    if (P->members.empty()) return pfail(P, LBVE_ESTATE, "the pool has no members");
+    // classes by nx, largest total cells first
+    std::map<int, long long> cells;
+    for (lbve_ctx *c : P->members) cells[c->p.nx] += (long long)c->p.nx * c->p.ny * c->p.nz;
+    std::vector<std::pair<long long, int>> order;
+    for (auto &kv : cells) order.push_back({-kv.second, kv.first});
+    std::sort(order.begin(), order.end());
+    auto step = [&](int n) { return lbve_pool_step(P, n); };
+    auto set_class = [&](int nx, int lb, int fv) {
+        for (lbve_ctx *c : P->members)
+            if (c->p.nx == nx) {
+                c->lb_tx = lb;
+                c->fv_tx = fv;
+            }
+        P->dirty = true;
+    };
+    double base = 0.0;
+    lbve_status s = time_steps(P->stream, steps, 2, step, base, P->err);
+    if (s != LBVE_OK) return s;
+    double best = base;
+    std::vector<std::array<int, 3>> chosen;
+    for (auto &o : order) {
+        const int nx = o.second;
+        lbve_ctx *rep = nullptr;
+        for (lbve_ctx *c : P->members)
+            if (c->p.nx == nx) rep = c;
+        int cur_lb = 0, cur_fv = 0;
+        P->kt->batch_tiles(rep->d, rep->lb_tx, rep->fv_tx, &cur_lb, &cur_fv);
+        const int wmax = std::max(16, std::min(128, pow2_at_least(nx)));
+        // stream-collide tile width
+        for (int lb : {16, 32, 64, 128}) {
+            if (lb > wmax || lb == cur_lb) continue;
+            set_class(nx, lb, cur_fv);
+            double ms = 0.0;
+            s = time_steps(P->stream, steps, 2, step, ms, P->err);
+            if (s != LBVE_OK) return s;
+            if (ms < best) {
+                best = ms;
+                cur_lb = lb;
+            }
+        }
+        // stress tile width
+        for (int fv : {16, 32, 64}) {
+            int e_lb = 0, e_fv = 0;
+            P->kt->batch_tiles(rep->d, cur_lb, fv, &e_lb, &e_fv);
+            if (e_fv != fv || fv == cur_fv || fv > std::max(16, pow2_at_least(nx))) continue;
+            set_class(nx, cur_lb, fv);
+            double ms = 0.0;
+            s = time_steps(P->stream, steps, 2, step, ms, P->err);
+            if (s != LBVE_OK) return s;
+            if (ms < best) {
+                best = ms;
+                cur_fv = fv;
+            }
+        }
+        set_class(nx, cur_lb, cur_fv);
+        chosen.push_back({nx, cur_lb, cur_fv});
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        g_tuned_tiles[{P->prec, nx}] = {cur_lb, cur_fv};
+    }
+    if (n_classes) *n_classes = (int)chosen.size();
+    for (int k = 0; k < (int)chosen.size() && k < max_classes; ++k) {
+        if (class_nx) class_nx[k] = chosen[k][0];
+        if (lb_tx) lb_tx[k] = chosen[k][1];
+        if (fv_tx) fv_tx[k] = chosen[k][2];
+    }
+    if (ms_before) *ms_before = base;
+    if (ms_after) *ms_after = best;
+    return LBVE_OK;
+}
 
 } // extern "C"

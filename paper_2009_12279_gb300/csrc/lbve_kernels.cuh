@@ -516,7 +516,15 @@ __global__ void __launch_bounds__(FT_X * FT_Y, sizeof(typename Store<S>::R) == 8
 // four-plane shared-memory ring filled with cp.async one plane ahead, so every stencil
 // read of the update comes from shared memory.
 // ---------------------------------------------------------------------------------
-constexpr int FV_X = 32, FV_Y = 8;
+// Stress tiles: 256 threads over TX x (256 / TX) cells; the single-solve kernel uses
+// 32 x 8, the batched kernel picks 16 x 16, 32 x 8 or 64 x 4 per solve.
+constexpr int FV_NT = 256;
+constexpr int FV_X = 32, FV_Y = FV_NT / FV_X;
+template <int TX>
+struct FvTile {
+    static constexpr int TY = FV_NT / TX;
+    static constexpr int HX = TX + 2, HN = (TX + 2) * (TY + 2);  // halo row, halo cells
+};
 constexpr int FVH_X = FV_X + 2, FVH_Y = FV_Y + 2, FVH_N = FVH_X * FVH_Y;
 
 // planes fetched beyond z + 1 while plane z is updated; the ring holds z - 1, z, z + 1
@@ -527,21 +535,21 @@ constexpr int FVH_X = FV_X + 2, FVH_Y = FV_Y + 2, FVH_N = FVH_X * FVH_Y;
 constexpr int FV_RING = LBVE_FV_AHEAD + 3;
 __device__ __forceinline__ int fv_slot(int z) { return ((z % FV_RING) + FV_RING) % FV_RING; }
 
-template <class R>
+template <class R, int NH = FVH_N>
 struct FvSmem {
-    R tau[FV_RING][6][FVH_N];
-    R u[FV_RING][3][FVH_N];
+    R tau[FV_RING][6][NH];
+    R u[FV_RING][3][NH];
 };
 
-template <class S>
+template <class S, int HX, int NH>
 struct FvSmemNb {
     using R = typename Store<S>::R;
-    const FvSmem<R> &sm;
+    const FvSmem<R, NH> &sm;
     const KArgs<S> &a;
     int sc, sd, su, c, xg, yg, zg;
     __device__ __forceinline__ int slot(int l) const { return l == 4 ? su : (l == 5 ? sd : sc); }
     __device__ __forceinline__ int cell(int l) const {
-        return l == 0 ? c + 1 : l == 1 ? c - 1 : l == 2 ? c + FVH_X : l == 3 ? c - FVH_X : c;
+        return l == 0 ? c + 1 : l == 1 ? c - 1 : l == 2 ? c + HX : l == 3 ? c - HX : c;
     }
     __device__ __forceinline__ R u(int l, int j) const { return sm.u[slot(l)][j][cell(l)]; }
     __device__ __forceinline__ R tau(int l, int cc) const { return sm.tau[slot(l)][cc][cell(l)]; }
@@ -556,16 +564,18 @@ struct FvSmemNb {
     }
 };
 
-// Stress update of work item `item` (x-y tile, z-chunk) of one solve.
-template <class S>
-__device__ __forceinline__ void fv_tile(const KArgs<S> &a, FvSmem<typename Store<S>::R> &sm, int item, int zchunk) {
+// Stress update of work item `item` (TX x TY tile, z-chunk) of one solve.
+template <class S, int TX = FV_X>
+__device__ __forceinline__ void fv_tile(const KArgs<S> &a, FvSmem<typename Store<S>::R, FvTile<TX>::HN> &sm, int item,
+                                        int zchunk) {
     using R = typename Store<S>::R;
     constexpr bool SH = Store<S>::shifted;
-    constexpr int NT = FV_X * FV_Y;
+    constexpr int NT = FV_NT, TY = FvTile<TX>::TY, FVH_X = FvTile<TX>::HX, FVH_N = FvTile<TX>::HN;
+    static_assert(FVH_N <= 2 * NT, "two halo cells per thread at most");
     const int tid = threadIdx.x;
-    const int tiles_x = (a.g.nx + FV_X - 1) / FV_X, tiles_y = (a.g.ny + FV_Y - 1) / FV_Y;
+    const int tiles_x = (a.g.nx + TX - 1) / TX, tiles_y = (a.g.ny + TY - 1) / TY;
     const int tx = item % tiles_x, ty = (item / tiles_x) % tiles_y, zc = item / (tiles_x * tiles_y);
-    const int x0 = tx * FV_X, y0 = ty * FV_Y;
+    const int x0 = tx * TX, y0 = ty * TY;
     const int z0 = zc * zchunk, z1 = min(a.g.nz, z0 + zchunk);
     const size_t np = (size_t)a.g.np;
     const unsigned nx = (unsigned)a.g.nx, nxy = (unsigned)a.g.nx * (unsigned)a.g.ny;
@@ -602,7 +612,7 @@ __device__ __forceinline__ void fv_tile(const KArgs<S> &a, FvSmem<typename Store
         }
         cp_async_commit();
     };
-    const int ti = tid % FV_X, tj = tid / FV_X;
+    const int ti = tid % TX, tj = tid / TX;
     const int x = x0 + ti, y = y0 + tj;
     const int kc = (ti + 1) + (tj + 1) * FVH_X;
     const bool own = x < a.g.nx && y < a.g.ny;
@@ -636,7 +646,7 @@ __device__ __forceinline__ void fv_tile(const KArgs<S> &a, FvSmem<typename Store
                 for (int c = 0; c < 6; ++c) tr[c] = sm.tau[sc][c][kc];
 #pragma unroll
                 for (int j = 0; j < 3; ++j) ur[j] = sm.u[sc][j][kc];
-                const FvSmemNb<S> nb{sm, a, sc, sd, su, kc, x, y, z};
+                const FvSmemNb<S, FVH_X, FVH_N> nb{sm, a, sc, sd, su, kc, x, y, z};
                 fv_core<R, SH>(a.ph, tr, ur, m, nb, out);
             }
 #pragma unroll
@@ -670,6 +680,16 @@ struct BatchEntry {
     int parity0;     // AA parity at k = 0
     int lb_first, lb_items;
     int fv_first, fv_items, fv_zchunk;
+    int lb_tx;       // stream-collide tile: lb_tx x (128 / lb_tx) cells (16, 32, 64, 128)
+    int fv_tx;       // stress tile: fv_tx x (256 / fv_tx) cells (16, 32, 64; 32 for FP64)
+};
+
+// Stress tile widths the batched kernels support for real type R (FP64: 32 x 8 only,
+// which keeps 2 blocks per SM).
+template <class R>
+struct FvBatchTiles {
+    static constexpr bool wide = sizeof(R) == 4;
+    __host__ __device__ static bool ok(int tx) { return tx == 32 || (wide && (tx == 16 || tx == 64)); }
 };
 
 // the entry whose [first, first + items) range holds work item `it` (binary search)
@@ -700,26 +720,28 @@ template <class S>
 __global__ void __launch_bounds__(BLB_X * BLB_Y, LBVE_LBB_MIN_BLOCKS) k_lb_batched(const BatchEntry<S> *__restrict__ e,
                                                                                  int nsolves, int total, int k) {
     __shared__ KArgs<S> sa;
-    const int tid = threadIdx.x + BLB_X * threadIdx.y;
+    const int tid = threadIdx.x;  // 1-D blocks of BLB_X * BLB_Y threads
     // items blockIdx.x, + gridDim.x, ...: the resident blocks sweep neighbouring tiles
     // together (halos shared through L2); a block's items only increase, so its solve
     // advances by a forward scan
     if ((int)blockIdx.x >= total) return;
-    int sv = batch_find<S>(e, nsolves, blockIdx.x, false), end = -1, first = 0, parity = 0;
+    int sv = batch_find<S>(e, nsolves, blockIdx.x, false), end = -1, first = 0, parity = 0, lx = 5;
     for (int it = blockIdx.x; it < total; it += gridDim.x) {
         if (it >= end) {
             while (it >= e[sv].lb_first + e[sv].lb_items) ++sv;
             first = e[sv].lb_first;
             end = first + e[sv].lb_items;
             parity = (e[sv].parity0 + k) & 1;
+            lx = __ffs(e[sv].lb_tx) - 1;  // log2 of the tile width
             __syncthreads();  // every thread is done with the previous solve's arguments
             batch_load<S>(sa, e[sv], k, tid, BLB_X * BLB_Y);
             __syncthreads();
         }
         const int local = it - first;
-        const int tiles_x = (sa.g.nx + BLB_X - 1) / BLB_X, tiles_y = (sa.g.ny + BLB_Y - 1) / BLB_Y;
+        const int tw = 1 << lx, th = (BLB_X * BLB_Y) >> lx;
+        const int tiles_x = (sa.g.nx + tw - 1) >> lx, tiles_y = (sa.g.ny + th - 1) / th;
         const int bx = local % tiles_x, by = (local / tiles_x) % tiles_y, z = local / (tiles_x * tiles_y);
-        const int x = bx * BLB_X + threadIdx.x, y = by * BLB_Y + threadIdx.y;
+        const int x = (bx << lx) + (tid & (tw - 1)), y = by * th + (tid >> lx);
         if (x < sa.g.nx && y < sa.g.ny) {
             if (parity == 0)
                 lb_cell_at<S, 0>(sa, x, y, z);
@@ -729,12 +751,14 @@ __global__ void __launch_bounds__(BLB_X * BLB_Y, LBVE_LBB_MIN_BLOCKS) k_lb_batch
     }
 }
 
-template <class S>
-__global__ void __launch_bounds__(FV_X * FV_Y, sizeof(typename Store<S>::R) == 8 ? 2 : LBVE_FV_MIN_BLOCKS) k_fv_batched(
+// Batched stress update over the solves whose stress tile is TX wide (the pool launches
+// one of these per tile width present; fv_first counts within that group).
+template <class S, int TX>
+__global__ void __launch_bounds__(FV_NT, sizeof(typename Store<S>::R) == 8 ? 2 : LBVE_FV_MIN_BLOCKS) k_fv_batched(
     const BatchEntry<S> *__restrict__ e, int nsolves, int total, int k) {
     using R = typename Store<S>::R;
     extern __shared__ __align__(16) unsigned char fv_smem_raw[];
-    FvSmem<R> &sm = *reinterpret_cast<FvSmem<R> *>(fv_smem_raw);
+    FvSmem<R, FvTile<TX>::HN> &sm = *reinterpret_cast<FvSmem<R, FvTile<TX>::HN> *>(fv_smem_raw);
     __shared__ KArgs<S> sa;
     if ((int)blockIdx.x >= total) return;
     int sv = batch_find<S>(e, nsolves, blockIdx.x, true), end = -1, first = 0, zchunk = 1;
@@ -745,10 +769,10 @@ __global__ void __launch_bounds__(FV_X * FV_Y, sizeof(typename Store<S>::R) == 8
             end = first + e[sv].fv_items;
             zchunk = e[sv].fv_zchunk;
             __syncthreads();
-            batch_load<S>(sa, e[sv], k, threadIdx.x, FV_X * FV_Y);
+            batch_load<S>(sa, e[sv], k, threadIdx.x, FV_NT);
             __syncthreads();
         }
-        fv_tile<S>(sa, sm, it - first, zchunk);
+        fv_tile<S, TX>(sa, sm, it - first, zchunk);
         __syncthreads();
     }
 }

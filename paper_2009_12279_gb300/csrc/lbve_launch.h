@@ -60,6 +60,7 @@ struct DevState {
     PartDev *parts;   // MAX_PART entries
     int cur;          // index of tau^t in tau[]
     int block_x;      // threads per block along x
+    int fv_zchunk;    // z-planes per block of the stress kernel (0: by the SM count)
 };
 
 struct KernelTable {
@@ -89,12 +90,17 @@ struct KernelTable {
     cudaError_t (*fused)(const DevState &, int parity, int zchunk, cudaStream_t);
     // batched schedule (pools)
     size_t batch_entry_bytes;
-    void (*fill_entry)(const DevState &, int parity, int lb_first, int fv_first, int fv_zchunk, void *entry,
-                       int *lb_items, int *fv_items);
+    // lb_tx / fv_tx: the solve's tile widths in the batched kernels (0: default by nx)
+    void (*fill_entry)(const DevState &, int parity, int lb_first, int fv_first, int fv_zchunk, int lb_tx, int fv_tx,
+                       void *entry, int *lb_items, int *fv_items);
     cudaError_t (*lb_batched)(const void *entries, int n, int total, int k, int grid, cudaStream_t);
-    cudaError_t (*fv_batched)(const void *entries, int n, int total, int k, int grid, cudaStream_t);
-    int (*batched_grid)(int which);  // resident blocks for the persistent grids (0: LB, 1: FV)
+    // stress update of the solves with stress tile width tx (entries: that group only)
+    cudaError_t (*fv_batched)(const void *entries, int n, int total, int k, int grid, int tx, cudaStream_t);
+    int (*batched_grid)(int which);  // resident blocks: 0 stream-collide, else stress tile width
     cudaError_t (*residual)(const DevState &, void *usnap, double *partial, int nblocks, cudaStream_t);
+    // the tile widths fill_entry will use for requested widths (0: default by nx)
+    void (*batch_tiles)(const DevState &, int lb_tx, int fv_tx, int *lb_eff, int *fv_eff);
+    int (*fv_zchunk_of)(const DevState &);  // z-planes per block the stress kernel will use
 };
 
 // Bounding-box side used to size the per-particle scratch (cells within R + margin).

@@ -115,6 +115,7 @@ lbve_status lbve_step_noalloc(const lbve_params *p, void *f, void *tau_a, void *
     d.parts = (PartDev *)parts;
     d.cur = 0;
     d.block_x = default_block_x(*p);
+    d.fv_zchunk = 0;
     const KernelTable *kt = table_for(p->pdf_prec);
     cudaStream_t s = (cudaStream_t)cuda_stream;
     e = kt->build_mask(d, 0, 0, 0, p->nx, p->ny, p->nz, s);

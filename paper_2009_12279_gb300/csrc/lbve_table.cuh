@@ -76,6 +76,7 @@ struct Launch {
     }
     // z-planes per block of the z-marching stress update (enough blocks for ~16 waves)
     static int fv_zchunk(const DevState &d) {
+        if (d.fv_zchunk > 0) return d.fv_zchunk < d.g.nz ? d.fv_zchunk : d.g.nz;
         const long long tiles = (long long)((d.g.nx + FV_X - 1) / FV_X) * ((d.g.ny + FV_Y - 1) / FV_Y);
         int dev = 0, sms = 148;
         if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
@@ -229,19 +230,28 @@ struct Launch {
         return cudaGetLastError();
     }
 
-    static void fill_entry(const DevState &d, int parity, int lb_first, int fv_first, int fv_zchunk, void *entry,
-                           int *lb_items, int *fv_items) {
+    // default tiles of a solve in the batched kernels (the pool autotuner may pick others)
+    static int default_lb_tx(const DevState &) { return 32; }
+    static int default_fv_tx(const DevState &) { return 32; }
+    static void batch_tiles(const DevState &d, int lb_tx, int fv_tx, int *lb_eff, int *fv_eff) {
+        *lb_eff = (lb_tx == 16 || lb_tx == 32 || lb_tx == 64 || lb_tx == 128) ? lb_tx : default_lb_tx(d);
+        *fv_eff = FvBatchTiles<R>::ok(fv_tx) ? fv_tx : default_fv_tx(d);
+    }
+    static void fill_entry(const DevState &d, int parity, int lb_first, int fv_first, int fv_zchunk, int lb_tx,
+                           int fv_tx, void *entry, int *lb_items, int *fv_items) {
         BatchEntry<S> &e = *reinterpret_cast<BatchEntry<S> *>(entry);
         e.a[0] = args(d);
         DevState d1 = d;  // odd steps of a launch sequence: stress ping-pong swapped
         d1.cur ^= 1;
         e.a[1] = args(d1);
         e.parity0 = parity;
+        batch_tiles(d, lb_tx, fv_tx, &e.lb_tx, &e.fv_tx);
+        const int lth = BLB_X * BLB_Y / e.lb_tx, fth = FV_NT / e.fv_tx;
         e.lb_first = lb_first;
-        e.lb_items = ((d.g.nx + BLB_X - 1) / BLB_X) * ((d.g.ny + BLB_Y - 1) / BLB_Y) * d.g.nz;
+        e.lb_items = ((d.g.nx + e.lb_tx - 1) / e.lb_tx) * ((d.g.ny + lth - 1) / lth) * d.g.nz;
         e.fv_first = fv_first;
         e.fv_zchunk = fv_zchunk > 0 ? fv_zchunk : fv_zchunk_of(d);
-        e.fv_items = ((d.g.nx + FV_X - 1) / FV_X) * ((d.g.ny + FV_Y - 1) / FV_Y) *
+        e.fv_items = ((d.g.nx + e.fv_tx - 1) / e.fv_tx) * ((d.g.ny + fth - 1) / fth) *
                      ((d.g.nz + e.fv_zchunk - 1) / e.fv_zchunk);
         *lb_items = e.lb_items;
         *fv_items = e.fv_items;
@@ -249,30 +259,50 @@ struct Launch {
     static int fv_zchunk_of(const DevState &d) { return fv_zchunk(d); }
     static cudaError_t lb_batched(const void *entries, int n, int total, int k, int grid, cudaStream_t s) {
         if (total <= 0) return cudaSuccess;
-        k_lb_batched<S><<<grid, dim3(BLB_X, BLB_Y), 0, s>>>((const BatchEntry<S> *)entries, n, total, k);
+        k_lb_batched<S><<<grid, BLB_X * BLB_Y, 0, s>>>((const BatchEntry<S> *)entries, n, total, k);
         return cudaGetLastError();
     }
-    static cudaError_t fv_batched(const void *entries, int n, int total, int k, int grid, cudaStream_t s) {
-        if (total <= 0) return cudaSuccess;
-        const size_t sm = sizeof(FvSmem<R>);
+    template <int TX>
+    static cudaError_t fv_batched_tx(const void *entries, int n, int total, int k, int grid, cudaStream_t s) {
+        const size_t sm = sizeof(FvSmem<R, FvTile<TX>::HN>);
         static bool configured = false;
         if (!configured) {
-            cudaError_t e = cudaFuncSetAttribute(k_fv_batched<S>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+            cudaError_t e = cudaFuncSetAttribute(k_fv_batched<S, TX>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
             if (e != cudaSuccess) return e;
             configured = true;
         }
-        k_fv_batched<S><<<grid, FV_X * FV_Y, sm, s>>>((const BatchEntry<S> *)entries, n, total, k);
+        k_fv_batched<S, TX><<<grid, FV_NT, sm, s>>>((const BatchEntry<S> *)entries, n, total, k);
         return cudaGetLastError();
     }
+    static cudaError_t fv_batched(const void *entries, int n, int total, int k, int grid, int tx, cudaStream_t s) {
+        if (total <= 0) return cudaSuccess;
+        if constexpr (FvBatchTiles<R>::wide) {
+            if (tx == 16) return fv_batched_tx<16>(entries, n, total, k, grid, s);
+            if (tx == 64) return fv_batched_tx<64>(entries, n, total, k, grid, s);
+        }
+        return fv_batched_tx<32>(entries, n, total, k, grid, s);
+    }
+    template <int TX>
+    static int fv_resident() {
+        int per = 1;
+        const size_t sm = sizeof(FvSmem<R, FvTile<TX>::HN>);
+        cudaFuncSetAttribute(k_fv_batched<S, TX>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_fv_batched<S, TX>, FV_NT, sm);
+        return per;
+    }
+    // resident blocks of the persistent grids: which = 0 for the stream-collide, else the
+    // stress kernel of tile width `which`
     static int batched_grid(int which) {
         int dev = 0, sms = 148, per = 1;
         if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
         if (which == 0) {
             cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_lb_batched<S>, BLB_X * BLB_Y, 0);
         } else {
-            const size_t sm = sizeof(FvSmem<R>);
-            cudaFuncSetAttribute(k_fv_batched<S>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_fv_batched<S>, FV_X * FV_Y, sm);
+            per = fv_resident<32>();
+            if constexpr (FvBatchTiles<R>::wide) {
+                if (which == 16) per = fv_resident<16>();
+                if (which == 64) per = fv_resident<64>();
+            }
         }
         cudaGetLastError();
         if (per < 1) per = 1;
@@ -298,7 +328,8 @@ const KernelTable *Launch<S>::table(int prec) {
                                       &particle_update, &particle_links, &fill_drain, &read,
                                       &pdfs_io,       &reduce,          &probe,      &build_mask,
                                       &fused,         sizeof(BatchEntry<S>), &fill_entry, &lb_batched,
-                                      &fv_batched,    &batched_grid,    &residual};
+                                      &fv_batched,    &batched_grid,    &residual,   &batch_tiles,
+                                      &fv_zchunk_of};
         return &t;
 }
 

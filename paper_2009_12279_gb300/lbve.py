@@ -31,7 +31,15 @@ EXPORTS = [
     "lbve_reduce", "lbve_residual", "lbve_pool_create", "lbve_pool_destroy", "lbve_pool_fits", "lbve_pool_admit",
     "lbve_pool_remove", "lbve_pool_step", "lbve_pool_residuals", "lbve_pool_size", "lbve_pool_bytes_in_use",
     "lbve_pool_set_graphs", "lbve_pool_last_error", "lbve_step_noalloc", "lbve_noalloc_last_error", "lbve_set_kernel_timing", "lbve_read_kernel_times", "lbve_time", "lbve_synchronize", "lbve_last_error", "lbve_status_string",
+    "lbve_autotune", "lbve_pool_autotune",
 ]
+
+
+class Tuning(ct.Structure):
+    """lbve_tuning: the schedule lbve_autotune chose and what it measured."""
+
+    _fields_ = [("block_x", ct.c_int), ("fv_zchunk", ct.c_int), ("candidates", ct.c_int),
+                ("steps_taken", ct.c_longlong), ("ms_per_step", ct.c_double), ("ms_per_step_default", ct.c_double)]
 
 
 class LbveError(RuntimeError):
@@ -117,6 +125,9 @@ def load(path: str | None = None):
         L.lbve_last_error.restype = ct.c_char_p
         L.lbve_status_string.argtypes = [ct.c_int]
         L.lbve_status_string.restype = ct.c_char_p
+        L.lbve_autotune.argtypes = [vp, ct.c_int, ct.POINTER(Tuning)]
+        ip = ct.POINTER(ct.c_int)
+        L.lbve_pool_autotune.argtypes = [vp, ct.c_int, ct.c_int, ip, ip, ip, ip, dp, dp]
         _lib = L
         return L
 
@@ -316,6 +327,13 @@ class Solver:
         self._check(self._L.lbve_read_kernel_times(self._h, _dp(ms), cnt))
         return {k: (float(ms[i]), int(cnt[i])) for i, k in enumerate(KERNEL_KINDS) if k and cnt[i] > 0}
 
+    def autotune(self, steps: int = 20) -> dict:
+        """Pick the stream-collide block width and stress z-chunk by timing candidates on
+        this solve's own steps (it advances by them); see lbve_autotune."""
+        t = Tuning()
+        self._check(self._L.lbve_autotune(self._h, int(steps), ct.byref(t)))
+        return {f: getattr(t, f) for f, _ in Tuning._fields_}
+
     def residual(self) -> tuple:
         """(|u - u_prev| / |u|, |u|) since the previous call (see lbve_residual)."""
         o = np.zeros(2)
@@ -360,6 +378,20 @@ class Pool:
 
     def step(self, n: int = 1):
         self._check(self._L.lbve_pool_step(self._h, int(n)))
+
+    def autotune(self, steps: int = 10, max_classes: int = 64) -> dict:
+        """Per-class (by nx) tile widths of the batched kernels, chosen by timing candidates
+        on the members' own steps (they advance by them); see lbve_pool_autotune."""
+        n = ct.c_int(0)
+        nx = (ct.c_int * max_classes)()
+        lb = (ct.c_int * max_classes)()
+        fv = (ct.c_int * max_classes)()
+        before, after = ct.c_double(0.0), ct.c_double(0.0)
+        self._check(self._L.lbve_pool_autotune(self._h, int(steps), int(max_classes), ct.byref(n), nx, lb, fv,
+                                               ct.byref(before), ct.byref(after)))
+        k = min(n.value, max_classes)
+        return {"classes": [{"nx": nx[i], "lb_tx": lb[i], "fv_tx": fv[i]} for i in range(k)],
+                "ms_per_step_before": before.value, "ms_per_step_after": after.value}
 
     def residuals(self) -> np.ndarray:
         o = np.zeros((max(len(self.members), 1), 2))
