@@ -274,11 +274,32 @@ def bench_serving(args, torch):
     """Bounded sample of the serving workload: batched BF16 pool vs one-at-a-time FP32."""
     import numpy as np
 
-    from paper_2009_12279_gb300 import serve
+    from paper_2009_12279_gb300 import lbve, serve
 
     stream = torch.cuda.Stream()
     kw = dict(max_steps_cap=args.serving_cap)
     reqs0 = serve.make_requests(args.serving_requests, seed=0, mean_interarrival=0.0, **kw)
+    # tile autotuning (outside the timed runs): one solve per domain width of the stream
+    # in a scratch pool; the recorded choices apply to every pool admitted to later
+    tuning = {}
+    for prec in ("bf16", "f32"):
+        t0 = time.perf_counter()
+        pool = lbve.Pool(prec, budget_bytes=int(args.serving_budget_gb * 1e9), stream=stream.cuda_stream)
+        seen, scratch = set(), []
+        for r in reqs0:
+            if r.shape[0] in seen:
+                continue
+            seen.add(r.shape[0])
+            sv = serve.build_solver(r, prec, stream.cuda_stream)
+            pool.admit(sv)
+            scratch.append(sv)
+        res = pool.autotune(steps=10)
+        pool.close()
+        for sv in scratch:
+            sv.close()
+        torch.cuda.synchronize()
+        res["tuning_s"] = time.perf_counter() - t0
+        tuning[prec] = res
     # throughput mode (all requests waiting at t = 0)
     t0 = time.perf_counter()
     solo, fsolo = serve.run_one_at_a_time(reqs0, precision="f32", stream=stream.cuda_stream, keep_fields=True)
@@ -334,6 +355,7 @@ def bench_serving(args, torch):
                               "p50_latency_s": s_solo["p50_latency_s"], "p99_latency_s": s_solo["p99_latency_s"],
                               "poisson_wall_s": wall_lat_solo, "mlups": serve.summarize(solo, wall_solo)["mlups"]},
         "speedup_solves_per_s": (len(mix) / wall_mix) / (len(solo) / wall_solo),
+        "tile_autotune": tuning,
         "mean_interarrival_s": mean_gap,
         "bf16_vs_f32_u_rel_l2": {"median": float(np.median(errs)) if errs else None,
                                  "max": float(np.max(errs)) if errs else None},
@@ -378,6 +400,13 @@ def run_ours(args):
     clocks = None
     for prec in args.precisions:
         s, cfg = build_solver(n, prec, args.schedule, stream, torch)
+        tuned = None
+        if args.schedule != "fused" and not args.no_autotune:
+            # schedule autotuning on the solve's own steps (launch shapes do not change
+            # results); these steps come before the warm-up and the timed region
+            t0 = time.perf_counter()
+            tuned = s.autotune(steps=4)
+            tuned["tuning_s"] = time.perf_counter() - t0
         sampler = ClockSampler(local) if prec == args.precisions[0] else None
         if sampler:
             sampler.start()
@@ -414,6 +443,7 @@ def run_ours(args):
                          "bytes_per_cell": kb, "peak_source": peak_kind},
             "gpu_launches": launches,
             "healthy": not health["bad"],
+            "schedule_tuning": tuned,
         }
     serving = None
     if rank == 0 and not args.no_serving:
@@ -434,6 +464,7 @@ def run_ours(args):
                                    f"beta 0.5, lambda 1000, eta 1/6, {args.precisions[0]} PDF storage",
                        "cells": n ** 3, "schedule": args.schedule, "parallelism": f"replicas{world}",
                        "l2": "state larger than L2 (no flush needed)",
+                       "schedule_tuning": main.get("schedule_tuning"),
                        "step_bytes_per_cell": main["step_bytes_per_cell"]},
             "roofline": main["roofline"],
             "step_roofline_frac": main["step_roofline_frac"],
@@ -496,6 +527,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-serving", action="store_true")
+    ap.add_argument("--no-autotune", action="store_true", help="time the default schedule")
     ap.add_argument("--serving-requests", type=int, default=48)
     ap.add_argument("--serving-cap", type=int, default=1000, help="step cap per solve in the serving sample")
     ap.add_argument("--serving-budget-gb", type=float, default=150.0)
