@@ -254,12 +254,27 @@ def time_e2e(n, prec, schedule, steps, torch, stream_obj):
     out_tau = torch.empty((6, n, n, n), dtype=torch.float64).pin_memory()
     sched = {"auto": lbve.SCHED_AUTO, "split": lbve.SCHED_SPLIT, "fused": lbve.SCHED_FUSED}[schedule]
     torch.cuda.synchronize()
+    phases = {}
     t0 = time.perf_counter()
+    tp = t0
+
+    def mark(name):
+        nonlocal tp
+        s.synchronize()
+        now = time.perf_counter()
+        phases[name] = now - tp
+        tp = now
+
     s = Solver(cfg["shape"], precision=prec, schedule=sched, stream=stream_obj.cuda_stream, **cfg["params"])
+    mark("create_s")
     s.set_geometry(flags.numpy())
+    mark("geometry_s")
     s.init_fields_ptr(0, u.data_ptr(), 0)
+    mark("upload_s")
     s.step(steps)
+    mark("steps_s")
     s.read_fields_ptr(out_rho.data_ptr(), out_u.data_ptr(), out_tau.data_ptr())
+    mark("read_back_s")
     dt = time.perf_counter() - t0
     s.close()
     h2d = flags.numel() + u.numel() * 8
@@ -267,7 +282,7 @@ def time_e2e(n, prec, schedule, steps, torch, stream_obj):
     finite = bool(torch.isfinite(out_u).all())
     return {"value": n ** 3 * steps / dt / 1e6, "unit": UNIT, "h2d_bytes_per_step": h2d / steps,
             "d2h_bytes_per_step": d2h / steps, "wall_s": dt, "job": f"create + upload + {steps} steps + read-back",
-            "finite": finite}
+            "phases": phases, "finite": finite}
 
 
 def bench_serving(args, torch):

@@ -57,7 +57,6 @@ struct lbve_ctx {
     double *red = nullptr;       // device reduction scratch
     size_t red_cap = 0;
     double *red_out = nullptr;   // device, 6 doubles
-    std::vector<uint8_t> flags_host;
     bool geometry_set = false;
     int nparts = 0;
     PartDev parts_host[MAX_PART];
@@ -332,14 +331,18 @@ __global__ void k_final_sum(const double *__restrict__ partial, long long nblock
 // Host-side list of links (fluid cell r, direction i with r + c_i a wall-class cell),
 // ordered by flag value, then cell, then direction (the order of a plain cell loop
 // within each body).  Built from the wall-class cells, so its cost is O(wall cells).
-void build_wall_links(lbve_ctx *c) {
+void build_wall_links(lbve_ctx *c, const uint8_t *fl, bool any_wall) {
     std::vector<long long> &links = c->wall_links;
     std::vector<int> &seg = c->wall_seg_begin, &seg_flag = c->wall_seg_flag, &seg_count = c->wall_seg_count;
+    links.clear();
+    seg.clear();
+    seg_flag.clear();
+    seg_count.clear();
+    if (!any_wall) return;
     static const int CX[Q] = {0, 1, -1, 0, 0, 0, 0, 1, -1, 1, -1, 1, -1, 1, -1, 0, 0, 0, 0};
     static const int CY[Q] = {0, 0, 0, 1, -1, 0, 0, 1, -1, -1, 1, 0, 0, 0, 0, 1, -1, 1, -1};
     static const int CZ[Q] = {0, 0, 0, 0, 0, 1, -1, 0, 0, 0, 0, 1, -1, -1, 1, 1, -1, -1, 1};
     const int nx = c->p.nx, ny = c->p.ny, nz = c->p.nz;
-    const std::vector<uint8_t> &fl = c->flags_host;
     const long long n = (long long)nx * ny * nz;
     std::vector<std::pair<int, long long>> tmp;  // (flag, (r << 5) | i)
     for (long long rw = 0; rw < n; ++rw) {
@@ -362,10 +365,6 @@ void build_wall_links(lbve_ctx *c) {
         }
     }
     std::sort(tmp.begin(), tmp.end());
-    links.clear();
-    seg.clear();
-    seg_flag.clear();
-    seg_count.clear();
     for (size_t k = 0; k < tmp.size(); ++k) {
         if (k == 0 || tmp[k].first != tmp[k - 1].first) {
             seg.push_back((int)links.size());
@@ -497,7 +496,6 @@ lbve_status create_impl(const lbve_params *p, void *stream, lbve_alloc_fn alloc,
         lbve_destroy(c);
         return LBVE_ENOMEM;
     }
-    c->flags_host.assign((size_t)g.n, 0);
     cudaError_t e = cudaMemsetAsync(c->d.flag, 0, (size_t)np, c->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(c->d.u[0], 0, (size_t)3 * np * c->kt->real_bytes, c->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(c->d.u[1], 0, (size_t)3 * np * c->kt->real_bytes, c->stream);
@@ -631,11 +629,13 @@ lbve_status lbve_set_geometry(lbve_ctx *c, const uint8_t *flags, const double *w
     if (n_wall < 0 || n_wall > MAX_WALL || (n_wall > 0 && !wall_vel))
         return fail(c, LBVE_EINVAL, "n_wall must be in [0, 16] with wall_vel given");
     const int nx = c->p.nx, ny = c->p.ny, nz = c->p.nz;
-    bool ok[256] = {false};
-    ok[FLAG_FLUID] = ok[FLAG_NOSLIP] = true;
-    for (int k = 0; k < n_wall; ++k) ok[FLAG_WALL0 + k] = true;
-    for (long long r = 0; r < c->d.g.n; ++r) {
-        if (!ok[flags[r]]) {
+    // valid flags form the range [0, FLAG_WALL0 + n_wall): one (vectorisable) maximum
+    // checks them all and tells whether any wall class is present
+    uint8_t fmax = 0;
+    for (long long r = 0; r < c->d.g.n; ++r) fmax = flags[r] > fmax ? flags[r] : fmax;
+    if (fmax >= FLAG_WALL0 + n_wall) {
+        for (long long r = 0; r < c->d.g.n; ++r) {
+            if (flags[r] < FLAG_WALL0 + n_wall) continue;
             char b[128];
             std::snprintf(b, sizeof b, "flag %d at cell %lld is not fluid, no-slip or a declared wall class",
                           (int)flags[r], r);
@@ -659,12 +659,13 @@ lbve_status lbve_set_geometry(lbve_ctx *c, const uint8_t *flags, const double *w
     }
     for (int k = 0; k < MAX_WALL; ++k)
         for (int a = 0; a < 3; ++a) c->d.ph.wall_vel[k][a] = k < n_wall ? wall_vel[3 * k + a] : 0.0;
-    std::memcpy(c->flags_host.data(), flags, (size_t)c->d.g.n);
     CK(cudaMemcpyAsync(c->d.flag, flags, (size_t)c->d.g.n, cudaMemcpyHostToDevice, c->stream), "upload flags");
     CK(c->kt->build_mask(c->d, 0, 0, 0, c->p.nx, c->p.ny, c->p.nz, c->stream), "neighbour masks");
-    build_wall_links(c);
+    build_wall_links(c, flags, fmax >= FLAG_WALL0);
     lbve_status s = layout_links(c);
     if (s != LBVE_OK) return s;
+    // the caller's buffer may be pinned: the copy has to be done when the call returns
+    CK(cudaStreamSynchronize(c->stream), "geometry sync");
     c->geometry_set = true;
     return LBVE_OK;
 }
