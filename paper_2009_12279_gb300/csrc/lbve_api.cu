@@ -300,6 +300,9 @@ __global__ void __launch_bounds__(192) k_body_partials(const double *__restrict_
     }
 }
 
+// Advance a pool's device step counter (after each step's stream-collide).
+__global__ void k_step_count(unsigned *dstep) { *dstep += 1u; }
+
 // Launch the per-body force / torque sums of a context's momentum exchange.
 cudaError_t body_sums(const lbve_ctx *c, PartDev *parts, cudaStream_t st) {
     if (c->p.pdf_prec == LBVE_F64)
@@ -822,11 +825,13 @@ lbve_status lbve_step(lbve_ctx *c, int nsteps) {
         // stream-collide of the first step, fused (stress of step t-1 + stream-collide of
         // step t) for the others, stress update of the last step
         const int zc = fused_zchunk(c);
+        c->d.step = (unsigned)c->t;
         CK(timed_begin(c, LBVE_KT_LB), "timing");
         CK(c->kt->lb(c->d, (int)(c->t & 1), c->stream), "lb kernel");
         CK(timed_end(c), "timing");
         c->t++;
         for (int s = 1; s < nsteps; ++s) {
+            c->d.step = (unsigned)c->t;
             CK(timed_begin(c, LBVE_KT_FUSED), "timing");
             CK(c->kt->fused(c->d, (int)(c->t & 1), zc, c->stream), "fused kernel");
             CK(timed_end(c), "timing");
@@ -843,6 +848,7 @@ lbve_status lbve_step(lbve_ctx *c, int nsteps) {
     }
     for (int s = 0; s < nsteps; ++s) {
         const int parity = (int)(c->t & 1);
+        c->d.step = (unsigned)c->t;
         if (c->nbody > 0) {
             CK(timed_begin(c, LBVE_KT_ME), "timing");
             CK(c->kt->momentum_exchange(c->d, parity, c->links, c->seg_begin, c->seg_count, c->nbody, c->max_seg_len,
@@ -1078,6 +1084,7 @@ struct lbve_pool {
     size_t entries_cap = 0;
     int total_lb = 0;
     int grid_lb = 0;
+    unsigned *dstep = nullptr;  // device: steps since the entries were built
     struct FvGroup {
         int tx, start, n, total, grid;  // stress tile width, first entry, entries, items, grid
     };
@@ -1149,8 +1156,10 @@ lbve_status build_entries(lbve_pool *P) {
             P->kt->batch_tiles(c->d, c->lb_tx, c->fv_tx, &lbe, &fve);
             if (fve != tx) continue;
             const int parity = (int)(c->t & 1);
+            DevState d = c->d;
+            d.step = (unsigned)c->t;  // step k of a launch sequence performs step t + k
             int lbi = 0, fvi = 0;
-            P->kt->fill_entry(c->d, parity, lb_first, fv_first, 0, lbe, fve, host.data() + eb * slot, &lbi, &fvi);
+            P->kt->fill_entry(d, parity, lb_first, fv_first, 0, lbe, fve, host.data() + eb * slot, &lbi, &fvi);
             lb_first += lbi;
             fv_first += fvi;
             ++slot;
@@ -1164,6 +1173,7 @@ lbve_status build_entries(lbve_pool *P) {
     if (slot != n) return pfail(P, LBVE_ECUDA, "internal: stress tile of a member not covered");
     P->total_lb = lb_first;
     if (n) PCK(cudaMemcpyAsync(P->entries[0], host.data(), eb * n, cudaMemcpyHostToDevice, P->stream), "upload entries");
+    PCK(cudaMemsetAsync(P->dstep, 0, sizeof(unsigned), P->stream), "step counter reset");
     PCK(cudaStreamSynchronize(P->stream), "entries sync");
     if (!P->grid_lb) P->grid_lb = P->kt->batched_grid(0);
     P->dirty = false;
@@ -1229,7 +1239,9 @@ lbve_status enqueue_steps(lbve_pool *P, int q, int nsteps) {
             return LBVE_OK;
         });
         if (s != LBVE_OK) return s;
-        PCK(P->kt->lb_batched(P->entries[0], n, P->total_lb, kk, P->grid_lb, P->stream), "batched lb");
+        PCK(P->kt->lb_batched(P->entries[0], n, P->total_lb, kk, P->grid_lb, P->dstep, P->stream), "batched lb");
+        k_step_count<<<1, 1, 0, P->stream>>>(P->dstep);
+        PCK(cudaGetLastError(), "step counter");
         for (const lbve_pool::FvGroup &grp : P->fv_groups)
             PCK(P->kt->fv_batched((const unsigned char *)P->entries[0] + (size_t)grp.start * P->kt->batch_entry_bytes,
                                   grp.n, grp.total, kk, grp.grid, grp.tx, P->stream),
@@ -1266,6 +1278,11 @@ lbve_status lbve_pool_create(int pdf_prec, size_t budget_bytes, void *cuda_strea
     P->budget = budget_bytes;
     P->stream = (cudaStream_t)cuda_stream;
     P->kt = kt;
+    if (cudaMalloc(&P->dstep, sizeof(unsigned)) != cudaSuccess) {
+        cudaGetLastError();
+        delete P;
+        return LBVE_ENOMEM;
+    }
     *out = P;
     return LBVE_OK;
 }
@@ -1285,6 +1302,7 @@ lbve_status lbve_pool_destroy(lbve_pool *P) {
     for (int k = 0; k < 2; ++k)
         if (P->entries[k]) cudaFree(P->entries[k]);
     if (P->res_dev) cudaFree(P->res_dev);
+    if (P->dstep) cudaFree(P->dstep);
     for (lbve_ctx *c : P->members) c->pool = nullptr;
     delete P;
     return LBVE_OK;

@@ -70,31 +70,57 @@ template <>
 struct Store<double> {
     using R = double;
     static constexpr bool shifted = false;
+    static constexpr bool keyed = false;
     __device__ static __forceinline__ double ld(const double *p, double) { return *p; }
     __device__ static __forceinline__ void st(double *p, double v, double) { *p = v; }
+    __device__ static __forceinline__ void st(double *p, double v, double, uint32_t) { *p = v; }
 };
 template <>
 struct Store<float> {
     using R = float;
     static constexpr bool shifted = true;
+    static constexpr bool keyed = false;
     // FP32 keeps its exponent range: stored unscaled (the scale argument is 1)
     __device__ static __forceinline__ float ld(const float *p, float) { return *p; }
     __device__ static __forceinline__ void st(float *p, float v, float) { *p = v; }
+    __device__ static __forceinline__ void st(float *p, float v, float, uint32_t) { *p = v; }
 };
 template <>
 struct Store<__half> {
     using R = float;
     static constexpr bool shifted = true;
+    static constexpr bool keyed = false;
     __device__ static __forceinline__ float ld(const __half *p, float inv) { return __half2float(*p) * inv; }
     __device__ static __forceinline__ void st(__half *p, float v, float sc) { *p = __float2half_rn(v * sc); }
+    __device__ static __forceinline__ void st(__half *p, float v, float sc, uint32_t) { st(p, v, sc); }
 };
+#ifndef LBVE_BF16_STOCHASTIC
+#define LBVE_BF16_STOCHASTIC 1
+#endif
 template <>
 struct Store<__nv_bfloat16> {
     using R = float;
     static constexpr bool shifted = true;
+    static constexpr bool keyed = LBVE_BF16_STOCHASTIC;  // stores take a rounding key
     // BF16 has the FP32 exponent range: stored unscaled (the scale argument is 1)
     __device__ static __forceinline__ float ld(const __nv_bfloat16 *p, float) { return __bfloat162float(*p); }
     __device__ static __forceinline__ void st(__nv_bfloat16 *p, float v, float) { *p = __float2bfloat16_rn(v); }
+    // Stochastic rounding.  With 8 significant bits, the per-step change of a slowly
+    // accelerating flow can be below half a unit of the stored deviation, and
+    // round-to-nearest then drops it every step.  Adding 16 uniform bits below the kept
+    // ones before truncating rounds up with probability equal to the dropped fraction
+    // (unbiased).  The bits hash a key of (step, cell, direction) with the value, so the
+    // result is deterministic and the same for a solve alone and in a pool.
+    __device__ static __forceinline__ void st(__nv_bfloat16 *p, float v, float, uint32_t key) {
+#if LBVE_BF16_STOCHASTIC
+        const uint32_t b = __float_as_uint(v);
+        const uint32_t h = ((b ^ key) * 0x9E3779B1u) >> 16;  // high half of a multiplicative hash
+        const bool finite = (b & 0x7F800000u) != 0x7F800000u;
+        *p = finite ? __ushort_as_bfloat16((unsigned short)((b + h) >> 16)) : __float2bfloat16_rn(v);
+#else
+        *p = __float2bfloat16_rn(v);
+#endif
+    }
 };
 
 // Coordinates of one cell and its periodically wrapped neighbours; cell indices are

@@ -10,6 +10,8 @@
 // The fused schedule (k_fused) merges k_fv of step t with k_lb of step t+1.
 #pragma once
 
+#include <cstddef>
+
 #include "lbve_device.cuh"
 #include "lbve_launch.h"
 
@@ -45,6 +47,7 @@ struct KArgs {
     const uint8_t *flag;
     const uint32_t *mask;
     const PartDev *parts;
+    unsigned step;  // index of the step being performed (rounding keys of keyed stores)
     // per-direction / per-component bases (f + i np, tau + c np, u_out + k np), so that an
     // address is one multiply-add of a 32-bit cell index; set by link_dirs
     S *fq[Q];
@@ -111,21 +114,25 @@ __device__ __forceinline__ void store_pdfs(const KArgs<S> &a, const Cell &cl, un
     const size_t np = (size_t)a.g.np;
     const R sc = a.ph.scale;
     const bool moving = mask & MASK_MOVING;  // else every solid neighbour is a resting no-slip wall
-    Store<S>::st(a.fq[0] + r, fs[0], sc);
+    // rounding key of (step, cell, direction) for keyed stores (0 for the others)
+    const uint32_t kb = Store<S>::keyed ? (r * 0x9E3779B1u) ^ (a.step * 0x85EBCA6Bu) : 0u;
+#define LBVE_KEY(i) (kb + (uint32_t)(i) * 0x27D4EB2Fu)
+    Store<S>::st(a.fq[0] + r, fs[0], sc, LBVE_KEY(0));
     if (!__any_sync(__activemask(), moving)) {
         // no lane of the warp next to a moving boundary: bounce-back is a predicated store
 #pragma unroll
         for (int i = 1; i < Q; ++i) {
             const unsigned nb = cl.idx(cx(i), cy(i), cz(i));
-            Store<S>::st(PAR == 0 ? a.fq[copp(i)] + r : a.fq[i] + nb, fs[i], sc);
-            if (nb_solid(mask, i)) Store<S>::st(PAR == 0 ? a.fq[i] + nb : a.fq[copp(i)] + r, fs[i], sc);
+            Store<S>::st(PAR == 0 ? a.fq[copp(i)] + r : a.fq[i] + nb, fs[i], sc, LBVE_KEY(i));
+            if (nb_solid(mask, i))
+                Store<S>::st(PAR == 0 ? a.fq[i] + nb : a.fq[copp(i)] + r, fs[i], sc, LBVE_KEY(Q + i));
         }
         return;
     }
 #pragma unroll
     for (int i = 1; i < Q; ++i) {
         const unsigned nb = cl.idx(cx(i), cy(i), cz(i));
-        Store<S>::st(PAR == 0 ? a.fq[copp(i)] + r : a.fq[i] + nb, fs[i], sc);
+        Store<S>::st(PAR == 0 ? a.fq[copp(i)] + r : a.fq[i] + nb, fs[i], sc, LBVE_KEY(i));
         if (nb_solid(mask, i)) {
             R X = R(0);
             if (moving) {
@@ -133,9 +140,10 @@ __device__ __forceinline__ void store_pdfs(const KArgs<S> &a, const Cell &cl, un
                 if (fl != FLAG_NOSLIP)
                     X = moving_wall_term<R>(a.g, a.ph, a.parts, fl, cl.X(cx(i)), cl.Y(cy(i)), cl.Z(cz(i)), i, rho);
             }
-            Store<S>::st(PAR == 0 ? a.fq[i] + nb : a.fq[copp(i)] + r, fs[i] - X, sc);
+            Store<S>::st(PAR == 0 ? a.fq[i] + nb : a.fq[copp(i)] + r, fs[i] - X, sc, LBVE_KEY(Q + i));
         }
     }
+#undef LBVE_KEY
 }
 
 // LB half of the step for one fluid cell, given its own stress tr and an accessor tn for
@@ -708,23 +716,30 @@ __device__ __forceinline__ int batch_find(const BatchEntry<S> *__restrict__ e, i
 }
 
 // Cooperative copy of a solve's arguments for step k into shared memory (all threads).
+// The step index word gets `dstep` added: the steps the pool has taken since the
+// arguments were built.
 template <class S>
-__device__ __forceinline__ void batch_load(KArgs<S> &sa, const BatchEntry<S> &e, int k, int tid, int nt) {
+__device__ __forceinline__ void batch_load(KArgs<S> &sa, const BatchEntry<S> &e, int k, unsigned dstep, int tid,
+                                           int nt) {
     static_assert(sizeof(KArgs<S>) % 4 == 0, "argument block copied as words");
-    const int *src = reinterpret_cast<const int *>(&e.a[k & 1]);
-    int *dst = reinterpret_cast<int *>(&sa);
-    for (int w = tid; w < (int)(sizeof(KArgs<S>) / 4); w += nt) dst[w] = src[w];
+    static_assert(offsetof(KArgs<S>, step) % 4 == 0, "step index is one word");
+    constexpr int ws = (int)(offsetof(KArgs<S>, step) / 4);
+    const unsigned *src = reinterpret_cast<const unsigned *>(&e.a[k & 1]);
+    unsigned *dst = reinterpret_cast<unsigned *>(&sa);
+    for (int w = tid; w < (int)(sizeof(KArgs<S>) / 4); w += nt) dst[w] = w == ws ? src[w] + dstep : src[w];
 }
 
 template <class S>
 __global__ void __launch_bounds__(BLB_X * BLB_Y, LBVE_LBB_MIN_BLOCKS) k_lb_batched(const BatchEntry<S> *__restrict__ e,
-                                                                                 int nsolves, int total, int k) {
+                                                                                 int nsolves, int total, int k,
+                                                                                 const unsigned *__restrict__ dstep) {
     __shared__ KArgs<S> sa;
     const int tid = threadIdx.x;  // 1-D blocks of BLB_X * BLB_Y threads
     // items blockIdx.x, + gridDim.x, ...: the resident blocks sweep neighbouring tiles
     // together (halos shared through L2); a block's items only increase, so its solve
     // advances by a forward scan
     if ((int)blockIdx.x >= total) return;
+    const unsigned ds = *dstep;
     int sv = batch_find<S>(e, nsolves, blockIdx.x, false), end = -1, first = 0, parity = 0, lx = 5;
     for (int it = blockIdx.x; it < total; it += gridDim.x) {
         if (it >= end) {
@@ -734,7 +749,7 @@ __global__ void __launch_bounds__(BLB_X * BLB_Y, LBVE_LBB_MIN_BLOCKS) k_lb_batch
             parity = (e[sv].parity0 + k) & 1;
             lx = __ffs(e[sv].lb_tx) - 1;  // log2 of the tile width
             __syncthreads();  // every thread is done with the previous solve's arguments
-            batch_load<S>(sa, e[sv], k, tid, BLB_X * BLB_Y);
+            batch_load<S>(sa, e[sv], k, ds, tid, BLB_X * BLB_Y);
             __syncthreads();
         }
         const int local = it - first;
@@ -769,7 +784,7 @@ __global__ void __launch_bounds__(FV_NT, sizeof(typename Store<S>::R) == 8 ? 2 :
             end = first + e[sv].fv_items;
             zchunk = e[sv].fv_zchunk;
             __syncthreads();
-            batch_load<S>(sa, e[sv], k, threadIdx.x, FV_NT);
+            batch_load<S>(sa, e[sv], k, 0u, threadIdx.x, FV_NT);  // the stress update uses no step index
             __syncthreads();
         }
         fv_tile<S, TX>(sa, sm, it - first, zchunk);

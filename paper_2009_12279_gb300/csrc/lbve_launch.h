@@ -61,6 +61,7 @@ struct DevState {
     int cur;          // index of tau^t in tau[]
     int block_x;      // threads per block along x
     int fv_zchunk;    // z-planes per block of the stress kernel (0: by the SM count)
+    unsigned step;    // index of the step the next stream-collide performs (low 32 bits)
 };
 
 struct KernelTable {
@@ -93,7 +94,9 @@ struct KernelTable {
     // lb_tx / fv_tx: the solve's tile widths in the batched kernels (0: default by nx)
     void (*fill_entry)(const DevState &, int parity, int lb_first, int fv_first, int fv_zchunk, int lb_tx, int fv_tx,
                        void *entry, int *lb_items, int *fv_items);
-    cudaError_t (*lb_batched)(const void *entries, int n, int total, int k, int grid, cudaStream_t);
+    // dstep: device counter of the steps since the entries were built (their step index base)
+    cudaError_t (*lb_batched)(const void *entries, int n, int total, int k, int grid, const unsigned *dstep,
+                              cudaStream_t);
     // stress update of the solves with stress tile width tx (entries: that group only)
     cudaError_t (*fv_batched)(const void *entries, int n, int total, int k, int grid, int tx, cudaStream_t);
     int (*batched_grid)(int which);  // resident blocks: 0 stream-collide, else stress tile width

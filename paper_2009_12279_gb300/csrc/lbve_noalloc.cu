@@ -116,12 +116,14 @@ lbve_status lbve_step_noalloc(const lbve_params *p, void *f, void *tau_a, void *
     d.cur = 0;
     d.block_x = default_block_x(*p);
     d.fv_zchunk = 0;
+    d.step = (unsigned)t0;
     const KernelTable *kt = table_for(p->pdf_prec);
     cudaStream_t s = (cudaStream_t)cuda_stream;
     e = kt->build_mask(d, 0, 0, 0, p->nx, p->ny, p->nz, s);
     if (e != cudaSuccess) return fail(LBVE_ECUDA, std::string("mask kernel: ") + cudaGetErrorString(e));
     for (int k = 0; k < nsteps; ++k) {
         const int parity = (int)((t0 + k) & 1);
+        d.step = (unsigned)(t0 + k);
         e = kt->lb(d, parity, s);
         if (e == cudaSuccess) e = kt->fv(d, s);
         if (e != cudaSuccess) return fail(LBVE_ECUDA, std::string("step kernels: ") + cudaGetErrorString(e));

@@ -47,6 +47,7 @@ struct Launch {
         a.flag = d.flag;
         a.mask = d.mask;
         a.parts = d.parts;
+        a.step = d.step;
         link_dirs<S>(a);
         return a;
     }
@@ -257,9 +258,10 @@ struct Launch {
         *fv_items = e.fv_items;
     }
     static int fv_zchunk_of(const DevState &d) { return fv_zchunk(d); }
-    static cudaError_t lb_batched(const void *entries, int n, int total, int k, int grid, cudaStream_t s) {
+    static cudaError_t lb_batched(const void *entries, int n, int total, int k, int grid, const unsigned *dstep,
+                                  cudaStream_t s) {
         if (total <= 0) return cudaSuccess;
-        k_lb_batched<S><<<grid, BLB_X * BLB_Y, 0, s>>>((const BatchEntry<S> *)entries, n, total, k);
+        k_lb_batched<S><<<grid, BLB_X * BLB_Y, 0, s>>>((const BatchEntry<S> *)entries, n, total, k, dstep);
         return cudaGetLastError();
     }
     template <int TX>

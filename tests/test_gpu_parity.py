@@ -104,7 +104,7 @@ def test_fp32_obstacles_1000_steps():
     assert np.linalg.norm(bg[2] - bo[2]) <= 1e-4 * np.linalg.norm(bo[2])
 
 
-@pytest.mark.parametrize("precision,bound", [("f16", 5e-2), ("bf16", 2e-1)])
+@pytest.mark.parametrize("precision,bound", [("f16", 5e-2), ("bf16", 1e-2)])
 def test_reduced_precision_error_is_reported(precision, bound, capsys):
     shape, prm, fl, wall, rho0, u0, t0 = _obstacle_case()
     g, o = pair(shape, prm, fl, wall, rho=rho0, u=u0, tau=t0, precision=precision)
@@ -115,6 +115,22 @@ def test_reduced_precision_error_is_reported(precision, bound, capsys):
         print(f"\n[{precision}] rel L2 vs FP64 oracle after 1000 steps: u {e['u']:.3e} tau {e['tau']:.3e}")
     assert np.isfinite([e["u"], e["tau"]]).all()
     assert max(e["u"], e["tau"]) <= bound, e
+
+
+@pytest.mark.parametrize("precision", ["f16", "bf16"])
+def test_slowly_accelerating_channel_in_16_bit_storage(precision, capsys):
+    """Config-1 channel from rest (g = 1e-6): the per-step change of the PDFs is below half
+    a BF16 unit of the stored deviation, which round-to-nearest storage drops step after
+    step (the flow stalls).  BF16 stores round stochastically; both 16-bit modes must track
+    the FP64 oracle."""
+    shape, prm, fl = _channel_case()
+    g, o = pair(shape, prm, fl, precision=precision)
+    g.step(1000)
+    o.step(1000)
+    e = compare(g, o)
+    with capsys.disabled():
+        print(f"\n[{precision} config-1 channel] rel L2 after 1000 steps: u {e['u']:.3e} tau {e['tau']:.3e}")
+    assert max(e["u"], e["tau"]) <= (1e-2 if precision == "bf16" else 3e-2), e
 
 
 # ---------------------------------------------------------------------------------
