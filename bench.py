@@ -167,6 +167,24 @@ def cpu_baseline(target_s=15.0, side=64):
                                 "sample": f"32^3 box of the same workload, {steps1} steps, {dt1:.1f} s"}
     except Exception as exc:  # reported, not fatal: the multi-core figure stands
         out["single_thread"] = {"error": str(exc)[:200]}
+    # the plain-method channel (4 x 32 x 4, 20000 steps) in full
+    try:
+        from oracle import oracle
+        from paper_2009_12279_gb300 import workloads
+
+        cfg = workloads.config_channel()
+        prm = dict(cfg["params"])
+        prm["g"] = prm.pop("body_force")
+        o = oracle.Oracle(cfg["shape"], **prm)
+        o.set_flags(cfg["flags"])
+        t0 = time.perf_counter()
+        o.step(cfg["steps"])
+        dt = time.perf_counter() - t0
+        cells = cfg["shape"][0] * cfg["shape"][1] * cfg["shape"][2]
+        out["channel_full"] = {"value": cells * cfg["steps"] / dt / 1e6, "unit": UNIT, "seconds": dt,
+                               "sample": f"4x32x4 channel, {cfg['steps']} steps, FP64"}
+    except Exception as exc:
+        out["channel_full"] = {"error": str(exc)[:200]}
     return out
 
 
