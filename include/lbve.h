@@ -129,7 +129,9 @@ lbve_status lbve_set_geometry(lbve_ctx *ctx, const uint8_t *flags, const double 
 /*
  * Initial fields (host arrays, each may be NULL): rho (n), u (3n), tau (6n).  The
  * PDFs are set to the equilibrium of Eq. (lb-equilibrium) at (rho, u); tau is copied.
- * Resets the time counter to 0.  Particle cells keep their state.
+ * Resets the time counter to 0.  Particle cells keep their state.  Page-locked arrays
+ * the device can address (cudaHostAlloc, cudaHostRegister) are read in place by one
+ * kernel; other host memory goes through device staging in z-slabs.  Synchronises.
  */
 lbve_status lbve_init_fields(lbve_ctx *ctx, const double *rho, const double *u, const double *tau);
 
@@ -157,7 +159,9 @@ lbve_status lbve_step(lbve_ctx *ctx, int nsteps);
 /*
  * Copy the macroscopic fields to host arrays (each may be NULL): rho (n), u (3n, the
  * physical velocity (j + F/2)/rho of Eq. (macroscopic-velocity) with F = g + F^p),
- * tau (6n), flags (n).  Non-fluid cells read 0.  Synchronises the stream.
+ * tau (6n), flags (n).  Non-fluid cells read 0.  Page-locked arrays the device can
+ * address are written in place by one kernel; other host memory goes through device
+ * staging in z-slabs.  Synchronises the stream.
  */
 lbve_status lbve_read_fields(lbve_ctx *ctx, double *rho, double *u, double *tau, uint8_t *flags);
 

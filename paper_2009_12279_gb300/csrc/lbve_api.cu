@@ -300,6 +300,17 @@ __global__ void __launch_bounds__(192) k_body_partials(const double *__restrict_
     }
 }
 
+// Device address of a host buffer that is page-locked and mapped (cudaHostAlloc or
+// cudaHostRegister under unified addressing), else nullptr (pageable memory is staged).
+void *mapped_host(const void *p) {
+    cudaPointerAttributes at;
+    if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    return at.type == cudaMemoryTypeHost ? at.devicePointer : nullptr;
+}
+
 // Advance a pool's device step counter (after each step's stream-collide).
 __global__ void k_step_count(unsigned *dstep) { *dstep += 1u; }
 
@@ -677,6 +688,19 @@ lbve_status lbve_init_fields(lbve_ctx *c, const double *rho, const double *u, co
     if (!c) return LBVE_EINVAL;
     if (c->pool) return fail(c, LBVE_ESTATE, "fields cannot be reset while the solve is in a pool");
     const long long n = c->d.g.n, plane = (long long)c->p.nx * c->p.ny;
+    {
+        // page-locked buffers the device can address: one kernel reads them in place
+        const double *drho = rho ? (const double *)mapped_host(rho) : nullptr;
+        const double *du = u ? (const double *)mapped_host(u) : nullptr;
+        const double *dtau = tau ? (const double *)mapped_host(tau) : nullptr;
+        if ((!rho || drho) && (!u || du) && (!tau || dtau)) {
+            c->d.cur = 0;
+            CK(c->kt->init(c->d, drho, du, dtau, 0, n, n, c->stream), "init kernel");
+            CK(cudaStreamSynchronize(c->stream), "init sync");
+            c->t = 0;
+            return LBVE_OK;
+        }
+    }
     const int zs = slab_planes(c);
     const long long cap = plane * zs;
     double *st = (double *)dev_alloc(c, sizeof(double) * 10 * (size_t)cap);
@@ -889,7 +913,13 @@ lbve_status lbve_read_fields_device(lbve_ctx *c, double *rho, double *u, double 
 lbve_status lbve_read_fields(lbve_ctx *c, double *rho, double *u, double *tau, uint8_t *flags) {
     if (!c) return LBVE_EINVAL;
     const long long n = c->d.g.n, plane = (long long)c->p.nx * c->p.ny;
-    if (rho || u || tau) {
+    double *drho = rho ? (double *)mapped_host(rho) : nullptr;
+    double *du = u ? (double *)mapped_host(u) : nullptr;
+    double *dtau = tau ? (double *)mapped_host(tau) : nullptr;
+    if ((rho || u || tau) && (!rho || drho) && (!u || du) && (!tau || dtau)) {
+        // page-locked buffers the device can address: one kernel writes them in place
+        CK(c->kt->read(c->d, (int)(c->t & 1), drho, du, dtau, 0, c->p.nz, n, c->stream), "read kernel");
+    } else if (rho || u || tau) {
         const int zs = slab_planes(c);
         const long long cap = plane * zs;
         double *st = (double *)dev_alloc(c, sizeof(double) * 10 * (size_t)cap);

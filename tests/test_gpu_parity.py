@@ -305,3 +305,38 @@ def test_fp32_even_width_obstacles_1000_steps():
     o.step(1000)
     e = compare(g, o)
     assert max(e["u"], e["tau"]) <= TOL_F32, e
+
+
+def test_pinned_host_buffers_match_pageable():
+    """Page-locked host buffers are read and written in place by the kernels (no device
+    staging); the fields must be bitwise those of the staged path for pageable buffers."""
+    import torch
+
+    shape, prm, fl, wall, rho0, u0, t0 = _obstacle_case((36, 21, 19), seed=17)
+    out = []
+    for pinned in (False, True):
+        from paper_2009_12279_gb300 import Solver
+
+        s = Solver(shape, precision="f32", **prm)
+        s.set_geometry(fl, wall)
+        if pinned:
+            pr = torch.from_numpy(np.ascontiguousarray(rho0)).pin_memory()
+            pu = torch.from_numpy(np.ascontiguousarray(u0)).pin_memory()
+            pt = torch.from_numpy(np.ascontiguousarray(t0)).pin_memory()
+            s.init_fields_ptr(pr.data_ptr(), pu.data_ptr(), pt.data_ptr())
+        else:
+            s.init_fields(rho=rho0, u=u0, tau=t0)
+        s.step(37)
+        if pinned:
+            n = int(np.prod(shape))
+            orho = torch.empty(n, dtype=torch.float64).pin_memory()
+            ou = torch.empty(3 * n, dtype=torch.float64).pin_memory()
+            otau = torch.empty(6 * n, dtype=torch.float64).pin_memory()
+            s.read_fields_ptr(orho.data_ptr(), ou.data_ptr(), otau.data_ptr())
+            out.append((orho.numpy().copy(), ou.numpy().copy(), otau.numpy().copy()))
+        else:
+            rho, u, tau, _ = s.read_fields()
+            out.append((rho.reshape(-1), u.reshape(-1), tau.reshape(-1)))
+        s.close()
+    for a, b in zip(out[0], out[1]):
+        assert np.array_equal(a, b)
