@@ -85,14 +85,31 @@ struct Store<float> {
     __device__ static __forceinline__ void st(float *p, float v, float) { *p = v; }
     __device__ static __forceinline__ void st(float *p, float v, float, uint32_t) { *p = v; }
 };
+#ifndef LBVE_F16_STOCHASTIC
+#define LBVE_F16_STOCHASTIC 1
+#endif
 template <>
 struct Store<__half> {
     using R = float;
     static constexpr bool shifted = true;
-    static constexpr bool keyed = false;
+    static constexpr bool keyed = LBVE_F16_STOCHASTIC;
     __device__ static __forceinline__ float ld(const __half *p, float inv) { return __half2float(*p) * inv; }
     __device__ static __forceinline__ void st(__half *p, float v, float sc) { *p = __float2half_rn(v * sc); }
-    __device__ static __forceinline__ void st(__half *p, float v, float sc, uint32_t) { st(p, v, sc); }
+    // Stochastic rounding, as for BF16 below: 13 hashed bits (the float bits a normal half
+    // drops) are added before a round-toward-zero conversion.  In the half's subnormal
+    // range the conversion drops more bits than that and the rounding there leans
+    // towards zero.
+    __device__ static __forceinline__ void st(__half *p, float v, float sc, uint32_t key) {
+#if LBVE_F16_STOCHASTIC
+        const float x = v * sc;
+        const uint32_t b = __float_as_uint(x);
+        const uint32_t h = ((b ^ key) * 0x9E3779B1u) >> 19;  // high 13 bits of a multiplicative hash
+        const bool finite = (b & 0x7F800000u) != 0x7F800000u;
+        *p = finite ? __float2half_rz(__uint_as_float(b + h)) : __float2half_rn(x);
+#else
+        st(p, v, sc);
+#endif
+    }
 };
 #ifndef LBVE_BF16_STOCHASTIC
 #define LBVE_BF16_STOCHASTIC 1

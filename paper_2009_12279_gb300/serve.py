@@ -22,6 +22,11 @@ from . import lbve, workloads
 
 KINDS = ("channel", "sphere_duct", "sedimenting")
 
+# Residual per step below which a solve in this PDF storage cannot go: stochastically
+# rounded 16-bit storage leaves step-to-step noise in u (measured floors on channels and
+# ducts: BF16 ~2e-5, FP16 ~2.5e-6).  A solve counts as converged at max(tol, 2 x floor).
+RESIDUAL_FLOOR = {"bf16": 4e-5, "f16": 5e-6, "f32": 0.0, "f64": 0.0}
+
 
 @dataclasses.dataclass
 class Request:
@@ -238,7 +243,7 @@ class Server:
                 status = None
                 if not np.isfinite(r) or not np.isfinite(unorm):
                     status = "unstable"
-                elif per_step <= req.tol and steps > self.check_every:
+                elif per_step <= max(req.tol, RESIDUAL_FLOOR.get(self.precision, 0.0)) and steps > self.check_every:
                     status = "converged"
                 elif steps >= req.max_steps:
                     status = "capped"
@@ -282,7 +287,7 @@ def run_one_at_a_time(requests, precision="f32", check_every=100, stream=None, c
             per_step = r / check_every
             if not np.isfinite(r) or not np.isfinite(unorm):
                 status = "unstable"
-            elif per_step <= req.tol and steps > check_every:
+            elif per_step <= max(req.tol, RESIDUAL_FLOOR.get(precision, 0.0)) and steps > check_every:
                 status = "converged"
             elif steps >= req.max_steps:
                 status = "capped"

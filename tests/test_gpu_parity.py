@@ -104,7 +104,7 @@ def test_fp32_obstacles_1000_steps():
     assert np.linalg.norm(bg[2] - bo[2]) <= 1e-4 * np.linalg.norm(bo[2])
 
 
-@pytest.mark.parametrize("precision,bound", [("f16", 5e-2), ("bf16", 1e-2)])
+@pytest.mark.parametrize("precision,bound", [("f16", 2e-3), ("bf16", 1e-2)])
 def test_reduced_precision_error_is_reported(precision, bound, capsys):
     shape, prm, fl, wall, rho0, u0, t0 = _obstacle_case()
     g, o = pair(shape, prm, fl, wall, rho=rho0, u=u0, tau=t0, precision=precision)
@@ -121,8 +121,8 @@ def test_reduced_precision_error_is_reported(precision, bound, capsys):
 def test_slowly_accelerating_channel_in_16_bit_storage(precision, capsys):
     """Config-1 channel from rest (g = 1e-6): the per-step change of the PDFs is below half
     a BF16 unit of the stored deviation, which round-to-nearest storage drops step after
-    step (the flow stalls).  BF16 stores round stochastically; both 16-bit modes must track
-    the FP64 oracle."""
+    step (the flow stalls); in FP16 the same happens later.  Both 16-bit modes round
+    stochastically and must track the FP64 oracle."""
     shape, prm, fl = _channel_case()
     g, o = pair(shape, prm, fl, precision=precision)
     g.step(1000)
@@ -130,7 +130,7 @@ def test_slowly_accelerating_channel_in_16_bit_storage(precision, capsys):
     e = compare(g, o)
     with capsys.disabled():
         print(f"\n[{precision} config-1 channel] rel L2 after 1000 steps: u {e['u']:.3e} tau {e['tau']:.3e}")
-    assert max(e["u"], e["tau"]) <= (1e-2 if precision == "bf16" else 3e-2), e
+    assert max(e["u"], e["tau"]) <= (1e-2 if precision == "bf16" else 2e-3), e
 
 
 # ---------------------------------------------------------------------------------

@@ -184,3 +184,22 @@ def test_replica_timing_reduction_over_two_gloo_ranks():
         assert p.exitcode == 0
     for rank, t, w in res:
         assert t == 2.0 and w == 10.0  # max of per-rank times, sum of per-rank work
+
+
+def test_convergence_respects_the_storage_residual_floor():
+    """Stochastically rounded 16-bit storage cannot go below its residual floor: a BF16 or
+    FP16 solve converges at max(tol, floor), an FP32 solve at tol."""
+    steps = {}
+    for prec in ("f32", "f16", "bf16"):
+        reqs = _fake_requests(1, [10])
+        pool = FakePool(100)
+        srv = serve.Server(prec, pool=pool, solver_factory=lambda req, p, stream: FakeSolver(req),
+                           params_factory=lambda req, p: req.bytes, check_every=100)
+        results, _ = srv.run(reqs)
+        assert results[0].status == "converged"
+        steps[prec] = results[0].steps
+    # the fake residual per step is 1 / k^2 after k steps
+    for prec, n in steps.items():
+        tol = max(1e-6, serve.RESIDUAL_FLOOR[prec])
+        assert 1.0 / n ** 2 <= tol < 1.0 / (n - 100) ** 2
+    assert steps["bf16"] < steps["f16"] < steps["f32"]
