@@ -50,7 +50,13 @@ typedef enum {
 } lbve_status;
 
 /* Storage precision of the PDFs (arithmetic is FP64 for LBVE_F64, else FP32).
- * All reduced modes store the deviation f_i - w_i rho0 (FP16: times 2^pdf_scale_log2). */
+ * All reduced modes store the deviation f_i - w_i rho0 (FP16: times 2^pdf_scale_log2).
+ * The 16-bit modes round the stream-collide's stores stochastically (unbiased; the
+ * random bits hash the value with the step, cell and direction, so results are
+ * deterministic and the same alone and in a pool): round-to-nearest would drop per-step
+ * changes smaller than half a unit of the stored deviation, and slow flows would stall.
+ * The price is a noise floor in the steady-state residual (~2e-5 per step in BF16,
+ * ~2.5e-6 in FP16). */
 typedef enum { LBVE_F64 = 0, LBVE_F32 = 1, LBVE_F16_SHIFTED = 2, LBVE_BF16_SHIFTED = 3 } lbve_pdf_prec;
 
 #define LBVE_FLAG_FLUID 0
