@@ -1076,8 +1076,10 @@ __global__ void __launch_bounds__(256) k_particle_links(Geo g, const PartDev *__
     const int seg = first_seg + p;
     long long *out = links + seg_begin[seg];
     const int cap = capacity[p];
-    __shared__ int scan[256];
+    constexpr int NW = 256 / 32;
+    __shared__ int wsum[NW];
     __shared__ int base;
+    const int lane = (int)threadIdx.x & 31, warp = (int)threadIdx.x >> 5;
     if (threadIdx.x == 0) base = 0;
     __syncthreads();
     for (long long k0 = 0; k0 < nc; k0 += blockDim.x) {
@@ -1097,24 +1099,39 @@ __global__ void __launch_bounds__(256) k_particle_links(Geo g, const PartDev *__
                 }
             }
         }
+        // warp-level compaction in thread order: a ballot skips warps without links, a
+        // shuffle scan places each thread's links within its warp, the warp totals are
+        // scanned by the first warp
         const int cnt = __popc(mask);
-        scan[threadIdx.x] = cnt;
-        __syncthreads();
-        // inclusive Hillis-Steele scan over the block
-        for (int off = 1; off < (int)blockDim.x; off <<= 1) {
-            const int v = (int)threadIdx.x >= off ? scan[threadIdx.x - off] : 0;
-            __syncthreads();
-            scan[threadIdx.x] += v;
-            __syncthreads();
+        int incl = 0;
+        if (__ballot_sync(0xffffffffu, cnt != 0)) {
+            incl = cnt;
+#pragma unroll
+            for (int off = 1; off < 32; off <<= 1) {
+                const int t = __shfl_up_sync(0xffffffffu, incl, off);
+                if (lane >= off) incl += t;
+            }
         }
-        int pos = base + scan[threadIdx.x] - cnt;
+        if (lane == 31) wsum[warp] = incl;
+        __syncthreads();
+        if (warp == 0) {
+            int w = lane < NW ? wsum[lane] : 0;
+#pragma unroll
+            for (int off = 1; off < NW; off <<= 1) {
+                const int t = __shfl_up_sync(0xffffffffu, w, off);
+                if (lane >= off) w += t;
+            }
+            if (lane < NW) wsum[lane] = w;  // inclusive over the warps
+        }
+        __syncthreads();
+        int pos = base + (warp ? wsum[warp - 1] : 0) + incl - cnt;
         for (int i = 1; i < Q; ++i)
             if (mask & (1u << i)) {
                 if (pos < cap) out[pos] = (r << 5) | i;
                 pos++;
             }
         __syncthreads();
-        if (threadIdx.x == blockDim.x - 1) base += scan[threadIdx.x];
+        if (threadIdx.x == 0) base += wsum[NW - 1];
         __syncthreads();
     }
     if (threadIdx.x == 0) seg_count[seg] = base < cap ? base : cap;
