@@ -32,7 +32,12 @@
  *     D_i = w_i [3 (1 - omega-/2) c.F + 9/2 (1 - omega+/2) (uF + Fu):(cc - I/3)].
  *   - Upwind flux: donor cell on the D3Q7 faces, max(+-u_k,0) tau of the upwind cell,
  *     no transverse overlap factors (they are O(u^2) like the dropped edge fluxes).
- *   - The tau div(u) source term is dropped, as the paper marks it zero.
+ *     Variant ORC_FV_CTU keeps them: the donor cell displaced by its velocity overlaps
+ *     the face neighbour along k by |u_k| (1 - |u_a|)(1 - |u_b|) (a, b the other two
+ *     axes), the corner-transport-upwind overlap restricted to the D3Q7 faces; the edge
+ *     and corner overlaps stay in the donor cell.
+ *   - The tau div(u) source term is dropped, as the paper marks it zero (variant
+ *     ORC_FV_DIVU adds it, with div(u) the trace of the central-point gradient).
  *   - grad u next to a solid cell uses the boundary velocity as the face value.
  *   - Stress extrapolation is per link: the face value towards a solid cell is tau(r).
  *   - Momentum exchange on a link r -> r+c_i (solid): c_i (2 f*_i - 6 w_i rho c_i.u_b),
@@ -317,6 +322,8 @@ static void fv_update(orc_state *s, const double *u, const double *tau, double *
     long n = s->n;
     int flux_on = (s->p.fv_terms & ORC_FV_FLUX) != 0;
     int src_on = (s->p.fv_terms & ORC_FV_SOURCE) != 0;
+    int ctu_on = (s->p.fv_terms & ORC_FV_CTU) != 0;
+    int divu_on = (s->p.fv_terms & ORC_FV_DIVU) != 0;
 #pragma omp parallel for schedule(static) if (n >= 32768)
     for (long r = 0; r < n; ++r) {
         if (!is_fluid(s, r)) {
@@ -353,9 +360,16 @@ static void fv_update(orc_state *s, const double *u, const double *tau, double *
                 if (!is_fluid(s, nb)) continue;
                 double vout = sg * u[(long)k * n + r];
                 double vin = -sg * u[(long)k * n + nb];
+                /* transverse overlap of the displaced donor cell with the face neighbour */
+                double tout = 1.0, tin = 1.0;
+                if (ctu_on) {
+                    int a = (k + 1) % 3, b = (k + 2) % 3;
+                    tout = (1.0 - fabs(u[(long)a * n + r])) * (1.0 - fabs(u[(long)b * n + r]));
+                    tin = (1.0 - fabs(u[(long)a * n + nb])) * (1.0 - fabs(u[(long)b * n + nb]));
+                }
                 for (int c = 0; c < 6; ++c) {
-                    double Jo = vout > 0.0 ? vout * tr[c] : 0.0;
-                    double Ji = vin > 0.0 ? vin * tau[(long)c * n + nb] : 0.0;
+                    double Jo = vout > 0.0 ? (vout * tout) * tr[c] : 0.0;
+                    double Ji = vin > 0.0 ? (vin * tin) * tau[(long)c * n + nb] : 0.0;
                     double J = Jo - Ji;
                     net[c] += J;
                 }
@@ -363,6 +377,10 @@ static void fv_update(orc_state *s, const double *u, const double *tau, double *
         }
         double S[6] = {0, 0, 0, 0, 0, 0};
         if (src_on) orc_source(tr, G, s->ep_l, s->inv_l, S);
+        if (divu_on) {
+            double divu = (G[0] + G[4]) + G[8];
+            for (int c = 0; c < 6; ++c) S[c] = S[c] + tr[c] * divu;
+        }
         for (int c = 0; c < 6; ++c) taun[(long)c * n + r] = tr[c] - net[c] + S[c];
     }
 }

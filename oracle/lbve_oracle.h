@@ -40,6 +40,9 @@ extern "C" {
 /* fv_terms bits: which parts of the finite-volume stress update run. */
 #define ORC_FV_FLUX 1   /* upwind advective flux (Stability improvements) */
 #define ORC_FV_SOURCE 2 /* Eq. (source) */
+#define ORC_FV_CTU 4    /* face fluxes scaled by the corner-transport-upwind transverse
+                           overlap (1 - |u_a|)(1 - |u_b|) of the donor cell */
+#define ORC_FV_DIVU 8   /* the tau_ij div(u) term of Eq. (source), which the paper sets to 0 */
 
 typedef struct {
     int nx, ny, nz;
@@ -52,7 +55,7 @@ typedef struct {
     double magic;    /* TRT magic parameter, 3/16 in the paper */
     int n_wall;      /* number of moving-wall classes */
     double wall_vel[ORC_MAX_WALL][3];
-    int fv_terms;    /* ORC_FV_FLUX | ORC_FV_SOURCE for the method */
+    int fv_terms;    /* ORC_FV_* bits; ORC_FV_FLUX | ORC_FV_SOURCE for the method */
 } orc_params;
 
 typedef struct orc_state orc_state;

@@ -20,6 +20,7 @@ LIB = os.path.join(HERE, "liblbve_oracle.so")
 
 FLUID, NOSLIP, WALL0, PART0 = 0, 1, 2, 64
 FV_FLUX, FV_SOURCE = 1, 2
+FV_CTU, FV_DIVU = 4, 8  # variants: transverse CTU overlap on the face fluxes; tau div(u) source
 
 _lock = threading.Lock()
 _lib = None

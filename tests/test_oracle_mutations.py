@@ -18,6 +18,10 @@ MUTANTS = {
     "half_force_shift_dropped": ("u[a] = (j[a] + 0.5 * F[a]) / r;", "u[a] = j[a] / r;"),
     "source_transposed_gradient": ("b += T[k][j] * G[k * 3 + i];", "b += T[k][j] * G[i * 3 + k];"),
     "source_relaxation_dropped": (" - inv_l * T[i][j];", ";"),
+    "ctu_transverse_axes": ("int a = (k + 1) % 3, b = (k + 2) % 3;", "int a = k, b = (k + 2) % 3;"),
+    "ctu_inflow_overlap_of_receiver": ("tin = (1.0 - fabs(u[(long)a * n + nb])) * (1.0 - fabs(u[(long)b * n + nb]));",
+                                       "tin = (1.0 - fabs(u[(long)a * n + r])) * (1.0 - fabs(u[(long)b * n + r]));"),
+    "divu_offdiagonal_trace": ("double divu = (G[0] + G[4]) + G[8];", "double divu = (G[0] + G[1]) + G[8];"),
     "upwind_inflow_sign": ("double vin = -sg * u[(long)k * n + nb];", "double vin = sg * u[(long)k * n + nb];"),
     "force_extrapolation_zero": ("double tf = fl ? 0.5 * (tr + tau[(long)c * s->n + nb]) : tr;",
                                  "double tf = fl ? 0.5 * (tr + tau[(long)c * s->n + nb]) : 0.0;"),

@@ -242,11 +242,106 @@ def test_upwind_advection_is_multinomial(oracle_mod, sign):
         assert np.allclose(tau[c], (c + 1.0) * expect, atol=1e-15)
 
 
-def test_flux_conserves_stress_with_walls(oracle_mod):
-    """With the source off, the FV update conserves sum tau over fluid cells exactly,
-    also with obstacles (zero flux across solid links) and a non-uniform velocity."""
+def _box_overlap(d, vel):
+    """Volume of the unit cell displaced by vel (lattice units, one step) that lies in
+    the cell at integer offset d: the product of the 1-D interval overlaps."""
+    vol = 1.0
+    for a in range(3):
+        vol *= max(0.0, min(1.0 + vel[a], d[a] + 1.0) - max(vel[a], float(d[a])))
+    return vol
+
+
+@pytest.mark.parametrize("vel", [(0.11, 0.07, 0.05), (-0.09, 0.13, -0.06), (0.12, -0.04, 0.0)])
+def test_ctu_advection_moves_face_overlap_volumes(oracle_mod, vel):
+    """Corner-transport-upwind variant (Sec. "Stability improvements"): a point stress
+    under a uniform velocity hands each face neighbour the volume by which the displaced
+    cell overlaps it, computed here from the geometry of the displaced cube; the edge and
+    corner overlaps stay behind.  After k steps the result is the multinomial of those
+    per-step fractions."""
+    n = 16
+    o = oracle_mod.Oracle((n, n, n), beta=0.0, lambda_p=0.0, fv_terms=oracle_mod.FV_FLUX | oracle_mod.FV_CTU)
+    vel = np.array(vel)
+    u = np.broadcast_to(vel[:, None, None, None], (3, n, n, n)).copy()
+    tau = np.zeros((6, n, n, n))
+    tau[:, 8, 8, 8] = np.arange(1.0, 7.0)
+    k = 4
+    for _ in range(k):
+        o.write_tau(tau)
+        tau = o.fv_update(u)
+    moves = []  # (offset, fraction) per face neighbour with a nonzero overlap
+    for axis in range(3):
+        for sg in (1, -1):
+            d = [0, 0, 0]
+            d[axis] = sg
+            frac = _box_overlap(d, vel)
+            if frac > 0.0:
+                moves.append((np.array(d), frac))
+    assert all(abs(f - abs(vel[np.flatnonzero(d)[0]]) * np.prod([1 - abs(vel[a]) for a in range(3) if d[a] == 0])) < 1e-15
+               for d, f in moves)
+    stay = 1.0 - sum(f for _, f in moves)
+    expect = np.zeros((n, n, n))
+    m = len(moves)
+    for counts in np.ndindex(*([k + 1] * m)):
+        if sum(counts) > k:
+            continue
+        c0 = k - sum(counts)
+        coef = math.factorial(k) / math.prod(math.factorial(c) for c in (*counts, c0))
+        p = stay**c0 * math.prod(f**c for (_, f), c in zip(moves, counts))
+        pos = np.array([8, 8, 8]) + sum((c * d for (d, _), c in zip(moves, counts)), np.zeros(3, int))
+        expect[pos[2], pos[1], pos[0]] += coef * p
+    for c in range(6):
+        assert np.abs(tau[c] - (c + 1.0) * expect).max() <= 1e-14 * (c + 1.0)
+
+
+def test_ctu_reduces_to_donor_cell_without_transverse_velocity(oracle_mod):
+    """With the velocity along one axis only the transverse overlap factors are 1, so the
+    corner-transport-upwind update equals the donor-cell one bit for bit."""
+    n = 10
+    u = np.zeros((3, n, n, n))
+    u[1] = 0.08 * RNG.standard_normal((n, n, n))
+    tau = RNG.standard_normal((6, n, n, n))
+    out = []
+    for terms in (oracle_mod.FV_FLUX | oracle_mod.FV_SOURCE,
+                  oracle_mod.FV_FLUX | oracle_mod.FV_SOURCE | oracle_mod.FV_CTU):
+        o = oracle_mod.Oracle((n, n, n), beta=0.4, lambda_p=30.0, fv_terms=terms)
+        o.write_tau(tau)
+        out.append(o.fv_update(u))
+    assert np.array_equal(out[0], out[1])
+    o.write_tau(tau)
+    u[0] = 0.05 * RNG.standard_normal((n, n, n))
+    assert not np.array_equal(o.fv_update(u), out[1])
+
+
+def test_divu_source_adds_stress_times_trace(oracle_mod):
+    """The tau div(u) term of Eq. (source): on a linear velocity field u_j = A_jk r_k the
+    central difference is exact, so switching the term on adds tau_ij tr(A) in the
+    interior, and alone (no flux, no other source) it is the whole update."""
     n = 12
-    o = oracle_mod.Oracle((n, n, n), beta=0.0, lambda_p=0.0, fv_terms=oracle_mod.FV_FLUX)
+    Amat = 1e-3 * RNG.standard_normal((3, 3))
+    z, y, x = np.meshgrid(np.arange(n), np.arange(n), np.arange(n), indexing="ij")
+    r = np.stack([x, y, z]).astype(float)
+    u = np.einsum("jk,k...->j...", Amat, r)
+    tau = RNG.standard_normal((6, n, n, n))
+    inner = (slice(None), slice(1, n - 1), slice(1, n - 1), slice(1, n - 1))
+    res = {}
+    for terms in (oracle_mod.FV_SOURCE, oracle_mod.FV_SOURCE | oracle_mod.FV_DIVU, oracle_mod.FV_DIVU):
+        o = oracle_mod.Oracle((n, n, n), eta=0.3, beta=0.5, lambda_p=40.0, fv_terms=terms)
+        o.write_tau(tau)
+        res[terms] = o.fv_update(u)
+    tr = np.trace(Amat)
+    d = res[oracle_mod.FV_SOURCE | oracle_mod.FV_DIVU] - res[oracle_mod.FV_SOURCE]
+    assert np.allclose(d[inner], (tau * tr)[inner], rtol=1e-9, atol=1e-17)
+    assert np.allclose(res[oracle_mod.FV_DIVU][inner], (tau * (1.0 + tr))[inner], rtol=1e-12, atol=0)
+
+
+@pytest.mark.parametrize("ctu", [False, True])
+def test_flux_conserves_stress_with_walls(oracle_mod, ctu):
+    """With the source off, the FV update conserves sum tau over fluid cells exactly,
+    also with obstacles (zero flux across solid links) and a non-uniform velocity, with
+    and without the transverse overlap factors."""
+    n = 12
+    terms = oracle_mod.FV_FLUX | (oracle_mod.FV_CTU if ctu else 0)
+    o = oracle_mod.Oracle((n, n, n), beta=0.0, lambda_p=0.0, fv_terms=terms)
     fl = (RNG.random((n, n, n)) < 0.15).astype(np.uint8)
     o.set_flags(fl)
     u = 0.05 * RNG.standard_normal((3, n, n, n))
