@@ -66,9 +66,18 @@ typedef enum { LBVE_F64 = 0, LBVE_F32 = 1, LBVE_F16_SHIFTED = 2, LBVE_BF16_SHIFT
 #define LBVE_FLAG_PARTICLE0 64
 #define LBVE_MAX_PARTICLES 64
 
-/* Finite-volume terms (Sec. "Finite volume method"): bit 0 advective flux, bit 1 source. */
+/* Finite-volume terms (Sec. "Finite volume method"): bit 0 advective flux, bit 1 source.
+ * When neither bit is set both are selected.  Two variants may be added:
+ * LBVE_FV_CTU scales each D3Q7 face flux by the corner-transport-upwind transverse
+ * overlap (1 - |u_a|)(1 - |u_b|) of the donor cell (Sec. "Stability improvements": the
+ * donor cell displaced by its velocity overlaps the face neighbour along k by
+ * |u_k|(1 - |u_a|)(1 - |u_b|); the edge and corner overlaps stay in the donor cell).
+ * LBVE_FV_DIVU adds the tau_ij div(u) term of Eq. (source), which the paper sets to 0,
+ * with div(u) the trace of the central-point velocity gradient. */
 #define LBVE_FV_FLUX 1
 #define LBVE_FV_SOURCE 2
+#define LBVE_FV_CTU 4
+#define LBVE_FV_DIVU 8
 
 /* Kernel schedule: two kernels per step (LB, then FV), or one fused kernel per step. */
 #define LBVE_SCHED_AUTO 0
@@ -93,7 +102,7 @@ typedef struct {
     int pdf_prec;        /* lbve_pdf_prec */
     int pdf_scale_log2;  /* FP16 storage scale 2^k of the shifted PDFs (-1: k = 15); FP32
                             and BF16 keep the FP32 exponent range and store unscaled */
-    int fv_terms;        /* LBVE_FV_* bits; 0 selects both */
+    int fv_terms;        /* LBVE_FV_* bits; no FLUX or SOURCE bit selects both */
     int schedule;        /* LBVE_SCHED_* */
     int block_x;         /* per-cell kernels: threads per block along x (32, 64 or 128; blocks
                             hold 128 threads); 0 selects the default */

@@ -24,6 +24,8 @@ UNITS = {
     "lbve_api.cu": [],
     "lbve_f64.cu": ["--fmad=false"],
     "lbve_f32.cu": [],
+    "lbve_f16.cu": [],
+    "lbve_bf16.cu": [],
     "lbve_noalloc.cu": [],
 }
 

@@ -154,7 +154,7 @@ bool valid_params(const lbve_params *p, std::string &why) {
     if (p->beta > 0.0 && !(p->lambda_p > 0.0)) return why = "lambda_p must be > 0 when beta > 0", false;
     if (p->pdf_prec < LBVE_F64 || p->pdf_prec > LBVE_BF16_SHIFTED) return why = "unknown pdf_prec", false;
     if (p->pdf_scale_log2 < -1 || p->pdf_scale_log2 > 24) return why = "pdf_scale_log2 out of range", false;
-    if (p->fv_terms < 0 || p->fv_terms > 3) return why = "fv_terms out of range", false;
+    if (p->fv_terms < 0 || p->fv_terms > 15) return why = "fv_terms out of range", false;
     if (p->block_x != 0 && p->block_x != 32 && p->block_x != 64 && p->block_x != 128)
         return why = "block_x must be 0, 32, 64 or 128", false;
     if (!(p->magic >= 0.0)) return why = "magic must be >= 0", false;
@@ -215,9 +215,12 @@ void lbve::fill_phys(const lbve_params &p, Phys<double> &ph) {
     if (p.pdf_prec != LBVE_F16_SHIFTED) k = 0;
     ph.scale = std::ldexp(1.0, k);
     ph.inv_scale = std::ldexp(1.0, -k);
-    const int terms = p.fv_terms == 0 ? (LBVE_FV_FLUX | LBVE_FV_SOURCE) : p.fv_terms;
+    const int base = LBVE_FV_FLUX | LBVE_FV_SOURCE;
+    const int terms = (p.fv_terms & base) == 0 ? (p.fv_terms | base) : p.fv_terms;
     ph.flux_on = (terms & LBVE_FV_FLUX) != 0;
     ph.src_on = (terms & LBVE_FV_SOURCE) != 0;
+    ph.ctu_on = (terms & LBVE_FV_CTU) != 0;
+    ph.divu_on = (terms & LBVE_FV_DIVU) != 0;
 }
 
 bool lbve::params_valid(const lbve_params *p, std::string &why) { return valid_params(p, why); }
@@ -1117,6 +1120,7 @@ struct lbve_pool {
     unsigned *dstep = nullptr;  // device: steps since the entries were built
     struct FvGroup {
         int tx, start, n, total, grid;  // stress tile width, first entry, entries, items, grid
+        int var;                        // 1 when a member of the group uses a finite-volume variant
     };
     std::vector<FvGroup> fv_groups;
     bool dirty = true;
@@ -1178,7 +1182,7 @@ lbve_status build_entries(lbve_pool *P) {
     int lb_first = 0;
     size_t slot = 0;
     for (int tx : {16, 32, 64}) {
-        lbve_pool::FvGroup grp{tx, (int)slot, 0, 0, 0};
+        lbve_pool::FvGroup grp{tx, (int)slot, 0, 0, 0, 0};
         int fv_first = 0;
         for (size_t m = 0; m < n; ++m) {
             const lbve_ctx *c = P->members[m];
@@ -1194,6 +1198,7 @@ lbve_status build_entries(lbve_pool *P) {
             fv_first += fvi;
             ++slot;
             ++grp.n;
+            grp.var |= P->kt->fv_variant_of(c->d);
         }
         if (grp.n == 0) continue;
         grp.total = fv_first;
@@ -1274,7 +1279,7 @@ lbve_status enqueue_steps(lbve_pool *P, int q, int nsteps) {
         PCK(cudaGetLastError(), "step counter");
         for (const lbve_pool::FvGroup &grp : P->fv_groups)
             PCK(P->kt->fv_batched((const unsigned char *)P->entries[0] + (size_t)grp.start * P->kt->batch_entry_bytes,
-                                  grp.n, grp.total, kk, grp.grid, grp.tx, P->stream),
+                                  grp.n, grp.total, kk, grp.grid, grp.tx, grp.var, P->stream),
                 "batched fv");
         s = fan_out(P, with_parts, [&](lbve_ctx *c, cudaStream_t st) -> lbve_status {
             DevState d = c->d;

@@ -408,11 +408,14 @@ __device__ __forceinline__ void collide(R (&f)[Q], R rho, R drho, const R u[3], 
 // improvements"): velocity gradient by the central-point rule (boundary velocity as the
 // face value towards solid cells), donor-cell flux on the D3Q7 faces with zero flux
 // across solid links, source Eq. (source) without the tau div u term, explicit Euler.
+// Variants (compiled in when VAR, then chosen per solve): ph.ctu_on scales a face flux by
+// the donor cell's transverse overlap (1 - |u_a|)(1 - |u_b|); ph.divu_on adds tau div u
+// to the source.  With VAR false the method's own update is all that is compiled.
 // nb.u(l, k), nb.tau(l, c): velocity / stress of the face-l neighbour (fluid only);
 // nb.ub(l, out): boundary velocity of a solid face-l neighbour.
 // FP64 mode keeps the face-by-face order of the plain statement; shifted modes gather
 // the outflow as (sum of outgoing face velocities) * tau(r).
-template <class R, bool SH, class Nb>
+template <class R, bool SH, bool VAR, class Nb>
 __device__ __forceinline__ void fv_core(const Phys<R> &ph, const R (&tr)[6], const R (&ur)[3], uint32_t mask,
                                         const Nb &nb, R out[6]) {
     R un[6][3];
@@ -449,10 +452,16 @@ __device__ __forceinline__ void fv_core(const Phys<R> &ph, const R (&tr)[6], con
                 if (nb_solid(mask, l + 1)) continue;
                 const R vout = s > 0 ? ur[k] : -ur[k];
                 const R vin = s > 0 ? -un[l][k] : un[l][k];
+                R tout = R(1), tin = R(1);
+                if (VAR && ph.ctu_on) {
+                    const int ta = k == 2 ? 0 : k + 1, tb = k == 0 ? 2 : k - 1;
+                    tout = (R(1) - fabs(ur[ta])) * (R(1) - fabs(ur[tb]));
+                    tin = (R(1) - fabs(un[l][ta])) * (R(1) - fabs(un[l][tb]));
+                }
 #pragma unroll
                 for (int c = 0; c < 6; ++c) {
-                    const R Jo = vout > R(0) ? vout * tr[c] : R(0);
-                    const R Ji = vin > R(0) ? vin * nb.tau(l, c) : R(0);
+                    const R Jo = vout > R(0) ? (vout * tout) * tr[c] : R(0);
+                    const R Ji = vin > R(0) ? (vin * tin) * nb.tau(l, c) : R(0);
                     net[c] = net[c] + (Jo - Ji);
                 }
             }
@@ -466,8 +475,14 @@ __device__ __forceinline__ void fv_core(const Phys<R> &ph, const R (&tr)[6], con
                 if (nb_solid(mask, l + 1)) continue;
                 const R vout = s > 0 ? ur[k] : -ur[k];
                 const R vin = s > 0 ? -un[l][k] : un[l][k];
-                aout += vout > R(0) ? vout : R(0);
-                const R b = vin > R(0) ? vin : R(0);
+                R ao = vout > R(0) ? vout : R(0);
+                R b = vin > R(0) ? vin : R(0);
+                if (VAR && ph.ctu_on) {
+                    const int ta = k == 2 ? 0 : k + 1, tb = k == 0 ? 2 : k - 1;
+                    ao *= (R(1) - fabs(ur[ta])) * (R(1) - fabs(ur[tb]));
+                    b *= (R(1) - fabs(un[l][ta])) * (R(1) - fabs(un[l][tb]));
+                }
+                aout += ao;
 #pragma unroll
                 for (int c = 0; c < 6; ++c) inflow[c] += b * nb.tau(l, c);
             }
@@ -487,6 +502,7 @@ __device__ __forceinline__ void fv_core(const Phys<R> &ph, const R (&tr)[6], con
             for (int k = 0; k < 3; ++k) b = b + tr[comp(k, j)] * G[k][i];
             S = a + b + ph.ep_l * (G[i][j] + G[j][i]) - ph.inv_l * tr[c];
         }
+        if (VAR && ph.divu_on) S = S + tr[c] * ((G[0][0] + G[1][1]) + G[2][2]);
         out[c] = tr[c] - net[c] + S;
     }
 }

@@ -1,8 +1,7 @@
-// lbve_f32.cu -- FP32 arithmetic with FP32, FP16 or BF16 storage of the shifted PDFs.
+// lbve_f32.cu -- FP32 storage and arithmetic.  The FP16 and BF16 storage modes (also with
+// FP32 arithmetic) have units of their own, so that the three compile in parallel.
 #include "lbve_table.cuh"
 
 namespace lbve {
 const KernelTable *table_f32() { return Launch<float>::table(1); }
-const KernelTable *table_f16() { return Launch<__half>::table(2); }
-const KernelTable *table_bf16() { return Launch<__nv_bfloat16>::table(3); }
 } // namespace lbve

@@ -263,7 +263,7 @@ __global__ void __launch_bounds__(128) k_fv(KArgs<S> a) {
     for (int j = 0; j < 3; ++j) ur[j] = a.u_in[j * np + r];
     const GlobalNb<R> gn{a.g, a.ph, cl, a.tau, a.u_in, a.flag, a.parts};
     const NbAdapter<R> nb{gn};
-    fv_core<R, SH>(a.ph, tr, ur, m, nb, out);
+    fv_core<R, SH, true>(a.ph, tr, ur, m, nb, out);
 #pragma unroll
     for (int c = 0; c < 6; ++c) a.tau_out[c * np + r] = out[c];
 }
@@ -481,7 +481,7 @@ __global__ void __launch_bounds__(FT_X * FT_Y, sizeof(typename Store<S>::R) == 8
                     const int xg = side_coord(x0 - 1 + hi, a.g.nx, a.g.per[0]);
                     const int yg = side_coord(y0 - 1 + hj, a.g.ny, a.g.per[1]);
                     const SmemNb<S> nb{sm, a, sc, sd, su, c2, xg, yg, zg};
-                    fv_core<R, SH>(a.ph, tr, ur, m, nb, out);
+                    fv_core<R, SH, true>(a.ph, tr, ur, m, nb, out);
                 }
 #pragma unroll
                 for (int c = 0; c < 6; ++c) sm.tnew[sc][c][k] = out[c];
@@ -572,8 +572,9 @@ struct FvSmemNb {
     }
 };
 
-// Stress update of work item `item` (TX x TY tile, z-chunk) of one solve.
-template <class S, int TX = FV_X>
+// Stress update of work item `item` (TX x TY tile, z-chunk) of one solve; VAR compiles in
+// the optional finite-volume variants.
+template <class S, int TX, bool VAR>
 __device__ __forceinline__ void fv_tile(const KArgs<S> &a, FvSmem<typename Store<S>::R, FvTile<TX>::HN> &sm, int item,
                                         int zchunk) {
     using R = typename Store<S>::R;
@@ -655,7 +656,7 @@ __device__ __forceinline__ void fv_tile(const KArgs<S> &a, FvSmem<typename Store
 #pragma unroll
                 for (int j = 0; j < 3; ++j) ur[j] = sm.u[sc][j][kc];
                 const FvSmemNb<S, FVH_X, FVH_N> nb{sm, a, sc, sd, su, kc, x, y, z};
-                fv_core<R, SH>(a.ph, tr, ur, m, nb, out);
+                fv_core<R, SH, VAR>(a.ph, tr, ur, m, nb, out);
             }
 #pragma unroll
             for (int c = 0; c < 6; ++c) a.tau_out[c * np + r] = out[c];
@@ -665,12 +666,12 @@ __device__ __forceinline__ void fv_tile(const KArgs<S> &a, FvSmem<typename Store
     cp_async_wait_all();
 }
 
-template <class S>
+template <class S, bool VAR>
 __global__ void __launch_bounds__(FV_X * FV_Y, sizeof(typename Store<S>::R) == 8 ? 2 : LBVE_FV_MIN_BLOCKS) k_fv_tiled(KArgs<S> a, int zchunk) {
     using R = typename Store<S>::R;
     extern __shared__ __align__(16) unsigned char fv_smem_raw[];
     FvSmem<R> &sm = *reinterpret_cast<FvSmem<R> *>(fv_smem_raw);
-    fv_tile<S>(a, sm, blockIdx.x, zchunk);
+    fv_tile<S, FV_X, VAR>(a, sm, blockIdx.x, zchunk);
 }
 
 // ---------------------------------------------------------------------------------
@@ -767,8 +768,9 @@ __global__ void __launch_bounds__(BLB_X * BLB_Y, LBVE_LBB_MIN_BLOCKS) k_lb_batch
 }
 
 // Batched stress update over the solves whose stress tile is TX wide (the pool launches
-// one of these per tile width present; fv_first counts within that group).
-template <class S, int TX>
+// one of these per tile width present; fv_first counts within that group).  VAR when a
+// solve of the group uses a finite-volume variant (the others compute as without it).
+template <class S, int TX, bool VAR>
 __global__ void __launch_bounds__(FV_NT, sizeof(typename Store<S>::R) == 8 ? 2 : LBVE_FV_MIN_BLOCKS) k_fv_batched(
     const BatchEntry<S> *__restrict__ e, int nsolves, int total, int k) {
     using R = typename Store<S>::R;
@@ -787,7 +789,7 @@ __global__ void __launch_bounds__(FV_NT, sizeof(typename Store<S>::R) == 8 ? 2 :
             batch_load<S>(sa, e[sv], k, 0u, threadIdx.x, FV_NT);  // the stress update uses no step index
             __syncthreads();
         }
-        fv_tile<S, TX>(sa, sm, it - first, zchunk);
+        fv_tile<S, TX, VAR>(sa, sm, it - first, zchunk);
         __syncthreads();
     }
 }

@@ -34,6 +34,8 @@ struct Phys {
     R rho_ref;     // reference density rho0 of the solve (all modes)
     R scale, inv_scale;
     int flux_on, src_on;
+    int ctu_on;   // face fluxes scaled by the transverse overlap of the displaced donor cell
+    int divu_on;  // the tau div(u) source term
     R wall_vel[MAX_WALL][3];
 };
 
@@ -97,13 +99,15 @@ struct KernelTable {
     // dstep: device counter of the steps since the entries were built (their step index base)
     cudaError_t (*lb_batched)(const void *entries, int n, int total, int k, int grid, const unsigned *dstep,
                               cudaStream_t);
-    // stress update of the solves with stress tile width tx (entries: that group only)
-    cudaError_t (*fv_batched)(const void *entries, int n, int total, int k, int grid, int tx, cudaStream_t);
+    // stress update of the solves with stress tile width tx (entries: that group only);
+    // var: some solve of the group uses a finite-volume variant
+    cudaError_t (*fv_batched)(const void *entries, int n, int total, int k, int grid, int tx, int var, cudaStream_t);
     int (*batched_grid)(int which);  // resident blocks: 0 stream-collide, else stress tile width
     cudaError_t (*residual)(const DevState &, void *usnap, double *partial, int nblocks, cudaStream_t);
     // the tile widths fill_entry will use for requested widths (0: default by nx)
     void (*batch_tiles)(const DevState &, int lb_tx, int fv_tx, int *lb_eff, int *fv_eff);
     int (*fv_zchunk_of)(const DevState &);  // z-planes per block the stress kernel will use
+    int (*fv_variant_of)(const DevState &);  // 1 when the solve uses a finite-volume variant
 };
 
 // Bounding-box side used to size the per-particle scratch (cells within R + margin).

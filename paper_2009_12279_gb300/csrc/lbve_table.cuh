@@ -24,6 +24,8 @@ inline Phys<R> convert_phys(const Phys<double> &p) {
     o.inv_scale = (R)p.inv_scale;
     o.flux_on = p.flux_on;
     o.src_on = p.src_on;
+    o.ctu_on = p.ctu_on;
+    o.divu_on = p.divu_on;
     for (int c = 0; c < MAX_WALL; ++c)
         for (int k = 0; k < 3; ++k) o.wall_vel[c][k] = (R)p.wall_vel[c][k];
     return o;
@@ -88,7 +90,9 @@ struct Launch {
         if (zc > d.g.nz) zc = d.g.nz;
         return (int)zc;
     }
-    static cudaError_t fv(const DevState &d, cudaStream_t s) {
+    static bool fv_variant(const DevState &d) { return d.ph.ctu_on || d.ph.divu_on; }
+    template <bool VAR>
+    static cudaError_t fv_var(const DevState &d, cudaStream_t s) {
         KArgs<S> a = args(d);
         const int zc = fv_zchunk(d);
         const int tiles = ((d.g.nx + FV_X - 1) / FV_X) * ((d.g.ny + FV_Y - 1) / FV_Y);
@@ -96,12 +100,15 @@ struct Launch {
         const size_t sm = sizeof(FvSmem<R>);
         static bool configured = false;
         if (!configured) {
-            cudaError_t e = cudaFuncSetAttribute(k_fv_tiled<S>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+            cudaError_t e = cudaFuncSetAttribute(k_fv_tiled<S, VAR>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
             if (e != cudaSuccess) return e;
             configured = true;
         }
-        k_fv_tiled<S><<<nblk, FV_X * FV_Y, sm, s>>>(a, zc);
+        k_fv_tiled<S, VAR><<<nblk, FV_X * FV_Y, sm, s>>>(a, zc);
         return cudaGetLastError();
+    }
+    static cudaError_t fv(const DevState &d, cudaStream_t s) {
+        return fv_variant(d) ? fv_var<true>(d, s) : fv_var<false>(d, s);
     }
     static cudaError_t momentum_exchange(const DevState &d, int parity, const long long *links, const int *seg_begin,
                                          const int *seg_count, int nseg, int max_len, double *contrib, cudaStream_t s) {
@@ -264,34 +271,44 @@ struct Launch {
         k_lb_batched<S><<<grid, BLB_X * BLB_Y, 0, s>>>((const BatchEntry<S> *)entries, n, total, k, dstep);
         return cudaGetLastError();
     }
-    template <int TX>
+    template <int TX, bool VAR>
     static cudaError_t fv_batched_tx(const void *entries, int n, int total, int k, int grid, cudaStream_t s) {
         const size_t sm = sizeof(FvSmem<R, FvTile<TX>::HN>);
         static bool configured = false;
         if (!configured) {
-            cudaError_t e = cudaFuncSetAttribute(k_fv_batched<S, TX>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+            cudaError_t e =
+                cudaFuncSetAttribute(k_fv_batched<S, TX, VAR>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
             if (e != cudaSuccess) return e;
             configured = true;
         }
-        k_fv_batched<S, TX><<<grid, FV_NT, sm, s>>>((const BatchEntry<S> *)entries, n, total, k);
+        k_fv_batched<S, TX, VAR><<<grid, FV_NT, sm, s>>>((const BatchEntry<S> *)entries, n, total, k);
         return cudaGetLastError();
     }
-    static cudaError_t fv_batched(const void *entries, int n, int total, int k, int grid, int tx, cudaStream_t s) {
-        if (total <= 0) return cudaSuccess;
+    template <bool VAR>
+    static cudaError_t fv_batched_var(const void *entries, int n, int total, int k, int grid, int tx, cudaStream_t s) {
         if constexpr (FvBatchTiles<R>::wide) {
-            if (tx == 16) return fv_batched_tx<16>(entries, n, total, k, grid, s);
-            if (tx == 64) return fv_batched_tx<64>(entries, n, total, k, grid, s);
+            if (tx == 16) return fv_batched_tx<16, VAR>(entries, n, total, k, grid, s);
+            if (tx == 64) return fv_batched_tx<64, VAR>(entries, n, total, k, grid, s);
         }
-        return fv_batched_tx<32>(entries, n, total, k, grid, s);
+        return fv_batched_tx<32, VAR>(entries, n, total, k, grid, s);
     }
+    static cudaError_t fv_batched(const void *entries, int n, int total, int k, int grid, int tx, int var,
+                                  cudaStream_t s) {
+        if (total <= 0) return cudaSuccess;
+        return var ? fv_batched_var<true>(entries, n, total, k, grid, tx, s)
+                   : fv_batched_var<false>(entries, n, total, k, grid, tx, s);
+    }
+    // resident blocks per SM of the batched stress kernel (both builds are held to the
+    // same launch bound, so one grid serves both)
     template <int TX>
     static int fv_resident() {
         int per = 1;
         const size_t sm = sizeof(FvSmem<R, FvTile<TX>::HN>);
-        cudaFuncSetAttribute(k_fv_batched<S, TX>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_fv_batched<S, TX>, FV_NT, sm);
+        cudaFuncSetAttribute(k_fv_batched<S, TX, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_fv_batched<S, TX, false>, FV_NT, sm);
         return per;
     }
+    static int fv_variant_of(const DevState &d) { return fv_variant(d) ? 1 : 0; }
     // resident blocks of the persistent grids: which = 0 for the stream-collide, else the
     // stress kernel of tile width `which`
     static int batched_grid(int which) {
@@ -331,7 +348,7 @@ const KernelTable *Launch<S>::table(int prec) {
                                       &pdfs_io,       &reduce,          &probe,      &build_mask,
                                       &fused,         sizeof(BatchEntry<S>), &fill_entry, &lb_batched,
                                       &fv_batched,    &batched_grid,    &residual,   &batch_tiles,
-                                      &fv_zchunk_of};
+                                      &fv_zchunk_of,  &fv_variant_of};
         return &t;
 }
 
