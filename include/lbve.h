@@ -176,14 +176,16 @@ lbve_status lbve_step(lbve_ctx *ctx, int nsteps);
  * physical velocity (j + F/2)/rho of Eq. (macroscopic-velocity) with F = g + F^p),
  * tau (6n), flags (n).  Non-fluid cells read 0.  Page-locked arrays the device can
  * address are written in place by one kernel; other host memory goes through device
- * staging in z-slabs.  Synchronises the stream.
+ * staging in z-slabs, after one byte per page of it has been written (outputs only:
+ * copies into pages never touched before are slow).  Synchronises the stream.
  */
 lbve_status lbve_read_fields(lbve_ctx *ctx, double *rho, double *u, double *tau, uint8_t *flags);
 
 /* Same fields into device buffers of FP64 (each may be NULL); asynchronous. */
 lbve_status lbve_read_fields_device(lbve_ctx *ctx, double *rho, double *u, double *tau);
 
-/* PDFs f_i (19n, unshifted, FP64) to / from host memory, in the D3Q19 order above. */
+/* PDFs f_i (19n, unshifted, FP64) to / from host memory, in the D3Q19 order above
+ * (pageable output pages are touched before the copy, as for lbve_read_fields). */
 lbve_status lbve_read_pdfs(lbve_ctx *ctx, double *f);
 lbve_status lbve_write_pdfs(lbve_ctx *ctx, const double *f);
 

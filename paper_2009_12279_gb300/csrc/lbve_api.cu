@@ -4,6 +4,7 @@
 // flags, particles, boundary-link list) and enqueues the step kernels of the
 // per-precision kernel tables on its stream.
 #include <cuda_runtime.h>
+#include <unistd.h>
 
 #include <algorithm>
 #include <array>
@@ -312,6 +313,21 @@ void *mapped_host(const void *p) {
         return nullptr;
     }
     return at.type == cudaMemoryTypeHost ? at.devicePointer : nullptr;
+}
+
+// Fault in the pages of a pageable host output buffer before a device-to-host copy into
+// it: one write per page.  Copies into pages that were never touched (fresh calloc/mmap
+// memory) ran 10-15x slower than into touched ones, the pages being brought in one by one
+// on the copy path.  The buffer is output-only, so the bytes written here are overwritten.
+void prefault_output(void *p, size_t bytes) {
+    if (!p || bytes == 0) return;
+    static const size_t page = [] {
+        const long v = sysconf(_SC_PAGESIZE);
+        return v > 0 ? (size_t)v : (size_t)4096;
+    }();
+    volatile unsigned char *b = (volatile unsigned char *)p;
+    for (size_t o = 0; o < bytes; o += page) b[o] = 0;
+    b[bytes - 1] = 0;
 }
 
 // Advance a pool's device step counter (after each step's stream-collide).
@@ -927,6 +943,9 @@ lbve_status lbve_read_fields(lbve_ctx *c, double *rho, double *u, double *tau, u
         const long long cap = plane * zs;
         double *st = (double *)dev_alloc(c, sizeof(double) * 10 * (size_t)cap);
         if (!st) return fail(c, LBVE_ENOMEM, "read staging allocation failed");
+        prefault_output(rho, sizeof(double) * (size_t)n);
+        prefault_output(u, sizeof(double) * 3 * (size_t)n);
+        prefault_output(tau, sizeof(double) * 6 * (size_t)n);
         for (int z0 = 0; z0 < c->p.nz; z0 += zs) {
             const int z1 = std::min(c->p.nz, z0 + zs);
             const long long r0 = (long long)z0 * plane, cnt = (long long)(z1 - z0) * plane;
@@ -946,7 +965,10 @@ lbve_status lbve_read_fields(lbve_ctx *c, double *rho, double *u, double *tau, u
         CK(cudaStreamSynchronize(c->stream), "read sync");
         dev_free(c, st);
     }
-    if (flags) CK(cudaMemcpyAsync(flags, c->d.flag, (size_t)n, cudaMemcpyDeviceToHost, c->stream), "read flags");
+    if (flags) {
+        if (!mapped_host(flags)) prefault_output(flags, (size_t)n);
+        CK(cudaMemcpyAsync(flags, c->d.flag, (size_t)n, cudaMemcpyDeviceToHost, c->stream), "read flags");
+    }
     CK(cudaStreamSynchronize(c->stream), "read sync");
     return LBVE_OK;
 }
@@ -957,6 +979,7 @@ lbve_status lbve_read_pdfs(lbve_ctx *c, double *f) {
     double *d = (double *)dev_alloc(c, sizeof(double) * Q * n);
     if (!d) return fail(c, LBVE_ENOMEM, "pdf staging allocation failed");
     CK(c->kt->pdfs_io(c->d, (int)(c->t & 1), d, 0, c->stream), "pdf read kernel");
+    if (!mapped_host(f)) prefault_output(f, sizeof(double) * Q * (size_t)n);
     CK(cudaMemcpyAsync(f, d, sizeof(double) * Q * n, cudaMemcpyDeviceToHost, c->stream), "pdf copy");
     CK(cudaStreamSynchronize(c->stream), "pdf sync");
     dev_free(c, d);
