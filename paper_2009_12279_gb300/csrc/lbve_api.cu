@@ -1158,7 +1158,9 @@ struct lbve_pool {
     // side streams: the members' small per-step kernels (momentum exchange, body sums,
     // particle update, fill/drain, links) touch only their own buffers, so the chains of
     // different members run side by side, forked from and joined back to the pool stream
-    static constexpr int kSide = 8;
+    // (in a captured graph, one branch per side stream: 64 measured 6 % faster per pool
+    // step than 8 on a 48-member mix, 32 5 %)
+    static constexpr int kSide = 64;
     cudaStream_t side[kSide] = {};
     cudaEvent_t ev_fork = nullptr, ev_join[kSide] = {};
     bool side_ready = false;
