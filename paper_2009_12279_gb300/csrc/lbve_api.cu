@@ -1138,6 +1138,10 @@ struct lbve_pool {
     // k after the build swaps the stress ping-pong and the AA parity k times
     void *entries[2] = {nullptr, nullptr};
     size_t entries_cap = 0;
+    // particle-phase entries of the members with particles (one block each per step)
+    void *pentries = nullptr;
+    size_t pentries_cap = 0;
+    int n_pentries = 0;
     int total_lb = 0;
     int grid_lb = 0;
     unsigned *dstep = nullptr;  // device: steps since the entries were built
@@ -1233,6 +1237,37 @@ lbve_status build_entries(lbve_pool *P) {
     if (slot != n) return pfail(P, LBVE_ECUDA, "internal: stress tile of a member not covered");
     P->total_lb = lb_first;
     if (n) PCK(cudaMemcpyAsync(P->entries[0], host.data(), eb * n, cudaMemcpyHostToDevice, P->stream), "upload entries");
+    // particle-phase entries, in member order
+    const size_t pb = P->kt->part_entry_bytes;
+    std::vector<unsigned char> phost;
+    int np_ = 0;
+    for (lbve_ctx *c : P->members) {
+        if (c->nparts <= 0) continue;
+        phost.resize(pb * (size_t)(np_ + 1));
+        PartScratch ps;
+        ps.nparts = c->nparts;
+        ps.first_seg = (int)c->wall_seg_begin.size();
+        ps.kind = c->pkind;
+        ps.nf = c->pnf;
+        ps.delta = c->pdelta;
+        ps.diag = c->pdiag;
+        ps.conv = c->pconv;
+        ps.links = c->links;
+        ps.seg_begin = c->seg_begin;
+        ps.seg_count = c->seg_count;
+        ps.capacity = c->part_cap;
+        P->kt->fill_part_entry(c->d, (int)((c->t + 1) & 1), ps, phost.data() + pb * (size_t)np_);
+        ++np_;
+    }
+    if ((size_t)np_ > P->pentries_cap) {
+        if (P->pentries) cudaFree(P->pentries);
+        P->pentries = nullptr;
+        P->pentries_cap = std::max<size_t>((size_t)np_, 16);
+        PCK(cudaMalloc(&P->pentries, pb * P->pentries_cap), "pool particle entries");
+    }
+    P->n_pentries = np_;
+    if (np_) PCK(cudaMemcpyAsync(P->pentries, phost.data(), pb * (size_t)np_, cudaMemcpyHostToDevice, P->stream),
+                 "upload particle entries");
     PCK(cudaMemsetAsync(P->dstep, 0, sizeof(unsigned), P->stream), "step counter reset");
     PCK(cudaStreamSynchronize(P->stream), "entries sync");
     if (!P->grid_lb) P->grid_lb = P->kt->batched_grid(0);
@@ -1306,19 +1341,10 @@ lbve_status enqueue_steps(lbve_pool *P, int q, int nsteps) {
             PCK(P->kt->fv_batched((const unsigned char *)P->entries[0] + (size_t)grp.start * P->kt->batch_entry_bytes,
                                   grp.n, grp.total, kk, grp.grid, grp.tx, grp.var, P->stream),
                 "batched fv");
-        s = fan_out(P, with_parts, [&](lbve_ctx *c, cudaStream_t st) -> lbve_status {
-            DevState d = c->d;
-            if ((k + 1) & 1) d.cur ^= 1;  // after the stress swap of this step
-            const int parity_next = (int)((c->t + k + 1) & 1);
-            PCK(c->kt->particle_update(d, c->nparts, st), "pool particle update");
-            PCK(c->kt->fill_drain(d, parity_next, c->nparts, c->pkind, c->pnf, c->pdelta, c->pconv, c->pdiag, st),
-                "pool fill/drain");
-            PCK(c->kt->particle_links(d, c->nparts, c->links, c->seg_begin, c->seg_count,
-                                      (int)c->wall_seg_begin.size(), c->part_cap, st),
-                "pool particle links");
-            return LBVE_OK;
-        });
-        if (s != LBVE_OK) return s;
+        // particle update, fill/drain and links of every member with particles: one block
+        // per member in one launch
+        if (!with_parts.empty())
+            PCK(P->kt->particle_phase_batched(P->pentries, P->n_pentries, kk, P->stream), "pool particle phase");
     }
     return LBVE_OK;
 }
@@ -1361,6 +1387,7 @@ lbve_status lbve_pool_destroy(lbve_pool *P) {
     }
     for (int k = 0; k < 2; ++k)
         if (P->entries[k]) cudaFree(P->entries[k]);
+    if (P->pentries) cudaFree(P->pentries);
     if (P->res_dev) cudaFree(P->res_dev);
     if (P->dstep) cudaFree(P->dstep);
     for (lbve_ctx *c : P->members) c->pool = nullptr;

@@ -992,9 +992,12 @@ __host__ __device__ inline int bbox_capacity_side(double R, int margin) { return
 __device__ __forceinline__ int wrapc(int v, int n) { return ((v % n) + n) % n; }
 
 __device__ __forceinline__ long long bbox_cell(const Geo &g, const BBox &b, long long k, int &x, int &y, int &z) {
-    const int ix = (int)(k % b.ext[0]);
-    const int iy = (int)((k / b.ext[0]) % b.ext[1]);
-    const int iz = (int)(k / ((long long)b.ext[0] * b.ext[1]));
+    // a particle box holds far fewer than 2^32 cells: 32-bit division (64-bit division is
+    // a long software sequence)
+    const unsigned kk = (unsigned)k, row = kk / (unsigned)b.ext[0];
+    const int ix = (int)(kk - row * (unsigned)b.ext[0]);
+    const int iy = (int)(row % (unsigned)b.ext[1]);
+    const int iz = (int)(row / (unsigned)b.ext[1]);
     x = wrapc(b.lo[0] + ix, g.nx);
     y = wrapc(b.lo[1] + iy, g.ny);
     z = wrapc(b.lo[2] + iz, g.nz);
@@ -1023,6 +1026,49 @@ __device__ __forceinline__ void min_image(const Geo &g, const double X[3], int x
     }
 }
 
+// Sphere test |r - X|^2 <= R^2 of Sec. "Moving boundaries" (minimum image), decided as in
+// FP64 but mostly computed in FP32: FP64 runs at a small fraction of the FP32 rate here,
+// and the fill/drain classification tests every cell of a particle's box each step.
+// The FP32 distance differs from the FP64 one by less than `tol` (bounded from the
+// magnitudes involved, see sphere_filter), so outside a shell |d^2 - R^2| <= tol the FP32
+// outcome is the FP64 outcome; inside the shell the FP64 test decides.
+struct SphereFilter {
+    float X[3], inv_n[3], n[3], R2, tol;
+};
+__device__ __forceinline__ SphereFilter sphere_filter(const Geo &g, const PartDev &P) {
+    SphereFilter f;
+    const int nn[3] = {g.nx, g.ny, g.nz};
+    double S = P.R + 4.0;
+    for (int k = 0; k < 3; ++k) {
+        f.X[k] = (float)P.X[k];
+        f.n[k] = (float)nn[k];
+        f.inv_n[k] = 1.0f / (float)nn[k];
+        S += fabs(P.X[k]) + (double)nn[k];
+    }
+    f.R2 = (float)(P.R * P.R);
+    // each FP32 displacement is within ~2^-21 S of the FP64 one (rounding of X, of the
+    // difference and of the periodic shift); the sum of squares then within 2^-18 S^2, and
+    // twice that is kept as the margin
+    f.tol = (float)(S * S * 0x1p-17);
+    return f;
+}
+__device__ __forceinline__ bool inside_sphere(const Geo &g, const PartDev &P, const SphereFilter &f, int x, int y,
+                                              int z) {
+    const int q[3] = {x, y, z};
+    float d2 = 0.0f;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        float dk = (float)q[k] - f.X[k];
+        if (g.per[k]) dk -= f.n[k] * floorf(dk * f.inv_n[k] + 0.5f);
+        d2 += dk * dk;
+    }
+    if (d2 < f.R2 - f.tol) return true;
+    if (d2 > f.R2 + f.tol) return false;
+    double d[3];
+    min_image(g, P.X, x, y, z, d);
+    return d[0] * d[0] + d[1] * d[1] + d[2] * d[2] <= P.R * P.R;
+}
+
 // Initial placement: covered fluid cells become particle cells, their stress is zeroed.
 template <class S>
 __global__ void k_voxelise(KArgs<S> a, PartDev *__restrict__ parts, int p, uint8_t *__restrict__ flag,
@@ -1049,28 +1095,28 @@ __global__ void k_voxelise(KArgs<S> a, PartDev *__restrict__ parts, int p, uint8
 // Symplectic Euler (Sec. "Moving boundaries"): velocities with the momentum-exchange
 // force and torque of this step plus the external ones, then the position with the new
 // velocity.  One thread per particle, FP64.
-template <class S>
-__global__ void k_particle_update(PartDev *__restrict__ parts, int nparts) {
-    const int p = blockIdx.x * blockDim.x + threadIdx.x;
-    if (p >= nparts) return;
-    PartDev &P = parts[p];
+__device__ __forceinline__ void particle_update_one(PartDev &P) {
     for (int k = 0; k < 3; ++k) {
         P.v[k] += (P.Fme[k] + P.Fext[k]) / P.m;
         P.w[k] += (P.Tme[k] + P.Text[k]) / P.I;
         P.X[k] += P.v[k];
     }
 }
+template <class S>
+__global__ void k_particle_update(PartDev *__restrict__ parts, int nparts) {
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= nparts) return;
+    particle_update_one(parts[p]);
+}
 
 // Boundary links of each particle (one block per particle): every (fluid cell r,
 // direction i) with r + c_i covered by the particle, in cell order then direction
 // order, compacted with a block-wide prefix sum so the order is deterministic.
-template <class S>
-__global__ void __launch_bounds__(256) k_particle_links(Geo g, const PartDev *__restrict__ parts,
-                                                        const uint8_t *__restrict__ flag,
-                                                        long long *__restrict__ links,
-                                                        const int *__restrict__ seg_begin, int *__restrict__ seg_count,
-                                                        int first_seg, const int *__restrict__ capacity) {
-    const int p = blockIdx.x;
+template <class S, int NT>
+__device__ __forceinline__ void particle_links_block(const Geo &g, const PartDev *__restrict__ parts, int p,
+                                                     const uint8_t *__restrict__ flag, long long *__restrict__ links,
+                                                     const int *__restrict__ seg_begin, int *__restrict__ seg_count,
+                                                     int first_seg, const int *__restrict__ capacity) {
     const PartDev &P = parts[p];
     if (!P.changed) return;  // no cell converted since the last build: the links still hold
     const BBox b = particle_bbox(g, P.X, P.R, 2);
@@ -1078,7 +1124,7 @@ __global__ void __launch_bounds__(256) k_particle_links(Geo g, const PartDev *__
     const int seg = first_seg + p;
     long long *out = links + seg_begin[seg];
     const int cap = capacity[p];
-    constexpr int NW = 256 / 32;
+    constexpr int NW = NT / 32;
     __shared__ int wsum[NW];
     __shared__ int base;
     const int lane = (int)threadIdx.x & 31, warp = (int)threadIdx.x >> 5;
@@ -1138,6 +1184,14 @@ __global__ void __launch_bounds__(256) k_particle_links(Geo g, const PartDev *__
     }
     if (threadIdx.x == 0) seg_count[seg] = base < cap ? base : cap;
 }
+template <class S>
+__global__ void __launch_bounds__(256) k_particle_links(Geo g, const PartDev *__restrict__ parts,
+                                                        const uint8_t *__restrict__ flag,
+                                                        long long *__restrict__ links,
+                                                        const int *__restrict__ seg_begin, int *__restrict__ seg_count,
+                                                        int first_seg, const int *__restrict__ capacity) {
+    particle_links_block<S, 256>(g, parts, (int)blockIdx.x, flag, links, seg_begin, seg_count, first_seg, capacity);
+}
 
 // Fill/drain after re-voxelisation at the particles' new positions (one block, the
 // particles one after another).  f is the state at time t+1 in the layout PAR reads.
@@ -1148,12 +1202,12 @@ __global__ void __launch_bounds__(256) k_particle_links(Geo g, const PartDev *__
 //                them gives up tau(c)/N_f;
 // the deleted / created momentum goes to the particle as an impulse at the cell.
 template <class S, int PAR>
-__global__ void __launch_bounds__(512) k_fill_drain(KArgs<S> a, PartDev *__restrict__ parts, int nparts,
-                                                    uint8_t *__restrict__ flag, uint32_t *__restrict__ mask,
-                                                    typename Store<S>::R *__restrict__ tau,
-                                                    uint8_t *__restrict__ kind, uint8_t *__restrict__ nf_arr,
-                                                    double *__restrict__ delta, int *__restrict__ conv,
-                                                    double *__restrict__ diag) {
+__device__ __forceinline__ void fill_drain_block(const KArgs<S> &a, PartDev *__restrict__ parts, int nparts,
+                                                 uint8_t *__restrict__ flag, uint32_t *__restrict__ mask,
+                                                 typename Store<S>::R *__restrict__ tau,
+                                                 uint8_t *__restrict__ kind, uint8_t *__restrict__ nf_arr,
+                                                 double *__restrict__ delta, int *__restrict__ conv,
+                                                 double *__restrict__ diag, double (*s_pm)[6]) {
     using R = typename Store<S>::R;
     constexpr bool SH = Store<S>::shifted;
     const long long np = a.g.np;
@@ -1166,17 +1220,17 @@ __global__ void __launch_bounds__(512) k_fill_drain(KArgs<S> a, PartDev *__restr
         PartDev &P = parts[p];
         const BBox b = particle_bbox(a.g, P.X, P.R, 3);
         const long long nc = b.cells();
-        // A: classify
+        const SphereFilter sf = sphere_filter(a.g, P);
+        // A: classify (unrolled: several cells' flag loads in flight per thread)
         int any_local = 0;
+#pragma unroll 4
         for (long long k = threadIdx.x; k < nc; k += blockDim.x) {
             int x, y, z;
             const long long r = bbox_cell(a.g, b, k, x, y, z);
             const int old = flag[r];
             int kd = 0;
             if (old == FLAG_FLUID || old == FLAG_PART0 + p) {
-                double d[3];
-                min_image(a.g, P.X, x, y, z, d);
-                const bool inside = d[0] * d[0] + d[1] * d[1] + d[2] * d[2] <= P.R * P.R;
+                const bool inside = inside_sphere(a.g, P, sf, x, y, z);
                 if (old == FLAG_FLUID) kd = inside ? 2 : 1;
                 else kd = inside ? 0 : 3;
             }
@@ -1192,33 +1246,41 @@ __global__ void __launch_bounds__(512) k_fill_drain(KArgs<S> a, PartDev *__restr
             __syncthreads();
             continue;
         }
-        // A': ordered list of the converted cells (warp ballots + a scan over the warps)
-        __shared__ int s_wsum[32], s_base, s_total;
-        if (threadIdx.x == 0) s_base = 0;
-        __syncthreads();
+        // A': ordered list of the converted cells.  Each thread counts the converted cells
+        // of its own contiguous range of the box, one block-wide exclusive scan of the
+        // counts (warp shuffles, then the warp totals) gives each range's offset, and each
+        // thread writes its cells in increasing order: the list is in cell order.
+        __shared__ int s_wsum[32], s_total;
         const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = (blockDim.x + 31) >> 5;
-        for (long long k0 = 0; k0 < nc; k0 += blockDim.x) {
-            const long long k = k0 + threadIdx.x;
-            const bool pred = k < nc && (kind[k] == 2 || kind[k] == 3);
-            const unsigned bal = __ballot_sync(0xffffffffu, pred);
-            if (lane == 0) s_wsum[warp] = __popc(bal);
-            __syncthreads();
-            if (threadIdx.x == 0) {
-                int acc = 0;
-                for (int w = 0; w < nwarp; ++w) {
-                    const int v = s_wsum[w];
-                    s_wsum[w] = acc;
-                    acc += v;
-                }
-                s_total = acc;
-            }
-            __syncthreads();
-            if (pred) conv[s_base + s_wsum[warp] + __popc(bal & ((1u << lane) - 1u))] = (int)k;
-            __syncthreads();
-            if (threadIdx.x == 0) s_base += s_total;
-            __syncthreads();
+        const long long per = (nc + blockDim.x - 1) / blockDim.x;
+        const long long k_lo = min(nc, per * threadIdx.x), k_hi = min(nc, k_lo + per);
+        int cnt = 0;
+        for (long long k = k_lo; k < k_hi; ++k) cnt += (kind[k] == 2 || kind[k] == 3) ? 1 : 0;
+        int incl = cnt;  // inclusive scan within the warp
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int v = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += v;
         }
-        const int nconv = s_base;
+        if (lane == 31) s_wsum[warp] = incl;
+        __syncthreads();
+        if (warp == 0) {
+            const int w = lane < nwarp ? s_wsum[lane] : 0;
+            int wi = w;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int v = __shfl_up_sync(0xffffffffu, wi, o);
+                if (lane >= o) wi += v;
+            }
+            if (lane < nwarp) s_wsum[lane] = wi - w;  // exclusive offsets of the warps
+            if (lane == 31) s_total = wi;
+        }
+        __syncthreads();
+        int pos = s_wsum[warp] + incl - cnt;
+        for (long long k = k_lo; k < k_hi && pos < s_wsum[warp] + incl; ++k)
+            if (kind[k] == 2 || kind[k] == 3) conv[pos++] = (int)k;
+        const int nconv = s_total;
+        __syncthreads();
         // B: N_f of converted cells, new stress of created cells
         for (int q = threadIdx.x; q < nconv; q += blockDim.x) {
             const long long k = conv[q];
@@ -1280,93 +1342,116 @@ __global__ void __launch_bounds__(512) k_fill_drain(KArgs<S> a, PartDev *__restr
             }
         }
         __syncthreads();
-        // D: impulses (sequential, cell order: destroyed cells, then created cells) and
-        // the populations of created cells
-        if (threadIdx.x == 0) {
-            double dP[3] = {0, 0, 0}, dL[3] = {0, 0, 0};
-            for (int q = 0; q < nconv; ++q) {
-                const long long k = conv[q];
-                if (kind[k] != 2) continue;
-                int x, y, z;
-                const unsigned r = (unsigned)bbox_cell(a.g, b, k, x, y, z);
-                const Cell cl(a.g, x, y, z);
-                R f[Q];
-                load_pdfs<S, PAR>(a, cl, r, f);
-                double Pm[3] = {0, 0, 0};
-                for (int c3 = 0; c3 < 3; ++c3)
-                    for (int i = 0; i < Q; ++i) {
-                        const double fi = (double)f[i] + (SH ? wgt<double>(i) * (double)a.ph.rho0 : 0.0);
-                        Pm[c3] += fi * (double)cdir(i, c3);
+        // D: impulses and the populations of created cells.  A chunk of converted cells at a
+        // time, one per thread, computes its momentum (deleted populations of a destroyed
+        // cell; f^eq(rho_bar, u_b) of a created cell, whose populations it also writes) and
+        // lever arm; thread 0 then adds them to the impulse in the sequential order of the
+        // method: destroyed cells in cell order, then created cells in cell order.  A created
+        // cell reads only stable cells' populations and writes only its own, so the cells of
+        // a chunk are independent.
+        double dP[3] = {0, 0, 0}, dL[3] = {0, 0, 0};
+        for (int pass = 0; pass < 2; ++pass) {
+            const int want = pass == 0 ? 2 : 3;
+            for (int q0 = 0; q0 < nconv; q0 += blockDim.x) {
+                const int q = q0 + (int)threadIdx.x;
+                if (q < nconv && kind[conv[q]] == want) {
+                    const long long k = conv[q];
+                    int x, y, z;
+                    const unsigned r = (unsigned)bbox_cell(a.g, b, k, x, y, z);
+                    const Cell cl(a.g, x, y, z);
+                    double Pm[3] = {0, 0, 0}, d[3];
+                    min_image(a.g, P.X, x, y, z, d);
+                    if (want == 2) {
+                        R f[Q];
+                        load_pdfs<S, PAR>(a, cl, r, f);
+                        for (int c3 = 0; c3 < 3; ++c3)
+                            for (int i = 0; i < Q; ++i) {
+                                const double fi = (double)f[i] + (SH ? wgt<double>(i) * (double)a.ph.rho0 : 0.0);
+                                Pm[c3] += fi * (double)cdir(i, c3);
+                            }
+                    } else {
+                        double rsum = 0.0;
+                        int cnt = 0;
+                        for (int i = 1; i < Q; ++i) {
+                            if (!a.g.per[0] && (x + cx(i) < 0 || x + cx(i) >= a.g.nx)) continue;
+                            if (!a.g.per[1] && (y + cy(i) < 0 || y + cy(i) >= a.g.ny)) continue;
+                            if (!a.g.per[2] && (z + cz(i) < 0 || z + cz(i) >= a.g.nz)) continue;
+                            const int xq = cl.X(cx(i)), yq = cl.Y(cy(i)), zq = cl.Z(cz(i));
+                            if (kind_of(b, xq, yq, zq) != 1) continue;
+                            const unsigned nb =
+                                (unsigned)xq + (unsigned)a.g.nx * ((unsigned)yq + (unsigned)a.g.ny * (unsigned)zq);
+                            const Cell cn(a.g, xq, yq, zq);
+                            R fn[Q];
+                            load_pdfs<S, PAR>(a, cn, nb, fn);
+                            double rn = 0.0;
+                            for (int j = 0; j < Q; ++j) rn += (double)fn[j] + (SH ? wgt<double>(j) * (double)a.ph.rho0 : 0.0);
+                            rsum += rn;
+                            cnt++;
+                        }
+                        const double rho_bar = cnt > 0 ? rsum / (double)cnt : (double)a.ph.rho_ref;
+                        double ub[3];
+                        const double wxd[3] = {P.w[1] * d[2] - P.w[2] * d[1], P.w[2] * d[0] - P.w[0] * d[2],
+                                               P.w[0] * d[1] - P.w[1] * d[0]};
+                        for (int c3 = 0; c3 < 3; ++c3) ub[c3] = P.v[c3] + wxd[c3];
+                        const double usq = ub[0] * ub[0] + ub[1] * ub[1] + ub[2] * ub[2];
+                        double feq[Q];
+                        for (int i = 0; i < Q; ++i) {
+                            const double cu = cx(i) * ub[0] + cy(i) * ub[1] + cz(i) * ub[2];
+                            feq[i] = wgt<double>(i) * rho_bar * (1.0 + 3.0 * cu + 4.5 * cu * cu - 1.5 * usq);
+                        }
+                        for (int i = 0; i < Q; ++i) {
+                            S *dst = PAR == 0 ? a.f + (long long)i * np + r
+                                              : a.f + (long long)copp(i) * np + cl.idx(-cx(i), -cy(i), -cz(i));
+                            const double v = SH ? feq[i] - wgt<double>(i) * (double)a.ph.rho0 : feq[i];
+                            Store<S>::st(dst, (R)v, a.ph.scale);
+                        }
+                        for (int c3 = 0; c3 < 3; ++c3)
+                            for (int i = 0; i < Q; ++i) Pm[c3] += feq[i] * (double)cdir(i, c3);
                     }
-                double d[3];
-                min_image(a.g, P.X, x, y, z, d);
-                dP[0] += Pm[0];
-                dP[1] += Pm[1];
-                dP[2] += Pm[2];
-                dL[0] += d[1] * Pm[2] - d[2] * Pm[1];
-                dL[1] += d[2] * Pm[0] - d[0] * Pm[2];
-                dL[2] += d[0] * Pm[1] - d[1] * Pm[0];
-                if (nf_arr[k] == 0)
-                    for (int c = 0; c < 6; ++c) diag[c] += (double)tau[c * np + r];
-                diag[6] += 1.0;
+                    for (int c3 = 0; c3 < 3; ++c3) {
+                        s_pm[threadIdx.x][c3] = Pm[c3];
+                        s_pm[threadIdx.x][3 + c3] = d[c3];
+                    }
+                }
+                __syncthreads();
+                if (threadIdx.x == 0) {
+                    const int m = min((int)blockDim.x, nconv - q0);
+                    for (int t = 0; t < m; ++t) {
+                        const long long k = conv[q0 + t];
+                        if (kind[k] != want) continue;
+                        const double *Pm = s_pm[t], *d = s_pm[t] + 3;
+                        if (want == 2) {
+                            dP[0] += Pm[0];
+                            dP[1] += Pm[1];
+                            dP[2] += Pm[2];
+                            dL[0] += d[1] * Pm[2] - d[2] * Pm[1];
+                            dL[1] += d[2] * Pm[0] - d[0] * Pm[2];
+                            dL[2] += d[0] * Pm[1] - d[1] * Pm[0];
+                            if (nf_arr[k] == 0) {
+                                int x, y, z;
+                                const long long r = bbox_cell(a.g, b, k, x, y, z);
+                                for (int c = 0; c < 6; ++c) diag[c] += (double)tau[c * np + r];
+                            }
+                            diag[6] += 1.0;
+                        } else {
+                            dP[0] -= Pm[0];
+                            dP[1] -= Pm[1];
+                            dP[2] -= Pm[2];
+                            dL[0] -= d[1] * Pm[2] - d[2] * Pm[1];
+                            dL[1] -= d[2] * Pm[0] - d[0] * Pm[2];
+                            dL[2] -= d[0] * Pm[1] - d[1] * Pm[0];
+                            diag[7] += 1.0;
+                        }
+                    }
+                }
+                __syncthreads();
             }
-            for (int q = 0; q < nconv; ++q) {
-                const long long k = conv[q];
-                if (kind[k] != 3) continue;
-                int x, y, z;
-                const long long r = bbox_cell(a.g, b, k, x, y, z);
-                const Cell cl(a.g, x, y, z);
-                double rsum = 0.0;
-                int cnt = 0;
-                for (int i = 1; i < Q; ++i) {
-                    if (!a.g.per[0] && (x + cx(i) < 0 || x + cx(i) >= a.g.nx)) continue;
-                    if (!a.g.per[1] && (y + cy(i) < 0 || y + cy(i) >= a.g.ny)) continue;
-                    if (!a.g.per[2] && (z + cz(i) < 0 || z + cz(i) >= a.g.nz)) continue;
-                    const int xq = cl.X(cx(i)), yq = cl.Y(cy(i)), zq = cl.Z(cz(i));
-                    if (kind_of(b, xq, yq, zq) != 1) continue;
-                    const unsigned nb = (unsigned)xq + (unsigned)a.g.nx * ((unsigned)yq + (unsigned)a.g.ny * (unsigned)zq);
-                    const Cell cn(a.g, xq, yq, zq);
-                    R fn[Q];
-                    load_pdfs<S, PAR>(a, cn, nb, fn);
-                    double rn = 0.0;
-                    for (int j = 0; j < Q; ++j) rn += (double)fn[j] + (SH ? wgt<double>(j) * (double)a.ph.rho0 : 0.0);
-                    rsum += rn;
-                    cnt++;
-                }
-                const double rho_bar = cnt > 0 ? rsum / (double)cnt : (double)a.ph.rho_ref;
-                double d[3], ub[3];
-                min_image(a.g, P.X, x, y, z, d);
-                const double wxd[3] = {P.w[1] * d[2] - P.w[2] * d[1], P.w[2] * d[0] - P.w[0] * d[2],
-                                       P.w[0] * d[1] - P.w[1] * d[0]};
-                for (int c3 = 0; c3 < 3; ++c3) ub[c3] = P.v[c3] + wxd[c3];
-                const double usq = ub[0] * ub[0] + ub[1] * ub[1] + ub[2] * ub[2];
-                double feq[Q];
-                for (int i = 0; i < Q; ++i) {
-                    const double cu = cx(i) * ub[0] + cy(i) * ub[1] + cz(i) * ub[2];
-                    feq[i] = wgt<double>(i) * rho_bar * (1.0 + 3.0 * cu + 4.5 * cu * cu - 1.5 * usq);
-                }
-                for (int i = 0; i < Q; ++i) {
-                    S *dst = PAR == 0 ? a.f + (long long)i * np + r
-                                      : a.f + (long long)copp(i) * np + cl.idx(-cx(i), -cy(i), -cz(i));
-                    const double v = SH ? feq[i] - wgt<double>(i) * (double)a.ph.rho0 : feq[i];
-                    Store<S>::st(dst, (R)v, a.ph.scale);
-                }
-                double Pm[3] = {0, 0, 0};
-                for (int c3 = 0; c3 < 3; ++c3)
-                    for (int i = 0; i < Q; ++i) Pm[c3] += feq[i] * (double)cdir(i, c3);
-                dP[0] -= Pm[0];
-                dP[1] -= Pm[1];
-                dP[2] -= Pm[2];
-                dL[0] -= d[1] * Pm[2] - d[2] * Pm[1];
-                dL[1] -= d[2] * Pm[0] - d[0] * Pm[2];
-                dL[2] -= d[0] * Pm[1] - d[1] * Pm[0];
-                diag[7] += 1.0;
-            }
+        }
+        if (threadIdx.x == 0)
             for (int c3 = 0; c3 < 3; ++c3) {
                 P.dP[c3] = dP[c3];
                 P.dL[c3] = dL[c3];
             }
-        }
         __syncthreads();
         // E: apply the stress moves and the new flags
         for (long long k = threadIdx.x; k < nc; k += blockDim.x) {
@@ -1411,6 +1496,58 @@ __global__ void __launch_bounds__(512) k_fill_drain(KArgs<S> a, PartDev *__restr
         }
         // clear the stable-cell marks for the next particle / step
         for (long long k = threadIdx.x; k < nc; k += blockDim.x) nf_arr[k] = 0;
+        __syncthreads();
+    }
+}
+template <class S, int PAR>
+__global__ void __launch_bounds__(512) k_fill_drain(KArgs<S> a, PartDev *__restrict__ parts, int nparts,
+                                                    uint8_t *__restrict__ flag, uint32_t *__restrict__ mask,
+                                                    typename Store<S>::R *__restrict__ tau,
+                                                    uint8_t *__restrict__ kind, uint8_t *__restrict__ nf_arr,
+                                                    double *__restrict__ delta, int *__restrict__ conv,
+                                                    double *__restrict__ diag) {
+    __shared__ double s_pm[512][6];  // per-thread momentum and lever arm of a converted cell
+    fill_drain_block<S, PAR>(a, parts, nparts, flag, mask, tau, kind, nf_arr, delta, conv, diag, s_pm);
+}
+
+// Particle phase of a pool step for every member with particles, one 512-thread block per
+// member: particle update, fill/drain, and the links of the particles whose cells
+// converted -- the per-member code of the three separate kernels of a single solve, in
+// the same order, so each member's results are those it gets alone.
+template <class S>
+struct PartEntry {
+    KArgs<S> a[2];   // for even / odd steps k of a launch sequence (the stress ping-pong
+                     // after the step's swap), pointers linked on the host
+    int parity0;     // AA parity fill/drain works in at k = 0
+    int nparts, first_seg;
+    PartDev *parts;
+    uint8_t *flag;
+    uint32_t *mask;
+    uint8_t *kind, *nf;
+    double *delta, *diag;
+    int *conv;
+    long long *links;
+    const int *seg_begin;
+    int *seg_count;
+    const int *capacity;
+};
+template <class S>
+__global__ void __launch_bounds__(512) k_particle_phase_batched(const PartEntry<S> *__restrict__ e, int k) {
+    using R = typename Store<S>::R;
+    const PartEntry<S> &E = e[blockIdx.x];
+    const KArgs<S> &a = E.a[k & 1];
+    for (int p = (int)threadIdx.x; p < E.nparts; p += (int)blockDim.x) particle_update_one(E.parts[p]);
+    __syncthreads();
+    R *tau = const_cast<R *>(a.tau);
+    __shared__ double s_pm[512][6];
+    if (((E.parity0 + k) & 1) == 0)
+        fill_drain_block<S, 0>(a, E.parts, E.nparts, E.flag, E.mask, tau, E.kind, E.nf, E.delta, E.conv, E.diag, s_pm);
+    else
+        fill_drain_block<S, 1>(a, E.parts, E.nparts, E.flag, E.mask, tau, E.kind, E.nf, E.delta, E.conv, E.diag, s_pm);
+    __syncthreads();
+    for (int p = 0; p < E.nparts; ++p) {
+        particle_links_block<S, 512>(a.g, E.parts, p, E.flag, E.links, E.seg_begin, E.seg_count, E.first_seg,
+                                     E.capacity);
         __syncthreads();
     }
 }

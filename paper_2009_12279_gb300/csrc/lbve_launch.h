@@ -49,6 +49,18 @@ struct PartDev {
     int changed;  // 1 when the last fill/drain converted cells (links must be rebuilt)
 };
 
+// A solve's particle scratch and link arrays, as the particle-phase kernels take them.
+struct PartScratch {
+    int nparts, first_seg;
+    uint8_t *kind, *nf;
+    double *delta, *diag;
+    int *conv;
+    long long *links;
+    const int *seg_begin;
+    int *seg_count;
+    const int *capacity;
+};
+
 // Device buffers of one solve.
 struct DevState {
     Geo g;
@@ -108,6 +120,11 @@ struct KernelTable {
     void (*batch_tiles)(const DevState &, int lb_tx, int fv_tx, int *lb_eff, int *fv_eff);
     int (*fv_zchunk_of)(const DevState &);  // z-planes per block the stress kernel will use
     int (*fv_variant_of)(const DevState &);  // 1 when the solve uses a finite-volume variant
+    // pools: the particle phase (update, fill/drain, links) of every member with
+    // particles in one launch; entries built per member like the batch entries
+    size_t part_entry_bytes;
+    void (*fill_part_entry)(const DevState &, int parity0, const PartScratch &, void *entry);
+    cudaError_t (*particle_phase_batched)(const void *entries, int n, int k, cudaStream_t);
 };
 
 // Bounding-box side used to size the per-particle scratch (cells within R + margin).

@@ -309,6 +309,35 @@ struct Launch {
         return per;
     }
     static int fv_variant_of(const DevState &d) { return fv_variant(d) ? 1 : 0; }
+    // d: the member's state when the entries are built; step k after that uses the stress
+    // ping-pong after the step's swap (cur ^ 1 for even k) and AA parity parity0 ^ (k & 1)
+    static void fill_part_entry(const DevState &d, int parity0, const PartScratch &ps, void *entry) {
+        PartEntry<S> &e = *reinterpret_cast<PartEntry<S> *>(entry);
+        DevState d0 = d;
+        d0.cur ^= 1;
+        e.a[0] = args(d0);
+        e.a[1] = args(d);
+        e.parity0 = parity0;
+        e.nparts = ps.nparts;
+        e.first_seg = ps.first_seg;
+        e.parts = d.parts;
+        e.flag = d.flag;
+        e.mask = d.mask;
+        e.kind = ps.kind;
+        e.nf = ps.nf;
+        e.delta = ps.delta;
+        e.diag = ps.diag;
+        e.conv = ps.conv;
+        e.links = ps.links;
+        e.seg_begin = ps.seg_begin;
+        e.seg_count = ps.seg_count;
+        e.capacity = ps.capacity;
+    }
+    static cudaError_t particle_phase_batched(const void *entries, int n, int k, cudaStream_t s) {
+        if (n <= 0) return cudaSuccess;
+        k_particle_phase_batched<S><<<n, 512, 0, s>>>((const PartEntry<S> *)entries, k);
+        return cudaGetLastError();
+    }
     // resident blocks of the persistent grids: which = 0 for the stream-collide, else the
     // stress kernel of tile width `which`
     static int batched_grid(int which) {
@@ -348,7 +377,8 @@ const KernelTable *Launch<S>::table(int prec) {
                                       &pdfs_io,       &reduce,          &probe,      &build_mask,
                                       &fused,         sizeof(BatchEntry<S>), &fill_entry, &lb_batched,
                                       &fv_batched,    &batched_grid,    &residual,   &batch_tiles,
-                                      &fv_zchunk_of,  &fv_variant_of};
+                                      &fv_zchunk_of,  &fv_variant_of,   sizeof(PartEntry<S>), &fill_part_entry,
+                                      &particle_phase_batched};
         return &t;
 }
 
