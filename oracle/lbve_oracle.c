@@ -38,6 +38,10 @@
  *     and corner overlaps stay in the donor cell.
  *   - The tau div(u) source term is dropped, as the paper marks it zero (variant
  *     ORC_FV_DIVU adds it, with div(u) the trace of the central-point gradient).
+ *   - Giesekus (named among the constitutive laws of Sec. "Oldroyd-B fluids", no
+ *     equation printed): the textbook law tau + lambda tau_(1) + (alpha lambda / eta_p)
+ *     tau.tau = eta_p (grad u + grad u^T) adds -(alpha / eta_p) tau.tau to the source of
+ *     Eq. (source); alpha = 0 is Oldroyd-B.
  *   - grad u next to a solid cell uses the boundary velocity as the face value.
  *   - Stress extrapolation is per link: the face value towards a solid cell is tau(r).
  *   - Momentum exchange on a link r -> r+c_i (solid): c_i (2 f*_i - 6 w_i rho c_i.u_b),
@@ -92,6 +96,7 @@ struct orc_state {
     orc_params p;
     long n;
     double omega_p, omega_m, eta_p, ep_l, inv_l;
+    double gk; /* alpha / eta_p of the Giesekus term (0: Oldroyd-B) */
     double *f, *fn;     /* [19][n] */
     double *tau, *taun; /* [6][n] */
     double *rho, *u, *F; /* per-step scratch: [n], [3][n], [3][n] */
@@ -381,6 +386,15 @@ static void fv_update(orc_state *s, const double *u, const double *tau, double *
             double divu = (G[0] + G[4]) + G[8];
             for (int c = 0; c < 6; ++c) S[c] = S[c] + tr[c] * divu;
         }
+        /* Giesekus: -(alpha / eta_p) (tau . tau)_ij */
+        if (src_on && s->gk != 0.0) {
+            for (int c = 0; c < 6; ++c) {
+                int i = CI[c], j = CJ[c];
+                double q = 0.0;
+                for (int k = 0; k < 3; ++k) q += tr[COMP[i][k]] * tr[COMP[k][j]];
+                S[c] = S[c] - s->gk * q;
+            }
+        }
         for (int c = 0; c < 6; ++c) taun[(long)c * n + r] = tr[c] - net[c] + S[c];
     }
 }
@@ -648,6 +662,7 @@ orc_state *orc_create(const orc_params *p) {
     if (!(p->eta > 0.0) || !(p->beta >= 0.0 && p->beta < 1.0) || !(p->rho0 > 0.0)) return NULL;
     if (p->beta > 0.0 && !(p->lambda_p > 0.0)) return NULL;
     if (p->n_wall < 0 || p->n_wall > ORC_MAX_WALL) return NULL;
+    if (!(p->giesekus_alpha >= 0.0 && p->giesekus_alpha <= 0.5)) return NULL;
     orc_state *s = (orc_state *)calloc(1, sizeof(orc_state));
     s->p = *p;
     s->n = (long)p->nx * p->ny * p->nz;
@@ -669,6 +684,7 @@ orc_state *orc_create(const orc_params *p) {
     s->eta_p = p->beta * p->eta;
     s->ep_l = p->beta > 0.0 ? s->eta_p / p->lambda_p : 0.0;
     s->inv_l = p->lambda_p > 0.0 ? 1.0 / p->lambda_p : 0.0;
+    s->gk = p->beta > 0.0 ? p->giesekus_alpha / s->eta_p : 0.0;
     orc_init_fields(s, NULL, NULL, NULL);
     return s;
 }

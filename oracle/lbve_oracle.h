@@ -56,6 +56,7 @@ typedef struct {
     int n_wall;      /* number of moving-wall classes */
     double wall_vel[ORC_MAX_WALL][3];
     int fv_terms;    /* ORC_FV_* bits; ORC_FV_FLUX | ORC_FV_SOURCE for the method */
+    double giesekus_alpha; /* Giesekus mobility in [0, 1/2]; 0 is Oldroyd-B (the method) */
 } orc_params;
 
 typedef struct orc_state orc_state;

@@ -64,6 +64,7 @@ class _Params(ct.Structure):
         ("n_wall", ct.c_int),
         ("wall_vel", (ct.c_double * 3) * 16),
         ("fv_terms", ct.c_int),
+        ("giesekus_alpha", ct.c_double),
     ]
 
 
@@ -155,7 +156,8 @@ class Oracle:
     """One solve held by the CPU oracle.  Arrays are numpy, shape (..., nz, ny, nx)."""
 
     def __init__(self, shape, *, periodic=(1, 1, 1), eta=1.0 / 6.0, beta=0.5, lambda_p=3000.0,
-                 rho0=1.0, g=(0.0, 0.0, 0.0), magic=3.0 / 16.0, wall_vel=(), fv_terms=FV_FLUX | FV_SOURCE):
+                 rho0=1.0, g=(0.0, 0.0, 0.0), magic=3.0 / 16.0, wall_vel=(), fv_terms=FV_FLUX | FV_SOURCE,
+                 giesekus_alpha=0.0):
         nx, ny, nz = (int(v) for v in shape)
         p = _Params()
         p.nx, p.ny, p.nz = nx, ny, nz
@@ -168,6 +170,7 @@ class Oracle:
             for a in range(3):
                 p.wall_vel[k][a] = float(v[a])
         p.fv_terms = int(fv_terms)
+        p.giesekus_alpha = float(giesekus_alpha)
         self._p = p
         self.shape = (nx, ny, nz)
         self.n = nx * ny * nz

@@ -22,6 +22,8 @@ MUTANTS = {
     "ctu_inflow_overlap_of_receiver": ("tin = (1.0 - fabs(u[(long)a * n + nb])) * (1.0 - fabs(u[(long)b * n + nb]));",
                                        "tin = (1.0 - fabs(u[(long)a * n + r])) * (1.0 - fabs(u[(long)b * n + r]));"),
     "divu_offdiagonal_trace": ("double divu = (G[0] + G[4]) + G[8];", "double divu = (G[0] + G[1]) + G[8];"),
+    "giesekus_sign": ("S[c] = S[c] - s->gk * q;", "S[c] = S[c] + s->gk * q;"),
+    "giesekus_product_index": ("q += tr[COMP[i][k]] * tr[COMP[k][j]];", "q += tr[COMP[i][k]] * tr[COMP[i][j]];"),
     "upwind_inflow_sign": ("double vin = -sg * u[(long)k * n + nb];", "double vin = sg * u[(long)k * n + nb];"),
     "force_extrapolation_zero": ("double tf = fl ? 0.5 * (tr + tau[(long)c * s->n + nb]) : tr;",
                                  "double tf = fl ? 0.5 * (tr + tau[(long)c * s->n + nb]) : 0.0;"),

@@ -334,6 +334,57 @@ def test_divu_source_adds_stress_times_trace(oracle_mod):
     assert np.allclose(res[oracle_mod.FV_DIVU][inner], (tau * (1.0 + tr))[inner], rtol=1e-12, atol=0)
 
 
+def _giesekus_steady_shear(eta_p, lam, alpha, gdot):
+    """Steady simple shear u = (gdot y, 0, 0) of the Giesekus law
+    tau + lam tau_(1) + (alpha lam / eta_p) tau.tau = eta_p (L + L^T), tau_(1) the upper
+    convected derivative, L_ij = d u_i / d x_j: its xx, yy and xy components (zz, xz and
+    yz vanish), solved by Newton's method from the Oldroyd-B state."""
+    from scipy.optimize import fsolve
+
+    a = alpha * lam / eta_p
+
+    def eqs(t):
+        txx, tyy, txy = t
+        return [txx - 2 * lam * gdot * txy + a * (txx * txx + txy * txy),
+                tyy + a * (txy * txy + tyy * tyy),
+                txy - lam * gdot * tyy + a * txy * (txx + tyy) - eta_p * gdot]
+
+    t0 = [2 * eta_p * lam * gdot * gdot, 0.0, eta_p * gdot]
+    sol = fsolve(eqs, t0, xtol=1e-13)
+    assert np.abs(eqs(sol)).max() <= 1e-15 * max(1.0, eta_p * gdot) * 10
+    return sol
+
+
+@pytest.mark.parametrize("alpha", [0.0, 0.2, 0.5])
+def test_giesekus_steady_shear(oracle_mod, alpha):
+    """Giesekus variant of the source (constitutive laws of Sec. "Oldroyd-B fluids"):
+    iterating the stress update on a simple shear field (central difference exact, no
+    flux) converges to the root of the steady constitutive equations written out above;
+    alpha > 0 shear-thins (tau_xy < eta_p gdot) and gives a negative second normal
+    stress difference, alpha = 0 is the Oldroyd-B state."""
+    n = 8
+    eta, beta, lam, gdot = 0.4, 0.5, 12.0, 0.1  # Wi = 1.2
+    eta_p = beta * eta
+    o = oracle_mod.Oracle((n, n, n), eta=eta, beta=beta, lambda_p=lam, fv_terms=oracle_mod.FV_SOURCE,
+                          giesekus_alpha=alpha)
+    z, y, x = np.meshgrid(np.arange(n), np.arange(n), np.arange(n), indexing="ij")
+    u = np.zeros((3, n, n, n))
+    u[0] = gdot * y
+    tau = np.zeros((6, n, n, n))
+    for _ in range(1200):
+        o.write_tau(tau)
+        tau = o.fv_update(u)
+    inner = (slice(1, n - 1),) * 3
+    txx, tyy, txy = _giesekus_steady_shear(eta_p, lam, alpha, gdot)
+    expect = {0: txx, 1: tyy, 2: 0.0, 3: txy, 4: 0.0, 5: 0.0}
+    for c, v in expect.items():
+        assert np.allclose(tau[c][inner], v, rtol=1e-10, atol=1e-14), (c, tau[c][inner].ravel()[:3], v)
+    if alpha == 0.0:
+        assert np.isclose(txy, eta_p * gdot, rtol=1e-12) and np.isclose(txx, 2 * eta_p * lam * gdot**2, rtol=1e-12)
+    else:
+        assert txy < eta_p * gdot and tyy < 0.0
+
+
 @pytest.mark.parametrize("ctu", [False, True])
 def test_flux_conserves_stress_with_walls(oracle_mod, ctu):
     """With the source off, the FV update conserves sum tau over fluid cells exactly,
