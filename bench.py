@@ -215,10 +215,16 @@ def run_reference(args):
 # ---------------------------------------------------------------------------------
 # our arm
 # ---------------------------------------------------------------------------------
+# finite-volume variants of the stress update (--fv-terms, --giesekus-alpha); the default is
+# the method's own update
+FV_EXTRA = {}
+
+
 def build_solver(n, prec, schedule, stream, torch):
     from paper_2009_12279_gb300 import Solver, lbve, workloads
 
     cfg = workloads.config_throughput(n)
+    cfg["params"].update(FV_EXTRA)
     sched = {"auto": lbve.SCHED_AUTO, "split": lbve.SCHED_SPLIT, "fused": lbve.SCHED_FUSED}[schedule]
     s = Solver(cfg["shape"], precision=prec, schedule=sched, stream=stream, **cfg["params"])
     flags = cfg["flags_fn"]()
@@ -496,6 +502,7 @@ def run_ours(args):
             "config": {"workload": f"throughput {n}^3 periodic, 1% Bernoulli obstacles, u~U(-1e-3,1e-3), "
                                    f"beta 0.5, lambda 1000, eta 1/6, {args.precisions[0]} PDF storage",
                        "cells": n ** 3, "schedule": args.schedule, "parallelism": f"replicas{world}",
+                       **({"fv_variants": dict(FV_EXTRA)} if FV_EXTRA else {}),
                        "l2": "state larger than L2 (no flush needed)",
                        "schedule_tuning": main.get("schedule_tuning"),
                        "step_bytes_per_cell": main["step_bytes_per_cell"]},
@@ -564,10 +571,18 @@ def main():
     ap.add_argument("--serving-requests", type=int, default=48)
     ap.add_argument("--serving-cap", type=int, default=1000, help="step cap per solve in the serving sample")
     ap.add_argument("--serving-budget-gb", type=float, default=150.0)
+    ap.add_argument("--fv-terms", type=int, default=0,
+                    help="LBVE_FV_* bits of the throughput solve (0: flux and source, the method)")
+    ap.add_argument("--giesekus-alpha", type=float, default=0.0,
+                    help="Giesekus mobility of the throughput solve (0: Oldroyd-B, the method)")
     args = ap.parse_args()
     args.precisions = [p.strip() for p in args.precisions.split(",") if p.strip()]
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
+    if args.fv_terms:
+        FV_EXTRA["fv_terms"] = args.fv_terms
+    if args.giesekus_alpha:
+        FV_EXTRA["giesekus_alpha"] = args.giesekus_alpha
     if args.impl == "reference":
         return run_reference(args)
     return run_ours(args)

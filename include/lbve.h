@@ -106,6 +106,12 @@ typedef struct {
     int schedule;        /* LBVE_SCHED_* */
     int block_x;         /* per-cell kernels: threads per block along x (32, 64 or 128; blocks
                             hold 128 threads); 0 selects the default */
+    double giesekus_alpha; /* Giesekus mobility alpha in [0, 1/2]; 0 (the default) is
+                            Oldroyd-B.  The paper names the Giesekus law among those its
+                            finite-volume scheme extends to (Sec. "Oldroyd-B fluids") without
+                            printing it; the textbook law tau + lambda tau_(1) +
+                            (alpha lambda / eta_p) tau.tau = eta_p (grad u + grad u^T) adds
+                            -(alpha / eta_p) tau.tau to the source of Eq. (source) */
 } lbve_params;
 
 /* Optional device allocator (e.g. a framework's caching allocator).  alloc returns a

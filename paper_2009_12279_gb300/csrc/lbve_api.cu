@@ -156,6 +156,7 @@ bool valid_params(const lbve_params *p, std::string &why) {
     if (p->pdf_prec < LBVE_F64 || p->pdf_prec > LBVE_BF16_SHIFTED) return why = "unknown pdf_prec", false;
     if (p->pdf_scale_log2 < -1 || p->pdf_scale_log2 > 24) return why = "pdf_scale_log2 out of range", false;
     if (p->fv_terms < 0 || p->fv_terms > 15) return why = "fv_terms out of range", false;
+    if (!(p->giesekus_alpha >= 0.0 && p->giesekus_alpha <= 0.5)) return why = "giesekus_alpha must be in [0, 1/2]", false;
     if (p->block_x != 0 && p->block_x != 32 && p->block_x != 64 && p->block_x != 128)
         return why = "block_x must be 0, 32, 64 or 128", false;
     if (!(p->magic >= 0.0)) return why = "magic must be >= 0", false;
@@ -222,6 +223,7 @@ void lbve::fill_phys(const lbve_params &p, Phys<double> &ph) {
     ph.src_on = (terms & LBVE_FV_SOURCE) != 0;
     ph.ctu_on = (terms & LBVE_FV_CTU) != 0;
     ph.divu_on = (terms & LBVE_FV_DIVU) != 0;
+    ph.gk = p.beta > 0.0 ? p.giesekus_alpha / (p.beta * p.eta) : 0.0;
 }
 
 bool lbve::params_valid(const lbve_params *p, std::string &why) { return valid_params(p, why); }

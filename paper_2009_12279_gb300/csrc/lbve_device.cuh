@@ -410,7 +410,8 @@ __device__ __forceinline__ void collide(R (&f)[Q], R rho, R drho, const R u[3], 
 // across solid links, source Eq. (source) without the tau div u term, explicit Euler.
 // Variants (compiled in when VAR, then chosen per solve): ph.ctu_on scales a face flux by
 // the donor cell's transverse overlap (1 - |u_a|)(1 - |u_b|); ph.divu_on adds tau div u
-// to the source.  With VAR false the method's own update is all that is compiled.
+// to the source; ph.gk != 0 adds the Giesekus term -(alpha / eta_p)(tau . tau) to it
+// (with the source on).  With VAR false the method's own update is all that is compiled.
 // nb.u(l, k), nb.tau(l, c): velocity / stress of the face-l neighbour (fluid only);
 // nb.ub(l, out): boundary velocity of a solid face-l neighbour.
 // FP64 mode keeps the face-by-face order of the plain statement; shifted modes gather
@@ -503,6 +504,13 @@ __device__ __forceinline__ void fv_core(const Phys<R> &ph, const R (&tr)[6], con
             S = a + b + ph.ep_l * (G[i][j] + G[j][i]) - ph.inv_l * tr[c];
         }
         if (VAR && ph.divu_on) S = S + tr[c] * ((G[0][0] + G[1][1]) + G[2][2]);
+        if (VAR && ph.src_on && ph.gk != R(0)) {
+            const int i = comp_i(c), j = comp_j(c);
+            R q = R(0);
+#pragma unroll
+            for (int k = 0; k < 3; ++k) q = q + tr[comp(i, k)] * tr[comp(k, j)];
+            S = S - ph.gk * q;
+        }
         out[c] = tr[c] - net[c] + S;
     }
 }

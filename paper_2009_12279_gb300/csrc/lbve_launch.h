@@ -36,6 +36,7 @@ struct Phys {
     int flux_on, src_on;
     int ctu_on;   // face fluxes scaled by the transverse overlap of the displaced donor cell
     int divu_on;  // the tau div(u) source term
+    R gk;         // alpha / eta_p of the Giesekus source term (0: Oldroyd-B)
     R wall_vel[MAX_WALL][3];
 };
 

@@ -26,6 +26,7 @@ inline Phys<R> convert_phys(const Phys<double> &p) {
     o.src_on = p.src_on;
     o.ctu_on = p.ctu_on;
     o.divu_on = p.divu_on;
+    o.gk = (R)p.gk;
     for (int c = 0; c < MAX_WALL; ++c)
         for (int k = 0; k < 3; ++k) o.wall_vel[c][k] = (R)p.wall_vel[c][k];
     return o;
@@ -90,7 +91,7 @@ struct Launch {
         if (zc > d.g.nz) zc = d.g.nz;
         return (int)zc;
     }
-    static bool fv_variant(const DevState &d) { return d.ph.ctu_on || d.ph.divu_on; }
+    static bool fv_variant(const DevState &d) { return d.ph.ctu_on || d.ph.divu_on || d.ph.gk != 0.0; }
     template <bool VAR>
     static cudaError_t fv_var(const DevState &d, cudaStream_t s) {
         KArgs<S> a = args(d);

@@ -59,6 +59,7 @@ class Params(ct.Structure):
         ("magic", ct.c_double),
         ("pdf_prec", ct.c_int), ("pdf_scale_log2", ct.c_int), ("fv_terms", ct.c_int),
         ("schedule", ct.c_int), ("block_x", ct.c_int),
+        ("giesekus_alpha", ct.c_double),
     ]
 
 
@@ -149,7 +150,7 @@ def default_params() -> Params:
 
 def make_params(shape, *, periodic=(1, 1, 1), eta=1.0 / 6.0, beta=0.5, lambda_p=1000.0, rho0=1.0,
                 body_force=(0.0, 0.0, 0.0), magic=3.0 / 16.0, precision="f32", pdf_scale_log2=-1,
-                fv_terms=FV_FLUX | FV_SOURCE, schedule=SCHED_AUTO, block_x=0) -> Params:
+                fv_terms=FV_FLUX | FV_SOURCE, schedule=SCHED_AUTO, block_x=0, giesekus_alpha=0.0) -> Params:
     p = default_params()
     p.nx, p.ny, p.nz = (int(v) for v in shape)
     for a in range(3):
@@ -158,6 +159,7 @@ def make_params(shape, *, periodic=(1, 1, 1), eta=1.0 / 6.0, beta=0.5, lambda_p=
     p.eta, p.beta, p.lambda_p, p.rho0, p.magic = float(eta), float(beta), float(lambda_p), float(rho0), float(magic)
     p.pdf_prec = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
     p.pdf_scale_log2, p.fv_terms, p.schedule, p.block_x = int(pdf_scale_log2), int(fv_terms), int(schedule), int(block_x)
+    p.giesekus_alpha = float(giesekus_alpha)
     return p
 
 
