@@ -17,21 +17,21 @@
 
 namespace lbve {
 
-// 128-thread stream-collide blocks, at least 8 resident per SM (64 registers per thread):
-// without the cap the odd-parity kernel keeps all 37 neighbour addresses live and
-// drops to ~10 % occupancy.
-#ifndef LBVE_LB_MIN_BLOCKS
-#define LBVE_LB_MIN_BLOCKS 8
-#endif
+// 128-thread stream-collide blocks with a resident-block floor per SM, i.e. a register
+// cap of 65536 / (128 x floor): without a cap the odd-parity kernel keeps all 37
+// neighbour addresses live and drops to ~10 % occupancy.  Measured at 512^3: FP32 runs
+// fastest at 7 blocks (72 registers; 8 blocks spill more, 9 or more lose), 16-bit
+// storage at 8 for the even and 7 for the odd parity; FP64 keeps 8.
+template <class S, int PAR>
+constexpr int lb_min_blocks() {
+    return sizeof(S) == 4 ? 7 : (sizeof(S) == 2 ? (PAR ? 7 : 8) : 8);
+}
 // 256-thread stress blocks, 3 resident per SM (80 registers: no spills at 4)
 #ifndef LBVE_FV_MIN_BLOCKS
 #define LBVE_FV_MIN_BLOCKS 3
 #endif
 #ifndef LBVE_LBB_MIN_BLOCKS  // batched stream-collide (both parities in one kernel)
 #define LBVE_LBB_MIN_BLOCKS 8
-#endif
-#ifndef LBVE_LB_MIN_BLOCKS_ODD
-#define LBVE_LB_MIN_BLOCKS_ODD LBVE_LB_MIN_BLOCKS
 #endif
 
 template <class S>
@@ -234,7 +234,7 @@ __device__ __forceinline__ void lb_cell_at(const KArgs<S> &a, int x, int y, int 
 }
 
 template <class S, int PAR>
-__global__ void __launch_bounds__(128, PAR ? LBVE_LB_MIN_BLOCKS_ODD : LBVE_LB_MIN_BLOCKS) k_lb(KArgs<S> a) {
+__global__ void __launch_bounds__(128, lb_min_blocks<S, PAR>()) k_lb(KArgs<S> a) {
     int x, y, z;
     if (!cell_of_thread(a.g, x, y, z)) return;
     lb_cell_at<S, PAR>(a, x, y, z);
