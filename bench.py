@@ -404,6 +404,41 @@ def bench_serving(args, torch):
     }
 
 
+def profile_pool_steps(args):
+    """Pool steps of the serving mix between cudaProfilerStart / Stop, for a launch list
+    taken with `ncu --profile-from-start off`: the first args.serving_requests requests of
+    the serving stream (all resident, BF16 storage), 200 untimed pool steps (graph
+    capture), 200 timed ones, then args.profile_pool_steps profiled steps.  Prints the
+    mean pool step time of the timed steps."""
+    import numpy as np
+    import torch
+
+    from paper_2009_12279_gb300 import lbve, serve
+
+    stream = torch.cuda.Stream()
+    reqs = serve.make_requests(args.serving_requests, seed=0, mean_interarrival=0.0, max_steps_cap=args.serving_cap)
+    pool = lbve.Pool("bf16", budget_bytes=int(args.serving_budget_gb * 1e9), stream=stream.cuda_stream)
+    solvers = [serve.build_solver(r, "bf16", stream.cuda_stream) for r in reqs]
+    for s in solvers:
+        pool.admit(s)
+    pool.step(200)  # captures the step graph of a 200-step call
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    pool.step(200)  # replays it
+    torch.cuda.synchronize()
+    ms = (time.perf_counter() - t0) / 200 * 1e3
+    torch.cuda.profiler.start()
+    pool.step(args.profile_pool_steps)
+    torch.cuda.synchronize()
+    torch.cuda.profiler.stop()
+    print(json.dumps({"pool_step_ms": ms, "members": len(solvers), "profiled_steps": args.profile_pool_steps,
+                      "cells": int(sum(np.prod(r.shape) for r in reqs))}), flush=True)
+    pool.close()
+    for s in solvers:
+        s.close()
+    return 0
+
+
 def run_ours(args):
     import torch
 
@@ -573,6 +608,8 @@ def main():
     ap.add_argument("--serving-budget-gb", type=float, default=150.0)
     ap.add_argument("--fv-terms", type=int, default=0,
                     help="LBVE_FV_* bits of the throughput solve (0: flux and source, the method)")
+    ap.add_argument("--profile-pool-steps", type=int, default=0,
+                    help="only run this many pool steps of the serving mix under cudaProfilerStart/Stop")
     ap.add_argument("--giesekus-alpha", type=float, default=0.0,
                     help="Giesekus mobility of the throughput solve (0: Oldroyd-B, the method)")
     args = ap.parse_args()
@@ -583,6 +620,8 @@ def main():
         FV_EXTRA["fv_terms"] = args.fv_terms
     if args.giesekus_alpha:
         FV_EXTRA["giesekus_alpha"] = args.giesekus_alpha
+    if args.profile_pool_steps:
+        return profile_pool_steps(args)
     if args.impl == "reference":
         return run_reference(args)
     return run_ours(args)
