@@ -323,6 +323,13 @@ void *mapped_host(const void *p) {
 // on the copy path.  The buffer is output-only, so the bytes written here are overwritten.
 void prefault_output(void *p, size_t bytes) {
     if (!p || bytes == 0) return;
+    // plain pageable host memory only (not device, managed or page-locked memory)
+    cudaPointerAttributes at;
+    if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+        cudaGetLastError();
+        return;
+    }
+    if (at.type != cudaMemoryTypeUnregistered) return;
     static const size_t page = [] {
         const long v = sysconf(_SC_PAGESIZE);
         return v > 0 ? (size_t)v : (size_t)4096;
@@ -968,7 +975,7 @@ lbve_status lbve_read_fields(lbve_ctx *c, double *rho, double *u, double *tau, u
         dev_free(c, st);
     }
     if (flags) {
-        if (!mapped_host(flags)) prefault_output(flags, (size_t)n);
+        prefault_output(flags, (size_t)n);
         CK(cudaMemcpyAsync(flags, c->d.flag, (size_t)n, cudaMemcpyDeviceToHost, c->stream), "read flags");
     }
     CK(cudaStreamSynchronize(c->stream), "read sync");
@@ -981,7 +988,7 @@ lbve_status lbve_read_pdfs(lbve_ctx *c, double *f) {
     double *d = (double *)dev_alloc(c, sizeof(double) * Q * n);
     if (!d) return fail(c, LBVE_ENOMEM, "pdf staging allocation failed");
     CK(c->kt->pdfs_io(c->d, (int)(c->t & 1), d, 0, c->stream), "pdf read kernel");
-    if (!mapped_host(f)) prefault_output(f, sizeof(double) * Q * (size_t)n);
+    prefault_output(f, sizeof(double) * Q * (size_t)n);
     CK(cudaMemcpyAsync(f, d, sizeof(double) * Q * n, cudaMemcpyDeviceToHost, c->stream), "pdf copy");
     CK(cudaStreamSynchronize(c->stream), "pdf sync");
     dev_free(c, d);
