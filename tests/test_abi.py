@@ -60,7 +60,8 @@ def test_default_params_and_memory_estimate(lib):
 
 
 @pytest.mark.parametrize("bad", [dict(eta=-1.0), dict(beta=1.0), dict(beta=0.5, lambda_p=0.0),
-                                 dict(rho0=0.0), dict(precision=7), dict(block_x=48)])
+                                 dict(rho0=0.0), dict(precision=7), dict(block_x=48), dict(fv_terms=16),
+                                 dict(fv_terms=-1), dict(giesekus_alpha=-0.1), dict(giesekus_alpha=0.51)])
 def test_invalid_parameters_are_rejected_before_any_gpu_work(lib, bad):
     import ctypes as ct
 
@@ -73,6 +74,18 @@ def test_invalid_parameters_are_rejected_before_any_gpu_work(lib, bad):
     assert rc == 1 and not h.value
     assert lib.lbve_last_error(None)
     assert lbve.device_bytes(p) == 0
+
+
+@pytest.mark.parametrize("ok", [dict(fv_terms=4), dict(fv_terms=15), dict(giesekus_alpha=0.5),
+                                dict(giesekus_alpha=0.2, fv_terms=9)])
+def test_finite_volume_variant_parameters_are_accepted(lib, ok):
+    """Variant settings pass validation: the memory estimate (which validates without
+    touching a GPU) is that of the plain method."""
+    from paper_2009_12279_gb300 import lbve
+
+    base = dict(eta=1.0 / 6.0, beta=0.5, lambda_p=100.0, precision="f32")
+    assert lbve.device_bytes(lbve.make_params((8, 8, 8), **base, **ok)) == \
+        lbve.device_bytes(lbve.make_params((8, 8, 8), **base)) > 0
 
 
 def test_status_strings(lib):
