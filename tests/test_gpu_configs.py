@@ -133,3 +133,41 @@ def test_sedimentation_full_size_curve(capsys):
     assert convs["f32"] == convs["f64"]
     assert err["f32"][1] <= 5e-4 and err["f32"][2] <= 1e-4
     assert err["bf16"][1] <= 2e-3 and err["bf16"][2] <= 1e-3
+
+
+def test_sphere_duct_drag_over_the_full_run(capsys):
+    """The duct's 50,000 steps in FP32 and BF16 storage, the drag on the fixed sphere
+    every 2000 steps; the FP64 mode (the oracle's arithmetic, as the short run above
+    shows) runs the first 4000 steps only, FP64 arithmetic being slow on this part (the
+    whole run in FP64 took ~6 min).  No cell converts, so the drag histories are smooth
+    and compared sample by sample: FP32 and BF16 against FP64 where it ran, BF16 against
+    FP32 over the whole run."""
+    from paper_2009_12279_gb300 import Solver
+
+    cfg = _duct()
+    hist = {}
+    for prec, steps in (("f64", 4000), ("f32", cfg["steps"]), ("bf16", cfg["steps"])):
+        s = Solver(cfg["shape"], precision=prec, **cfg["params"])
+        s.set_geometry(cfg["flags"], cfg["wall_vel"])
+        d = []
+        for _ in range(steps // 2000):
+            s.step(2000)
+            d.append(s.body_forces()[2][0])
+        hist[prec] = np.array(d)
+        s.close()
+    ref, d32, d16 = hist["f64"], hist["f32"], hist["bf16"]
+    k = len(ref)
+    e32 = np.abs(d32[:k] - ref).max() / np.abs(ref).max()
+    e16 = np.abs(d16[:k] - ref).max() / np.abs(ref).max()
+    e16_32 = np.abs(d16 - d32).max() / np.abs(d32).max()
+    # Stokes drag of the sphere at the empty-duct centreline velocity (no wall correction)
+    stokes = 6.0 * np.pi * cfg["params"]["eta"] * 12.0 * cfg["u_ref"]
+    with capsys.disabled():
+        print(f"\n[sphere duct 128^3, {cfg['steps']} steps] drag f32 {d32[-1]:.5e} "
+              f"({d32[-1] / stokes:.2f} x Stokes at u_ref); first {2000 * k} steps against f64: f32 {e32:.2e}, "
+              f"bf16 {e16:.2e}; whole run bf16 against f32 {e16_32:.2e}")
+    assert np.all(np.isfinite(d32)) and d32[-1] > 0.0
+    assert abs(d32[-1] - d32[-2]) <= 0.05 * d32[-1]  # close to steady
+    assert e32 <= 1e-4
+    assert e16 <= 1e-2
+    assert e16_32 <= 1e-2
