@@ -102,3 +102,16 @@ def test_product_path_does_not_import_the_oracle():
                 text = open(os.path.join(dirpath, f)).read()
                 assert not re.search(r"^\s*(import|from)\s+oracle", text, re.M), f
                 assert "lbve_oracle" not in text and "orc_" not in text, f
+
+
+def test_no_cpu_fallback_without_a_gpu():
+    """On a machine without a GPU the product path fails loudly: creating a solve reports
+    a CUDA error instead of computing anywhere else."""
+    import torch
+
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    from paper_2009_12279_gb300 import LbveError, Solver
+
+    with pytest.raises(LbveError, match="LBVE_ECUDA|LBVE_ENOMEM"):
+        Solver((8, 8, 8), precision="f32", eta=1.0 / 6.0, beta=0.5, lambda_p=100.0)
