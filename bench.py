@@ -21,6 +21,7 @@ import os
 import statistics
 import subprocess
 import sys
+import tempfile
 import time
 
 ROOT = os.path.dirname(os.path.abspath(__file__))
@@ -73,7 +74,9 @@ class ClockSampler:
     def __init__(self, index):
         self.index = index
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_{os.getpid()}.csv")
+        # raw samples: LBVE_CLOCKS_DIR if set, else the system temporary directory
+        d = os.environ.get("LBVE_CLOCKS_DIR") or tempfile.gettempdir()
+        self.path = os.path.join(d, f"lbve_clocks_{os.getpid()}.csv")
 
     def start(self):
         try:
