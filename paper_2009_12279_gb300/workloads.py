@@ -74,7 +74,9 @@ def duct_centreline_factor(aspect=1.0, terms=60):
     """u_c = factor * g H^2 / eta for a square duct of side H (textbook Fourier series)."""
     s = 0.0
     for n in range(1, 2 * terms, 2):
-        s += (-1) ** ((n - 1) // 2) / n ** 3 * (1.0 - 1.0 / math.cosh(n * math.pi * aspect / 2.0))
+        x = n * math.pi * aspect / 2.0
+        sech = 0.0 if x > 700.0 else 1.0 / math.cosh(x)  # cosh overflows beyond ~710
+        s += (-1) ** ((n - 1) // 2) / n ** 3 * (1.0 - sech)
     return 4.0 / math.pi ** 3 * s / 1.0
 
 
