@@ -115,3 +115,40 @@ def test_no_cpu_fallback_without_a_gpu():
 
     with pytest.raises(LbveError, match="LBVE_ECUDA|LBVE_ENOMEM"):
         Solver((8, 8, 8), precision="f32", eta=1.0 / 6.0, beta=0.5, lambda_p=100.0)
+
+
+def test_binding_constants_match_the_header():
+    """The Python binding's constants and parameter struct follow include/lbve.h."""
+    import ctypes as ct
+    import re
+
+    from paper_2009_12279_gb300 import lbve
+
+    hdr = open(os.path.join(ROOT, "include", "lbve.h")).read()
+    defs = {m.group(1): m.group(2) for m in re.finditer(r"^#define (LBVE_\w+) (\S+)", hdr, re.M)}
+    pairs = {"LBVE_FV_FLUX": lbve.FV_FLUX, "LBVE_FV_SOURCE": lbve.FV_SOURCE, "LBVE_FV_CTU": lbve.FV_CTU,
+             "LBVE_FV_DIVU": lbve.FV_DIVU, "LBVE_SCHED_AUTO": lbve.SCHED_AUTO, "LBVE_SCHED_SPLIT": lbve.SCHED_SPLIT,
+             "LBVE_SCHED_FUSED": lbve.SCHED_FUSED, "LBVE_FLAG_FLUID": lbve.FLAG_FLUID,
+             "LBVE_FLAG_NOSLIP": lbve.FLAG_NOSLIP, "LBVE_FLAG_WALL0": lbve.FLAG_WALL0,
+             "LBVE_FLAG_PARTICLE0": lbve.FLAG_PARTICLE0}
+    for name, value in pairs.items():
+        assert int(defs[name]) == value, name
+    m = re.search(r"^#define LBVE_NOALLOC_MAX_CELLS \(1 << (\d+)\)", hdr, re.M)
+    assert m and 1 << int(m.group(1)) == lbve.NOALLOC_MAX_CELLS
+    # lbve_params field order and types, as declared
+    body = re.search(r"typedef struct \{(.*?)\} lbve_params;", hdr, re.S).group(1)
+    body = re.sub(r"/\*.*?\*/", "", body, flags=re.S)
+    fields = []
+    for decl in body.split(";"):
+        decl = decl.strip()
+        if not decl:
+            continue
+        ctype, names = decl.split(None, 1)
+        for nm in names.split(","):
+            nm = nm.strip()
+            fields.append((re.sub(r"\[.*\]", "", nm), ctype, "[" in nm))
+    py = [(f[0], f[1]) for f in lbve.Params._fields_]
+    assert [f[0] for f in fields] == [p[0] for p in py]
+    for (name, ctype, is_array), (_, pytype) in zip(fields, py):
+        base = pytype._type_ if is_array else pytype
+        assert base == {"int": ct.c_int, "double": ct.c_double}[ctype], name
