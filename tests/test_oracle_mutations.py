@@ -53,3 +53,55 @@ def test_pins_catch_mutant(name, tmp_path):
                         os.path.join(HERE, "test_oracle_pins.py")], env=env, capture_output=True, text=True,
                        timeout=600)
     assert r.returncode != 0, f"mutant {name} survived the pins:\n{r.stdout[-2000:]}"
+
+
+# Mistakes in the arithmetic of single boundary-adjacent cells.  Each keeps every integral,
+# balance and analytic profile of the pin suite intact (it survives test_oracle_pins.py),
+# and only the cell-by-cell brute-force comparison (test_oracle_brute_force.py) sees it.
+BRUTE_FORCE_ONLY = {
+    # a cell between two solid faces along an axis (a one-cell gap) gets no gradient there
+    "gradient_between_two_solid_faces": (
+        "G[k * 3 + j] = up - um;",
+        "G[k * 3 + j] = (!is_fluid(s, np_) && !is_fluid(s, nm_)) ? 0.0 : up - um;"),
+    # the stress face value towards a particle cell taken as zero, not tau(r)
+    "force_extrapolation_next_to_particle": (
+        "double tf = fl ? 0.5 * (tr + tau[(long)c * s->n + nb]) : tr;",
+        "double tf = fl ? 0.5 * (tr + tau[(long)c * s->n + nb]) : "
+        "(nb >= 0 && s->flag[nb] >= ORC_PART0 ? 0.0 : tr);"),
+    # the torque lever arm of a momentum-exchange link measured from the fluid cell
+    "torque_lever_arm_of_fluid_cell": (
+        "displacement(s, nb, P->X, d);\n                cross(d, Fl, T);",
+        "displacement(s, r, P->X, d);\n                cross(d, Fl, T);"),
+    # the density of a created cell averaged over its D3Q7 neighbours only
+    "created_density_face_neighbours_only": (
+        "for (int i = 1; i < 19; ++i) {\n            long nb = neighbour(s, r, C[i][0], C[i][1], C[i][2]);\n"
+        "            if (nb < 0 || kind[nb] != 1) continue;",
+        "for (int i = 1; i < 7; ++i) {\n            long nb = neighbour(s, r, C[i][0], C[i][1], C[i][2]);\n"
+        "            if (nb < 0 || kind[nb] != 1) continue;"),
+}
+
+
+def _mutant_lib(tmp_path, old, new):
+    src = open(os.path.join(ROOT, "oracle", "lbve_oracle.c")).read()
+    assert src.count(old) == 1, "mutation site not found or not unique"
+    (tmp_path / "lbve_oracle.c").write_text(src.replace(old, new))
+    shutil.copy(os.path.join(ROOT, "oracle", "lbve_oracle.h"), tmp_path / "lbve_oracle.h")
+    so = tmp_path / "mutant.so"
+    subprocess.run(["gcc", "-O2", "-std=gnu11", "-fPIC", "-shared", "-ffp-contract=off", "-fopenmp",
+                    str(tmp_path / "lbve_oracle.c"), "-o", str(so), "-lm"], check=True)
+    return so
+
+
+def _run_suite(so, test_file):
+    env = dict(os.environ, LBVE_ORACLE_LIB=str(so), OMP_NUM_THREADS="2")
+    return subprocess.run([sys.executable, "-m", "pytest", "-x", "-q", "-p", "no:cacheprovider",
+                           os.path.join(HERE, test_file)], env=env, capture_output=True, text=True, timeout=600)
+
+
+@pytest.mark.parametrize("name", sorted(BRUTE_FORCE_ONLY))
+def test_only_the_brute_force_catches_mutant(name, tmp_path):
+    so = _mutant_lib(tmp_path, *BRUTE_FORCE_ONLY[name])
+    pins = _run_suite(so, "test_oracle_pins.py")
+    assert pins.returncode == 0, f"mutant {name} is caught by the pins as well:\n{pins.stdout[-1500:]}"
+    brute = _run_suite(so, "test_oracle_brute_force.py")
+    assert brute.returncode != 0, f"mutant {name} survived the brute-force comparison:\n{brute.stdout[-2000:]}"
