@@ -344,8 +344,15 @@ __device__ __forceinline__ R cdot(int i, const R v[3]) {
 // deviations, with feq_i - w_i rho0 = w_i (drho + rho (3 cu + 9/2 cu^2 - 3/2 u^2)), and
 // fold the pair (i, -i) algebraically:
 //   f*_{+-i} = f_{+-i} - P -+ M,
-//   P = omega+/2 (f_i + f_-i) - omega+ w_i (drho + rho (9/2 cu^2 - 3/2 u^2)) - w_i B (9 cu cF - 3 u.F)
-//   M = omega-/2 (f_i - f_-i) - w_i (3 omega- rho cu + A cF).
+//   P = omega+/(2 k2) (k2 (f_i + f_-i) - (drho + rho (9/2 cu^2 - 3/2 u^2))) - w_i B (9 cu cF - 3 u.F)
+//   M = omega-/(2 k)  (k  (f_i - f_-i) - rho cu)                           - w_i A cF
+// with k = 1/(6 w_i) and k2 = 1/(2 w_i), small integers (3 and 9 for w = 1/18, 6 and 18 for
+// w = 1/36).  The non-equilibrium parts are formed first, by an exact integer multiple inside
+// one fused multiply-add, and only then scaled by a rounded constant.  Scaling the large
+// antisymmetric equilibrium 3 w_i rho cu by rounded FP32 weights instead makes the lattice
+// sum of the relaxed momentum differ from rho u by a fixed relative ~3e-8 every step: a
+// systematic momentum drift that, in a flow accelerating from rest, grows linearly in time
+// (relative error 1.1e-5 after 1000 steps of the config-1 channel, against 1.3e-7 in this form).
 template <class R, bool SH>
 __device__ __forceinline__ void collide(R (&f)[Q], R rho, R drho, const R u[3], const R F[3], const Phys<R> &ph) {
     const R usq = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
@@ -380,22 +387,28 @@ __device__ __forceinline__ void collide(R (&f)[Q], R rho, R drho, const R u[3], 
             f[ip] = fo;
         }
     } else {
-        const R hp = R(0.5) * wp, hm = R(0.5) * wm;
         const R q = R(1.5) * usq;
-        const R k3 = R(3) * wm * rho;
         const R u3F = R(3) * uF;
+        // omega+/(2 k2) and omega-/(2 k) of the directions with w = 1/18 (halved for 1/36);
+        // these rounded constants scale only the small non-equilibrium parts
+        const R cp = wp * R(1.0 / 18.0), cm = wm * R(1.0 / 6.0);
         // rest population: feq0 - w0 rho0 = w0 (drho - rho q), forcing w0 B (-3 u.F)
         f[0] = f[0] - wp * (f[0] - wgt<R>(0) * (drho - rho * q)) - wgt<R>(0) * ph.B * u3F;
 #pragma unroll
         for (int i = 1; i < Q; i += 2) {
             const int ip = i + 1;
             const R w = wgt<R>(i);
+            const bool axis = i < 7;  // w = 1/18
+            const R k = axis ? R(3) : R(6), k2 = axis ? R(9) : R(18);
+            const R sp = axis ? cp : R(0.5) * cp, sm = axis ? cm : R(0.5) * cm;
             const R cu = cdot<R>(i, u);
             const R cF = cdot<R>(i, F);
-            const R sym = drho + rho * (R(4.5) * cu * cu - q);
+            const R esym = drho + rho * (R(4.5) * cu * cu - q);
             const R x9 = R(9) * cu * cF - u3F;
-            const R P = hp * (f[i] + f[ip]) - (wp * w) * sym - (w * ph.B) * x9;
-            const R M = hm * (f[i] - f[ip]) - w * (k3 * cu + ph.A * cF);
+            const R nsym = __fmaf_rn(k2, f[i] + f[ip], -esym);    // k2 (f_i + f_-i) - esym, one rounding
+            const R nanti = __fmaf_rn(k, f[i] - f[ip], -(rho * cu));  // k (f_i - f_-i) - rho cu, one rounding
+            const R P = sp * nsym - (w * ph.B) * x9;
+            const R M = sm * nanti - (w * ph.A) * cF;
             const R fi = f[i] - P - M;
             const R fo = f[ip] - P + M;
             f[i] = fi;
