@@ -42,6 +42,19 @@
  *     equation printed): the textbook law tau + lambda tau_(1) + (alpha lambda / eta_p)
  *     tau.tau = eta_p (grad u + grad u^T) adds -(alpha / eta_p) tau.tau to the source of
  *     Eq. (source); alpha = 0 is Oldroyd-B.
+ *   - FENE-P (named beside Giesekus among the laws of Sec. "Oldroyd-B fluids" and Sec.
+ *     "Implementation and extensibility", no equation printed): the textbook Peterlin
+ *     closure written for the conformation tensor A, which is what the finite-volume
+ *     update then transports (the paper's scheme carries "stress or conformation"):
+ *         A_(1) = -(1/lambda) (f A - I),   tau = (eta_p / lambda) (f A - I),
+ *         f = 1 / (1 - tr A / L^2),
+ *     so the source of Eq. (source) becomes A.grad u + (A.grad u)^T - (f A - I)/lambda
+ *     (no eta_p/lambda (grad u + grad u^T) term), the flux moves A, and the polymer force
+ *     of Eq. (force) takes the stress of each cell's A.  L^2 -> infinity recovers
+ *     Oldroyd-B with tau = (eta_p/lambda)(A - I).  Stress given or read at the boundary
+ *     of the solver converts by A = (I + lambda tau / eta_p) / f, f = 1 + (3 + lambda
+ *     tr tau / eta_p) / L^2 (the closed-form inverse).  Moving particles are not
+ *     combined with FENE-P.
  *   - grad u next to a solid cell uses the boundary velocity as the face value.
  *   - Stress extrapolation is per link: the face value towards a solid cell is tau(r).
  *   - Momentum exchange on a link r -> r+c_i (solid): c_i (2 f*_i - 6 w_i rho c_i.u_b),
@@ -97,6 +110,7 @@ struct orc_state {
     long n;
     double omega_p, omega_m, eta_p, ep_l, inv_l;
     double gk; /* alpha / eta_p of the Giesekus term (0: Oldroyd-B) */
+    int fene;  /* FENE-P: the stored tensor is the conformation A */
     double *f, *fn;     /* [19][n] */
     double *tau, *taun; /* [6][n] */
     double *rho, *u, *F; /* per-step scratch: [n], [3][n], [3][n] */
@@ -256,6 +270,21 @@ void orc_source(const double tau[6], const double G[9], double ep_l, double inv_
     }
 }
 
+/* FENE-P stress of a conformation tensor: tau = (eta_p/lambda)(f A - I),
+ * f = 1 / (1 - tr A / L^2). */
+void orc_fene_stress(const double A[6], double eta_p, double lambda_p, double L2, double tau[6]) {
+    double f = 1.0 / (1.0 - (A[0] + A[1] + A[2]) / L2);
+    for (int c = 0; c < 6; ++c) tau[c] = (eta_p / lambda_p) * (f * A[c] - (c < 3 ? 1.0 : 0.0));
+}
+
+/* Its inverse: f A = I + lambda tau / eta_p, and taking the trace with
+ * 1/f = 1 - tr A / L^2 gives f = 1 + (3 + lambda tr tau / eta_p) / L^2. */
+void orc_fene_conformation(const double tau[6], double eta_p, double lambda_p, double L2, double A[6]) {
+    double s = 3.0 + lambda_p * (tau[0] + tau[1] + tau[2]) / eta_p;
+    double f = 1.0 + s / L2;
+    for (int c = 0; c < 6; ++c) A[c] = ((c < 3 ? 1.0 : 0.0) + lambda_p * tau[c] / eta_p) / f;
+}
+
 /* ------------------------------------------------------------------------- */
 /* fields                                                                    */
 /* ------------------------------------------------------------------------- */
@@ -265,8 +294,21 @@ static void gather_f(const orc_state *s, const double *f, long r, double out[19]
 
 /* Eq. (force) on the D3Q7 faces (A_0 = 1, |c| = 1), faces by Eq. (interpolation),
  * a solid neighbour's stress replaced by tau(r) per Eq. (extrapolation). */
+/* Stress of cell r from the stored tensor: tau itself, or in FENE-P mode the stress of
+ * the conformation tensor A. */
+static void cell_stress(const orc_state *s, const double *stored, long r, double t[6]) {
+    double a[6];
+    for (int c = 0; c < 6; ++c) a[c] = stored[(long)c * s->n + r];
+    if (s->fene)
+        orc_fene_stress(a, s->eta_p, s->p.lambda_p, s->p.fene_L2, t);
+    else
+        for (int c = 0; c < 6; ++c) t[c] = a[c];
+}
+
 static void polymer_force_cell(const orc_state *s, const double *tau, long r, double Fp[3]) {
     Fp[0] = Fp[1] = Fp[2] = 0.0;
+    double tr6[6], tn6[6];
+    cell_stress(s, tau, r, tr6);
     for (int l = 0; l < 6; ++l) {
         int k = FACE_AXIS[l];
         double sg = FACE_SIGN[l];
@@ -274,10 +316,11 @@ static void polymer_force_cell(const orc_state *s, const double *tau, long r, do
         d[k] = (int)sg;
         long nb = neighbour(s, r, d[0], d[1], d[2]);
         int fl = is_fluid(s, nb);
+        if (fl) cell_stress(s, tau, nb, tn6);
         for (int j = 0; j < 3; ++j) {
             int c = COMP[k][j];
-            double tr = tau[(long)c * s->n + r];
-            double tf = fl ? 0.5 * (tr + tau[(long)c * s->n + nb]) : tr;
+            double tr = tr6[c];
+            double tf = fl ? 0.5 * (tr + tn6[c]) : tr;
             Fp[j] += sg * tf;
         }
     }
@@ -381,7 +424,18 @@ static void fv_update(orc_state *s, const double *u, const double *tau, double *
             }
         }
         double S[6] = {0, 0, 0, 0, 0, 0};
-        if (src_on) orc_source(tr, G, s->ep_l, s->inv_l, S);
+        if (src_on && !s->fene) orc_source(tr, G, s->ep_l, s->inv_l, S);
+        if (src_on && s->fene) {
+            /* A.grad u + (A.grad u)^T - (f A - I) / lambda, f = 1 / (1 - tr A / L^2) */
+            double fA = 1.0 / (1.0 - (tr[0] + tr[1] + tr[2]) / s->p.fene_L2);
+            for (int c = 0; c < 6; ++c) {
+                int i = CI[c], j = CJ[c];
+                double a = 0.0, b = 0.0;
+                for (int k = 0; k < 3; ++k) a += tr[COMP[i][k]] * G[k * 3 + j];
+                for (int k = 0; k < 3; ++k) b += tr[COMP[k][j]] * G[k * 3 + i];
+                S[c] = a + b - s->inv_l * (fA * tr[c] - (i == j ? 1.0 : 0.0));
+            }
+        }
         if (divu_on) {
             double divu = (G[0] + G[4]) + G[8];
             for (int c = 0; c < 6; ++c) S[c] = S[c] + tr[c] * divu;
@@ -663,6 +717,8 @@ orc_state *orc_create(const orc_params *p) {
     if (p->beta > 0.0 && !(p->lambda_p > 0.0)) return NULL;
     if (p->n_wall < 0 || p->n_wall > ORC_MAX_WALL) return NULL;
     if (!(p->giesekus_alpha >= 0.0 && p->giesekus_alpha <= 0.5)) return NULL;
+    if (!(p->fene_L2 == 0.0 || p->fene_L2 > 3.0)) return NULL;
+    if (p->fene_L2 > 0.0 && (!(p->beta > 0.0) || p->giesekus_alpha != 0.0)) return NULL;
     orc_state *s = (orc_state *)calloc(1, sizeof(orc_state));
     s->p = *p;
     s->n = (long)p->nx * p->ny * p->nz;
@@ -685,6 +741,7 @@ orc_state *orc_create(const orc_params *p) {
     s->ep_l = p->beta > 0.0 ? s->eta_p / p->lambda_p : 0.0;
     s->inv_l = p->lambda_p > 0.0 ? 1.0 / p->lambda_p : 0.0;
     s->gk = p->beta > 0.0 ? p->giesekus_alpha / s->eta_p : 0.0;
+    s->fene = p->fene_L2 > 0.0;
     orc_init_fields(s, NULL, NULL, NULL);
     return s;
 }
@@ -728,14 +785,17 @@ int orc_init_fields(orc_state *s, const double *rho, const double *u, const doub
             for (int a = 0; a < 3; ++a) uu[a] = u[(long)a * n + r];
         orc_equilibrium(rr, uu, feq);
         for (int i = 0; i < 19; ++i) s->f[(long)i * n + r] = feq[i];
-        for (int c = 0; c < 6; ++c) s->tau[(long)c * n + r] = tau ? tau[(long)c * n + r] : 0.0;
+        double t6[6], a6[6];
+        for (int c = 0; c < 6; ++c) t6[c] = tau ? tau[(long)c * n + r] : 0.0;
+        if (s->fene) orc_fene_conformation(t6, s->eta_p, s->p.lambda_p, s->p.fene_L2, a6);
+        for (int c = 0; c < 6; ++c) s->tau[(long)c * n + r] = s->fene ? a6[c] : t6[c];
     }
     return 0;
 }
 
 int orc_add_particle(orc_state *s, const double X[3], double R, double rho_p, const double v[3],
                      const double w[3], const double Fext[3], const double Text[3]) {
-    if (s->np >= ORC_MAX_PART || !(R > 0.0) || !(rho_p > 0.0)) return -1;
+    if (s->np >= ORC_MAX_PART || !(R > 0.0) || !(rho_p > 0.0) || s->fene) return -1;
     int id = s->np++;
     orc_particle *P = &s->part[id];
     memset(P, 0, sizeof(*P));
@@ -775,8 +835,11 @@ void orc_read_fields(orc_state *s, double *rho, double *u, double *tau, uint8_t 
     if (rho) memcpy(rho, s->rho, sizeof(double) * (size_t)n);
     if (u) memcpy(u, s->u, sizeof(double) * 3 * (size_t)n);
     if (tau)
-        for (long r = 0; r < n; ++r)
-            for (int c = 0; c < 6; ++c) tau[(long)c * n + r] = is_fluid(s, r) ? s->tau[(long)c * n + r] : 0.0;
+        for (long r = 0; r < n; ++r) {
+            double t6[6] = {0, 0, 0, 0, 0, 0};
+            if (is_fluid(s, r)) cell_stress(s, s->tau, r, t6);
+            for (int c = 0; c < 6; ++c) tau[(long)c * n + r] = t6[c];
+        }
     if (flags) memcpy(flags, s->flag, (size_t)n);
 }
 

@@ -57,6 +57,9 @@ typedef struct {
     double wall_vel[ORC_MAX_WALL][3];
     int fv_terms;    /* ORC_FV_* bits; ORC_FV_FLUX | ORC_FV_SOURCE for the method */
     double giesekus_alpha; /* Giesekus mobility in [0, 1/2]; 0 is Oldroyd-B (the method) */
+    double fene_L2;  /* FENE-P maximum extensibility L^2 (> 3); 0 is Oldroyd-B (the method).
+                        In FENE-P mode the stored tensor is the conformation A (see the
+                        oracle's header); fields are read and written as stress tau */
 } orc_params;
 
 typedef struct orc_state orc_state;
@@ -93,6 +96,9 @@ void orc_equilibrium(double rho, const double u[3], double feq[19]);
 void orc_forcing(const double u[3], const double F[3], double omega_p, double omega_m, double D[19]);
 void orc_collide(const double f[19], const double F[3], double omega_p, double omega_m, double fs[19]);
 void orc_source(const double tau[6], const double G[9], double ep_l, double inv_l, double S[6]);
+/* FENE-P: stress of a conformation tensor, and the conformation of a stress. */
+void orc_fene_stress(const double A[6], double eta_p, double lambda_p, double L2, double tau[6]);
+void orc_fene_conformation(const double tau[6], double eta_p, double lambda_p, double L2, double A[6]);
 void orc_polymer_force_field(orc_state *s, double *Fp);
 void orc_velocity_field(orc_state *s, double *u);
 void orc_fv_update_field(orc_state *s, const double *u, double *tau_out);

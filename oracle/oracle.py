@@ -17,6 +17,8 @@ import numpy as np
 HERE = os.path.dirname(os.path.abspath(__file__))
 SRC = os.path.join(HERE, "lbve_oracle.c")
 LIB = os.path.join(HERE, "liblbve_oracle.so")
+SRC2D = os.path.join(HERE, "lbve2d_oracle.c")
+LIB2D = os.path.join(HERE, "liblbve2d_oracle.so")
 
 FLUID, NOSLIP, WALL0, PART0 = 0, 1, 2, 64
 FV_FLUX, FV_SOURCE = 1, 2
@@ -27,8 +29,10 @@ _lib = None
 
 
 def _fresh() -> bool:
-    return os.path.exists(LIB) and os.path.getmtime(LIB) >= max(
-        os.path.getmtime(SRC), os.path.getmtime(os.path.join(HERE, "lbve_oracle.h")))
+    def ok(lib, src, hdr):
+        return os.path.exists(lib) and os.path.getmtime(lib) >= max(os.path.getmtime(src),
+                                                                     os.path.getmtime(os.path.join(HERE, hdr)))
+    return ok(LIB, SRC, "lbve_oracle.h") and ok(LIB2D, SRC2D, "lbve2d_oracle.h")
 
 
 def build(force: bool = False) -> str:
@@ -46,11 +50,12 @@ def build(force: bool = False) -> str:
 
 
 def _compile() -> str:
-    tmp = LIB + f".tmp{os.getpid()}"
-    cmd = ["gcc", "-O2", "-std=gnu11", "-fPIC", "-shared", "-ffp-contract=off", "-fopenmp",
-           SRC, "-o", tmp, "-lm"]
-    subprocess.run(cmd, check=True)
-    os.replace(tmp, LIB)
+    for src, lib in ((SRC, LIB), (SRC2D, LIB2D)):
+        tmp = lib + f".tmp{os.getpid()}"
+        cmd = ["gcc", "-O2", "-std=gnu11", "-fPIC", "-shared", "-ffp-contract=off", "-fopenmp",
+               src, "-o", tmp, "-lm"]
+        subprocess.run(cmd, check=True)
+        os.replace(tmp, lib)
     return LIB
 
 
@@ -65,6 +70,7 @@ class _Params(ct.Structure):
         ("wall_vel", (ct.c_double * 3) * 16),
         ("fv_terms", ct.c_int),
         ("giesekus_alpha", ct.c_double),
+        ("fene_L2", ct.c_double),
     ]
 
 
@@ -99,6 +105,8 @@ def lib():
             L.orc_forcing.argtypes = [dp, dp, ct.c_double, ct.c_double, dp]
             L.orc_collide.argtypes = [dp, dp, ct.c_double, ct.c_double, dp]
             L.orc_source.argtypes = [dp, dp, ct.c_double, ct.c_double, dp]
+            L.orc_fene_stress.argtypes = [dp, ct.c_double, ct.c_double, ct.c_double, dp]
+            L.orc_fene_conformation.argtypes = [dp, ct.c_double, ct.c_double, ct.c_double, dp]
             L.orc_polymer_force_field.argtypes = [ct.c_void_p, ct.c_void_p]
             L.orc_velocity_field.argtypes = [ct.c_void_p, ct.c_void_p]
             L.orc_fv_update_field.argtypes = [ct.c_void_p, ct.c_void_p, ct.c_void_p]
@@ -152,12 +160,26 @@ def source(tau6, G, ep_l: float, inv_l: float) -> np.ndarray:
     return out
 
 
+def fene_stress(A6, eta_p, lambda_p, L2):
+    a = np.ascontiguousarray(np.asarray(A6, dtype=np.float64))
+    out = np.zeros(6)
+    lib().orc_fene_stress(_dp(a), float(eta_p), float(lambda_p), float(L2), _dp(out))
+    return out
+
+
+def fene_conformation(tau6, eta_p, lambda_p, L2):
+    t = np.ascontiguousarray(np.asarray(tau6, dtype=np.float64))
+    out = np.zeros(6)
+    lib().orc_fene_conformation(_dp(t), float(eta_p), float(lambda_p), float(L2), _dp(out))
+    return out
+
+
 class Oracle:
     """One solve held by the CPU oracle.  Arrays are numpy, shape (..., nz, ny, nx)."""
 
     def __init__(self, shape, *, periodic=(1, 1, 1), eta=1.0 / 6.0, beta=0.5, lambda_p=3000.0,
                  rho0=1.0, g=(0.0, 0.0, 0.0), magic=3.0 / 16.0, wall_vel=(), fv_terms=FV_FLUX | FV_SOURCE,
-                 giesekus_alpha=0.0):
+                 giesekus_alpha=0.0, fene_L2=0.0):
         nx, ny, nz = (int(v) for v in shape)
         p = _Params()
         p.nx, p.ny, p.nz = nx, ny, nz
@@ -171,6 +193,7 @@ class Oracle:
                 p.wall_vel[k][a] = float(v[a])
         p.fv_terms = int(fv_terms)
         p.giesekus_alpha = float(giesekus_alpha)
+        p.fene_L2 = float(fene_L2)
         self._p = p
         self.shape = (nx, ny, nz)
         self.n = nx * ny * nz
@@ -244,6 +267,7 @@ class Oracle:
         lib().orc_write_pdfs(self._h, f.ctypes.data)
 
     def write_tau(self, tau):
+        """Overwrite the stored tensor (the stress; the conformation A in FENE-P mode)."""
         t = np.ascontiguousarray(tau, dtype=np.float64).reshape(self._grid(6))
         lib().orc_write_tau(self._h, t.ctypes.data)
 
@@ -288,3 +312,128 @@ class Oracle:
 
     def fill_drain(self):
         lib().orc_fill_drain(self._h)
+
+
+# ---------------------------------------------------------------------------------
+# two-dimensional form (D2Q9 lattice Boltzmann, D2Q5 finite-volume stress)
+# ---------------------------------------------------------------------------------
+class _Params2D(ct.Structure):
+    _fields_ = [
+        ("nx", ct.c_int), ("ny", ct.c_int), ("periodic", ct.c_int * 2),
+        ("eta", ct.c_double), ("beta", ct.c_double), ("lambda_p", ct.c_double), ("rho0", ct.c_double),
+        ("g", ct.c_double * 2), ("magic", ct.c_double), ("fv_terms", ct.c_int),
+    ]
+
+
+_lib2d = None
+
+
+def lib2d():
+    global _lib2d
+    with _lock:
+        if _lib2d is None:
+            build()
+            L = ct.CDLL(os.environ.get("LBVE_ORACLE2D_LIB") or LIB2D)
+            vp = ct.c_void_p
+            L.orc2_create.restype = vp
+            L.orc2_create.argtypes = [ct.POINTER(_Params2D)]
+            L.orc2_destroy.argtypes = [vp]
+            L.orc2_set_flags.argtypes = [vp, vp, vp]
+            L.orc2_set_force.argtypes = [vp, vp]
+            L.orc2_init_fields.argtypes = [vp, vp, vp, vp]
+            L.orc2_step.argtypes = [vp, ct.c_int]
+            L.orc2_time.argtypes = [vp]
+            L.orc2_time.restype = ct.c_long
+            L.orc2_read_fields.argtypes = [vp, vp, vp, vp]
+            L.orc2_read_pdfs.argtypes = [vp, vp]
+            L.orc2_write_pdfs.argtypes = [vp, vp]
+            L.orc2_write_tau.argtypes = [vp, vp]
+            L.orc2_lattice.argtypes = [vp, vp, vp]
+            L.orc2_fv_update_field.argtypes = [vp, vp, vp]
+            _lib2d = L
+    return _lib2d
+
+
+def lattice2d():
+    """(c[9,2] int, w[9], opp[9]) of the D2Q9 set."""
+    c = np.zeros((9, 2), dtype=np.int32)
+    w = np.zeros(9)
+    opp = np.zeros(9, dtype=np.int32)
+    lib2d().orc2_lattice(c.ctypes.data, w.ctypes.data, opp.ctypes.data)
+    return c.astype(np.int64), w, opp.astype(np.int64)
+
+
+class Oracle2D:
+    """One two-dimensional solve held by the CPU oracle.  Arrays (..., ny, nx)."""
+
+    def __init__(self, shape, *, periodic=(1, 1), eta=1.0 / 6.0, beta=0.5, lambda_p=3000.0, rho0=1.0,
+                 g=(0.0, 0.0), magic=3.0 / 16.0, fv_terms=FV_FLUX | FV_SOURCE):
+        p = _Params2D()
+        p.nx, p.ny = (int(v) for v in shape)
+        for a in range(2):
+            p.periodic[a] = int(periodic[a])
+            p.g[a] = float(g[a])
+        p.eta, p.beta, p.lambda_p, p.rho0, p.magic = float(eta), float(beta), float(lambda_p), float(rho0), float(magic)
+        p.fv_terms = int(fv_terms)
+        self.shape = (p.nx, p.ny)
+        self._h = lib2d().orc2_create(ct.byref(p))
+        if not self._h:
+            raise ValueError("oracle rejected the parameters")
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib2d().orc2_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        self.close()
+
+    def _grid(self, k=None):
+        nx, ny = self.shape
+        return (ny, nx) if k is None else (k, ny, nx)
+
+    def set_geometry(self, flags, ub=None):
+        fl = np.ascontiguousarray(flags, dtype=np.uint8).reshape(self._grid())
+        u = None if ub is None else np.ascontiguousarray(ub, dtype=np.float64).reshape(self._grid(2))
+        if lib2d().orc2_set_flags(self._h, fl.ctypes.data, None if u is None else u.ctypes.data) != 0:
+            raise ValueError("oracle rejected the flag field")
+
+    def set_force(self, F=None):
+        a = None if F is None else np.ascontiguousarray(F, dtype=np.float64).reshape(self._grid(2))
+        lib2d().orc2_set_force(self._h, None if a is None else a.ctypes.data)
+
+    def init_fields(self, rho=None, u=None, tau=None):
+        keep = [None if a is None else np.ascontiguousarray(a, dtype=np.float64).reshape(self._grid(k))
+                for a, k in ((rho, None), (u, 2), (tau, 3))]
+        lib2d().orc2_init_fields(self._h, *[None if a is None else a.ctypes.data for a in keep])
+
+    def step(self, n=1):
+        lib2d().orc2_step(self._h, int(n))
+
+    @property
+    def time(self):
+        return int(lib2d().orc2_time(self._h))
+
+    def read_fields(self):
+        rho, u, tau = np.zeros(self._grid()), np.zeros(self._grid(2)), np.zeros(self._grid(3))
+        lib2d().orc2_read_fields(self._h, rho.ctypes.data, u.ctypes.data, tau.ctypes.data)
+        return rho, u, tau
+
+    def read_pdfs(self):
+        f = np.zeros(self._grid(9))
+        lib2d().orc2_read_pdfs(self._h, f.ctypes.data)
+        return f
+
+    def write_pdfs(self, f):
+        a = np.ascontiguousarray(f, dtype=np.float64).reshape(self._grid(9))
+        lib2d().orc2_write_pdfs(self._h, a.ctypes.data)
+
+    def write_tau(self, tau):
+        a = np.ascontiguousarray(tau, dtype=np.float64).reshape(self._grid(3))
+        lib2d().orc2_write_tau(self._h, a.ctypes.data)
+
+    def fv_update(self, u):
+        uu = np.ascontiguousarray(u, dtype=np.float64).reshape(self._grid(2))
+        o = np.zeros(self._grid(3))
+        lib2d().orc2_fv_update_field(self._h, uu.ctypes.data, o.ctypes.data)
+        return o

@@ -117,3 +117,53 @@ def config_throughput(n=512, seed=0, obstacle_fraction=0.01, beta=0.5, lam=1000.
         "u_fn": lambda: random_velocity(shape, 1e-3, seed + 1),
         "steps": 1000,
     }
+
+
+# ---------------------------------------------------------------------------------
+# two-dimensional workloads (D2Q9 / D2Q5)
+# ---------------------------------------------------------------------------------
+def cavity2d(L=194, u0=1e-4, beta=0.5, wi=0.5, eta_n=1.0):
+    """Lid-driven cavity of Sec. "Lid-driven cavity": an L x L fluid cell inside solid
+    walls (grid (L + 2)^2, halfway walls at 0.5 and L + 0.5), the top wall moving along x
+    with the regularised profile 16 u0 xi^2 (1 - xi)^2, xi = (x - 0.5) / L clamped to
+    [0, 1] and evaluated at the solid cell's centre.  eta_n is the Newtonian viscosity,
+    eta_p = beta / (1 - beta) eta_n, Wi = lambda u0 / L."""
+    n = L + 2
+    fl = np.ones((n, n), np.uint8)
+    fl[1:-1, 1:-1] = 0
+    ub = np.zeros((2, n, n))
+    xi = np.clip((np.arange(n) - 0.5) / L, 0.0, 1.0)
+    ub[0, -1, :] = 16.0 * u0 * xi ** 2 * (1.0 - xi) ** 2
+    eta = eta_n / (1.0 - beta)
+    lam = max(wi * L / u0, 1.0)
+    return {"shape": (n, n), "flags": fl, "ub": ub,
+            "params": dict(periodic=(0, 0), eta=eta, beta=beta, lambda_p=lam, body_force=(0.0, 0.0))}
+
+
+def four_roll_mill2d(N=214, u0=1e-3, beta=1.0 / 3.0, eta_n=1.5, wi=0.5, rotated=True):
+    """Four-roll mill of Sec. "Four-roll mill" on an N x N periodic lattice.  The force
+    density F0 (sin kx cos ky, -cos kx sin ky), F0 = 8 pi^2 eta_n u0 / L^2, k = 2 pi / L,
+    drives four counter-rotating rolls (the printed second component carries no minus
+    sign, which would make the field a pure gradient that drives no flow).  rotated: the
+    lattice is turned by 45 degrees against the system, x = (x' + y') / sqrt 2,
+    y = (y' - x') / sqrt 2, with L = N sqrt 2 so that the N x N lattice stays periodic;
+    else L = N.  Returns the force field at the cell centres in lattice components
+    (2, N, N), L, k and the parameters (Wi = 4 pi lambda u0 / L)."""
+    L = N * math.sqrt(2.0) if rotated else float(N)
+    k = 2.0 * math.pi / L
+    yl, xl = np.meshgrid(np.arange(N, dtype=float), np.arange(N, dtype=float), indexing="ij")
+    if rotated:
+        x = (xl + yl) / math.sqrt(2.0)
+        y = (yl - xl) / math.sqrt(2.0)
+    else:
+        x, y = xl, yl
+    F0 = 8.0 * math.pi ** 2 * eta_n * u0 / L ** 2
+    Fs = np.stack([F0 * np.sin(k * x) * np.cos(k * y), -F0 * np.cos(k * x) * np.sin(k * y)])
+    if rotated:  # system components -> lattice components
+        F = np.stack([(Fs[0] - Fs[1]) / math.sqrt(2.0), (Fs[0] + Fs[1]) / math.sqrt(2.0)])
+    else:
+        F = Fs
+    eta = eta_n / (1.0 - beta)
+    lam = max(wi * L / (4.0 * math.pi * u0), 1.0)
+    return {"shape": (N, N), "force": F, "L": L, "k": k,
+            "params": dict(periodic=(1, 1), eta=eta, beta=beta, lambda_p=lam, body_force=(0.0, 0.0))}

@@ -73,3 +73,10 @@ def startup_newtonian_centre(t, *, g, rho, eta, L, nmodes=401):
         amp = 4.0 * g / (n * math.pi * eta * k * k)
         u += amp * (1.0 - np.exp(-nu * k * k * t)) * math.sin(k * L / 2)
     return u
+
+
+def four_roll_mill_newtonian(F, k, eta):
+    """Steady Stokes flow under the four-roll-mill force F0 (sin kx cos ky, -cos kx sin ky):
+    the field is divergence free and an eigenfunction of the Laplacian (eigenvalue -2 k^2),
+    so eta lap u + F = 0 with no pressure gradient gives u = F / (2 k^2 eta) (any frame)."""
+    return np.asarray(F) / (2.0 * k * k * eta)

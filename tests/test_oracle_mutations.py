@@ -34,6 +34,12 @@ MUTANTS = {
     "created_stress_mean": ("sum[c] / (double)(Nf[r] + 1)", "sum[c] / (double)(Nf[r] ? Nf[r] : 1)"),
     "destroyed_impulse_sign": ("P->dP[a] += Pm[a];", "P->dP[a] -= Pm[a];"),
     "symplectic_order": ("P->X[a] += P->v[a];\n", "P->X[a] += P->v[a] - (P->Fme[a] + P->Fext[a]) / P->m;\n"),
+    "fene_relaxation_without_closure": ("S[c] = a + b - s->inv_l * (fA * tr[c] - (i == j ? 1.0 : 0.0));",
+                                        "S[c] = a + b - s->inv_l * (tr[c] - (i == j ? 1.0 : 0.0));"),
+    "fene_stress_identity_scaled": ("tau[c] = (eta_p / lambda_p) * (f * A[c] - (c < 3 ? 1.0 : 0.0));",
+                                    "tau[c] = (eta_p / lambda_p) * f * (A[c] - (c < 3 ? 1.0 : 0.0));"),
+    "fene_trace_offdiagonal": ("double fA = 1.0 / (1.0 - (tr[0] + tr[1] + tr[2]) / s->p.fene_L2);",
+                               "double fA = 1.0 / (1.0 - (tr[0] + tr[1] + tr[3]) / s->p.fene_L2);"),
 }
 
 
@@ -105,3 +111,34 @@ def test_only_the_brute_force_catches_mutant(name, tmp_path):
     assert pins.returncode == 0, f"mutant {name} is caught by the pins as well:\n{pins.stdout[-1500:]}"
     brute = _run_suite(so, "test_oracle_brute_force.py")
     assert brute.returncode != 0, f"mutant {name} survived the brute-force comparison:\n{brute.stdout[-2000:]}"
+
+
+# Plausible mistakes in the two-dimensional oracle, each caught by its pin suite.
+MUTANTS_2D = {
+    "2d_forcing_first_order_unweighted": ("double A = 3.0 * (1.0 - 0.5 * s->omega_m)", "double A = 3.0 * (1.0 + 0.0 * s->omega_m)"),
+    "2d_moving_wall_sign": ("s->f[(long)OPP2[i] * n + r] = fsi - 6.0 * W2[i] * s->rho[r] * cub;",
+                           "s->f[(long)OPP2[i] * n + r] = fsi + 6.0 * W2[i] * s->rho[r] * cub;"),
+    "2d_source_transposed_gradient": ("for (int k = 0; k < 2; ++k) b += tr[CMP[k][j]] * G[k * 2 + i];",
+                                      "for (int k = 0; k < 2; ++k) b += tr[CMP[k][j]] * G[i * 2 + k];"),
+    "2d_field_force_dropped": ("F[a] = (s->p.g[a] + s->Ff[(long)a * n + r]) + Fp[a];", "F[a] = s->p.g[a] + Fp[a];"),
+    "2d_wall_gradient_uses_cell": ("double up = fluid2(s, np_) ? 0.5 * (ur + u[(long)j * n + np_]) : ubp[j];",
+                                   "double up = fluid2(s, np_) ? 0.5 * (ur + u[(long)j * n + np_]) : ur;"),
+    "2d_diagonal_weight": ("for (int i = 5; i < 9; ++i) W2[i] = 1.0 / 36.0;", "for (int i = 5; i < 9; ++i) W2[i] = 1.0 / 35.0;"),
+}
+
+
+@pytest.mark.parametrize("name", sorted(MUTANTS_2D))
+def test_2d_pins_catch_mutant(name, tmp_path):
+    old, new = MUTANTS_2D[name]
+    src = open(os.path.join(ROOT, "oracle", "lbve2d_oracle.c")).read()
+    assert src.count(old) == 1, f"mutation site for {name} not found or not unique"
+    (tmp_path / "lbve2d_oracle.c").write_text(src.replace(old, new))
+    shutil.copy(os.path.join(ROOT, "oracle", "lbve2d_oracle.h"), tmp_path / "lbve2d_oracle.h")
+    so = tmp_path / "mutant2d.so"
+    subprocess.run(["gcc", "-O2", "-std=gnu11", "-fPIC", "-shared", "-ffp-contract=off", "-fopenmp",
+                    str(tmp_path / "lbve2d_oracle.c"), "-o", str(so), "-lm"], check=True)
+    env = dict(os.environ, LBVE_ORACLE2D_LIB=str(so), OMP_NUM_THREADS="2")
+    r = subprocess.run([sys.executable, "-m", "pytest", "-x", "-q", "-p", "no:cacheprovider",
+                        os.path.join(HERE, "test_oracle2d_pins.py")], env=env, capture_output=True, text=True,
+                       timeout=600)
+    assert r.returncode != 0, f"mutant {name} survived the 2-D pins:\n{r.stdout[-2000:]}"

@@ -806,3 +806,95 @@ def test_subbox_centre_equals_full_periodic_solve():
     assert np.array_equal(got[:19], full2.read_pdfs().reshape(19, -1)[:, r])
     _, u2, _, _ = full2.read_fields()
     assert np.array_equal(got[20:23], u2.reshape(3, -1)[:, r])
+
+
+# ---------------------------------------------------------------------------------
+# FENE-P (conformation tensor with the Peterlin closure)
+# ---------------------------------------------------------------------------------
+def test_fene_conformation_and_stress_are_inverse(oracle_mod):
+    """tau = (eta_p/lambda)(f A - I) with f = 1/(1 - tr A / L^2), and the closed-form
+    inverse A = (I + lambda tau / eta_p) / f, f = 1 + (3 + lambda tr tau / eta_p) / L^2:
+    round trips to rounding, f obeys its definition, and zero stress is the isotropic
+    equilibrium A = I L^2 / (L^2 + 3)."""
+    eta_p, lam, L2 = 0.12, 40.0, 60.0
+    for _ in range(20):
+        t = 1e-3 * RNG.standard_normal(6)
+        A = oracle_mod.fene_conformation(t, eta_p, lam, L2)
+        assert np.allclose(oracle_mod.fene_stress(A, eta_p, lam, L2), t, rtol=1e-12, atol=1e-17)
+        f = 1.0 / (1.0 - A[:3].sum() / L2)
+        assert np.allclose(f * A[:3] - 1.0, lam * t[:3] / eta_p, rtol=1e-12, atol=1e-15)
+    A0 = oracle_mod.fene_conformation(np.zeros(6), eta_p, lam, L2)
+    assert np.allclose(A0, [L2 / (L2 + 3.0)] * 3 + [0.0] * 3, rtol=1e-15, atol=0)
+
+
+def _fene_steady_shear(lam, L2, gdot):
+    """Steady homogeneous simple shear u_x = gdot y of the FENE-P conformation equations
+    A_(1) = -(f A - I)/lambda, written out component by component (xx, yy = zz, xy; xz
+    and yz vanish) and solved by Newton's method from the Oldroyd-B state."""
+    from scipy.optimize import fsolve
+
+    def eqs(a):
+        axx, ayy, axy = a
+        f = 1.0 / (1.0 - (axx + 2.0 * ayy) / L2)
+        return [2.0 * gdot * axy - (f * axx - 1.0) / lam,
+                -(f * ayy - 1.0) / lam,
+                gdot * ayy - f * axy / lam]
+
+    a0 = [1.0 + 2.0 * (lam * gdot) ** 2, 1.0, lam * gdot]
+    sol = fsolve(eqs, a0, xtol=1e-13)
+    assert np.abs(eqs(sol)).max() <= 1e-15
+    return sol
+
+
+@pytest.mark.parametrize("L2", [10.0, 50.0, 1e12])
+def test_fene_steady_shear(oracle_mod, L2):
+    """FENE-P in simple shear: iterating the conformation update (source only) converges
+    to the root of the steady equations above; the stress read back shear-thins (tau_xy <
+    eta_p gdot, N1 < 2 eta_p lambda gdot^2) for finite L^2, and L^2 -> infinity is the
+    Oldroyd-B state."""
+    n = 8
+    eta, beta, lam, gdot = 0.4, 0.5, 12.0, 0.1  # Wi = 1.2
+    eta_p = beta * eta
+    o = oracle_mod.Oracle((n, n, n), eta=eta, beta=beta, lambda_p=lam, fv_terms=oracle_mod.FV_SOURCE, fene_L2=L2)
+    z, y, x = np.meshgrid(np.arange(n), np.arange(n), np.arange(n), indexing="ij")
+    u = np.zeros((3, n, n, n))
+    u[0] = gdot * y
+    A = np.zeros((6, n, n, n))
+    A[:3] = L2 / (L2 + 3.0)  # zero stress
+    for _ in range(1500):
+        o.write_tau(A)
+        A = o.fv_update(u)
+    inner = (slice(1, n - 1),) * 3
+    axx, ayy, axy = _fene_steady_shear(lam, L2, gdot)
+    for c, v in {0: axx, 1: ayy, 2: ayy, 3: axy, 4: 0.0, 5: 0.0}.items():
+        assert np.allclose(A[c][inner], v, rtol=1e-10, atol=1e-14), (c, A[c][inner].ravel()[:2], v)
+    o.write_tau(A)
+    _, _, tau, _ = o.read_fields()
+    txy = tau[3][inner].mean()
+    n1 = (tau[0] - tau[1])[inner].mean()
+    if L2 > 1e6:
+        assert np.isclose(txy, eta_p * gdot, rtol=1e-9) and np.isclose(n1, 2 * eta_p * lam * gdot**2, rtol=1e-9)
+    else:
+        assert txy < eta_p * gdot and n1 < 2 * eta_p * lam * gdot**2
+
+
+def test_fene_large_extensibility_is_oldroyd_b(oracle_mod):
+    """One source-only update of a random conformation field under a random velocity
+    field: with L^2 = 1e15 the FENE-P update, mapped to stress by
+    tau = (eta_p/lambda)(A - I), is the Oldroyd-B update of Eq. (source)."""
+    n = 6
+    eta, beta, lam = 0.3, 0.6, 25.0
+    eta_p = beta * eta
+    u = 0.02 * RNG.standard_normal((3, n, n, n))
+    tau = 1e-3 * RNG.standard_normal((6, n, n, n))
+    ob = oracle_mod.Oracle((n, n, n), eta=eta, beta=beta, lambda_p=lam, fv_terms=oracle_mod.FV_SOURCE)
+    ob.write_tau(tau)
+    t_ob = ob.fv_update(u)
+    fe = oracle_mod.Oracle((n, n, n), eta=eta, beta=beta, lambda_p=lam, fv_terms=oracle_mod.FV_SOURCE, fene_L2=1e15)
+    A = lam * tau / eta_p
+    A[:3] += 1.0
+    fe.write_tau(A)
+    A1 = fe.fv_update(u)
+    t_fe = eta_p / lam * A1
+    t_fe[:3] -= eta_p / lam
+    assert np.allclose(t_fe, t_ob, rtol=1e-9, atol=1e-12 * np.abs(t_ob).max())
