@@ -51,12 +51,13 @@ typedef enum {
 
 /* Storage precision of the PDFs (arithmetic is FP64 for LBVE_F64, else FP32).
  * All reduced modes store the deviation f_i - w_i rho0 (FP16: times 2^pdf_scale_log2).
- * The 16-bit modes round the stream-collide's stores stochastically (unbiased; the
- * random bits hash the value with the step, cell and direction, so results are
- * deterministic and the same alone and in a pool): round-to-nearest would drop per-step
- * changes smaller than half a unit of the stored deviation, and slow flows would stall.
- * The price is a noise floor in the steady-state residual (~2e-5 per step in BF16,
- * ~2.5e-6 in FP16). */
+ * The 16-bit modes round the stream-collide's stores stochastically (unbiased: the
+ * hardware's stochastic-rounding conversion of two values at a time, with random bits
+ * from a counter-based hash of the step, the cell and the direction pair, so results are
+ * deterministic and the same alone, in a pool or in z-slabs): round-to-nearest would drop
+ * per-step changes smaller than half a unit of the stored deviation, and slow flows would
+ * stall.  The price is a noise floor in the steady-state residual (~2e-5 per step in
+ * BF16, ~2.5e-6 in FP16). */
 typedef enum { LBVE_F64 = 0, LBVE_F32 = 1, LBVE_F16_SHIFTED = 2, LBVE_BF16_SHIFTED = 3 } lbve_pdf_prec;
 
 #define LBVE_FLAG_FLUID 0
@@ -112,6 +113,15 @@ typedef struct {
                             printing it; the textbook law tau + lambda tau_(1) +
                             (alpha lambda / eta_p) tau.tau = eta_p (grad u + grad u^T) adds
                             -(alpha / eta_p) tau.tau to the source of Eq. (source) */
+    double fene_L2;      /* FENE-P maximum extensibility L^2 (> 3); 0 (the default) is
+                            Oldroyd-B.  The paper names FENE-P among the laws its scheme
+                            extends to without printing it; the textbook Peterlin closure is
+                            written for the conformation tensor A, which the stress arrays
+                            then hold: A_(1) = -(f A - I) / lambda_p, tau = (eta_p / lambda_p)
+                            (f A - I), f = 1 / (1 - tr A / L^2).  Fields are still given and
+                            read as stress tau (converted per cell).  Needs beta > 0 and
+                            giesekus_alpha = 0; runs with lbve_step on the split schedule
+                            only (no particles, pools, fused schedule or lbve_step_noalloc) */
 } lbve_params;
 
 /* Optional device allocator (e.g. a framework's caching allocator).  alloc returns a
@@ -173,9 +183,64 @@ lbve_status lbve_add_particle(lbve_ctx *ctx, const double X[3], double R, double
 /*
  * Advance nsteps time steps (Eqs. (lb), (continuity)-(source), moving boundaries).
  * Asynchronous on the context's stream unless the context has particles with a
- * host-side check pending; returns after enqueueing.  Errors: EINVAL, ECUDA.
+ * host-side check pending; returns after enqueueing.  Errors: EINVAL, ECUDA, EUNSTABLE.
+ *
+ * Instability: every stream-collide checks each fluid cell for rho <= 0, |u|^2 >= 1/3
+ * (the lattice sound speed squared, beyond which the equilibrium of Eq.
+ * (lb-equilibrium) has no meaning) or a NaN, and sets a flag in page-locked host memory
+ * when it finds one (no synchronisation, no extra traffic).  lbve_step returns
+ * LBVE_EUNSTABLE without stepping once the flag of an earlier step has reached the
+ * host; lbve_synchronize returns it after synchronising.  The state stays readable.
+ * lbve_init_fields[_device] and lbve_write_pdfs clear the flag.
  */
 lbve_status lbve_step(lbve_ctx *ctx, int nsteps);
+
+/*
+ * Decomposition of one domain into z-slabs (the paper's runs are distributed over
+ * waLBerla's block forest, Sec. "Implementation and extensibility"), one context per
+ * slab, with the halo exchange done by the caller between steps (same device, peer
+ * devices or ranks).  A slab context holds its planes
+ * plus one ghost plane on each side: create it with nz = planes + 2 and periodic[2] = 0,
+ * call lbve_set_z_range(ctx, 1, nz - 1, z_origin) before lbve_set_geometry (z_origin: the
+ * domain's plane index of the slab's first computed plane, which keeps the rounding keys of
+ * the 16-bit stores those of the undecomposed domain), and give the ghost
+ * planes the flags (and initial fields) of the neighbouring slabs' boundary planes (solid
+ * planes beyond a closed domain).  Only planes [z_lo, z_hi) are computed; wall links of
+ * the ghost planes are left out, so body forces of the slabs add up to the domain's.
+ * Particles, pools and the fused schedule are not combined with z-slabs.
+ *
+ * One step of a decomposed domain, every slab on the same schedule:
+ *   lbve_step_phase(s, 0) on every slab          (stream-collide)
+ *   exchange LBVE_HALO_F and LBVE_HALO_U           (between neighbouring slabs)
+ *   lbve_step_phase(s, 1) on every slab          (stress update; the step completes)
+ *   exchange LBVE_HALO_TAU
+ * Exchanging `what` between a lower slab A and an upper slab B: pack(A, what, 1, buf),
+ * unpack(B, what, 0, buf), and pack(B, what, 0, buf2), unpack(A, what, 1, buf2).  Buffers
+ * are device memory of lbve_halo_bytes(ctx, what) bytes: plane-major values, one x-y plane
+ * of the slab per value, x fastest:
+ *   LBVE_HALO_F    the 5 PDFs per cell that cross the face in the step just taken (raw
+ *                  storage elements; which slots depends on that step's parity of the
+ *                  in-place layout, handled by the library): 5 storage elements per cell;
+ *   LBVE_HALO_U    u of the boundary plane, 3 reals per cell (into the ghost plane);
+ *   LBVE_HALO_TAU  the stress of the boundary plane, 6 reals per cell (into the ghost).
+ * A decomposed run gives bitwise the fields of the undecomposed one.  Calls enqueue on
+ * the context's stream.  Errors: EINVAL, ESTATE (not a z-slab, phases out of order).
+ */
+#define LBVE_HALO_F 0
+#define LBVE_HALO_U 1
+#define LBVE_HALO_TAU 2
+lbve_status lbve_set_z_range(lbve_ctx *ctx, int z_lo, int z_hi, int z_origin);
+/* phase 0: the stream-collide of the next step (with the momentum exchange before it);
+ * phase 1: its stress update, completing the step.  lbve_step refuses while a phase 0
+ * awaits its phase 1. */
+lbve_status lbve_step_phase(lbve_ctx *ctx, int phase);
+size_t lbve_halo_bytes(const lbve_ctx *ctx, int what);
+lbve_status lbve_halo_pack(lbve_ctx *ctx, int what, int side, void *dev_buf);
+lbve_status lbve_halo_unpack(lbve_ctx *ctx, int what, int side, const void *dev_buf);
+
+/* 1 if the context's instability flag is set (see lbve_step), 0 if not, -1 for NULL.
+ * Does not synchronise: steps still in flight may set it later. */
+int lbve_is_unstable(const lbve_ctx *ctx);
 
 /*
  * Copy the macroscopic fields to host arrays (each may be NULL): rho (n), u (3n, the
@@ -255,10 +320,16 @@ lbve_status lbve_read_kernel_times(lbve_ctx *ctx, double ms[LBVE_KT_COUNT], long
  *   flags  n bytes: 0 fluid, 1 no-slip, LBVE_FLAG_WALL0 + k wall class k < n_wall
  *          (velocities in wall_vel, host, 3 doubles each); particle flags act as
  *          resting walls.  Momentum-exchange forces are not computed by this call.
+ * Schedule: always the split kernels.  p->schedule must be LBVE_SCHED_AUTO or
+ * LBVE_SCHED_SPLIT (LBVE_SCHED_FUSED is rejected with EINVAL); p->block_x is honoured as
+ * by lbve_create, but schedules recorded by lbve_autotune are not applied and the stress
+ * kernel takes its default z-chunk.  None of these choices changes a result.
  * Validation: EINVAL for bad parameters, NULL buffers or more than
  * LBVE_NOALLOC_MAX_CELLS cells.  The first call on each device (with that device
- * current) looks up the address of the static array; make that first call before any
- * stream capture.  Every call shares the array, which keeps the last call's contents;
+ * current) looks up the address of the static array and keeps it for the life of the
+ * process; make that first call before any stream capture.  A reset of the device's
+ * primary context (cudaDeviceReset) discards the array and invalidates that address:
+ * do not call this entry point on a device after resetting it.  Every call shares the array, which keeps the last call's contents;
  * nothing in it needs to start at zero.  Calls that overlap on the GPU (other streams,
  * other threads) race on it: serialise them.  Enqueues the kernels on cuda_stream and
  * returns without synchronising.  Errors are described by lbve_noalloc_last_error().
@@ -298,6 +369,8 @@ int lbve_pool_fits(const lbve_pool *pool, const lbve_params *p);
 /* Errors: ENOMEM (over budget), ESTATE (precision or stream differ, already a member). */
 lbve_status lbve_pool_admit(lbve_pool *pool, lbve_ctx *ctx);
 lbve_status lbve_pool_remove(lbve_pool *pool, lbve_ctx *ctx);
+/* Errors: EUNSTABLE, without stepping, when a member's instability flag (lbve_step) is
+ * set: remove the members for which lbve_is_unstable returns 1 and step again. */
 lbve_status lbve_pool_step(lbve_pool *pool, int nsteps);
 /* Residuals of all members in admission order: 2 doubles each as in lbve_residual. */
 lbve_status lbve_pool_residuals(lbve_pool *pool, double *out);
@@ -343,6 +416,27 @@ lbve_status lbve_autotune(lbve_ctx *ctx, int steps, lbve_tuning *out);
  * ms_after: pool step time with the tiles before the call and with the choices. */
 lbve_status lbve_pool_autotune(lbve_pool *pool, int steps, int max_classes, int *n_classes, int *class_nx,
                                int *lb_tx, int *fv_tx, double *ms_before, double *ms_after);
+
+/*
+ * Checkpoint and restore of a solve at a step boundary (for restarts; the paper has no
+ * counterpart).  The record holds the raw device state: the PDF storage (19 np elements
+ * of the storage type, in the in-place layout of the current step parity), the current
+ * stress (6 np reals), the flag field (n bytes, particle cells included), the particle
+ * table, the conversion diagnostics and body forces of the last step, the step counter
+ * and the stress / velocity ping-pong indices, behind a header naming the grid, the
+ * precision and the particle count.  lbve_checkpoint_bytes gives its size.
+ * lbve_save copies it into caller-owned host memory (synchronises the stream).
+ * lbve_restore overwrites a context created with the same parameters, after
+ * lbve_set_geometry with the same no-slip and wall-class cells and the same number of
+ * lbve_add_particle calls (their link capacities), and rebuilds the neighbour masks and
+ * the particle link lists; stepping it then gives bitwise the results of stepping the
+ * saved solve.  The residual snapshot of lbve_residual is not part of the record.
+ * Errors: EINVAL (buffer too small, another grid, precision, particle count or static
+ * geometry), ESTATE (restore into a pool member), ECUDA.
+ */
+size_t lbve_checkpoint_bytes(const lbve_ctx *ctx);
+lbve_status lbve_save(lbve_ctx *ctx, void *buf, size_t bytes);
+lbve_status lbve_restore(lbve_ctx *ctx, const void *buf, size_t bytes);
 
 /* Steps done since the last lbve_init_fields. */
 long long lbve_time(const lbve_ctx *ctx);

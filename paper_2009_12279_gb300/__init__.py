@@ -4,4 +4,4 @@ The compute path is the CUDA library liblbve.so (C ABI in include/lbve.h); the P
 modules here marshal arguments (lbve), build the library (build), generate seeded
 synthetic workloads (workloads) and schedule many solves (serve).
 """
-from .lbve import LbveError, Solver, device_bytes, load, make_params  # noqa: F401
+from .lbve import LbveError, Pool, Solver, Solver2D, device_bytes, load, make_params  # noqa: F401

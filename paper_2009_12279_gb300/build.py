@@ -27,6 +27,7 @@ UNITS = {
     "lbve_f16.cu": [],
     "lbve_bf16.cu": [],
     "lbve_noalloc.cu": [],
+    "lbve2d.cu": ["--fmad=false"],  # the 2-D step; its FP64 mode evaluates as written
 }
 
 
@@ -38,7 +39,8 @@ def nvcc() -> str:
 
 
 def _sources_mtime() -> float:
-    paths = [os.path.join(CSRC, f) for f in os.listdir(CSRC)] + [os.path.join(INCLUDE, "lbve.h"), __file__]
+    paths = [os.path.join(CSRC, f) for f in os.listdir(CSRC)] + [os.path.join(INCLUDE, f) for f in os.listdir(INCLUDE)]
+    paths.append(__file__)
     return max(os.path.getmtime(p) for p in paths)
 
 

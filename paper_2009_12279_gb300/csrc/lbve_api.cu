@@ -72,6 +72,13 @@ struct lbve_ctx {
     void *usnap = nullptr;
     double *res_partial = nullptr;
     lbve_pool *pool = nullptr;
+    // instability flag: mapped page-locked word set by the stream-collide (d.bad is its
+    // device address); read by the host without synchronising
+    unsigned *h_bad = nullptr;
+    // z-slab stepping: AA parity of the last stream-collide, and a stream-collide whose
+    // stress update (lbve_step_phase 1) is still to come
+    int last_lb_parity = 0;
+    bool phase_pending = false;
 };
 
 namespace {
@@ -110,6 +117,17 @@ const char *kStatusNames[] = {"LBVE_OK",        "LBVE_EINVAL",   "LBVE_ENOMEM", 
 lbve_status fail(lbve_ctx *c, lbve_status s, const std::string &msg) {
     if (c) c->err = msg;
     return s;
+}
+
+// The instability flag of a context (set by a stream-collide of an earlier call; the
+// host sees it once that kernel has written it, without synchronising).
+bool unstable(const lbve_ctx *c) { return c->h_bad && *(volatile const unsigned *)c->h_bad != 0u; }
+std::string unstable_message(const lbve_ctx *c) {
+    return "instability detected at or before step " + std::to_string(c->t) +
+           ": a fluid cell had rho <= 0, |u|^2 >= 1/3 or a NaN";
+}
+void clear_unstable(lbve_ctx *c) {
+    if (c->h_bad) *(volatile unsigned *)c->h_bad = 0u;
 }
 
 lbve_status cuda_fail(lbve_ctx *c, cudaError_t e, const char *where) {
@@ -157,6 +175,11 @@ bool valid_params(const lbve_params *p, std::string &why) {
     if (p->pdf_scale_log2 < -1 || p->pdf_scale_log2 > 24) return why = "pdf_scale_log2 out of range", false;
     if (p->fv_terms < 0 || p->fv_terms > 15) return why = "fv_terms out of range", false;
     if (!(p->giesekus_alpha >= 0.0 && p->giesekus_alpha <= 0.5)) return why = "giesekus_alpha must be in [0, 1/2]", false;
+    if (!(p->fene_L2 == 0.0 || p->fene_L2 > 3.0)) return why = "fene_L2 must be 0 (Oldroyd-B) or > 3", false;
+    if (p->fene_L2 > 0.0 && !(p->beta > 0.0)) return why = "FENE-P needs a polymer (beta > 0)", false;
+    if (p->fene_L2 > 0.0 && p->giesekus_alpha != 0.0) return why = "FENE-P and Giesekus cannot be combined", false;
+    if (p->fene_L2 > 0.0 && p->schedule == LBVE_SCHED_FUSED)
+        return why = "FENE-P runs on the split schedule only", false;
     if (p->block_x != 0 && p->block_x != 32 && p->block_x != 64 && p->block_x != 128)
         return why = "block_x must be 0, 32, 64 or 128", false;
     if (!(p->magic >= 0.0)) return why = "magic must be >= 0", false;
@@ -224,6 +247,10 @@ void lbve::fill_phys(const lbve_params &p, Phys<double> &ph) {
     ph.ctu_on = (terms & LBVE_FV_CTU) != 0;
     ph.divu_on = (terms & LBVE_FV_DIVU) != 0;
     ph.gk = p.beta > 0.0 ? p.giesekus_alpha / (p.beta * p.eta) : 0.0;
+    ph.fene = p.fene_L2 > 0.0 ? 1 : 0;
+    ph.fene_L2 = p.fene_L2;
+    ph.eta_p = eta_p;
+    ph.lam = p.lambda_p;
 }
 
 bool lbve::params_valid(const lbve_params *p, std::string &why) { return valid_params(p, why); }
@@ -403,6 +430,7 @@ void build_wall_links(lbve_ctx *c, const uint8_t *fl, bool any_wall) {
                 zq = (zq + nz) % nz;
             }
             const long long r = xq + (long long)nx * (yq + (long long)ny * zq);
+            if (c->d.zhi > 0 && (zq < c->d.zlo || zq >= c->d.zhi)) continue;  // a ghost plane of a z-slab
             if (fl[r] == FLAG_FLUID) tmp.push_back({(int)f, (r << 5) | i});
         }
     }
@@ -538,7 +566,16 @@ lbve_status create_impl(const lbve_params *p, void *stream, lbve_alloc_fn alloc,
         lbve_destroy(c);
         return LBVE_ENOMEM;
     }
-    cudaError_t e = cudaMemsetAsync(c->d.flag, 0, (size_t)np, c->stream);
+    cudaError_t e = cudaHostAlloc((void **)&c->h_bad, sizeof(unsigned), cudaHostAllocMapped);
+    if (e == cudaSuccess) {
+        *c->h_bad = 0u;
+        void *dbad = nullptr;
+        e = cudaHostGetDevicePointer(&dbad, c->h_bad, 0);
+        c->d.bad = (unsigned *)dbad;
+    } else {
+        c->h_bad = nullptr;
+    }
+    if (e == cudaSuccess) e = cudaMemsetAsync(c->d.flag, 0, (size_t)np, c->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(c->d.u[0], 0, (size_t)3 * np * c->kt->real_bytes, c->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(c->d.u[1], 0, (size_t)3 * np * c->kt->real_bytes, c->stream);
     if (e == cudaSuccess) e = c->kt->build_mask(c->d, 0, 0, 0, g.nx, g.ny, g.nz, c->stream);
@@ -659,6 +696,7 @@ lbve_status lbve_destroy(lbve_ctx *c) {
         cudaEventDestroy(ev.second);
     }
     while (!c->blocks.empty()) dev_free(c, c->blocks.back().first);
+    if (c->h_bad) cudaFreeHost(c->h_bad);
     delete c;
     return LBVE_OK;
 }
@@ -688,6 +726,7 @@ lbve_status lbve_set_geometry(lbve_ctx *c, const uint8_t *flags, const double *w
     const int nn[3] = {nx, ny, nz};
     for (int a = 0; a < 3; ++a) {
         if (c->p.periodic[a]) continue;
+        if (a == 2 && c->d.zhi > 0) continue;  // a z-slab's outer planes are its ghost planes
         for (int side = 0; side < 2; ++side) {
             const int q = side ? nn[a] - 1 : 0;
             const int b1 = a == 0 ? ny : nx, b2 = a == 2 ? ny : nz;
@@ -725,6 +764,7 @@ lbve_status lbve_init_fields(lbve_ctx *c, const double *rho, const double *u, co
             c->d.cur = 0;
             CK(c->kt->init(c->d, drho, du, dtau, 0, n, n, c->stream), "init kernel");
             CK(cudaStreamSynchronize(c->stream), "init sync");
+            clear_unstable(c);
             c->t = 0;
             return LBVE_OK;
         }
@@ -751,6 +791,7 @@ lbve_status lbve_init_fields(lbve_ctx *c, const double *rho, const double *u, co
     }
     CK(cudaStreamSynchronize(c->stream), "init sync");
     dev_free(c, st);
+    clear_unstable(c);
     c->t = 0;
     return LBVE_OK;
 }
@@ -760,6 +801,8 @@ lbve_status lbve_init_fields_device(lbve_ctx *c, const double *rho, const double
     if (c->pool) return fail(c, LBVE_ESTATE, "fields cannot be reset while the solve is in a pool");
     c->d.cur = 0;
     CK(c->kt->init(c->d, rho, u, tau, 0, c->d.g.n, c->d.g.n, c->stream), "init kernel");
+    // the instability flag restarts with the new fields, in stream order
+    if (c->d.bad) CK(cudaMemsetAsync(c->d.bad, 0, sizeof(unsigned), c->stream), "flag reset");
     c->t = 0;
     return LBVE_OK;
 }
@@ -793,6 +836,8 @@ lbve_status lbve_add_particle(lbve_ctx *c, const double X[3], double R, double r
     if (!(R > 0.0) || !(rho_p > 0.0)) return fail(c, LBVE_EINVAL, "radius and density must be > 0");
     if (c->nparts >= MAX_PART) return fail(c, LBVE_ESTATE, "too many particles");
     if (c->pool) return fail(c, LBVE_ESTATE, "particles cannot be added while the solve is in a pool");
+    if (c->p.fene_L2 > 0.0) return fail(c, LBVE_ESTATE, "moving particles are not combined with FENE-P");
+    if (c->d.zhi > 0) return fail(c, LBVE_ESTATE, "moving particles are not combined with a z-slab");
     const int nn[3] = {c->p.nx, c->p.ny, c->p.nz};
     for (int a = 0; a < 3; ++a) {
         if (!std::isfinite(X[a])) return fail(c, LBVE_EINVAL, "X must be finite");
@@ -848,6 +893,130 @@ lbve_status lbve_read_conversions(lbve_ctx *c, double out[8]) {
     return LBVE_OK;
 }
 
+// ---------------------------------------------------------------------------------
+// checkpoint / restore: the raw state of a solve at a step boundary
+// ---------------------------------------------------------------------------------
+struct CkptHeader {
+    char magic[8];  // "LBVECKP1"
+    int nx, ny, nz, pdf_prec, nparts, cur, ucur, reserved;
+    long long t;
+    long long n, np;
+    unsigned long long pdf_bytes, real_bytes;
+};
+static size_t ckpt_bytes(const lbve_ctx *c) {
+    const long long np = c->d.g.np, n = c->d.g.n;
+    return sizeof(CkptHeader) + (size_t)Q * np * c->kt->pdf_bytes + (size_t)6 * np * c->kt->real_bytes + (size_t)n +
+           sizeof(PartDev) * (size_t)c->nparts + sizeof(double) * 8 + sizeof(double) * 256 * 3;
+}
+
+size_t lbve_checkpoint_bytes(const lbve_ctx *c) { return c ? ckpt_bytes(c) : 0; }
+
+lbve_status lbve_save(lbve_ctx *c, void *buf, size_t bytes) {
+    if (!c) return LBVE_EINVAL;
+    if (!buf || bytes < ckpt_bytes(c)) return fail(c, LBVE_EINVAL, "checkpoint buffer missing or too small");
+    const long long np = c->d.g.np, n = c->d.g.n;
+    CkptHeader h;
+    std::memset(&h, 0, sizeof h);
+    std::memcpy(h.magic, "LBVECKP1", 8);
+    h.nx = c->p.nx;
+    h.ny = c->p.ny;
+    h.nz = c->p.nz;
+    h.pdf_prec = c->p.pdf_prec;
+    h.nparts = c->nparts;
+    h.cur = c->d.cur;
+    h.ucur = c->d.ucur;
+    h.t = c->t;
+    h.n = n;
+    h.np = np;
+    h.pdf_bytes = c->kt->pdf_bytes;
+    h.real_bytes = c->kt->real_bytes;
+    char *o = (char *)buf;
+    std::memcpy(o, &h, sizeof h);
+    o += sizeof h;
+    const size_t fb = (size_t)Q * np * c->kt->pdf_bytes, tb = (size_t)6 * np * c->kt->real_bytes;
+    CK(cudaMemcpyAsync(o, c->d.f, fb, cudaMemcpyDeviceToHost, c->stream), "save pdfs");
+    o += fb;
+    CK(cudaMemcpyAsync(o, c->d.tau[c->d.cur], tb, cudaMemcpyDeviceToHost, c->stream), "save stress");
+    o += tb;
+    CK(cudaMemcpyAsync(o, c->d.flag, (size_t)n, cudaMemcpyDeviceToHost, c->stream), "save flags");
+    o += n;
+    if (c->nparts > 0)
+        CK(cudaMemcpyAsync(o, c->d.parts, sizeof(PartDev) * c->nparts, cudaMemcpyDeviceToHost, c->stream),
+           "save particles");
+    o += sizeof(PartDev) * c->nparts;
+    CK(cudaMemcpyAsync(o, c->pdiag, sizeof(double) * 8, cudaMemcpyDeviceToHost, c->stream), "save diag");
+    o += sizeof(double) * 8;
+    CK(cudaMemcpyAsync(o, c->body_F, sizeof(double) * 256 * 3, cudaMemcpyDeviceToHost, c->stream), "save forces");
+    CK(cudaStreamSynchronize(c->stream), "save sync");
+    return LBVE_OK;
+}
+
+lbve_status lbve_restore(lbve_ctx *c, const void *buf, size_t bytes) {
+    if (!c) return LBVE_EINVAL;
+    if (c->pool) return fail(c, LBVE_ESTATE, "a pool member cannot be restored");
+    if (!buf || bytes < sizeof(CkptHeader)) return fail(c, LBVE_EINVAL, "checkpoint buffer missing or too small");
+    CkptHeader h;
+    std::memcpy(&h, buf, sizeof h);
+    if (std::memcmp(h.magic, "LBVECKP1", 8) != 0) return fail(c, LBVE_EINVAL, "not a checkpoint record");
+    if (h.nx != c->p.nx || h.ny != c->p.ny || h.nz != c->p.nz || h.pdf_prec != c->p.pdf_prec ||
+        h.np != c->d.g.np || h.pdf_bytes != c->kt->pdf_bytes || h.real_bytes != c->kt->real_bytes)
+        return fail(c, LBVE_EINVAL, "checkpoint of a different grid or precision");
+    if (h.nparts != c->nparts) return fail(c, LBVE_EINVAL, "checkpoint has a different number of particles");
+    if (bytes < ckpt_bytes(c) || h.t < 0 || (h.cur & ~1) || (h.ucur & ~1))
+        return fail(c, LBVE_EINVAL, "checkpoint record truncated or inconsistent");
+    const long long np = c->d.g.np, n = c->d.g.n;
+    const size_t fb = (size_t)Q * np * c->kt->pdf_bytes, tb = (size_t)6 * np * c->kt->real_bytes;
+    const char *in = (const char *)buf + sizeof h;
+    const uint8_t *flags = (const uint8_t *)(in + fb + tb);
+    // the static geometry (no-slip cells and wall classes) must be the context's own: its
+    // wall links were built from it; only fluid and particle cells may differ
+    {
+        std::vector<uint8_t> mine((size_t)n);
+        CK(cudaMemcpyAsync(mine.data(), c->d.flag, (size_t)n, cudaMemcpyDeviceToHost, c->stream), "read flags");
+        CK(cudaStreamSynchronize(c->stream), "read flags sync");
+        for (long long r = 0; r < n; ++r) {
+            const bool sa = mine[r] != FLAG_FLUID && mine[r] < FLAG_PART0;
+            const bool sb = flags[r] != FLAG_FLUID && flags[r] < FLAG_PART0;
+            if (sa != sb || (sa && mine[r] != flags[r]))
+                return fail(c, LBVE_EINVAL, "checkpoint geometry differs from the context's (cell " +
+                                                std::to_string(r) + ")");
+            if (flags[r] >= FLAG_PART0 && flags[r] - FLAG_PART0 >= c->nparts)
+                return fail(c, LBVE_EINVAL, "checkpoint flags name a particle the context does not have");
+        }
+    }
+    c->d.cur = h.cur;
+    c->d.ucur = h.ucur;
+    CK(cudaMemcpyAsync(c->d.f, in, fb, cudaMemcpyHostToDevice, c->stream), "restore pdfs");
+    CK(cudaMemcpyAsync(c->d.tau[c->d.cur], in + fb, tb, cudaMemcpyHostToDevice, c->stream), "restore stress");
+    CK(cudaMemcpyAsync(c->d.flag, flags, (size_t)n, cudaMemcpyHostToDevice, c->stream), "restore flags");
+    const char *rest = in + fb + tb + n;
+    std::vector<PartDev> parts((size_t)c->nparts);
+    if (c->nparts > 0) {
+        std::memcpy(parts.data(), rest, sizeof(PartDev) * c->nparts);
+        for (auto &P : parts) P.changed = 1;  // rebuild every particle's links below
+        CK(cudaMemcpyAsync(c->d.parts, parts.data(), sizeof(PartDev) * c->nparts, cudaMemcpyHostToDevice, c->stream),
+           "restore particles");
+    }
+    rest += sizeof(PartDev) * c->nparts;
+    CK(cudaMemcpyAsync(c->pdiag, rest, sizeof(double) * 8, cudaMemcpyHostToDevice, c->stream), "restore diag");
+    rest += sizeof(double) * 8;
+    CK(cudaMemcpyAsync(c->body_F, rest, sizeof(double) * 256 * 3, cudaMemcpyHostToDevice, c->stream),
+       "restore forces");
+    CK(c->kt->build_mask(c->d, 0, 0, 0, c->p.nx, c->p.ny, c->p.nz, c->stream), "neighbour masks");
+    if (c->nparts > 0)
+        CK(c->kt->particle_links(c->d, c->nparts, c->links, c->seg_begin, c->seg_count, (int)c->wall_seg_begin.size(),
+                                 c->part_cap, c->stream),
+           "particle links");
+    CK(cudaStreamSynchronize(c->stream), "restore sync");
+    for (int p = 0; p < c->nparts; ++p) {
+        c->parts_host[p] = parts[p];
+        c->parts_host[p].changed = 0;
+    }
+    c->t = h.t;
+    clear_unstable(c);
+    return LBVE_OK;
+}
+
 // z-planes per block of the fused kernel: enough blocks for several waves over the
 // SMs, at least 8 planes so the two recomputed halo planes stay a small overhead.
 int fused_zchunk(const lbve_ctx *c) {
@@ -873,6 +1042,8 @@ lbve_status lbve_step(lbve_ctx *c, int nsteps) {
     if (!c) return LBVE_EINVAL;
     if (nsteps < 0) return fail(c, LBVE_EINVAL, "nsteps must be >= 0");
     if (c->pool) return fail(c, LBVE_ESTATE, "a pool member advances through lbve_pool_step");
+    if (c->phase_pending) return fail(c, LBVE_ESTATE, "a stream-collide of lbve_step_phase awaits its stress update");
+    if (unstable(c)) return fail(c, LBVE_EUNSTABLE, unstable_message(c));
     if (use_fused(c, nsteps)) {
         // stream-collide of the first step, fused (stress of step t-1 + stream-collide of
         // step t) for the others, stress update of the last step
@@ -912,6 +1083,7 @@ lbve_status lbve_step(lbve_ctx *c, int nsteps) {
         CK(timed_begin(c, LBVE_KT_LB), "timing");
         CK(c->kt->lb(c->d, parity, c->stream), "lb kernel");
         CK(timed_end(c), "timing");
+        c->last_lb_parity = parity;
         CK(timed_begin(c, LBVE_KT_FV), "timing");
         CK(c->kt->fv(c->d, c->stream), "fv kernel");
         CK(timed_end(c), "timing");
@@ -929,6 +1101,86 @@ lbve_status lbve_step(lbve_ctx *c, int nsteps) {
         c->t++;
         if (c->ev_used >= 4096) CK(harvest_times(c), "timing harvest");
     }
+    return LBVE_OK;
+}
+
+// ---------------------------------------------------------------------------------
+// z-slab decomposition of one domain (halo exchange by the caller)
+// ---------------------------------------------------------------------------------
+lbve_status lbve_set_z_range(lbve_ctx *c, int z_lo, int z_hi, int z_origin) {
+    if (!c) return LBVE_EINVAL;
+    if (c->geometry_set || c->nparts > 0) return fail(c, LBVE_ESTATE, "the z range is set before lbve_set_geometry");
+    if (c->pool) return fail(c, LBVE_ESTATE, "a pool member cannot become a z-slab");
+    if (c->p.periodic[2]) return fail(c, LBVE_EINVAL, "a z-slab is not periodic in z: its ghost planes hold the neighbours");
+    if (!(z_lo >= 1 && z_lo < z_hi && z_hi <= c->p.nz - 1))
+        return fail(c, LBVE_EINVAL, "the computed planes need one ghost plane on each side: 1 <= z_lo < z_hi <= nz - 1");
+    if (c->p.schedule == LBVE_SCHED_FUSED) return fail(c, LBVE_EINVAL, "z-slabs run on the split schedule");
+    if (z_origin < 0) return fail(c, LBVE_EINVAL, "z_origin must be >= 0");
+    c->d.zlo = z_lo;
+    c->d.zhi = z_hi;
+    // global index of local cell r: r + (z_origin - z_lo) nx ny (modulo 2^32, as the keys)
+    c->d.key_base = (unsigned)((long long)(z_origin - z_lo) * c->p.nx * c->p.ny);
+    return LBVE_OK;
+}
+
+lbve_status lbve_step_phase(lbve_ctx *c, int phase) {
+    if (!c) return LBVE_EINVAL;
+    if (c->pool) return fail(c, LBVE_ESTATE, "a pool member advances through lbve_pool_step");
+    if (phase == 0) {
+        if (c->phase_pending) return fail(c, LBVE_ESTATE, "phase 0 twice: the stress update of the last one is missing");
+        if (unstable(c)) return fail(c, LBVE_EUNSTABLE, unstable_message(c));
+        const int parity = (int)(c->t & 1);
+        c->d.step = (unsigned)c->t;
+        if (c->nbody > 0) {
+            CK(c->kt->momentum_exchange(c->d, parity, c->links, c->seg_begin, c->seg_count, c->nbody, c->max_seg_len,
+                                        c->contrib, c->stream),
+               "momentum exchange");
+            CK(body_sums(c, c->d.parts, c->stream), "body sums");
+        }
+        CK(c->kt->lb(c->d, parity, c->stream), "lb kernel");
+        c->last_lb_parity = parity;
+        c->phase_pending = true;
+        return LBVE_OK;
+    }
+    if (phase == 1) {
+        if (!c->phase_pending) return fail(c, LBVE_ESTATE, "phase 1 without the stream-collide of phase 0");
+        CK(c->kt->fv(c->d, c->stream), "fv kernel");
+        c->d.cur ^= 1;
+        c->t++;
+        c->phase_pending = false;
+        return LBVE_OK;
+    }
+    return fail(c, LBVE_EINVAL, "phase must be 0 or 1");
+}
+
+size_t lbve_halo_bytes(const lbve_ctx *c, int what) {
+    if (!c || what < LBVE_HALO_F || what > LBVE_HALO_TAU) return 0;
+    const size_t plane = (size_t)c->p.nx * (size_t)c->p.ny;
+    const size_t values = what == LBVE_HALO_F ? 5 : (what == LBVE_HALO_U ? 3 : 6);  // PDFs crossing a face, u, tau
+    return plane * values * (what == LBVE_HALO_F ? c->kt->pdf_bytes : c->kt->real_bytes);
+}
+
+static lbve_status halo_check(lbve_ctx *c, int what, int side, const void *buf) {
+    if (c->d.zhi <= 0) return fail(c, LBVE_ESTATE, "not a z-slab (lbve_set_z_range)");
+    if (what < LBVE_HALO_F || what > LBVE_HALO_TAU) return fail(c, LBVE_EINVAL, "unknown halo field");
+    if (side != 0 && side != 1) return fail(c, LBVE_EINVAL, "side must be 0 (low z) or 1 (high z)");
+    if (!buf) return fail(c, LBVE_EINVAL, "halo buffer is NULL");
+    return LBVE_OK;
+}
+
+lbve_status lbve_halo_pack(lbve_ctx *c, int what, int side, void *dev_buf) {
+    if (!c) return LBVE_EINVAL;
+    lbve_status s = halo_check(c, what, side, dev_buf);
+    if (s != LBVE_OK) return s;
+    CK(c->kt->halo_pack(c->d, what, side, c->last_lb_parity, dev_buf, c->stream), "halo pack");
+    return LBVE_OK;
+}
+
+lbve_status lbve_halo_unpack(lbve_ctx *c, int what, int side, const void *dev_buf) {
+    if (!c) return LBVE_EINVAL;
+    lbve_status s = halo_check(c, what, side, dev_buf);
+    if (s != LBVE_OK) return s;
+    CK(c->kt->halo_unpack(c->d, what, side, c->last_lb_parity, dev_buf, c->stream), "halo unpack");
     return LBVE_OK;
 }
 
@@ -1004,6 +1256,7 @@ lbve_status lbve_write_pdfs(lbve_ctx *c, const double *f) {
     CK(c->kt->pdfs_io(c->d, (int)(c->t & 1), d, 1, c->stream), "pdf write kernel");
     CK(cudaStreamSynchronize(c->stream), "pdf sync");
     dev_free(c, d);
+    clear_unstable(c);
     return LBVE_OK;
 }
 
@@ -1121,8 +1374,11 @@ long long lbve_time(const lbve_ctx *c) { return c ? c->t : -1; }
 lbve_status lbve_synchronize(lbve_ctx *c) {
     if (!c) return LBVE_EINVAL;
     CK(cudaStreamSynchronize(c->stream), "synchronize");
+    if (unstable(c)) return fail(c, LBVE_EUNSTABLE, unstable_message(c));
     return LBVE_OK;
 }
+
+int lbve_is_unstable(const lbve_ctx *c) { return c ? (unstable(c) ? 1 : 0) : -1; }
 
 const char *lbve_last_error(const lbve_ctx *c) { return c ? c->err.c_str() : g_create_error.c_str(); }
 
@@ -1415,6 +1671,8 @@ lbve_status lbve_pool_admit(lbve_pool *P, lbve_ctx *c) {
     if (c->pool) return pfail(P, LBVE_ESTATE, "context already belongs to a pool");
     if (c->p.pdf_prec != P->prec) return pfail(P, LBVE_ESTATE, "precision differs from the pool's");
     if (c->stream != P->stream) return pfail(P, LBVE_ESTATE, "stream differs from the pool's");
+    if (c->p.fene_L2 > 0.0) return pfail(P, LBVE_ESTATE, "FENE-P solves advance through lbve_step only");
+    if (c->d.zhi > 0) return pfail(P, LBVE_ESTATE, "z-slabs advance through lbve_step / lbve_step_phase only");
     const size_t b = lbve_device_bytes(&c->p);
     if (P->in_use + b > P->budget) return pfail(P, LBVE_ENOMEM, "device-memory budget exhausted");
     if (c->lb_tx == 0 && c->fv_tx == 0) tuned_tiles(P->prec, c->p.nx, c->lb_tx, c->fv_tx);
@@ -1445,6 +1703,10 @@ lbve_status lbve_pool_step(lbve_pool *P, int nsteps) {
     if (!P) return LBVE_EINVAL;
     if (nsteps < 0) return pfail(P, LBVE_EINVAL, "nsteps must be >= 0");
     if (nsteps == 0 || P->members.empty()) return LBVE_OK;
+    for (size_t k = 0; k < P->members.size(); ++k)
+        if (unstable(P->members[k]))
+            return pfail(P, LBVE_EUNSTABLE, "member " + std::to_string(k) + " is unstable (" +
+                                                unstable_message(P->members[k]) + "); remove it to continue");
     if (P->dirty) {
         lbve_status s = build_entries(P);
         if (s != LBVE_OK) return s;

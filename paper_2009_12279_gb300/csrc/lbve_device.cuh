@@ -73,7 +73,6 @@ struct Store<double> {
     static constexpr bool keyed = false;
     __device__ static __forceinline__ double ld(const double *p, double) { return *p; }
     __device__ static __forceinline__ void st(double *p, double v, double) { *p = v; }
-    __device__ static __forceinline__ void st(double *p, double v, double, uint32_t) { *p = v; }
 };
 template <>
 struct Store<float> {
@@ -83,62 +82,66 @@ struct Store<float> {
     // FP32 keeps its exponent range: stored unscaled (the scale argument is 1)
     __device__ static __forceinline__ float ld(const float *p, float) { return *p; }
     __device__ static __forceinline__ void st(float *p, float v, float) { *p = v; }
-    __device__ static __forceinline__ void st(float *p, float v, float, uint32_t) { *p = v; }
 };
-#ifndef LBVE_F16_STOCHASTIC
-#define LBVE_F16_STOCHASTIC 1
-#endif
+// The 16-bit modes round the stream-collide's stores stochastically: with 8 (BF16) or 11
+// (FP16) significant bits, the per-step change of a slowly evolving flow can be below half
+// a unit of the stored deviation, and round-to-nearest would drop it every step (the flow
+// stalls).  Stochastic rounding rounds up with probability equal to the dropped fraction
+// (unbiased).  Blackwell converts two FP32 values at once with it (cvt.rs, one instruction
+// per pair): the first value goes to the high half of the result, rounded with the high
+// 16 of the 32 random bits, the second to the low half with the low 16.  The random bits
+// come from a counter-based hash of (step, cell, direction), so results are deterministic
+// and the same for a solve alone and in a pool.  round2 returns the pair; store16 writes
+// one half.
 template <>
 struct Store<__half> {
     using R = float;
     static constexpr bool shifted = true;
-    static constexpr bool keyed = LBVE_F16_STOCHASTIC;
+    static constexpr bool keyed = true;
     __device__ static __forceinline__ float ld(const __half *p, float inv) { return __half2float(*p) * inv; }
     __device__ static __forceinline__ void st(__half *p, float v, float sc) { *p = __float2half_rn(v * sc); }
-    // Stochastic rounding, as for BF16 below: 13 hashed bits (the float bits a normal half
-    // drops) are added before a round-toward-zero conversion.  In the half's subnormal
-    // range the conversion drops more bits than that and the rounding there leans
-    // towards zero.
-    __device__ static __forceinline__ void st(__half *p, float v, float sc, uint32_t key) {
-#if LBVE_F16_STOCHASTIC
-        const float x = v * sc;
-        const uint32_t b = __float_as_uint(x);
-        const uint32_t h = ((b ^ key) * 0x9E3779B1u) >> 19;  // high 13 bits of a multiplicative hash
-        const bool finite = (b & 0x7F800000u) != 0x7F800000u;
-        *p = finite ? __float2half_rz(__uint_as_float(b + h)) : __float2half_rn(x);
-#else
-        st(p, v, sc);
-#endif
+    __device__ static __forceinline__ uint32_t round2(float a, float b, float sc, uint32_t rbits) {
+        uint32_t d;
+        asm("cvt.rs.f16x2.f32 %0, %1, %2, %3;" : "=r"(d) : "f"(a * sc), "f"(b * sc), "r"(rbits));
+        return d;
+    }
+    __device__ static __forceinline__ void store16(__half *p, uint32_t bits) {
+        *reinterpret_cast<unsigned short *>(p) = (unsigned short)bits;
     }
 };
-#ifndef LBVE_BF16_STOCHASTIC
-#define LBVE_BF16_STOCHASTIC 1
-#endif
 template <>
 struct Store<__nv_bfloat16> {
     using R = float;
     static constexpr bool shifted = true;
-    static constexpr bool keyed = LBVE_BF16_STOCHASTIC;  // stores take a rounding key
+    static constexpr bool keyed = true;
     // BF16 has the FP32 exponent range: stored unscaled (the scale argument is 1)
     __device__ static __forceinline__ float ld(const __nv_bfloat16 *p, float) { return __bfloat162float(*p); }
     __device__ static __forceinline__ void st(__nv_bfloat16 *p, float v, float) { *p = __float2bfloat16_rn(v); }
-    // Stochastic rounding.  With 8 significant bits, the per-step change of a slowly
-    // accelerating flow can be below half a unit of the stored deviation, and
-    // round-to-nearest then drops it every step.  Adding 16 uniform bits below the kept
-    // ones before truncating rounds up with probability equal to the dropped fraction
-    // (unbiased).  The bits hash a key of (step, cell, direction) with the value, so the
-    // result is deterministic and the same for a solve alone and in a pool.
-    __device__ static __forceinline__ void st(__nv_bfloat16 *p, float v, float, uint32_t key) {
-#if LBVE_BF16_STOCHASTIC
-        const uint32_t b = __float_as_uint(v);
-        const uint32_t h = ((b ^ key) * 0x9E3779B1u) >> 16;  // high half of a multiplicative hash
-        const bool finite = (b & 0x7F800000u) != 0x7F800000u;
-        *p = finite ? __ushort_as_bfloat16((unsigned short)((b + h) >> 16)) : __float2bfloat16_rn(v);
-#else
-        *p = __float2bfloat16_rn(v);
-#endif
+    __device__ static __forceinline__ uint32_t round2(float a, float b, float, uint32_t rbits) {
+        uint32_t d;
+        asm("cvt.rs.bf16x2.f32 %0, %1, %2, %3;" : "=r"(d) : "f"(a), "f"(b), "r"(rbits));
+        return d;
+    }
+    __device__ static __forceinline__ void store16(__nv_bfloat16 *p, uint32_t bits) {
+        *reinterpret_cast<unsigned short *>(p) = (unsigned short)bits;
     }
 };
+
+// Counter-based random bits: the 32-bit finaliser of MurmurHash3 (A. Appleby) over a cell
+// and step key, then per pair of directions a Weyl offset and one xor-shift-multiply round.
+__device__ __forceinline__ uint32_t fmix32(uint32_t x) {
+    x ^= x >> 16;
+    x *= 0x85EBCA6Bu;
+    x ^= x >> 13;
+    x *= 0xC2B2AE35u;
+    x ^= x >> 16;
+    return x;
+}
+__device__ __forceinline__ uint32_t pair_bits(uint32_t h, int p) {
+    uint32_t x = h + (uint32_t)p * 0x9E3779B9u;
+    x ^= x >> 15;
+    return x * 0x2C1B3C6Du;
+}
 
 // Coordinates of one cell and its periodically wrapped neighbours; cell indices are
 // 32-bit (grids are limited to 2^31 cells).
@@ -263,10 +266,53 @@ __device__ __forceinline__ void polymer_force_core(const R (&tr)[6], uint32_t ma
     }
 }
 
-// Same with the stress read from global memory.
+// FENE-P closure (the conformation tensor A in the stress arrays): the stress component c
+// of a cell, tau_c = (eta_p / lambda)(f A_c - delta_c), f = 1 / (1 - tr A / L^2).
 template <class R>
-__device__ __forceinline__ void polymer_force(const Geo &g, const Cell &cl, unsigned r, uint32_t mask,
-                                              const R *__restrict__ tau, R Fp[3]) {
+__device__ __forceinline__ R fene_factor(const Phys<R> &ph, R a0, R a1, R a2) {
+    return R(1) / (R(1) - ((a0 + a1) + a2) / ph.fene_L2);
+}
+template <class R>
+__device__ __forceinline__ R fene_component(const Phys<R> &ph, R f, R a, int c) {
+    return c < 3 ? ph.ep_l * (f * a - R(1)) : ph.ep_l * (f * a);
+}
+
+// Eq. (force) as polymer_force_core, with the stress of each cell computed from its
+// conformation tensor (FENE-P).  tn(l, c) returns component c of the face-l neighbour's A;
+// besides the face's row it reads the neighbour's diagonal for the trace.
+template <class R, class TauNb>
+__device__ __forceinline__ void polymer_force_core_fene(const R (&tr)[6], uint32_t mask, const TauNb &tn,
+                                                        const Phys<R> &ph, R Fp[3]) {
+    const R fr = fene_factor<R>(ph, tr[0], tr[1], tr[2]);
+    R ts[6];
+#pragma unroll
+    for (int c = 0; c < 6; ++c) ts[c] = fene_component<R>(ph, fr, tr[c], c);
+    Fp[0] = R(0);
+    Fp[1] = R(0);
+    Fp[2] = R(0);
+#pragma unroll
+    for (int l = 0; l < 6; ++l) {
+        const int k = l >> 1;
+        const int s = (l & 1) ? -1 : 1;
+        const bool fl = !nb_solid(mask, l + 1);
+        R fn = R(0);
+        if (fl) fn = fene_factor<R>(ph, tn(l, 0), tn(l, 1), tn(l, 2));
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+            const int c = comp(k, j);
+            const R tf = fl ? R(0.5) * (ts[c] + fene_component<R>(ph, fn, tn(l, c), c)) : ts[c];
+            if (s > 0)
+                Fp[j] = Fp[j] + tf;
+            else
+                Fp[j] = Fp[j] - tf;
+        }
+    }
+}
+
+// Same with the stress read from global memory (the FENE-P form when ph.fene).
+template <class R>
+__device__ __forceinline__ void polymer_force(const Geo &g, const Phys<R> &ph, const Cell &cl, unsigned r,
+                                              uint32_t mask, const R *__restrict__ tau, R Fp[3]) {
     const size_t np = (size_t)g.np;
     R tr[6];
 #pragma unroll
@@ -275,7 +321,17 @@ __device__ __forceinline__ void polymer_force(const Geo &g, const Cell &cl, unsi
         const int k = l >> 1, s = (l & 1) ? -1 : 1;
         return tau[c * np + cl.idx(k == 0 ? s : 0, k == 1 ? s : 0, k == 2 ? s : 0)];
     };
-    polymer_force_core<R>(tr, mask, tn, Fp);
+    if (ph.fene)
+        polymer_force_core_fene<R>(tr, mask, tn, ph, Fp);
+    else
+        polymer_force_core<R>(tr, mask, tn, Fp);
+}
+
+// Stress of a cell's stored tensor (itself, or the FENE-P stress of a conformation).
+template <class R>
+__device__ __forceinline__ R stored_to_stress(const Phys<R> &ph, const R (&a)[6], int c) {
+    if (!ph.fene) return a[c];
+    return fene_component<R>(ph, fene_factor<R>(ph, a[0], a[1], a[2]), a[c], c);
 }
 
 // Macroscopic moments, Eq. (macroscopic-velocity).  FP64 mode sums in direction order;
@@ -353,9 +409,12 @@ __device__ __forceinline__ R cdot(int i, const R v[3]) {
 // sum of the relaxed momentum differ from rho u by a fixed relative ~3e-8 every step: a
 // systematic momentum drift that, in a flow accelerating from rest, grows linearly in time
 // (relative error 1.1e-5 after 1000 steps of the config-1 channel, against 1.3e-7 in this form).
+// Returns true when the cell is unstable: rho <= 0, |u|^2 >= 1/3 (the lattice sound speed
+// squared) or a NaN in either (comparisons with a NaN are false).
 template <class R, bool SH>
-__device__ __forceinline__ void collide(R (&f)[Q], R rho, R drho, const R u[3], const R F[3], const Phys<R> &ph) {
+__device__ __forceinline__ bool collide(R (&f)[Q], R rho, R drho, const R u[3], const R F[3], const Phys<R> &ph) {
     const R usq = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
+    const bool unstable = !(rho > R(0)) || !(usq < R(1.0 / 3.0));
     const R uF = u[0] * F[0] + u[1] * F[1] + u[2] * F[2];
     const R wp = ph.omega_p, wm = ph.omega_m;
     if constexpr (!SH) {
@@ -415,6 +474,7 @@ __device__ __forceinline__ void collide(R (&f)[Q], R rho, R drho, const R u[3], 
             f[ip] = fo;
         }
     }
+    return unstable;
 }
 
 // Finite-volume stress update of one fluid cell (Sec. "Discretization", "Stability
@@ -514,7 +574,13 @@ __device__ __forceinline__ void fv_core(const Phys<R> &ph, const R (&tr)[6], con
             for (int k = 0; k < 3; ++k) a = a + tr[comp(i, k)] * G[k][j];
 #pragma unroll
             for (int k = 0; k < 3; ++k) b = b + tr[comp(k, j)] * G[k][i];
-            S = a + b + ph.ep_l * (G[i][j] + G[j][i]) - ph.inv_l * tr[c];
+            if (VAR && ph.fene) {
+                // FENE-P conformation: A.grad u + (A.grad u)^T - (f A - I) / lambda
+                const R fA = fene_factor<R>(ph, tr[0], tr[1], tr[2]);
+                S = a + b - ph.inv_l * (c < 3 ? fA * tr[c] - R(1) : fA * tr[c]);
+            } else {
+                S = a + b + ph.ep_l * (G[i][j] + G[j][i]) - ph.inv_l * tr[c];
+            }
         }
         if (VAR && ph.divu_on) S = S + tr[c] * ((G[0][0] + G[1][1]) + G[2][2]);
         if (VAR && ph.src_on && ph.gk != R(0)) {

@@ -48,6 +48,9 @@ struct KArgs {
     const uint32_t *mask;
     const PartDev *parts;
     unsigned step;  // index of the step being performed (rounding keys of keyed stores)
+    unsigned *bad;  // instability flag (mapped host word) or nullptr
+    int zlo, zhi;   // planes the step kernels compute
+    unsigned key_base;  // added to the cell index in rounding keys (a z-slab: its global offset)
     // per-direction / per-component bases (f + i np, tau + c np, u_out + k np), so that an
     // address is one multiply-add of a 32-bit cell index; set by link_dirs
     S *fq[Q];
@@ -114,25 +117,55 @@ __device__ __forceinline__ void store_pdfs(const KArgs<S> &a, const Cell &cl, un
     const size_t np = (size_t)a.g.np;
     const R sc = a.ph.scale;
     const bool moving = mask & MASK_MOVING;  // else every solid neighbour is a resting no-slip wall
-    // rounding key of (step, cell, direction) for keyed stores (0 for the others)
-    const uint32_t kb = Store<S>::keyed ? (r * 0x9E3779B1u) ^ (a.step * 0x85EBCA6Bu) : 0u;
-#define LBVE_KEY(i) (kb + (uint32_t)(i) * 0x27D4EB2Fu)
-    Store<S>::st(a.fq[0] + r, fs[0], sc, LBVE_KEY(0));
+    if constexpr (Store<S>::keyed) {
+        // 16-bit storage: the pairs (i, -i) round together (stochastically, see Store); a
+        // bounce from a resting wall stores the very bits of the normal store (one of the
+        // two copies is never read), a moving-wall bounce rounds its own value
+        const uint32_t h = fmix32((r + a.key_base) ^ (a.step * 0x9E3779B9u));
+        const uint32_t d0 = Store<S>::round2(fs[0], fs[0], sc, pair_bits(h, 0));
+        Store<S>::store16(a.fq[0] + r, d0);
+        const bool uniform = !__any_sync(__activemask(), moving);
+#pragma unroll
+        for (int i = 1; i < Q; i += 2) {
+            const uint32_t d = Store<S>::round2(fs[i], fs[i + 1], sc, pair_bits(h, (i + 1) >> 1));
+#pragma unroll
+            for (int q = 0; q < 2; ++q) {
+                const int j = i + q;
+                const uint32_t bits = q == 0 ? d >> 16 : d;
+                const unsigned nb = cl.idx(cx(j), cy(j), cz(j));
+                Store<S>::store16(PAR == 0 ? a.fq[copp(j)] + r : a.fq[j] + nb, bits);
+                if (!nb_solid(mask, j)) continue;
+                S *dst = PAR == 0 ? a.fq[j] + nb : a.fq[copp(j)] + r;
+                if (uniform) {  // no lane of the warp next to a moving boundary
+                    Store<S>::store16(dst, bits);
+                } else {
+                    const int fl = moving ? (int)a.flag[nb] : FLAG_NOSLIP;
+                    const R X = fl == FLAG_NOSLIP ? R(0)
+                                                  : moving_wall_term<R>(a.g, a.ph, a.parts, fl, cl.X(cx(j)), cl.Y(cy(j)),
+                                                                        cl.Z(cz(j)), j, rho);
+                    // a boundary at rest (X exactly zero) bounces the normal store's bits
+                    Store<S>::store16(dst, X == R(0) ? bits
+                                                     : Store<S>::round2(fs[j] - X, fs[j] - X, sc, pair_bits(h, Q + j)));
+                }
+            }
+        }
+        return;
+    }
+    Store<S>::st(a.fq[0] + r, fs[0], sc);
     if (!__any_sync(__activemask(), moving)) {
         // no lane of the warp next to a moving boundary: bounce-back is a predicated store
 #pragma unroll
         for (int i = 1; i < Q; ++i) {
             const unsigned nb = cl.idx(cx(i), cy(i), cz(i));
-            Store<S>::st(PAR == 0 ? a.fq[copp(i)] + r : a.fq[i] + nb, fs[i], sc, LBVE_KEY(i));
-            if (nb_solid(mask, i))
-                Store<S>::st(PAR == 0 ? a.fq[i] + nb : a.fq[copp(i)] + r, fs[i], sc, LBVE_KEY(Q + i));
+            Store<S>::st(PAR == 0 ? a.fq[copp(i)] + r : a.fq[i] + nb, fs[i], sc);
+            if (nb_solid(mask, i)) Store<S>::st(PAR == 0 ? a.fq[i] + nb : a.fq[copp(i)] + r, fs[i], sc);
         }
         return;
     }
 #pragma unroll
     for (int i = 1; i < Q; ++i) {
         const unsigned nb = cl.idx(cx(i), cy(i), cz(i));
-        Store<S>::st(PAR == 0 ? a.fq[copp(i)] + r : a.fq[i] + nb, fs[i], sc, LBVE_KEY(i));
+        Store<S>::st(PAR == 0 ? a.fq[copp(i)] + r : a.fq[i] + nb, fs[i], sc);
         if (nb_solid(mask, i)) {
             R X = R(0);
             if (moving) {
@@ -140,31 +173,36 @@ __device__ __forceinline__ void store_pdfs(const KArgs<S> &a, const Cell &cl, un
                 if (fl != FLAG_NOSLIP)
                     X = moving_wall_term<R>(a.g, a.ph, a.parts, fl, cl.X(cx(i)), cl.Y(cy(i)), cl.Z(cz(i)), i, rho);
             }
-            Store<S>::st(PAR == 0 ? a.fq[i] + nb : a.fq[copp(i)] + r, fs[i] - X, sc, LBVE_KEY(Q + i));
+            Store<S>::st(PAR == 0 ? a.fq[i] + nb : a.fq[copp(i)] + r, fs[i] - X, sc);
         }
     }
-#undef LBVE_KEY
 }
 
 // LB half of the step for one fluid cell, given its own stress tr and an accessor tn for
 // its face neighbours' stress (tau^t): F = g + F^p, moments, u^t written out, TRT
 // collision with forcing, AA streaming with bounce-back.
-template <class S, int PAR, class TauNb>
+template <class S, int PAR, bool FENE = false, class TauNb>
 __device__ __forceinline__ void lb_core_f(const KArgs<S> &a, const Cell &cl, unsigned r, uint32_t mask,
                                           const typename Store<S>::R (&tr)[6], const TauNb &tn,
                                           typename Store<S>::R (&f)[Q]) {
     using R = typename Store<S>::R;
     constexpr bool SH = Store<S>::shifted;
     R Fp[3], F[3], u[3], rho, drho;
-    polymer_force_core<R>(tr, mask, tn, Fp);
+    if constexpr (FENE)
+        polymer_force_core_fene<R>(tr, mask, tn, a.ph, Fp);
+    else
+        polymer_force_core<R>(tr, mask, tn, Fp);
 #pragma unroll
     for (int k = 0; k < 3; ++k) F[k] = a.ph.g[k] + Fp[k];
     moments<R, SH>(f, F, a.ph.rho0, rho, drho, u);
     const size_t np = (size_t)a.g.np;
 #pragma unroll
     for (int k = 0; k < 3; ++k) a.uq[k][r] = u[k];
-    collide<R, SH>(f, rho, drho, u, F, a.ph);
+    const bool bad = collide<R, SH>(f, rho, drho, u, F, a.ph);
     store_pdfs<S, PAR>(a, cl, r, mask, f, rho);
+    // instability (rho <= 0, |u| at or above the lattice sound speed, or a NaN): a rare
+    // store to the host-mapped flag
+    if (bad && a.bad != nullptr) *(volatile unsigned *)a.bad = 1u;
 }
 template <class S, int PAR, class TauNb>
 __device__ __forceinline__ void lb_core(const KArgs<S> &a, const Cell &cl, unsigned r, uint32_t mask,
@@ -213,7 +251,7 @@ __device__ __forceinline__ bool cell_of_thread(const Geo &g, int &x, int &y, int
 }
 
 // Stream-collide of the fluid cell (x, y, z) with the stress stencil read from global memory.
-template <class S, int PAR>
+template <class S, int PAR, bool FENE = false>
 __device__ __forceinline__ void lb_cell_at(const KArgs<S> &a, int x, int y, int z) {
     using R = typename Store<S>::R;
     const Cell cl(a.g, x, y, z);
@@ -230,14 +268,15 @@ __device__ __forceinline__ void lb_cell_at(const KArgs<S> &a, int x, int y, int 
         const int k = l >> 1, s = (l & 1) ? -1 : 1;
         return a.tq[c][cl.idx(k == 0 ? s : 0, k == 1 ? s : 0, k == 2 ? s : 0)];
     };
-    lb_core_f<S, PAR>(a, cl, r, m, tr, tn, f);
+    lb_core_f<S, PAR, FENE>(a, cl, r, m, tr, tn, f);
 }
 
-template <class S, int PAR>
+// FENE: the stress arrays hold FENE-P conformation tensors (see polymer_force_core_fene)
+template <class S, int PAR, bool FENE = false>
 __global__ void __launch_bounds__(128, lb_min_blocks<S, PAR>()) k_lb(KArgs<S> a) {
     int x, y, z;
     if (!cell_of_thread(a.g, x, y, z)) return;
-    lb_cell_at<S, PAR>(a, x, y, z);
+    lb_cell_at<S, PAR, FENE>(a, x, y, z + a.zlo);
 }
 
 template <class S>
@@ -573,8 +612,9 @@ struct FvSmemNb {
 };
 
 // Stress update of work item `item` (TX x TY tile, z-chunk) of one solve; VAR compiles in
-// the optional finite-volume variants.
-template <class S, int TX, bool VAR>
+// the optional finite-volume variants, ZR the restriction to planes [zlo, zhi) of a
+// z-slab (a separate build: the plain one keeps its register budget).
+template <class S, int TX, bool VAR, bool ZR = false>
 __device__ __forceinline__ void fv_tile(const KArgs<S> &a, FvSmem<typename Store<S>::R, FvTile<TX>::HN> &sm, int item,
                                         int zchunk) {
     using R = typename Store<S>::R;
@@ -585,7 +625,8 @@ __device__ __forceinline__ void fv_tile(const KArgs<S> &a, FvSmem<typename Store
     const int tiles_x = (a.g.nx + TX - 1) / TX, tiles_y = (a.g.ny + TY - 1) / TY;
     const int tx = item % tiles_x, ty = (item / tiles_x) % tiles_y, zc = item / (tiles_x * tiles_y);
     const int x0 = tx * TX, y0 = ty * TY;
-    const int z0 = zc * zchunk, z1 = min(a.g.nz, z0 + zchunk);
+    const int z0 = ZR ? a.zlo + zc * zchunk : zc * zchunk;
+    const int z1 = ZR ? min(a.zhi, z0 + zchunk) : min(a.g.nz, z0 + zchunk);
     const size_t np = (size_t)a.g.np;
     const unsigned nx = (unsigned)a.g.nx, nxy = (unsigned)a.g.nx * (unsigned)a.g.ny;
     int off[2];
@@ -666,12 +707,12 @@ __device__ __forceinline__ void fv_tile(const KArgs<S> &a, FvSmem<typename Store
     cp_async_wait_all();
 }
 
-template <class S, bool VAR>
+template <class S, bool VAR, bool ZR = false>
 __global__ void __launch_bounds__(FV_X * FV_Y, sizeof(typename Store<S>::R) == 8 ? 2 : LBVE_FV_MIN_BLOCKS) k_fv_tiled(KArgs<S> a, int zchunk) {
     using R = typename Store<S>::R;
     extern __shared__ __align__(16) unsigned char fv_smem_raw[];
     FvSmem<R> &sm = *reinterpret_cast<FvSmem<R> *>(fv_smem_raw);
-    fv_tile<S, FV_X, VAR>(a, sm, blockIdx.x, zchunk);
+    fv_tile<S, FV_X, VAR, ZR>(a, sm, blockIdx.x, zchunk);
 }
 
 // ---------------------------------------------------------------------------------
@@ -846,7 +887,7 @@ __device__ __forceinline__ void me_link(const KArgs<S> &a, long long code, doubl
     R f[Q];
     load_pdfs<S, PAR>(a, cl, r, f);
     R Fp[3], F[3], u[3], rho, drho;
-    polymer_force<R>(a.g, cl, r, a.mask[r], a.tau, Fp);
+    polymer_force<R>(a.g, a.ph, cl, r, a.mask[r], a.tau, Fp);
 #pragma unroll
     for (int k = 0; k < 3; ++k) F[k] = a.ph.g[k] + Fp[k];
     moments<R, SH>(f, F, a.ph.rho0, rho, drho, u);
@@ -1583,7 +1624,17 @@ __global__ void k_init(KArgs<S> a, const double *__restrict__ rho_in, const doub
         }
         Store<S>::st(a.f + (long long)i * a.g.np + r, (R)v, a.ph.scale);
     }
-    for (int c = 0; c < 6; ++c) tau_dst[c * a.g.np + r] = tau_in ? (R)tau_in[c * ld + k] : R(0);
+    double t6[6];
+    for (int c = 0; c < 6; ++c) t6[c] = tau_in ? tau_in[c * ld + k] : 0.0;
+    if (a.ph.fene) {
+        // FENE-P: the conformation of the given stress, A = (I + lambda tau / eta_p) / f with
+        // f = 1 + (3 + lambda tr tau / eta_p) / L^2
+        const double lam = (double)a.ph.lam, eta_p = (double)a.ph.eta_p;
+        const double s = 3.0 + lam * (t6[0] + t6[1] + t6[2]) / eta_p;
+        const double f = 1.0 + s / (double)a.ph.fene_L2;
+        for (int c = 0; c < 6; ++c) t6[c] = ((c < 3 ? 1.0 : 0.0) + lam * t6[c] / eta_p) / f;
+    }
+    for (int c = 0; c < 6; ++c) tau_dst[c * a.g.np + r] = (R)t6[c];
 }
 
 // rho, physical u and tau of the cells in z-planes z0.. (grid z extent), 0 in non-fluid
@@ -1609,15 +1660,20 @@ __global__ void k_read(KArgs<S> a, double *__restrict__ rho_out, double *__restr
     R f[Q];
     load_pdfs<S, PAR>(a, cl, r, f);
     R Fp[3], F[3], u[3], rho, drho;
-    polymer_force<R>(a.g, cl, r, a.mask[r], a.tau, Fp);
+    polymer_force<R>(a.g, a.ph, cl, r, a.mask[r], a.tau, Fp);
 #pragma unroll
     for (int j = 0; j < 3; ++j) F[j] = a.ph.g[j] + Fp[j];
     moments<R, SH>(f, F, a.ph.rho0, rho, drho, u);
     if (rho_out) rho_out[k] = SH ? (double)a.ph.rho0 + (double)drho : (double)rho;
     for (int j = 0; j < 3; ++j)
         if (u_out) u_out[j * ld + k] = (double)u[j];
-    for (int c = 0; c < 6; ++c)
-        if (tau_out) tau_out[c * ld + k] = (double)a.tau[c * a.g.np + r];
+    if (tau_out) {
+        R t6[6];
+#pragma unroll
+        for (int c = 0; c < 6; ++c) t6[c] = a.tau[c * a.g.np + r];
+#pragma unroll
+        for (int c = 0; c < 6; ++c) tau_out[c * ld + k] = (double)stored_to_stress<R>(a.ph, t6, c);
+    }
 }
 
 // PDFs of every cell to / from unshifted FP64 in the plain (pre-collision) layout.
@@ -1657,12 +1713,14 @@ __global__ void k_probe(KArgs<S> a, const long long *__restrict__ cells, int cou
     for (int j = 19; j < 29; ++j) o[j] = 0.0;
     if (a.flag[r] != FLAG_FLUID) return;
     R Fp[3], F[3], u[3], rho, drho;
-    polymer_force<R>(a.g, cl, r, a.mask[r], a.tau, Fp);
+    polymer_force<R>(a.g, a.ph, cl, r, a.mask[r], a.tau, Fp);
     for (int j = 0; j < 3; ++j) F[j] = a.ph.g[j] + Fp[j];
     moments<R, SH>(f, F, a.ph.rho0, rho, drho, u);
     o[19] = SH ? (double)a.ph.rho0 + (double)drho : (double)rho;
     for (int j = 0; j < 3; ++j) o[20 + j] = (double)u[j];
-    for (int c = 0; c < 6; ++c) o[23 + c] = (double)a.tau[c * a.g.np + r];
+    R t6[6];
+    for (int c = 0; c < 6; ++c) t6[c] = a.tau[c * a.g.np + r];
+    for (int c = 0; c < 6; ++c) o[23 + c] = (double)stored_to_stress<R>(a.ph, t6, c);
 }
 
 // Per-block FP64 partial sums over fluid cells: mass, momentum, count, bad-value flag.
@@ -1673,7 +1731,7 @@ __global__ void __launch_bounds__(256) k_reduce(KArgs<S> a, double *__restrict__
     if (x < a.g.nx) {
         const Cell cl(a.g, x, blockIdx.y, blockIdx.z);
         const unsigned r = cl.self();
-        if (a.flag[r] == FLAG_FLUID) {
+        if (a.flag[r] == FLAG_FLUID && (int)blockIdx.z >= a.zlo && (int)blockIdx.z < a.zhi) {
             typename Store<S>::R f[Q];
             load_pdfs<S, PAR>(a, cl, r, f);
             for (int i = 0; i < Q; ++i) {
@@ -1701,6 +1759,112 @@ __global__ void __launch_bounds__(256) k_reduce(KArgs<S> a, double *__restrict__
     if (threadIdx.x == 0) {
         const long long b = blockIdx.x + (long long)gridDim.x * (blockIdx.y + (long long)gridDim.y * blockIdx.z);
         for (int k = 0; k < 6; ++k) partial[b * 6 + k] = sh[k][0];
+    }
+}
+
+// ---------------------------------------------------------------------------------
+// z-slab decomposition: halo exchange between the slabs of one domain.  A slab computes
+// planes [zlo, zhi) and holds one ghost plane on each side (zlo - 1, zhi) mirroring the
+// neighbouring slab's boundary plane (its flags included).  Per step:
+//   after the stream-collide: u of the boundary planes -> the neighbours' ghost planes,
+//     and the 5 PDFs per cell that cross each face (below);
+//   after the stress update: tau of the boundary planes -> the neighbours' ghost planes.
+// The PDFs follow the in-place (AA) pattern.  D+ / D- are the directions with c_z = +1 /
+// -1 (5 each).  After an even step a fluid cell's slot -i holds its f*_i, which the next
+// odd step reads from the cell above (-i in D-, i moving up) or below: the boundary
+// plane's slots D- (high side) / D+ (low side) go into the neighbour's ghost plane, for
+// fluid ghost cells (a solid ghost cell's slots hold this slab's own bounced values).
+// After an odd step a fluid cell has written f*_i into slot i of r + c_i, in the ghost
+// plane for i crossing the face: the ghost plane's slots D+ (high side) / D- (low side)
+// go into the neighbour's boundary plane, where the source cell r - c_i is fluid (else
+// the slot holds that cell's own bounced value).
+// ---------------------------------------------------------------------------------
+__host__ __device__ constexpr int dir_zp(int k) { return k == 0 ? 5 : k == 1 ? 11 : k == 2 ? 14 : k == 3 ? 15 : 18; }
+__host__ __device__ constexpr int dir_zm(int k) { return k == 0 ? 6 : k == 1 ? 12 : k == 2 ? 13 : k == 3 ? 16 : 17; }
+
+__host__ __device__ constexpr int halo_values(int what) { return what == 0 ? 5 : (what == 1 ? 3 : 6); }
+
+// plane and slot set of a PDF pack (side: 0 low, 1 high; parity of the last stream-collide)
+__device__ __forceinline__ void halo_f_pack_plan(int side, int parity, int zlo, int zhi, int &z, bool &up) {
+    if (parity == 0) {
+        z = side ? zhi - 1 : zlo;
+        up = side == 0;  // low side sends D+, high side D-
+    } else {
+        z = side ? zhi : zlo - 1;
+        up = side == 1;  // from the ghost planes: high sends D+, low D-
+    }
+}
+
+template <class S>
+__global__ void k_halo_pack(KArgs<S> a, int what, int side, int parity, void *__restrict__ buf) {
+    using R = typename Store<S>::R;
+    const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y;
+    if (x >= a.g.nx) return;
+    const long long plane = (long long)a.g.nx * a.g.ny, p = x + (long long)a.g.nx * y;
+    const size_t np = (size_t)a.g.np;
+    if (what == 0) {
+        int z;
+        bool up;
+        halo_f_pack_plan(side, parity, a.zlo, a.zhi, z, up);
+        const unsigned r = (unsigned)(p + plane * z);
+        S *o = (S *)buf;
+#pragma unroll
+        for (int k = 0; k < 5; ++k) o[k * plane + p] = a.f[(up ? dir_zp(k) : dir_zm(k)) * np + r];
+    } else {
+        const int z = side ? a.zhi - 1 : a.zlo;
+        const unsigned r = (unsigned)(p + plane * z);
+        R *o = (R *)buf;
+        if (what == 1)
+            for (int j = 0; j < 3; ++j) o[j * plane + p] = a.u_out[j * np + r];
+        else
+            for (int c = 0; c < 6; ++c) o[c * plane + p] = a.tau[c * np + r];
+    }
+}
+
+template <class S>
+__global__ void k_halo_unpack(KArgs<S> a, int what, int side, int parity, const void *__restrict__ buf) {
+    using R = typename Store<S>::R;
+    const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y;
+    if (x >= a.g.nx) return;
+    const long long plane = (long long)a.g.nx * a.g.ny, p = x + (long long)a.g.nx * y;
+    const size_t np = (size_t)a.g.np;
+    if (what == 0) {
+        const S *in = (const S *)buf;
+        if (parity == 0) {
+            // into the ghost plane, for fluid ghost cells; the low side receives the lower
+            // slab's D-, the high side the upper slab's D+
+            const int z = side ? a.zhi : a.zlo - 1;
+            const unsigned r = (unsigned)(p + plane * z);
+            if (a.flag[r] != FLAG_FLUID) return;
+#pragma unroll
+            for (int k = 0; k < 5; ++k) a.f[(side ? dir_zp(k) : dir_zm(k)) * np + r] = in[k * plane + p];
+        } else {
+            // into the boundary plane, where the source cell r - c_i (in the ghost plane) is
+            // fluid: the low side receives D+ (moving up from the lower slab), the high
+            // side D- (moving down from the upper slab)
+            const int z = side ? a.zhi - 1 : a.zlo;
+            const unsigned r = (unsigned)(p + plane * z);
+            const Cell cl(a.g, x, y, z);
+            if (a.flag[r] != FLAG_FLUID) return;
+#pragma unroll
+            for (int k = 0; k < 5; ++k) {
+                const int i = side ? dir_zm(k) : dir_zp(k);
+                const int sx = -cx(i), sy = -cy(i);
+                const int xs = x + sx, ys = y + sy;
+                if ((xs < 0 || xs >= a.g.nx) && !a.g.per[0]) continue;
+                if ((ys < 0 || ys >= a.g.ny) && !a.g.per[1]) continue;
+                if (a.flag[cl.idx(sx, sy, -cz(i))] != FLAG_FLUID) continue;
+                a.f[i * np + r] = in[k * plane + p];
+            }
+        }
+    } else {
+        const int z = side ? a.zhi : a.zlo - 1;
+        const unsigned r = (unsigned)(p + plane * z);
+        const R *in = (const R *)buf;
+        if (what == 1)
+            for (int j = 0; j < 3; ++j) a.u_out[j * np + r] = in[j * plane + p];
+        else
+            for (int c = 0; c < 6; ++c) const_cast<R *>(a.tau)[c * np + r] = in[c * plane + p];
     }
 }
 

@@ -37,6 +37,9 @@ struct Phys {
     int ctu_on;   // face fluxes scaled by the transverse overlap of the displaced donor cell
     int divu_on;  // the tau div(u) source term
     R gk;         // alpha / eta_p of the Giesekus source term (0: Oldroyd-B)
+    int fene;     // FENE-P: the stress arrays hold the conformation tensor A
+    R fene_L2;    // its maximum extensibility L^2
+    R eta_p, lam; // polymer viscosity and relaxation time (stress <-> conformation)
     R wall_vel[MAX_WALL][3];
 };
 
@@ -77,6 +80,16 @@ struct DevState {
     int block_x;      // threads per block along x
     int fv_zchunk;    // z-planes per block of the stress kernel (0: by the SM count)
     unsigned step;    // index of the step the next stream-collide performs (low 32 bits)
+    // instability flag: a word of mapped page-locked host memory (its device address)
+    // that the stream-collide sets to 1 when a fluid cell has rho <= 0, |u|^2 >= 1/3
+    // (the lattice sound speed squared) or a NaN; nullptr: no check
+    unsigned *bad = nullptr;
+    // planes [zlo, zhi) that the step kernels compute (zhi 0: all); the planes outside are
+    // the ghost planes of a z-slab of a decomposed domain, filled by the halo exchange
+    int zlo = 0, zhi = 0;
+    // offset of this grid's cell indices in the decomposed domain's (rounding keys of the
+    // 16-bit stores use global cells, so a slab rounds as the undecomposed domain does)
+    unsigned key_base = 0;
 };
 
 struct KernelTable {
@@ -126,6 +139,11 @@ struct KernelTable {
     size_t part_entry_bytes;
     void (*fill_part_entry)(const DevState &, int parity0, const PartScratch &, void *entry);
     cudaError_t (*particle_phase_batched)(const void *entries, int n, int k, cudaStream_t);
+    // z-slab halo exchange: what 0 PDFs of the last stream-collide (its AA parity), 1 u,
+    // 2 tau; side 0 the low z side, 1 the high one; buf a device buffer of plane-major
+    // values (halo_values(what) per cell of an x-y plane, storage type for the PDFs)
+    cudaError_t (*halo_pack)(const DevState &, int what, int side, int parity, void *buf, cudaStream_t);
+    cudaError_t (*halo_unpack)(const DevState &, int what, int side, int parity, const void *buf, cudaStream_t);
 };
 
 // Bounding-box side used to size the per-particle scratch (cells within R + margin).

@@ -3,10 +3,30 @@
 #pragma once
 
 #include <algorithm>
+#include <atomic>
 
 #include "lbve_kernels.cuh"
 
 namespace lbve {
+
+// Dynamic shared-memory limit of a kernel raised once per device: the attribute is per
+// device, so the record is a bit per device ordinal (idempotent if two threads race).
+struct SmemAttrOnce {
+    std::atomic<unsigned long long> done[2] = {{0ull}, {0ull}};
+    template <class K>
+    cudaError_t ensure(K kernel, size_t bytes) {
+        int dev = 0;
+        cudaError_t e = cudaGetDevice(&dev);
+        if (e != cudaSuccess) return e;
+        if (dev < 0 || dev >= 128) return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+        const unsigned long long bit = 1ull << (dev & 63);
+        std::atomic<unsigned long long> &w = done[dev >> 6];
+        if (w.load(std::memory_order_acquire) & bit) return cudaSuccess;
+        e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+        if (e == cudaSuccess) w.fetch_or(bit, std::memory_order_acq_rel);
+        return e;
+    }
+};
 
 template <class R>
 inline Phys<R> convert_phys(const Phys<double> &p) {
@@ -27,6 +47,10 @@ inline Phys<R> convert_phys(const Phys<double> &p) {
     o.ctu_on = p.ctu_on;
     o.divu_on = p.divu_on;
     o.gk = (R)p.gk;
+    o.fene = p.fene;
+    o.fene_L2 = (R)p.fene_L2;
+    o.eta_p = (R)p.eta_p;
+    o.lam = (R)p.lam;
     for (int c = 0; c < MAX_WALL; ++c)
         for (int k = 0; k < 3; ++k) o.wall_vel[c][k] = (R)p.wall_vel[c][k];
     return o;
@@ -51,14 +75,19 @@ struct Launch {
         a.mask = d.mask;
         a.parts = d.parts;
         a.step = d.step;
+        a.bad = d.bad;
+        a.zlo = d.zlo;
+        a.zhi = d.zhi > 0 ? d.zhi : d.g.nz;
+        a.key_base = d.key_base;
         link_dirs<S>(a);
         return a;
     }
     // per-cell kernels: blocks of block_x x (128 / block_x) threads
     static dim3 block2(const DevState &d) { return dim3((unsigned)d.block_x, (unsigned)(128 / d.block_x)); }
+    static int zcount(const DevState &d) { return (d.zhi > 0 ? d.zhi : d.g.nz) - d.zlo; }
     static dim3 grid2(const DevState &d) {
         const dim3 b = block2(d);
-        return dim3((unsigned)((d.g.nx + b.x - 1) / b.x), (unsigned)((d.g.ny + b.y - 1) / b.y), (unsigned)d.g.nz);
+        return dim3((unsigned)((d.g.nx + b.x - 1) / b.x), (unsigned)((d.g.ny + b.y - 1) / b.y), (unsigned)zcount(d));
     }
     static dim3 grid3(const DevState &d) { return dim3((unsigned)((d.g.nx + d.block_x - 1) / d.block_x), d.g.ny, d.g.nz); }
 
@@ -72,39 +101,50 @@ struct Launch {
     }
     static cudaError_t lb(const DevState &d, int parity, cudaStream_t s) {
         KArgs<S> a = args(d);
-        if (parity == 0)
+        if (d.ph.fene) {  // the polymer force takes the stress of each cell's conformation
+            if (parity == 0)
+                k_lb<S, 0, true><<<grid2(d), block2(d), 0, s>>>(a);
+            else
+                k_lb<S, 1, true><<<grid2(d), block2(d), 0, s>>>(a);
+        } else if (parity == 0) {
             k_lb<S, 0><<<grid2(d), block2(d), 0, s>>>(a);
-        else
+        } else {
             k_lb<S, 1><<<grid2(d), block2(d), 0, s>>>(a);
+        }
         return cudaGetLastError();
     }
     // z-planes per block of the z-marching stress update (enough blocks for ~16 waves)
     static int fv_zchunk(const DevState &d) {
-        if (d.fv_zchunk > 0) return d.fv_zchunk < d.g.nz ? d.fv_zchunk : d.g.nz;
+        const int nz = zcount(d);
+        if (d.fv_zchunk > 0) return d.fv_zchunk < nz ? d.fv_zchunk : nz;
         const long long tiles = (long long)((d.g.nx + FV_X - 1) / FV_X) * ((d.g.ny + FV_Y - 1) / FV_Y);
         int dev = 0, sms = 148;
         if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
         const long long want = 16LL * LBVE_FV_MIN_BLOCKS * sms;  // ~16 waves of resident blocks
         const long long chunks = (want + tiles - 1) / tiles;
-        long long zc = (d.g.nz + chunks - 1) / chunks;
+        long long zc = (nz + chunks - 1) / chunks;
         if (zc < 16) zc = 16;
-        if (zc > d.g.nz) zc = d.g.nz;
+        if (zc > nz) zc = nz;
         return (int)zc;
     }
-    static bool fv_variant(const DevState &d) { return d.ph.ctu_on || d.ph.divu_on || d.ph.gk != 0.0; }
+    static bool fv_variant(const DevState &d) { return d.ph.ctu_on || d.ph.divu_on || d.ph.gk != 0.0 || d.ph.fene; }
     template <bool VAR>
     static cudaError_t fv_var(const DevState &d, cudaStream_t s) {
         KArgs<S> a = args(d);
         const int zc = fv_zchunk(d);
         const int tiles = ((d.g.nx + FV_X - 1) / FV_X) * ((d.g.ny + FV_Y - 1) / FV_Y);
-        const unsigned nblk = (unsigned)(tiles * ((d.g.nz + zc - 1) / zc));
+        const unsigned nblk = (unsigned)(tiles * ((zcount(d) + zc - 1) / zc));
         const size_t sm = sizeof(FvSmem<R>);
-        static bool configured = false;
-        if (!configured) {
-            cudaError_t e = cudaFuncSetAttribute(k_fv_tiled<S, VAR>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        if (d.zhi > 0) {  // a z-slab: planes [zlo, zhi) only
+            static SmemAttrOnce attr_zr;
+            cudaError_t e = attr_zr.ensure(k_fv_tiled<S, VAR, true>, sm);
             if (e != cudaSuccess) return e;
-            configured = true;
+            k_fv_tiled<S, VAR, true><<<nblk, FV_X * FV_Y, sm, s>>>(a, zc);
+            return cudaGetLastError();
         }
+        static SmemAttrOnce attr;
+        cudaError_t e = attr.ensure(k_fv_tiled<S, VAR>, sm);
+        if (e != cudaSuccess) return e;
         k_fv_tiled<S, VAR><<<nblk, FV_X * FV_Y, sm, s>>>(a, zc);
         return cudaGetLastError();
     }
@@ -129,6 +169,18 @@ struct Launch {
             else
                 k_momentum_exchange<S, 1><<<g, 128, 0, s>>>(a, links, seg_begin, seg_count, contrib);
         }
+        return cudaGetLastError();
+    }
+    static cudaError_t halo_pack(const DevState &d, int what, int side, int parity, void *buf, cudaStream_t s) {
+        KArgs<S> a = args(d);
+        k_halo_pack<S><<<dim3((unsigned)((d.g.nx + 127) / 128), (unsigned)d.g.ny), 128, 0, s>>>(a, what, side, parity, buf);
+        return cudaGetLastError();
+    }
+    static cudaError_t halo_unpack(const DevState &d, int what, int side, int parity, const void *buf,
+                                   cudaStream_t s) {
+        KArgs<S> a = args(d);
+        k_halo_unpack<S><<<dim3((unsigned)((d.g.nx + 127) / 128), (unsigned)d.g.ny), 128, 0, s>>>(a, what, side, parity,
+                                                                                                    buf);
         return cudaGetLastError();
     }
     static cudaError_t build_mask(const DevState &d, int lx, int ly, int lz, int ex, int ey, int ez, cudaStream_t s);
@@ -179,13 +231,9 @@ struct Launch {
         w.zchunk = zchunk;
         w.nzchunks = (d.g.nz + zchunk - 1) / zchunk;
         const size_t sm = sizeof(FusedSmem<R>);
-        static bool configured[2] = {false, false};
-        if (!configured[parity]) {
-            cudaError_t e = parity == 0 ? cudaFuncSetAttribute(k_fused<S, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm)
-                                        : cudaFuncSetAttribute(k_fused<S, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-            if (e != cudaSuccess) return e;
-            configured[parity] = true;
-        }
+        static SmemAttrOnce attr[2];
+        cudaError_t e = parity == 0 ? attr[0].ensure(k_fused<S, 0>, sm) : attr[1].ensure(k_fused<S, 1>, sm);
+        if (e != cudaSuccess) return e;
         const unsigned nblk = (unsigned)w.tiles_x * w.tiles_y * w.nzchunks;
         if (parity == 0)
             k_fused<S, 0><<<nblk, FT_X * FT_Y, sm, s>>>(a, w);
@@ -275,13 +323,9 @@ struct Launch {
     template <int TX, bool VAR>
     static cudaError_t fv_batched_tx(const void *entries, int n, int total, int k, int grid, cudaStream_t s) {
         const size_t sm = sizeof(FvSmem<R, FvTile<TX>::HN>);
-        static bool configured = false;
-        if (!configured) {
-            cudaError_t e =
-                cudaFuncSetAttribute(k_fv_batched<S, TX, VAR>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-            if (e != cudaSuccess) return e;
-            configured = true;
-        }
+        static SmemAttrOnce attr;
+        cudaError_t e = attr.ensure(k_fv_batched<S, TX, VAR>, sm);
+        if (e != cudaSuccess) return e;
         k_fv_batched<S, TX, VAR><<<grid, FV_NT, sm, s>>>((const BatchEntry<S> *)entries, n, total, k);
         return cudaGetLastError();
     }
@@ -379,7 +423,7 @@ const KernelTable *Launch<S>::table(int prec) {
                                       &fused,         sizeof(BatchEntry<S>), &fill_entry, &lb_batched,
                                       &fv_batched,    &batched_grid,    &residual,   &batch_tiles,
                                       &fv_zchunk_of,  &fv_variant_of,   sizeof(PartEntry<S>), &fill_part_entry,
-                                      &particle_phase_batched};
+                                      &particle_phase_batched, &halo_pack, &halo_unpack};
         return &t;
 }
 

@@ -22,6 +22,8 @@ FV_CTU, FV_DIVU = 4, 8  # variants: transverse CTU overlap on the face fluxes; t
 SCHED_AUTO, SCHED_SPLIT, SCHED_FUSED = 0, 1, 2
 FLAG_FLUID, FLAG_NOSLIP, FLAG_WALL0, FLAG_PARTICLE0 = 0, 1, 2, 64
 KERNEL_KINDS = ["lb", "fv", "fused", "momentum_exchange", "particle", "", "", ""]
+EUNSTABLE = 4
+HALO_F, HALO_U, HALO_TAU = 0, 1, 2
 STATUS = ["LBVE_OK", "LBVE_EINVAL", "LBVE_ENOMEM", "LBVE_ECUDA", "LBVE_EUNSTABLE", "LBVE_ETIMEOUT", "LBVE_ESTATE"]
 
 # every entry point declared in include/lbve.h
@@ -31,8 +33,12 @@ EXPORTS = [
     "lbve_read_fields_device", "lbve_read_pdfs", "lbve_write_pdfs", "lbve_read_particle", "lbve_read_conversions", "lbve_read_body_forces",
     "lbve_reduce", "lbve_residual", "lbve_pool_create", "lbve_pool_destroy", "lbve_pool_fits", "lbve_pool_admit",
     "lbve_pool_remove", "lbve_pool_step", "lbve_pool_residuals", "lbve_pool_size", "lbve_pool_bytes_in_use",
-    "lbve_pool_set_graphs", "lbve_pool_last_error", "lbve_step_noalloc", "lbve_noalloc_last_error", "lbve_set_kernel_timing", "lbve_read_kernel_times", "lbve_time", "lbve_synchronize", "lbve_last_error", "lbve_status_string",
+    "lbve_pool_set_graphs", "lbve_pool_last_error", "lbve_step_noalloc", "lbve_noalloc_last_error", "lbve_set_kernel_timing", "lbve_read_kernel_times", "lbve_time", "lbve_synchronize", "lbve_is_unstable", "lbve_checkpoint_bytes", "lbve_save", "lbve_restore",
+    "lbve_set_z_range", "lbve_step_phase", "lbve_halo_bytes", "lbve_halo_pack", "lbve_halo_unpack", "lbve_last_error", "lbve_status_string",
     "lbve_autotune", "lbve_pool_autotune",
+    # include/lbve2d.h
+    "lbve2d_default_params", "lbve2d_create", "lbve2d_destroy", "lbve2d_set_geometry", "lbve2d_set_force_field",
+    "lbve2d_init_fields", "lbve2d_step", "lbve2d_read_fields", "lbve2d_read_pdfs", "lbve2d_time", "lbve2d_last_error",
 ]
 
 
@@ -41,6 +47,16 @@ class Tuning(ct.Structure):
 
     _fields_ = [("block_x", ct.c_int), ("fv_zchunk", ct.c_int), ("candidates", ct.c_int),
                 ("steps_taken", ct.c_longlong), ("ms_per_step", ct.c_double), ("ms_per_step_default", ct.c_double)]
+
+
+class Params2D(ct.Structure):
+    """lbve2d_params (include/lbve2d.h)."""
+
+    _fields_ = [
+        ("nx", ct.c_int), ("ny", ct.c_int), ("periodic", ct.c_int * 2),
+        ("eta", ct.c_double), ("beta", ct.c_double), ("lambda_p", ct.c_double), ("rho0", ct.c_double),
+        ("body_force", ct.c_double * 2), ("magic", ct.c_double), ("pdf_prec", ct.c_int), ("fv_terms", ct.c_int),
+    ]
 
 
 class LbveError(RuntimeError):
@@ -60,6 +76,7 @@ class Params(ct.Structure):
         ("pdf_prec", ct.c_int), ("pdf_scale_log2", ct.c_int), ("fv_terms", ct.c_int),
         ("schedule", ct.c_int), ("block_x", ct.c_int),
         ("giesekus_alpha", ct.c_double),
+        ("fene_L2", ct.c_double),
     ]
 
 
@@ -123,6 +140,17 @@ def load(path: str | None = None):
         L.lbve_time.argtypes = [vp]
         L.lbve_time.restype = ct.c_longlong
         L.lbve_synchronize.argtypes = [vp]
+        L.lbve_is_unstable.argtypes = [vp]
+        L.lbve_set_z_range.argtypes = [vp, ct.c_int, ct.c_int, ct.c_int]
+        L.lbve_step_phase.argtypes = [vp, ct.c_int]
+        L.lbve_halo_bytes.argtypes = [vp, ct.c_int]
+        L.lbve_halo_bytes.restype = ct.c_size_t
+        L.lbve_halo_pack.argtypes = [vp, ct.c_int, ct.c_int, vp]
+        L.lbve_halo_unpack.argtypes = [vp, ct.c_int, ct.c_int, vp]
+        L.lbve_checkpoint_bytes.argtypes = [vp]
+        L.lbve_checkpoint_bytes.restype = ct.c_size_t
+        L.lbve_save.argtypes = [vp, vp, ct.c_size_t]
+        L.lbve_restore.argtypes = [vp, vp, ct.c_size_t]
         L.lbve_last_error.argtypes = [vp]
         L.lbve_last_error.restype = ct.c_char_p
         L.lbve_status_string.argtypes = [ct.c_int]
@@ -130,6 +158,20 @@ def load(path: str | None = None):
         L.lbve_autotune.argtypes = [vp, ct.c_int, ct.POINTER(Tuning)]
         ip = ct.POINTER(ct.c_int)
         L.lbve_pool_autotune.argtypes = [vp, ct.c_int, ct.c_int, ip, ip, ip, ip, dp, dp]
+        p2 = ct.POINTER(Params2D)
+        L.lbve2d_default_params.argtypes = [p2]
+        L.lbve2d_create.argtypes = [p2, vp, ct.POINTER(vp)]
+        L.lbve2d_destroy.argtypes = [vp]
+        L.lbve2d_set_geometry.argtypes = [vp, vp, vp]
+        L.lbve2d_set_force_field.argtypes = [vp, vp]
+        L.lbve2d_init_fields.argtypes = [vp, vp, vp, vp]
+        L.lbve2d_step.argtypes = [vp, ct.c_int]
+        L.lbve2d_read_fields.argtypes = [vp, vp, vp, vp]
+        L.lbve2d_read_pdfs.argtypes = [vp, vp]
+        L.lbve2d_time.argtypes = [vp]
+        L.lbve2d_time.restype = ct.c_longlong
+        L.lbve2d_last_error.argtypes = [vp]
+        L.lbve2d_last_error.restype = ct.c_char_p
         _lib = L
         return L
 
@@ -150,7 +192,8 @@ def default_params() -> Params:
 
 def make_params(shape, *, periodic=(1, 1, 1), eta=1.0 / 6.0, beta=0.5, lambda_p=1000.0, rho0=1.0,
                 body_force=(0.0, 0.0, 0.0), magic=3.0 / 16.0, precision="f32", pdf_scale_log2=-1,
-                fv_terms=FV_FLUX | FV_SOURCE, schedule=SCHED_AUTO, block_x=0, giesekus_alpha=0.0) -> Params:
+                fv_terms=FV_FLUX | FV_SOURCE, schedule=SCHED_AUTO, block_x=0, giesekus_alpha=0.0,
+                fene_L2=0.0) -> Params:
     p = default_params()
     p.nx, p.ny, p.nz = (int(v) for v in shape)
     for a in range(3):
@@ -160,6 +203,7 @@ def make_params(shape, *, periodic=(1, 1, 1), eta=1.0 / 6.0, beta=0.5, lambda_p=
     p.pdf_prec = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
     p.pdf_scale_log2, p.fv_terms, p.schedule, p.block_x = int(pdf_scale_log2), int(fv_terms), int(schedule), int(block_x)
     p.giesekus_alpha = float(giesekus_alpha)
+    p.fene_L2 = float(fene_L2)
     return p
 
 
@@ -275,6 +319,39 @@ class Solver:
 
     def synchronize(self):
         self._check(self._L.lbve_synchronize(self._h))
+
+    # -- z-slab decomposition (see lbve_set_z_range in include/lbve.h) ------------------
+    def set_z_range(self, z_lo: int, z_hi: int, z_origin: int = 0):
+        self._check(self._L.lbve_set_z_range(self._h, int(z_lo), int(z_hi), int(z_origin)))
+
+    def step_phase(self, phase: int):
+        self._check(self._L.lbve_step_phase(self._h, int(phase)))
+
+    def halo_bytes(self, what: int) -> int:
+        return int(self._L.lbve_halo_bytes(self._h, int(what)))
+
+    def halo_pack(self, what: int, side: int, dev_ptr: int):
+        self._check(self._L.lbve_halo_pack(self._h, int(what), int(side), ct.c_void_p(dev_ptr)))
+
+    def halo_unpack(self, what: int, side: int, dev_ptr: int):
+        self._check(self._L.lbve_halo_unpack(self._h, int(what), int(side), ct.c_void_p(dev_ptr)))
+
+    def save(self) -> bytes:
+        """Checkpoint record of the solve's state at this step boundary (lbve_save)."""
+        n = int(self._L.lbve_checkpoint_bytes(self._h))
+        buf = ct.create_string_buffer(n)
+        self._check(self._L.lbve_save(self._h, buf, n))
+        return buf.raw
+
+    def restore(self, record: bytes):
+        """Overwrite the state from a record of lbve_save (same parameters, geometry and
+        particle count; see lbve_restore)."""
+        buf = ct.create_string_buffer(record, len(record))
+        self._check(self._L.lbve_restore(self._h, buf, len(record)))
+
+    def is_unstable(self) -> bool:
+        """True once a stream-collide has flagged rho <= 0, |u|^2 >= 1/3 or a NaN (no sync)."""
+        return self._L.lbve_is_unstable(self._h) == 1
 
     @property
     def time(self) -> int:
@@ -419,3 +496,80 @@ class Pool:
             self.close()
         except Exception:
             pass
+
+
+class Solver2D:
+    """One two-dimensional solve (include/lbve2d.h).  Host arrays are numpy, (..., ny, nx)."""
+
+    def __init__(self, shape, *, periodic=(1, 1), eta=1.0 / 6.0, beta=0.5, lambda_p=1000.0, rho0=1.0,
+                 body_force=(0.0, 0.0), magic=3.0 / 16.0, precision="f32", fv_terms=FV_FLUX | FV_SOURCE,
+                 stream: int | None = None):
+        self._L = load()
+        p = Params2D()
+        self._L.lbve2d_default_params(ct.byref(p))
+        p.nx, p.ny = (int(v) for v in shape)
+        for a in range(2):
+            p.periodic[a] = int(periodic[a])
+            p.body_force[a] = float(body_force[a])
+        p.eta, p.beta, p.lambda_p, p.rho0, p.magic = float(eta), float(beta), float(lambda_p), float(rho0), float(magic)
+        p.pdf_prec = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
+        p.fv_terms = int(fv_terms)
+        self.params = p
+        self.shape = (p.nx, p.ny)
+        h = ct.c_void_p()
+        rc = self._L.lbve2d_create(ct.byref(p), ct.c_void_p(stream or 0), ct.byref(h))
+        if rc != 0:
+            raise LbveError(rc, self._L.lbve2d_last_error(None).decode())
+        self._h = h
+
+    def _check(self, rc):
+        if rc != 0:
+            raise LbveError(rc, self._L.lbve2d_last_error(self._h).decode())
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._L.lbve2d_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _grid(self, k=None):
+        nx, ny = self.shape
+        return (ny, nx) if k is None else (k, ny, nx)
+
+    def _arr(self, a, k):
+        return None if a is None else np.ascontiguousarray(a, dtype=np.float64).reshape(self._grid(k))
+
+    def set_geometry(self, flags, ub=None):
+        fl = np.ascontiguousarray(flags, dtype=np.uint8).reshape(self._grid())
+        u = self._arr(ub, 2)
+        self._check(self._L.lbve2d_set_geometry(self._h, fl.ctypes.data, None if u is None else u.ctypes.data))
+
+    def set_force_field(self, F=None):
+        a = self._arr(F, 2)
+        self._check(self._L.lbve2d_set_force_field(self._h, None if a is None else a.ctypes.data))
+
+    def init_fields(self, rho=None, u=None, tau=None):
+        arrs = [self._arr(rho, None), self._arr(u, 2), self._arr(tau, 3)]
+        self._check(self._L.lbve2d_init_fields(self._h, *[None if a is None else a.ctypes.data for a in arrs]))
+
+    def step(self, n=1):
+        self._check(self._L.lbve2d_step(self._h, int(n)))
+
+    @property
+    def time(self) -> int:
+        return int(self._L.lbve2d_time(self._h))
+
+    def read_fields(self):
+        rho, u, tau = np.zeros(self._grid()), np.zeros(self._grid(2)), np.zeros(self._grid(3))
+        self._check(self._L.lbve2d_read_fields(self._h, rho.ctypes.data, u.ctypes.data, tau.ctypes.data))
+        return rho, u, tau
+
+    def read_pdfs(self):
+        f = np.zeros(self._grid(9))
+        self._check(self._L.lbve2d_read_pdfs(self._h, f.ctypes.data))
+        return f

@@ -230,7 +230,21 @@ class Server:
                         time.sleep(min(wait, 0.05))
                 continue
             ts = self.clock()
-            self.pool.step(self.check_every)
+            try:
+                self.pool.step(self.check_every)
+            except lbve.LbveError as exc:
+                if exc.status != lbve.EUNSTABLE:
+                    raise
+                # a member's stream-collide flagged an instability: evict it, step the rest
+                for item in [it for it in active if it[1].is_unstable()]:
+                    req, s, adm, steps = item
+                    self.pool.remove(s)
+                    s.close()
+                    active.remove(item)
+                    results.append(Result(req.rid, req.kind, int(np.prod(req.shape)), "unstable", steps,
+                                          float("nan"), req.arrival, adm, now()))
+                self.stats["step_s"] += self.clock() - ts
+                continue
             for item in active:
                 item[3] += self.check_every
             res = self.pool.residuals()
@@ -281,7 +295,13 @@ def run_one_at_a_time(requests, precision="f32", check_every=100, stream=None, c
             continue
         steps, status, per_step = 0, None, float("nan")
         while status is None:
-            s.step(check_every)
+            try:
+                s.step(check_every)
+            except lbve.LbveError as exc:
+                if exc.status != lbve.EUNSTABLE:
+                    raise
+                status = "unstable"
+                break
             steps += check_every
             r, unorm = s.residual()
             per_step = r / check_every

@@ -18,9 +18,13 @@ def lib():
 
 
 def declared_entry_points():
-    src = open(os.path.join(ROOT, "include", "lbve.h")).read()
-    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
-    return sorted(set(re.findall(r"\b(lbve_[a-z_0-9]+)\s*\(", src)))
+    names = set()
+    for h in sorted(os.listdir(os.path.join(ROOT, "include"))):
+        if h.endswith(".h"):
+            src = open(os.path.join(ROOT, "include", h)).read()
+            src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+            names |= set(re.findall(r"\b(lbve(?:2d)?_[a-z_0-9]+)\s*\(", src))
+    return sorted(names)
 
 
 def test_every_declared_symbol_is_exported(lib):
@@ -28,7 +32,7 @@ def test_every_declared_symbol_is_exported(lib):
 
     so = lbve.LIB_PATH
     out = subprocess.run(["nm", "-D", "--defined-only", so], capture_output=True, text=True, check=True).stdout
-    exported = set(re.findall(r"\bT (lbve_[a-z_0-9]+)", out))
+    exported = set(re.findall(r"\bT (lbve(?:2d)?_[a-z_0-9]+)", out))
     declared = declared_entry_points()
     assert declared, "no entry points parsed from lbve.h"
     missing = [s for s in declared if s not in exported]
@@ -152,3 +156,29 @@ def test_binding_constants_match_the_header():
     for (name, ctype, is_array), (_, pytype) in zip(fields, py):
         base = pytype._type_ if is_array else pytype
         assert base == {"int": ct.c_int, "double": ct.c_double}[ctype], name
+
+
+def test_noalloc_validates_on_the_host(lib):
+    """lbve_step_noalloc rejects, before any CUDA call: the fused schedule (it runs the
+    split kernels only), grids beyond its fixed scratch, and NULL buffers."""
+    from paper_2009_12279_gb300 import lbve
+
+    fused = lbve.make_params((8, 8, 8), precision="f32", schedule=lbve.SCHED_FUSED)
+    with pytest.raises(lbve.LbveError, match="split schedule only"):
+        lbve.step_noalloc(fused, 1, 1, 1, 1, nsteps=1)
+    big = lbve.make_params((128, 128, 64), precision="f32")
+    with pytest.raises(lbve.LbveError, match="LBVE_NOALLOC_MAX_CELLS"):
+        lbve.step_noalloc(big, 1, 1, 1, 1, nsteps=1)
+    ok = lbve.make_params((8, 8, 8), precision="f32", schedule=lbve.SCHED_SPLIT)
+    with pytest.raises(lbve.LbveError, match="NULL"):
+        lbve.step_noalloc(ok, 0, 1, 1, 1, nsteps=1)
+
+
+@pytest.mark.parametrize("bad", [dict(fene_L2=2.0), dict(fene_L2=-1.0), dict(fene_L2=10.0, beta=0.0),
+                                 dict(fene_L2=10.0, giesekus_alpha=0.1)])
+def test_fene_parameters_are_validated(lib, bad):
+    from paper_2009_12279_gb300 import lbve
+
+    kw = dict(dict(eta=1.0 / 6.0, beta=0.5, lambda_p=100.0, precision="f32"), **bad)
+    assert lbve.device_bytes(lbve.make_params((8, 8, 8), **kw)) == 0
+    assert lbve.device_bytes(lbve.make_params((8, 8, 8), eta=1.0 / 6.0, beta=0.5, lambda_p=100.0, fene_L2=10.0)) > 0

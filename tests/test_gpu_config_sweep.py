@@ -1,0 +1,195 @@
+"""The stated configurations over their parameter ranges, through the C ABI.
+
+* Config 1 (plain method): the full 20,000 steps of the 4 x 32 x 4 channel in FP64
+  (lbve_step) against the oracle, and against the analytic start-up series of the centre
+  velocity and the steady profiles tau_xy = eta_p gdot and N1 = 2 eta_p lambda gdot^2
+  (Sec. "Time-dependent Poiseuille flow", "Steady shear flow"); the same channel as a
+  member of a BF16 pool beside other solves, against the same analytic profiles.
+* Config 2 (fixed sphere in a 128^3 duct) at beta in {0.1, 0.5} x Wi in {0.1, 0.5, 1.0}:
+  16 steps against the oracle, FP64 to 1e-12 and FP32 to 1e-5, drag reported.
+* Config 3 (sedimenting sphere, 64 x 64 x 256) at Wi = 1.0: 24 steps against the oracle.
+"""
+import numpy as np
+import pytest
+
+import analytic as A
+from gpu_helpers import TOL_F32, TOL_F64, compare, pair, rel_l2, require_gpu
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _gpu():
+    require_gpu()
+
+
+def _channel():
+    from paper_2009_12279_gb300 import workloads
+
+    return workloads.config_channel()
+
+
+def _profiles(u, tau, beta, eta, lam, g):
+    """Errors of the steady channel profiles (x-z averaged) against the closed forms,
+    relative to each profile's maximum: (u, tau_xy interior, tau_xy all, N1 interior, N1 all)."""
+    ub = u[0].mean(axis=(0, 2))[1:-1]
+    txy = tau[3].mean(axis=(0, 2))[1:-1]
+    n1 = (tau[0] - tau[1]).mean(axis=(0, 2))[1:-1]
+    y = np.arange(1, 31, dtype=float)
+    ua = A.poiseuille_u(y, g, eta, 0.5, 30.5)
+    gd = A.poiseuille_shear_rate(y, g, eta, 0.5, 30.5)
+    eta_p = beta * eta
+    ta = eta_p * gd
+    na = 2 * eta_p * lam * gd ** 2
+    inner = slice(1, -1)
+    return (np.abs(ub - ua).max() / ua.max(),
+            np.abs(txy - ta)[inner].max() / np.abs(ta).max(), np.abs(txy - ta).max() / np.abs(ta).max(),
+            np.abs(n1 - na)[inner].max() / na.max(), np.abs(n1 - na).max() / na.max())
+
+
+def _centre_curve(step_fn, read_fn, chunks=100, every=200):
+    ts, uc = [], []
+    for k in range(chunks):
+        step_fn(every)
+        _, u, _, _ = read_fn()
+        ts.append((k + 1) * every)
+        uc.append(0.5 * (u[0, :, 15, :].mean() + u[0, :, 16, :].mean()))
+    return np.array(ts), np.array(uc)
+
+
+def test_config1_full_run_fp64_against_oracle_and_analytic(capsys):
+    cfg = _channel()
+    prm = cfg["params"]
+    g, o = pair(cfg["shape"], prm, cfg["flags"], precision="f64")
+    ts, uc = _centre_curve(g.step, g.read_fields)
+    o.step(cfg["steps"])
+    assert g.time == o.time == 20000
+    e = compare(g, o)
+    assert max(e["f"], e["u"], e["tau"]) <= TOL_F64, e
+    _, u, tau, _ = g.read_fields()
+    eta, beta, lam, gx = prm["eta"], prm["beta"], prm["lambda_p"], prm["body_force"][0]
+    ua = A.startup_poiseuille(ts, [14.5, 15.5], g=gx, rho=1.0, eta_n=(1 - beta) * eta, eta_p=beta * eta,
+                              lam=lam, L=30.0).mean(axis=1)
+    us = gx * 30.0 ** 2 / (8 * eta)
+    curve = np.abs(uc - ua).max() / us
+    prof = _profiles(u, tau, beta, eta, lam, gx)
+    with capsys.disabled():
+        print(f"\n[config 1, FP64, 20000 steps] vs oracle {e}; centre velocity vs start-up series "
+              f"{curve:.2e} of u_c; steady profiles u {prof[0]:.2e}, tau_xy {prof[1]:.2e} (interior) "
+              f"{prof[2]:.2e} (all), N1 {prof[3]:.2e} (interior) {prof[4]:.2e} (all)")
+    assert curve < 0.01  # the paper: ~1 % with the wall position fitted
+    assert uc.max() > 1.3 * us  # the elastic overshoot
+    assert prof[0] < 0.01 and prof[1] < 0.01 and prof[2] < 0.05 and prof[3] < 0.01 and prof[4] < 0.05
+
+
+def test_config1_as_a_bf16_pool_member_against_analytic(capsys):
+    """The config-1 channel stepped 20,000 times inside a BF16 pool with two other solves
+    (a sphere duct and a different channel): its result against the analytic steady
+    profiles and the FP64 run, errors printed."""
+    from paper_2009_12279_gb300 import Pool, Solver, workloads
+
+    cfg = _channel()
+    prm = cfg["params"]
+    pool = Pool("bf16", budget_bytes=2 * 10**9)
+    ch = Solver(cfg["shape"], precision="bf16", **prm)
+    ch.set_geometry(cfg["flags"])
+    ref = Solver(cfg["shape"], precision="f64", **prm)
+    ref.set_geometry(cfg["flags"])
+    other = workloads.config_sphere_duct(32, radius=4.0, beta=0.3, wi=0.4)
+    duct = Solver(other["shape"], precision="bf16", **other["params"])
+    duct.set_geometry(other["flags"], other["wall_vel"])
+    ch2 = Solver((8, 20, 6), precision="bf16", periodic=(1, 0, 1), eta=1.0 / 6.0, beta=0.7, lambda_p=500.0,
+                 body_force=(3e-6, 0.0, 0.0))
+    ch2.set_geometry(workloads.channel_flags((8, 20, 6), 1))
+    for s in (duct, ch, ch2):
+        pool.admit(s)
+    ts, uc = _centre_curve(pool.step, ch.read_fields)
+    ref.step(cfg["steps"])
+    assert ch.time == 20000
+    _, u, tau, _ = ch.read_fields()
+    _, u64, tau64, _ = ref.read_fields()
+    eta, beta, lam, gx = prm["eta"], prm["beta"], prm["lambda_p"], prm["body_force"][0]
+    ua = A.startup_poiseuille(ts, [14.5, 15.5], g=gx, rho=1.0, eta_n=(1 - beta) * eta, eta_p=beta * eta,
+                              lam=lam, L=30.0).mean(axis=1)
+    us = gx * 30.0 ** 2 / (8 * eta)
+    curve = np.abs(uc - ua).max() / us
+    prof = _profiles(u, tau, beta, eta, lam, gx)
+    fl = cfg["flags"] == 0
+    e64 = (rel_l2(u[:, fl], u64[:, fl]), rel_l2(tau[:, fl], tau64[:, fl]))
+    with capsys.disabled():
+        print(f"\n[config 1, BF16 pool member, 20000 steps] vs FP64 u {e64[0]:.2e} tau {e64[1]:.2e}; centre "
+              f"velocity vs start-up series {curve:.2e} of u_c; steady profiles u {prof[0]:.2e}, tau_xy "
+              f"{prof[1]:.2e} / {prof[2]:.2e}, N1 {prof[3]:.2e} / {prof[4]:.2e} (interior / all)")
+    assert np.isfinite(u).all() and not ch.is_unstable()
+    assert curve < 0.02
+    assert prof[0] < 0.02 and prof[1] < 0.02 and prof[2] < 0.05 and prof[3] < 0.03 and prof[4] < 0.06
+    assert e64[0] < 0.01 and e64[1] < 0.02
+    for s in (duct, ch, ch2):
+        pool.remove(s)
+        s.close()
+    pool.close()
+    ref.close()
+
+
+@pytest.mark.parametrize("beta", [0.1, 0.5])
+@pytest.mark.parametrize("wi", [0.1, 0.5, 1.0])
+def test_config2_sweep_matches_oracle(beta, wi, capsys):
+    from oracle import oracle
+    from paper_2009_12279_gb300 import Solver, workloads
+
+    from gpu_helpers import oracle_kwargs
+
+    cfg = workloads.config_sphere_duct(128, radius=12.0, beta=beta, wi=wi)
+    T = 16
+    o = oracle.Oracle(cfg["shape"], wall_vel=cfg["wall_vel"], **oracle_kwargs(cfg["params"]))
+    o.set_flags(cfg["flags"])
+    o.step(T)
+    _, uo, to, fo = o.read_fields()
+    po, drag_o = o.read_pdfs(), o.body_forces()[2].copy()
+    o.close()
+    fluid = fo == 0
+    for precision, tol in (("f64", TOL_F64), ("f32", TOL_F32)):
+        g = Solver(cfg["shape"], precision=precision, **cfg["params"])
+        g.set_geometry(cfg["flags"], cfg["wall_vel"])
+        g.step(T)
+        _, ug, tg, _ = g.read_fields()
+        e = {"u": rel_l2(ug[:, fluid], uo[:, fluid]), "tau": rel_l2(tg[:, fluid], to[:, fluid])}
+        drag_g = g.body_forces()[2]
+        ed = np.linalg.norm(drag_g - drag_o) / np.linalg.norm(drag_o)
+        with capsys.disabled():
+            print(f"\n[config 2 duct 128^3, beta {beta}, Wi {wi} (lambda {cfg['params']['lambda_p']:.4g}), "
+                  f"{precision}, {T} steps] u {e['u']:.2e} tau {e['tau']:.2e}; drag x oracle {drag_o[0]:.6e} "
+                  f"gpu {drag_g[0]:.6e} (rel {ed:.1e})")
+        assert max(e["u"], e["tau"]) <= tol, (precision, e)
+        assert ed <= tol, precision
+        if precision == "f64":
+            assert rel_l2(g.read_pdfs()[:, fluid], po[:, fluid]) <= TOL_F64
+        g.close()
+
+
+def test_config3_wi_1_matches_oracle(capsys):
+    """Sedimenting sphere at Wi = 1.0 (lambda = R Wi / v_St), 24 steps, FP64 and FP32."""
+    nx, ny, nz = 64, 64, 256
+    fl = np.ones((nz, ny, nx), np.uint8)
+    fl[1:-1, 1:-1, 1:-1] = 0
+    R, rho_p, eta = 8.0, 1.2, 1.0 / 6.0
+    v_st = 0.1 * eta / (2.0 * R)
+    F = 6.0 * np.pi * eta * R * v_st
+    prm = dict(periodic=(0, 0, 0), eta=eta, beta=0.5, lambda_p=1.0 * R / v_st)
+    part = dict(X=((nx - 1) / 2.0, (ny - 1) / 2.0, nz - 3 * R), R=R, rho_p=rho_p, Fext=(0.0, 0.0, -F))
+    for precision, tol in (("f64", TOL_F64), ("f32", TOL_F32)):
+        g, o = pair((nx, ny, nz), prm, fl, precision=precision)
+        for obj in (g, o):
+            obj.add_particle(part["X"], R, rho_p, v=(0, 0, 0), w=(0, 0, 0), Fext=part["Fext"], Text=(0, 0, 0))
+        g.step(24)
+        o.step(24)
+        e = compare(g, o)
+        pg, po = g.read_particle(0), o.read_particle(0)
+        perr = max(rel_l2(pg[k], po[k]) for k in ("X", "v"))
+        with capsys.disabled():
+            print(f"\n[config 3 sedimentation 64x64x256, Wi 1.0 (lambda {prm['lambda_p']:.4g}), {precision}, 24 steps] "
+                  f"{e}; particle X, v {perr:.2e}")
+        assert max(e["u"], e["tau"]) <= tol, e
+        assert perr <= tol
+        g.close()
+        o.close()

@@ -25,8 +25,8 @@ MUTANTS = {
     "giesekus_sign": ("S[c] = S[c] - s->gk * q;", "S[c] = S[c] + s->gk * q;"),
     "giesekus_product_index": ("q += tr[COMP[i][k]] * tr[COMP[k][j]];", "q += tr[COMP[i][k]] * tr[COMP[i][j]];"),
     "upwind_inflow_sign": ("double vin = -sg * u[(long)k * n + nb];", "double vin = sg * u[(long)k * n + nb];"),
-    "force_extrapolation_zero": ("double tf = fl ? 0.5 * (tr + tau[(long)c * s->n + nb]) : tr;",
-                                 "double tf = fl ? 0.5 * (tr + tau[(long)c * s->n + nb]) : 0.0;"),
+    "force_extrapolation_zero": ("double tf = fl ? 0.5 * (tr + tn6[c]) : tr;",
+                                 "double tf = fl ? 0.5 * (tr + tn6[c]) : 0.0;"),
     "wall_gradient_uses_cell": ("double up = is_fluid(s, np_) ? 0.5 * (ur + u[(long)j * n + np_]) : ubp[j];",
                                 "double up = is_fluid(s, np_) ? 0.5 * (ur + u[(long)j * n + np_]) : ur;"),
     "moving_wall_sign": ("s->fn[(long)OPP[i] * n + r] = fsi - X;", "s->fn[(long)OPP[i] * n + r] = fsi + X;"),
@@ -71,9 +71,8 @@ BRUTE_FORCE_ONLY = {
         "G[k * 3 + j] = (!is_fluid(s, np_) && !is_fluid(s, nm_)) ? 0.0 : up - um;"),
     # the stress face value towards a particle cell taken as zero, not tau(r)
     "force_extrapolation_next_to_particle": (
-        "double tf = fl ? 0.5 * (tr + tau[(long)c * s->n + nb]) : tr;",
-        "double tf = fl ? 0.5 * (tr + tau[(long)c * s->n + nb]) : "
-        "(nb >= 0 && s->flag[nb] >= ORC_PART0 ? 0.0 : tr);"),
+        "double tf = fl ? 0.5 * (tr + tn6[c]) : tr;",
+        "double tf = fl ? 0.5 * (tr + tn6[c]) : (nb >= 0 && s->flag[nb] >= ORC_PART0 ? 0.0 : tr);"),
     # the torque lever arm of a momentum-exchange link measured from the fluid cell
     "torque_lever_arm_of_fluid_cell": (
         "displacement(s, nb, P->X, d);\n                cross(d, Fl, T);",

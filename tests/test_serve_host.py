@@ -50,6 +50,9 @@ class FakeSolver:
     def close(self):
         self.closed = True
 
+    def is_unstable(self):
+        return getattr(self.req, "flagged", False)
+
 
 class FakePool:
     """Budget bookkeeping like lbve_pool; residual r = 1/steps (converges), NaN for
@@ -76,6 +79,10 @@ class FakePool:
         self.used -= s.req.bytes
 
     def step(self, n):
+        from paper_2009_12279_gb300 import lbve
+
+        if any(s.is_unstable() for s in self.members):  # as lbve_pool_step: refuse, no step
+            raise lbve.LbveError(lbve.EUNSTABLE, "member unstable")
         for s in self.members:
             self.steps[s.req.rid] += n
 
@@ -129,6 +136,19 @@ def test_faults_injected_on_the_host():
     results, _ = srv.run(reqs)
     st = {r.rid: r.status for r in results}
     assert st == {0: "converged", 1: "unstable", 2: "rejected", 3: "cancelled", 4: "converged"}
+    assert pool.used == 0
+
+
+def test_instability_status_of_the_pool_evicts_the_flagged_member():
+    """lbve_pool_step refuses to step while a member's instability flag is set (rho <= 0,
+    |u| at the sound speed, NaN): the server evicts exactly the flagged members and the
+    others continue to convergence."""
+    reqs = _fake_requests(4, [10, 10, 10, 10])
+    reqs[2].flagged = True
+    srv, pool = _server(100)
+    results, _ = srv.run(reqs)
+    st = {r.rid: r.status for r in results}
+    assert st == {0: "converged", 1: "converged", 2: "unstable", 3: "converged"}
     assert pool.used == 0
 
 
@@ -203,3 +223,83 @@ def test_convergence_respects_the_storage_residual_floor():
         tol = max(1e-6, serve.RESIDUAL_FLOOR[prec])
         assert 1.0 / n ** 2 <= tol < 1.0 / (n - 100) ** 2
     assert steps["bf16"] < steps["f16"] < steps["f32"]
+
+
+# ---------------------------------------------------------------------------------
+# z-slab decomposition: host logic (partition, ghost planes, neighbour exchange)
+# ---------------------------------------------------------------------------------
+def test_slab_partition_and_ghost_planes():
+    from paper_2009_12279_gb300 import slabs
+
+    r = slabs.split_planes(30, 4)
+    assert r == [(0, 8), (8, 16), (16, 23), (23, 30)]
+    assert slabs.ghost_planes(0, 8, 30, True) == [29] + list(range(0, 8)) + [8]
+    assert slabs.ghost_planes(23, 30, 30, False) == [22] + list(range(23, 30)) + [None]
+    assert slabs.neighbours(0, 4, True) == (3, 1) and slabs.neighbours(3, 4, False) == (2, None)
+    assert slabs.neighbours(0, 1, True) == (0, 0)
+    a = np.arange(5 * 2 * 3).reshape(5, 2, 3)
+    loc = slabs.slab_array(a, [4, 0, 1, None], 0, fill=-1)
+    assert (loc[0] == a[4]).all() and (loc[2] == a[1]).all() and (loc[3] == -1).all()
+    with pytest.raises(ValueError):
+        slabs.split_planes(3, 4)
+
+
+def _slab_worker(rank, world, port, periodic, out):
+    import torch
+    import torch.distributed as dist
+
+    from paper_2009_12279_gb300 import slabs
+
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    got = {}
+
+    def pack(what, side, buf):  # this rank's face data: (rank, field, side) stamped
+        buf.fill_(0)
+        buf[0], buf[1], buf[2] = rank, what, side
+
+    def unpack(what, side, buf):
+        got[(what, side)] = tuple(int(v) for v in buf[:3])
+
+    send = [torch.zeros(8, dtype=torch.int64) for _ in range(2)]
+    recv = [torch.zeros(8, dtype=torch.int64) for _ in range(2)]
+    for what in (0, 1, 2):
+        slabs.exchange_with_neighbours(what, rank, world, periodic, pack, unpack, send, recv)
+    out.put((rank, got))
+    dist.barrier()
+    dist.destroy_process_group()
+
+
+@pytest.mark.parametrize("world,periodic", [(2, True), (2, False), (3, True)])
+def test_halo_exchange_between_gloo_ranks(world, periodic):
+    """Each rank's low side receives what the rank below packed for its high side and vice
+    versa; no exchange across a closed domain's ends; two periodic ranks (both neighbours
+    the same rank) keep the two directions apart."""
+    import multiprocessing as mp
+    import socket
+
+    from paper_2009_12279_gb300 import slabs
+
+    with socket.socket() as sk:
+        sk.bind(("127.0.0.1", 0))
+        port = sk.getsockname()[1]
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    procs = [ctx.Process(target=_slab_worker, args=(r, world, port, periodic, q)) for r in range(world)]
+    for p in procs:
+        p.start()
+    res = dict(q.get(timeout=120) for _ in procs)
+    for p in procs:
+        p.join(timeout=60)
+        assert p.exitcode == 0
+    for rank, got in res.items():
+        lo, hi = slabs.neighbours(rank, world, periodic)
+        for what in (0, 1, 2):
+            if lo is None:
+                assert (what, 0) not in got
+            else:
+                assert got[(what, 0)] == (lo, what, 1)  # the lower rank's high-side pack
+            if hi is None:
+                assert (what, 1) not in got
+            else:
+                assert got[(what, 1)] == (hi, what, 0)  # the upper rank's low-side pack
