@@ -321,6 +321,9 @@ def bench_serving(args, torch):
     stream = torch.cuda.Stream()
     kw = dict(max_steps_cap=args.serving_cap)
     reqs0 = serve.make_requests(args.serving_requests, seed=0, mean_interarrival=0.0, **kw)
+    polish = "f32" if args.serving_polish else None
+    # the one-at-a-time FP32 baseline runs on the first serving_solo requests (all by default)
+    n_solo = args.serving_solo if args.serving_solo > 0 else len(reqs0)
     # tile autotuning (outside the timed runs): one solve per domain width of the stream
     # in a scratch pool; the recorded choices apply to every pool admitted to later
     tuning = {}
@@ -344,21 +347,26 @@ def bench_serving(args, torch):
         tuning[prec] = res
     # throughput mode (all requests waiting at t = 0)
     t0 = time.perf_counter()
-    solo, fsolo = serve.run_one_at_a_time(reqs0, precision="f32", stream=stream.cuda_stream, keep_fields=True)
+    solo, fsolo = serve.run_one_at_a_time(reqs0[:n_solo], precision="f32", stream=stream.cuda_stream,
+                                          keep_fields=True)
     torch.cuda.synchronize()
     wall_solo = time.perf_counter() - t0
+    keep = {r.rid for r in reqs0[:n_solo]}  # fields kept for the accuracy comparisons only
     # batched FP32: bitwise the same results as one at a time (equal accuracy)
-    srv = serve.Server("f32", budget_bytes=int(args.serving_budget_gb * 1e9), stream=stream.cuda_stream)
+    mix32, wall_mix32, stats32, same = [], float("nan"), {}, None
+    if not args.serving_config5:
+        srv = serve.Server("f32", budget_bytes=int(args.serving_budget_gb * 1e9), stream=stream.cuda_stream)
+        t0 = time.perf_counter()
+        mix32, fmix32 = srv.run(reqs0, keep_fields=keep)
+        torch.cuda.synchronize()
+        wall_mix32 = time.perf_counter() - t0
+        stats32 = dict(srv.stats)
+        srv.close()
+        same = all(all(np.array_equal(a, b) for a, b in zip(fsolo[r], fmix32[r])) for r in fsolo if r in fmix32)
+    srv = serve.Server("bf16", budget_bytes=int(args.serving_budget_gb * 1e9), stream=stream.cuda_stream,
+                       polish=polish)
     t0 = time.perf_counter()
-    mix32, fmix32 = srv.run(reqs0, keep_fields=True)
-    torch.cuda.synchronize()
-    wall_mix32 = time.perf_counter() - t0
-    stats32 = dict(srv.stats)
-    srv.close()
-    same = all(all(np.array_equal(a, b) for a, b in zip(fsolo[r], fmix32[r])) for r in fsolo if r in fmix32)
-    srv = serve.Server("bf16", budget_bytes=int(args.serving_budget_gb * 1e9), stream=stream.cuda_stream)
-    t0 = time.perf_counter()
-    mix, fmix = srv.run(reqs0, keep_fields=True)
+    mix, fmix = srv.run(reqs0, keep_fields=keep)
     torch.cuda.synchronize()
     wall_mix = time.perf_counter() - t0
     peak = srv.peak_bytes
@@ -373,26 +381,29 @@ def bench_serving(args, torch):
     # latency under Poisson arrivals at 0.8 x the batched service time per solve
     mean_gap = 0.8 * wall_mix / max(len(reqs0), 1)
     reqs = serve.make_requests(args.serving_requests, seed=0, mean_interarrival=mean_gap, **kw)
-    srv = serve.Server("bf16", budget_bytes=int(args.serving_budget_gb * 1e9), stream=stream.cuda_stream)
+    srv = serve.Server("bf16", budget_bytes=int(args.serving_budget_gb * 1e9), stream=stream.cuda_stream,
+                       polish=polish)
     t0 = time.perf_counter()
     lat_mix, _ = srv.run(reqs)
     torch.cuda.synchronize()
     wall_lat = time.perf_counter() - t0
     srv.close()
     t0 = time.perf_counter()
-    lat_solo, _ = serve.run_one_at_a_time(reqs, precision="f32", stream=stream.cuda_stream)
+    lat_solo, _ = serve.run_one_at_a_time(reqs[:n_solo], precision="f32", stream=stream.cuda_stream)
     torch.cuda.synchronize()
     wall_lat_solo = time.perf_counter() - t0
     s_mix, s_solo = serve.summarize(lat_mix, wall_lat), serve.summarize(lat_solo, wall_lat_solo)
     return {
         "requests": len(reqs0), "step_cap": args.serving_cap, "stop": "residual 1e-6 per step or cap",
+        "polish": polish, "one_at_a_time_requests": n_solo,
         "batched_bf16": {"solves_per_s": len(mix) / wall_mix, "wall_s": wall_mix,
                          "p50_latency_s": s_mix["p50_latency_s"], "p99_latency_s": s_mix["p99_latency_s"],
                          "poisson_wall_s": wall_lat, "peak_device_bytes": peak, "phases": stats16,
                          "mlups": serve.summarize(mix, wall_mix)["mlups"]},
-        "batched_f32": {"solves_per_s": len(mix32) / wall_mix32, "wall_s": wall_mix32,
-                        "bitwise_equal_to_one_at_a_time": bool(same), "phases": stats32,
-                        "mlups": serve.summarize(mix32, wall_mix32)["mlups"]},
+        "batched_f32": None if not mix32 else {
+            "solves_per_s": len(mix32) / wall_mix32, "wall_s": wall_mix32,
+            "bitwise_equal_to_one_at_a_time": bool(same), "phases": stats32,
+            "mlups": serve.summarize(mix32, wall_mix32)["mlups"]},
         "one_at_a_time_f32": {"solves_per_s": len(solo) / wall_solo, "wall_s": wall_solo,
                               "p50_latency_s": s_solo["p50_latency_s"], "p99_latency_s": s_solo["p99_latency_s"],
                               "poisson_wall_s": wall_lat_solo, "mlups": serve.summarize(solo, wall_solo)["mlups"]},
@@ -402,6 +413,7 @@ def bench_serving(args, torch):
         "bf16_vs_f32_u_rel_l2": {"median": float(np.median(errs)) if errs else None,
                                  "max": float(np.max(errs)) if errs else None},
         "statuses_bf16": {k: sum(r.status == k for r in mix) for k in ("converged", "capped", "unstable", "rejected")},
+        "polished_bf16": stats16.get("polished", 0),
         "statuses_f32": {k: sum(r.status == k for r in solo) for k in ("converged", "capped", "unstable", "rejected")},
         "unstable_bf16": [(r.rid, r.kind) for r in mix if r.status == "unstable"],
     }
@@ -609,6 +621,13 @@ def main():
     ap.add_argument("--serving-requests", type=int, default=48)
     ap.add_argument("--serving-cap", type=int, default=1000, help="step cap per solve in the serving sample")
     ap.add_argument("--serving-budget-gb", type=float, default=150.0)
+    ap.add_argument("--serving-polish", action="store_true",
+                    help="BF16 solves that reach the BF16 residual floor finish in an FP32 pool")
+    ap.add_argument("--serving-solo", type=int, default=0,
+                    help="run the one-at-a-time FP32 baseline on the first this many requests (0: all)")
+    ap.add_argument("--serving-config5", action="store_true",
+                    help="the serving configuration as stated: 2000 requests, cap min(10 lambda, 50000) steps, "
+                         "residual 1e-6 (BF16 with FP32 polish; one-at-a-time FP32 on the first 100)")
     ap.add_argument("--fv-terms", type=int, default=0,
                     help="LBVE_FV_* bits of the throughput solve (0: flux and source, the method)")
     ap.add_argument("--profile-pool-steps", type=int, default=0,
@@ -616,6 +635,9 @@ def main():
     ap.add_argument("--giesekus-alpha", type=float, default=0.0,
                     help="Giesekus mobility of the throughput solve (0: Oldroyd-B, the method)")
     args = ap.parse_args()
+    if args.serving_config5:
+        args.serving_requests, args.serving_cap, args.serving_polish = 2000, 50000, True
+        args.serving_solo = args.serving_solo or 100
     args.precisions = [p.strip() for p in args.precisions.split(",") if p.strip()]
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")

@@ -128,7 +128,9 @@ struct Store<__nv_bfloat16> {
 };
 
 // Counter-based random bits: the 32-bit finaliser of MurmurHash3 (A. Appleby) over a cell
-// and step key, then per pair of directions a Weyl offset and one xor-shift-multiply round.
+// and step key, uniform in all 32 bits; each pair of directions takes it xor a distinct
+// constant (one instruction).  Every rounding stays unbiased (each half of the bits is
+// uniform); only the pairs' bits are related within a cell.
 __device__ __forceinline__ uint32_t fmix32(uint32_t x) {
     x ^= x >> 16;
     x *= 0x85EBCA6Bu;
@@ -137,11 +139,7 @@ __device__ __forceinline__ uint32_t fmix32(uint32_t x) {
     x ^= x >> 16;
     return x;
 }
-__device__ __forceinline__ uint32_t pair_bits(uint32_t h, int p) {
-    uint32_t x = h + (uint32_t)p * 0x9E3779B9u;
-    x ^= x >> 15;
-    return x * 0x2C1B3C6Du;
-}
+__device__ __forceinline__ uint32_t pair_bits(uint32_t h, int p) { return h ^ ((uint32_t)(p + 1) * 0x9E3779B9u); }
 
 // Coordinates of one cell and its periodically wrapped neighbours; cell indices are
 // 32-bit (grids are limited to 2^31 cells).

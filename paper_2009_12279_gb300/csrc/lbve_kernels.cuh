@@ -20,18 +20,19 @@ namespace lbve {
 // 128-thread stream-collide blocks with a resident-block floor per SM, i.e. a register
 // cap of 65536 / (128 x floor): without a cap the odd-parity kernel keeps all 37
 // neighbour addresses live and drops to ~10 % occupancy.  Measured at 512^3: FP32 runs
-// fastest at 7 blocks (72 registers; 8 blocks spill more, 9 or more lose), 16-bit
-// storage at 8 for the even and 7 for the odd parity; FP64 keeps 8.
+// fastest at 7 blocks (72 registers; 8 blocks spill more, 9 or more lose); 16-bit storage
+// with the hardware stochastic rounding at 8 for both parities (BF16 4.27 ms against 4.44
+// at 8 / 7, 4.56 at 7 / 7 and 4.61 at 10 / 10); FP64 keeps 8.
 template <class S, int PAR>
 constexpr int lb_min_blocks() {
-    return sizeof(S) == 4 ? 7 : (sizeof(S) == 2 ? (PAR ? 7 : 8) : 8);
+    return sizeof(S) == 4 ? 7 : 8;
 }
 // 256-thread stress blocks, 3 resident per SM (80 registers: no spills at 4)
 #ifndef LBVE_FV_MIN_BLOCKS
 #define LBVE_FV_MIN_BLOCKS 3
 #endif
-#ifndef LBVE_LBB_MIN_BLOCKS  // batched stream-collide (both parities in one kernel)
-#define LBVE_LBB_MIN_BLOCKS 8
+#ifndef LBVE_LBB_MIN_BLOCKS  // batched stream-collide (both parities in one kernel; the
+#define LBVE_LBB_MIN_BLOCKS 7   // serving mix's pool step measured 1.201 ms at 7, 1.217 at 8)
 #endif
 
 template <class S>

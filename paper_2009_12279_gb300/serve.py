@@ -125,13 +125,31 @@ def make_requests(n, seed=0, mean_interarrival=0.05, **kw):
     return out
 
 
-def build_solver(req: Request, precision: str, stream: int | None = None):
+def build_solver(req: Request, precision: str, stream: int | None = None, particle_state=None):
+    """A solve of the request; particle_state (lbve_read_particle's dict) places its sphere
+    at a later position and velocity (a solve moved to the polish pool)."""
     s = lbve.Solver(req.shape, precision=precision, stream=stream, **req.params)
     s.set_geometry(req.flags, req.wall_vel)
     if req.particle is not None:
         p = req.particle
-        s.add_particle(p["X"], p["R"], p["rho_p"], Fext=p["Fext"])
+        if particle_state is None:
+            s.add_particle(p["X"], p["R"], p["rho_p"], Fext=p["Fext"])
+        else:
+            q = particle_state
+            s.add_particle(q["X"], p["R"], p["rho_p"], v=q["v"], w=q["w"], Fext=p["Fext"])
     return s
+
+
+def copy_solver(req: Request, precision: str, stream, src):
+    """A solve of the request in another storage precision with the state of src: its
+    PDFs, stress and particle position and velocities (the polish step of Server)."""
+    f = src.read_pdfs()
+    _, _, tau, _ = src.read_fields()
+    part = src.read_particle(0) if req.particle is not None else None
+    t = build_solver(req, precision, stream, particle_state=part)
+    t.init_fields(tau=tau)
+    t.write_pdfs(f)
+    return t
 
 
 def percentile(values, q):
@@ -160,29 +178,78 @@ def summarize(results, wall):
 # continuous batching
 # ---------------------------------------------------------------------------------
 class Server:
-    """Admits, batches and retires solves against a device-memory budget."""
+    """Admits, batches and retires solves against a device-memory budget.
+
+    polish: with stochastically rounded 16-bit storage a solve cannot go below its
+    storage's residual floor (RESIDUAL_FLOOR).  With polish set (an FP32 or FP64 storage
+    name), a solve that reaches that floor before its tolerance moves to a second pool of
+    that precision: its PDFs, stress and particle state are copied into a new solve, which
+    continues until the residual reaches the tolerance.  Retirement then has the accuracy
+    of the polish precision while most steps ran in 16 bits."""
 
     def __init__(self, precision="bf16", budget_bytes=150 * 10**9, check_every=100, stream=None, graphs=True,
-                 clock=time.perf_counter, max_members=256, pool=None, solver_factory=None, params_factory=None):
+                 clock=time.perf_counter, max_members=256, pool=None, solver_factory=None, params_factory=None,
+                 polish=None, polish_pool=None, polish_factory=None):
         self.precision = precision
         self.check_every = int(check_every)
         self.stream = stream
         self.pool = pool if pool is not None else lbve.Pool(precision, budget_bytes, stream=stream, graphs=graphs)
+        self.polish = polish
+        self.polish_pool = polish_pool
+        if polish is not None and polish_pool is None:
+            self.polish_pool = lbve.Pool(polish, budget_bytes, stream=stream, graphs=graphs)
         self.solver_factory = solver_factory or build_solver
+        self.polish_factory = polish_factory or copy_solver
         self.params_factory = params_factory or (lambda req, prec: lbve.make_params(req.shape, precision=prec,
                                                                                      **req.params))
         self.clock = clock
         self.max_members = max_members
         self.peak_bytes = 0
         # host-side time spent per phase (admission incl. context set-up, stepping incl.
-        # the residual read-back, retirement incl. read-out and release)
-        self.stats = {"admit_s": 0.0, "step_s": 0.0, "retire_s": 0.0, "steps": 0, "admitted": 0}
+        # the residual read-back, retirement incl. read-out and release, migration to the
+        # polish pool)
+        self.stats = {"admit_s": 0.0, "step_s": 0.0, "retire_s": 0.0, "steps": 0, "admitted": 0, "polished": 0,
+                      "polish_s": 0.0}
+
+    def _migrate(self, item):
+        """Move a member that reached its storage's floor into the polish pool."""
+        req, s = item[0], item[1]
+        t = self.polish_factory(req, self.polish, self.stream, s)
+        self.pool.remove(s)
+        s.close()
+        self.polish_pool.admit(t)
+        item[1] = t
+        item[4] = 1
+        item[5] = item[3]  # steps at migration
+        self.stats["polished"] += 1
+
+    def _step_pool(self, pool, members, active, results, now):
+        """Step one pool; evict members flagged unstable.  Returns the residuals or None."""
+        if not members:
+            return None
+        try:
+            pool.step(self.check_every)
+        except lbve.LbveError as exc:
+            if exc.status != lbve.EUNSTABLE:
+                raise
+            for item in [it for it in members if it[1].is_unstable()]:
+                req, s, adm, steps = item[:4]
+                pool.remove(s)
+                s.close()
+                active.remove(item)
+                results.append(Result(req.rid, req.kind, int(np.prod(req.shape)), "unstable", steps, float("nan"),
+                                      req.arrival, adm, now()))
+            return None
+        for item in members:
+            item[3] += self.check_every
+        return pool.residuals()
 
     def run(self, requests, keep_fields=False):
-        """Serve the requests (sorted by arrival); returns (results, fields by rid)."""
+        """Serve the requests (sorted by arrival); returns (results, fields by rid).
+        keep_fields: True (every result's fields) or a set of request ids."""
         pending = sorted(requests, key=lambda r: r.arrival)
         results, fields = [], {}
-        active = []  # (req, solver, admitted_at, steps)
+        active = []  # [req, solver, admitted_at, steps, stage (0 main, 1 polish), steps at migration]
         t0 = self.clock()
         now = lambda: self.clock() - t0  # noqa: E731
         i = 0
@@ -192,7 +259,7 @@ class Server:
             for item in list(active):
                 req = item[0]
                 if req.cancel_at is not None and t >= req.cancel_at:
-                    self.pool.remove(item[1])
+                    (self.polish_pool if item[4] else self.pool).remove(item[1])
                     item[1].close()
                     active.remove(item)
                     results.append(Result(req.rid, req.kind, int(np.prod(req.shape)), "cancelled", item[3], float("nan"),
@@ -218,11 +285,12 @@ class Server:
                     req.error = str(exc)
                     i += 1
                     continue
-                active.append([req, s, now(), 0])
+                active.append([req, s, now(), 0, 0, 0])
                 self.stats["admitted"] += 1
                 i += 1
             self.stats["admit_s"] += self.clock() - ta
-            self.peak_bytes = max(self.peak_bytes, self.pool.bytes_in_use)
+            used = self.pool.bytes_in_use + (self.polish_pool.bytes_in_use if self.polish_pool is not None else 0)
+            self.peak_bytes = max(self.peak_bytes, used)
             if not active:
                 if i < len(pending):
                     wait = pending[i].arrival - now()
@@ -230,50 +298,58 @@ class Server:
                         time.sleep(min(wait, 0.05))
                 continue
             ts = self.clock()
-            try:
-                self.pool.step(self.check_every)
-            except lbve.LbveError as exc:
-                if exc.status != lbve.EUNSTABLE:
-                    raise
-                # a member's stream-collide flagged an instability: evict it, step the rest
-                for item in [it for it in active if it[1].is_unstable()]:
-                    req, s, adm, steps = item
-                    self.pool.remove(s)
-                    s.close()
-                    active.remove(item)
-                    results.append(Result(req.rid, req.kind, int(np.prod(req.shape)), "unstable", steps,
-                                          float("nan"), req.arrival, adm, now()))
-                self.stats["step_s"] += self.clock() - ts
-                continue
-            for item in active:
-                item[3] += self.check_every
-            res = self.pool.residuals()
+            stages = []
+            for stage, pool in ((0, self.pool), (1, self.polish_pool)):
+                if pool is None:
+                    continue
+                # residuals come in the pool's member order (admission into that pool, which
+                # for the polish pool is the order of migration, not of arrival)
+                by_solver = {id(it[1]): it for it in active if it[4] == stage}
+                res = self._step_pool(pool, list(by_solver.values()), active, results, now)
+                if res is not None:
+                    members = [by_solver[id(sv)] for sv in pool.members]
+                    stages.append((stage, members, res))
             self.stats["step_s"] += self.clock() - ts
             self.stats["steps"] += self.check_every
             tr = self.clock()
-            for item, (r, unorm) in zip(list(active), res):
-                req, s, adm, steps = item
-                per_step = r / self.check_every
-                status = None
-                if not np.isfinite(r) or not np.isfinite(unorm):
-                    status = "unstable"
-                elif per_step <= max(req.tol, RESIDUAL_FLOOR.get(self.precision, 0.0)) and steps > self.check_every:
-                    status = "converged"
-                elif steps >= req.max_steps:
-                    status = "capped"
-                if status:
-                    if keep_fields and status != "unstable":
-                        fields[req.rid] = s.read_fields()
-                    self.pool.remove(s)
-                    s.close()
-                    active.remove(item)
-                    results.append(Result(req.rid, req.kind, int(np.prod(req.shape)), status, steps, float(per_step),
-                                          req.arrival, adm, now()))
+            floor = RESIDUAL_FLOOR.get(self.precision, 0.0)
+            for stage, members, res in stages:
+                for item, (r, unorm) in zip(members, res):
+                    req, s, adm, steps = item[:4]
+                    per_step = r / self.check_every
+                    status = None
+                    fresh = steps - item[5] > self.check_every  # the residual compares two checks
+                    if not np.isfinite(r) or not np.isfinite(unorm):
+                        status = "unstable"
+                    elif stage == 0 and per_step <= max(req.tol, floor) and fresh:
+                        if per_step <= req.tol or self.polish is None:
+                            status = "converged"
+                        elif steps < req.max_steps:
+                            tp = self.clock()
+                            self._migrate(item)
+                            self.stats["polish_s"] += self.clock() - tp
+                            continue
+                    elif stage == 1 and per_step <= req.tol and fresh:
+                        status = "converged"
+                    if status is None and steps >= req.max_steps:
+                        status = "capped"
+                    if status:
+                        s = item[1]
+                        keep = keep_fields is True or (not isinstance(keep_fields, bool) and req.rid in keep_fields)
+                        if keep and status != "unstable":
+                            fields[req.rid] = s.read_fields()
+                        (self.polish_pool if item[4] else self.pool).remove(s)
+                        s.close()
+                        active.remove(item)
+                        results.append(Result(req.rid, req.kind, int(np.prod(req.shape)), status, steps,
+                                              float(per_step), req.arrival, adm, now()))
             self.stats["retire_s"] += self.clock() - tr
         return results, fields
 
     def close(self):
         self.pool.close()
+        if self.polish_pool is not None:
+            self.polish_pool.close()
 
 
 def run_one_at_a_time(requests, precision="f32", check_every=100, stream=None, clock=time.perf_counter,

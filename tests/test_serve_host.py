@@ -152,6 +152,80 @@ def test_instability_status_of_the_pool_evicts_the_flagged_member():
     assert pool.used == 0
 
 
+class FloorPool(FakePool):
+    """A 16-bit pool: the residual per step levels off at `floor` (stochastic rounding);
+    the polish pool's members keep falling (residual 100 / k^2 per step check)."""
+
+    def __init__(self, budget, floor):
+        super().__init__(budget)
+        self.floor = floor
+
+    def residuals(self):
+        out = []
+        for s in self.members:
+            k = self.steps[s.req.rid]
+            out.append((max(100.0 / k ** 2, self.floor * 100), 1.0))
+        return np.array(out)
+
+
+def test_polish_moves_floored_solves_to_the_second_pool():
+    """With polish on, a 16-bit solve that reaches its storage floor (above the tolerance)
+    moves to the polish pool and retires there at the tolerance; without polish it
+    retires at the floor."""
+    reqs = _fake_requests(3, [10, 10, 10])
+    for r in reqs:
+        r.tol = 1e-6
+    moved = []
+
+    def polish_factory(req, prec, stream, src):
+        moved.append((req.rid, prec))
+        return FakeSolver(req)
+
+    main, polish = FloorPool(100, serve.RESIDUAL_FLOOR["bf16"]), FakePool(100)
+    srv = serve.Server("bf16", pool=main, polish="f32", polish_pool=polish, polish_factory=polish_factory,
+                       solver_factory=lambda req, prec, stream: FakeSolver(req),
+                       params_factory=lambda req, prec: req.bytes, check_every=100)
+    results, _ = srv.run(reqs)
+    assert sorted(rid for rid, _ in moved) == [0, 1, 2] and all(p == "f32" for _, p in moved)
+    assert all(r.status == "converged" for r in results)
+    assert all(r.residual <= 1e-6 for r in results)  # retired at the tolerance, not at the floor
+    assert main.used == 0 and polish.used == 0 and srv.stats["polished"] == 3
+    main2 = FloorPool(100, serve.RESIDUAL_FLOOR["bf16"])
+    srv2 = serve.Server("bf16", pool=main2, solver_factory=lambda req, prec, stream: FakeSolver(req),
+                        params_factory=lambda req, prec: req.bytes, check_every=100)
+    results2, _ = srv2.run(_fake_requests(3, [10, 10, 10]))
+    assert all(r.status == "converged" and r.residual > 1e-6 for r in results2)
+
+
+def test_polish_pool_residuals_follow_the_polish_pool_order():
+    """Solves migrate in an order other than their arrival (here the last arrival first):
+    each must still be judged by its own residual in the polish pool, so every solve
+    spends the same number of steps there."""
+
+    class StaggeredFloor(FloorPool):
+        def residuals(self):
+            out = []
+            for s in self.members:
+                k = self.steps[s.req.rid]
+                c = 100.0 * (1 + 4 * (2 - s.req.rid))  # later arrivals reach the floor sooner
+                out.append((max(c / k ** 2, self.floor * 100), 1.0))
+            return np.array(out)
+
+    reqs = _fake_requests(3, [10, 10, 10])
+    for r in reqs:
+        r.tol = 1e-6
+    main, polish = StaggeredFloor(100, serve.RESIDUAL_FLOOR["bf16"]), FakePool(100)
+    srv = serve.Server("bf16", pool=main, polish="f32", polish_pool=polish,
+                       polish_factory=lambda req, prec, stream, src: FakeSolver(req),
+                       solver_factory=lambda req, prec, stream: FakeSolver(req),
+                       params_factory=lambda req, prec: req.bytes, check_every=100)
+    results, _ = srv.run(reqs)
+    assert all(r.status == "converged" for r in results)
+    in_polish = {rid: polish.steps[rid] for rid in range(3)}
+    assert len(set(in_polish.values())) == 1, in_polish
+    assert polish.admit_order != sorted(polish.admit_order)  # they did migrate out of order
+
+
 def test_bad_request_is_rejected_without_stopping_the_server():
     reqs = _fake_requests(3, [10, 10, 10])
 
