@@ -612,7 +612,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--n", type=int, default=512, help="side of the cubic throughput domain")
-    ap.add_argument("--precisions", default="f32,f16", help="PDF storage modes; the first one is the headline")
+    ap.add_argument("--precisions", default="f32,f16,bf16", help="PDF storage modes; the first one is the headline")
     ap.add_argument("--schedule", choices=["auto", "split", "fused"], default="auto")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")

@@ -125,7 +125,10 @@ typedef struct {
 } lbve_params;
 
 /* Optional device allocator (e.g. a framework's caching allocator).  alloc returns a
- * device pointer of at least `bytes` usable on `stream`, or NULL on failure. */
+ * device pointer of at least `bytes` usable on `stream`, or NULL on failure; blocks must
+ * be at least 8-byte aligned.  With 16-byte aligned stress and velocity arrays (as from
+ * cudaMalloc) and nx a multiple of 4, the stress kernel stages its planes by 16-byte
+ * copies, else by 4-byte copies; the results are the same. */
 typedef void *(*lbve_alloc_fn)(size_t bytes, void *stream, void *user);
 typedef void (*lbve_free_fn)(void *ptr, size_t bytes, void *stream, void *user);
 
@@ -159,7 +162,9 @@ lbve_status lbve_set_geometry(lbve_ctx *ctx, const uint8_t *flags, const double 
 
 /*
  * Initial fields (host arrays, each may be NULL): rho (n), u (3n), tau (6n).  The
- * PDFs are set to the equilibrium of Eq. (lb-equilibrium) at (rho, u); tau is copied.
+ * PDFs are set to the equilibrium of Eq. (lb-equilibrium) at (rho, u); tau is copied
+ * into the fluid cells (non-fluid cells hold zero stress, here and after
+ * lbve_set_geometry, which zeroes it in the cells it makes solid).
  * Resets the time counter to 0.  Particle cells keep their state.  Page-locked arrays
  * the device can address (cudaHostAlloc, cudaHostRegister) are read in place by one
  * kernel; other host memory goes through device staging in z-slabs.  Synchronises.
@@ -320,6 +325,8 @@ lbve_status lbve_read_kernel_times(lbve_ctx *ctx, double ms[LBVE_KT_COUNT], long
  *   flags  n bytes: 0 fluid, 1 no-slip, LBVE_FLAG_WALL0 + k wall class k < n_wall
  *          (velocities in wall_vel, host, 3 doubles each); particle flags act as
  *          resting walls.  Momentum-exchange forces are not computed by this call.
+ *          The call sets the stress of every non-fluid cell to zero in tau_a and tau_b
+ *          (a solid cell carries no stress; the stress update relies on it).
  * Schedule: always the split kernels.  p->schedule must be LBVE_SCHED_AUTO or
  * LBVE_SCHED_SPLIT (LBVE_SCHED_FUSED is rejected with EINVAL); p->block_x is honoured as
  * by lbve_create, but schedules recorded by lbve_autotune are not applied and the stress

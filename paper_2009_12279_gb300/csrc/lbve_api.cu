@@ -1399,9 +1399,16 @@ struct lbve_pool {
     std::vector<lbve_ctx *> members;
     std::vector<size_t> member_bytes;
     std::string err;
-    // packed work list, built from the members' state when the membership changes; a step
-    // k after the build swaps the stress ping-pong and the AA parity k times
+    // packed work lists, built from the members' state when the membership changes; a step
+    // k after the build swaps the stress ping-pong and the AA parity k times.  entries[0]:
+    // the members grouped by stress tile width (one stress launch per group); entries[1]:
+    // the members grouped by their AA parity at the build (one stream-collide launch per
+    // group, lb_class[p] = {first entry, entries, work items} of the group of parity p)
     void *entries[2] = {nullptr, nullptr};
+    struct LbClass {
+        int start = 0, n = 0, total = 0;
+    };
+    LbClass lb_class[2];
     size_t entries_cap = 0;
     // particle-phase entries of the members with particles (one block each per step)
     void *pentries = nullptr;
@@ -1502,6 +1509,29 @@ lbve_status build_entries(lbve_pool *P) {
     if (slot != n) return pfail(P, LBVE_ECUDA, "internal: stress tile of a member not covered");
     P->total_lb = lb_first;
     if (n) PCK(cudaMemcpyAsync(P->entries[0], host.data(), eb * n, cudaMemcpyHostToDevice, P->stream), "upload entries");
+    // stream-collide lists: the members by AA parity at the build, items numbered per list
+    std::vector<unsigned char> host_lb(eb * std::max<size_t>(n, 1));
+    slot = 0;
+    for (int par = 0; par < 2; ++par) {
+        lbve_pool::LbClass &cl = P->lb_class[par];
+        cl.start = (int)slot;
+        cl.n = 0;
+        int first = 0;
+        for (size_t m = 0; m < n; ++m) {
+            const lbve_ctx *c = P->members[m];
+            if ((int)(c->t & 1) != par) continue;
+            DevState d = c->d;
+            d.step = (unsigned)c->t;
+            int lbi = 0, fvi = 0;
+            P->kt->fill_entry(d, par, first, 0, 0, c->lb_tx, c->fv_tx, host_lb.data() + eb * slot, &lbi, &fvi);
+            first += lbi;
+            ++slot;
+            ++cl.n;
+        }
+        cl.total = first;
+    }
+    if (n) PCK(cudaMemcpyAsync(P->entries[1], host_lb.data(), eb * n, cudaMemcpyHostToDevice, P->stream),
+               "upload stream-collide entries");
     // particle-phase entries, in member order
     const size_t pb = P->kt->part_entry_bytes;
     std::vector<unsigned char> phost;
@@ -1599,7 +1629,13 @@ lbve_status enqueue_steps(lbve_pool *P, int q, int nsteps) {
             return LBVE_OK;
         });
         if (s != LBVE_OK) return s;
-        PCK(P->kt->lb_batched(P->entries[0], n, P->total_lb, kk, P->grid_lb, P->dstep, P->stream), "batched lb");
+        for (int par = 0; par < 2; ++par) {  // the group of build parity par is at parity (par + kk) & 1
+            const lbve_pool::LbClass &cl = P->lb_class[par];
+            if (cl.n == 0) continue;
+            PCK(P->kt->lb_batched((const unsigned char *)P->entries[1] + (size_t)cl.start * P->kt->batch_entry_bytes,
+                                  cl.n, cl.total, kk, P->grid_lb, P->dstep, (par + kk) & 1, P->stream),
+                "batched lb");
+        }
         k_step_count<<<1, 1, 0, P->stream>>>(P->dstep);
         PCK(cudaGetLastError(), "step counter");
         for (const lbve_pool::FvGroup &grp : P->fv_groups)

@@ -483,35 +483,61 @@ __device__ __forceinline__ bool collide(R (&f)[Q], R rho, R drho, const R u[3], 
 // the donor cell's transverse overlap (1 - |u_a|)(1 - |u_b|); ph.divu_on adds tau div u
 // to the source; ph.gk != 0 adds the Giesekus term -(alpha / eta_p)(tau . tau) to it
 // (with the source on).  With VAR false the method's own update is all that is compiled.
-// nb.u(l, k), nb.tau(l, c): velocity / stress of the face-l neighbour (fluid only);
-// nb.ub(l, out): boundary velocity of a solid face-l neighbour.
+// nb.u(l, k), nb.tau(l, c): velocity / stress of the face-l neighbour (FP64 reads them
+// for fluid neighbours only; the shifted modes read every face neighbour, a solid cell
+// holding zero stress); nb.ub(l, out): boundary velocity of a solid face-l neighbour.
 // FP64 mode keeps the face-by-face order of the plain statement; shifted modes gather
 // the outflow as (sum of outgoing face velocities) * tau(r).
 template <class R, bool SH, bool VAR, class Nb>
 __device__ __forceinline__ void fv_core(const Phys<R> &ph, const R (&tr)[6], const R (&ur)[3], uint32_t mask,
                                         const Nb &nb, R out[6]) {
     R un[6][3];
-#pragma unroll
-    for (int l = 0; l < 6; ++l) {
-        if (!nb_solid(mask, l + 1)) {
-#pragma unroll
-            for (int j = 0; j < 3; ++j) un[l][j] = nb.u(l, j);
-        } else if (mask & MASK_MOVING) {
-            nb.ub(l, un[l]);
-        } else {  // a resting no-slip wall
-#pragma unroll
-            for (int j = 0; j < 3; ++j) un[l][j] = R(0);
-        }
-    }
     R G[3][3];
+    if constexpr (SH) {
+        // Branch-light form: every face neighbour's u is read (the staged halo and the
+        // periodically wrapped global neighbours are valid memory), and a solid face's u
+        // is replaced by the mirror value 2 u_b - u(r), whose average with u(r) is the
+        // face value u_b; the gradient is then half the difference of the two mirrored
+        // neighbours on every axis.  Only cells next to a moving boundary branch.
 #pragma unroll
-    for (int k = 0; k < 3; ++k) {
-        const bool fp_ = !nb_solid(mask, 2 * k + 1), fm_ = !nb_solid(mask, 2 * k + 2);
+        for (int k = 0; k < 3; ++k) {
 #pragma unroll
-        for (int j = 0; j < 3; ++j) {
-            const R up = fp_ ? R(0.5) * (ur[j] + un[2 * k][j]) : un[2 * k][j];
-            const R um = fm_ ? R(0.5) * (ur[j] + un[2 * k + 1][j]) : un[2 * k + 1][j];
-            G[k][j] = up - um;
+            for (int h = 0; h < 2; ++h) {
+                const int l = 2 * k + h;
+#pragma unroll
+                for (int j = 0; j < 3; ++j) un[l][j] = nb_solid(mask, l + 1) ? -ur[j] : nb.u(l, j);
+                if ((mask & MASK_MOVING) && nb_solid(mask, l + 1)) {
+                    R ub[3];
+                    nb.ub(l, ub);
+#pragma unroll
+                    for (int j = 0; j < 3; ++j) un[l][j] = R(2) * ub[j] - ur[j];
+                }
+            }
+#pragma unroll
+            for (int j = 0; j < 3; ++j) G[k][j] = R(0.5) * (un[2 * k][j] - un[2 * k + 1][j]);
+        }
+    } else {
+#pragma unroll
+        for (int l = 0; l < 6; ++l) {
+            if (!nb_solid(mask, l + 1)) {
+#pragma unroll
+                for (int j = 0; j < 3; ++j) un[l][j] = nb.u(l, j);
+            } else if (mask & MASK_MOVING) {
+                nb.ub(l, un[l]);
+            } else {  // a resting no-slip wall
+#pragma unroll
+                for (int j = 0; j < 3; ++j) un[l][j] = R(0);
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            const bool fp_ = !nb_solid(mask, 2 * k + 1), fm_ = !nb_solid(mask, 2 * k + 2);
+#pragma unroll
+            for (int j = 0; j < 3; ++j) {
+                const R up = fp_ ? R(0.5) * (ur[j] + un[2 * k][j]) : un[2 * k][j];
+                const R um = fm_ ? R(0.5) * (ur[j] + un[2 * k + 1][j]) : un[2 * k + 1][j];
+                G[k][j] = up - um;
+            }
         }
     }
     R net[6] = {R(0), R(0), R(0), R(0), R(0), R(0)};
@@ -544,11 +570,13 @@ __device__ __forceinline__ void fv_core(const Phys<R> &ph, const R (&tr)[6], con
             for (int l = 0; l < 6; ++l) {
                 const int k = l >> 1;
                 const int s = (l & 1) ? -1 : 1;
-                if (nb_solid(mask, l + 1)) continue;
+                // zero flux across a solid link: both coefficients selected to zero (a
+                // solid cell's stress is finite, so the inflow product below adds zero)
+                const bool open = !nb_solid(mask, l + 1);
                 const R vout = s > 0 ? ur[k] : -ur[k];
                 const R vin = s > 0 ? -un[l][k] : un[l][k];
-                R ao = vout > R(0) ? vout : R(0);
-                R b = vin > R(0) ? vin : R(0);
+                R ao = (open && vout > R(0)) ? vout : R(0);
+                R b = (open && vin > R(0)) ? vin : R(0);
                 if (VAR && ph.ctu_on) {
                     const int ta = k == 2 ? 0 : k + 1, tb = k == 0 ? 2 : k - 1;
                     ao *= (R(1) - fabs(ur[ta])) * (R(1) - fabs(ur[tb]));
@@ -562,10 +590,10 @@ __device__ __forceinline__ void fv_core(const Phys<R> &ph, const R (&tr)[6], con
             for (int c = 0; c < 6; ++c) net[c] = aout * tr[c] - inflow[c];
         }
     }
+    R Sv[6] = {R(0), R(0), R(0), R(0), R(0), R(0)};
+    if (ph.src_on) {  // one test for all six components
 #pragma unroll
-    for (int c = 0; c < 6; ++c) {
-        R S = R(0);
-        if (ph.src_on) {
+        for (int c = 0; c < 6; ++c) {
             const int i = comp_i(c), j = comp_j(c);
             R a = R(0), b = R(0);
 #pragma unroll
@@ -575,11 +603,15 @@ __device__ __forceinline__ void fv_core(const Phys<R> &ph, const R (&tr)[6], con
             if (VAR && ph.fene) {
                 // FENE-P conformation: A.grad u + (A.grad u)^T - (f A - I) / lambda
                 const R fA = fene_factor<R>(ph, tr[0], tr[1], tr[2]);
-                S = a + b - ph.inv_l * (c < 3 ? fA * tr[c] - R(1) : fA * tr[c]);
+                Sv[c] = a + b - ph.inv_l * (c < 3 ? fA * tr[c] - R(1) : fA * tr[c]);
             } else {
-                S = a + b + ph.ep_l * (G[i][j] + G[j][i]) - ph.inv_l * tr[c];
+                Sv[c] = a + b + ph.ep_l * (G[i][j] + G[j][i]) - ph.inv_l * tr[c];
             }
         }
+    }
+#pragma unroll
+    for (int c = 0; c < 6; ++c) {
+        R S = Sv[c];
         if (VAR && ph.divu_on) S = S + tr[c] * ((G[0][0] + G[1][1]) + G[2][2]);
         if (VAR && ph.src_on && ph.gk != R(0)) {
             const int i = comp_i(c), j = comp_j(c);

@@ -11,6 +11,7 @@
 #pragma once
 
 #include <cstddef>
+#include <type_traits>
 
 #include "lbve_device.cuh"
 #include "lbve_launch.h"
@@ -20,12 +21,12 @@ namespace lbve {
 // 128-thread stream-collide blocks with a resident-block floor per SM, i.e. a register
 // cap of 65536 / (128 x floor): without a cap the odd-parity kernel keeps all 37
 // neighbour addresses live and drops to ~10 % occupancy.  Measured at 512^3: FP32 runs
-// fastest at 7 blocks (72 registers; 8 blocks spill more, 9 or more lose); 16-bit storage
-// with the hardware stochastic rounding at 8 for both parities (BF16 4.27 ms against 4.44
-// at 8 / 7, 4.56 at 7 / 7 and 4.61 at 10 / 10); FP64 keeps 8.
+// fastest at 7 blocks (72 registers; 8 blocks spill more, 9 or more lose); with the
+// stochastically rounded 16-bit stores BF16 at 7 (4.00 ms against 4.03 at 8) and FP16 at
+// 8 (4.03 ms against 4.09 at 7); FP64 keeps 8.
 template <class S, int PAR>
 constexpr int lb_min_blocks() {
-    return sizeof(S) == 4 ? 7 : 8;
+    return (sizeof(S) == 4 || std::is_same<S, __nv_bfloat16>::value) ? 7 : 8;
 }
 // 256-thread stress blocks, 3 resident per SM (80 registers: no spills at 4)
 #ifndef LBVE_FV_MIN_BLOCKS
@@ -125,7 +126,23 @@ __device__ __forceinline__ void store_pdfs(const KArgs<S> &a, const Cell &cl, un
         const uint32_t h = fmix32((r + a.key_base) ^ (a.step * 0x9E3779B9u));
         const uint32_t d0 = Store<S>::round2(fs[0], fs[0], sc, pair_bits(h, 0));
         Store<S>::store16(a.fq[0] + r, d0);
-        const bool uniform = !__any_sync(__activemask(), moving);
+        if (!__any_sync(__activemask(), moving)) {
+            // no lane of the warp next to a moving boundary: every bounce is a predicated
+            // store of the normal store's bits
+#pragma unroll
+            for (int i = 1; i < Q; i += 2) {
+                const uint32_t d = Store<S>::round2(fs[i], fs[i + 1], sc, pair_bits(h, (i + 1) >> 1));
+#pragma unroll
+                for (int q = 0; q < 2; ++q) {
+                    const int j = i + q;
+                    const uint32_t bits = q == 0 ? d >> 16 : d;
+                    const unsigned nb = cl.idx(cx(j), cy(j), cz(j));
+                    Store<S>::store16(PAR == 0 ? a.fq[copp(j)] + r : a.fq[j] + nb, bits);
+                    if (nb_solid(mask, j)) Store<S>::store16(PAR == 0 ? a.fq[j] + nb : a.fq[copp(j)] + r, bits);
+                }
+            }
+            return;
+        }
 #pragma unroll
         for (int i = 1; i < Q; i += 2) {
             const uint32_t d = Store<S>::round2(fs[i], fs[i + 1], sc, pair_bits(h, (i + 1) >> 1));
@@ -137,17 +154,13 @@ __device__ __forceinline__ void store_pdfs(const KArgs<S> &a, const Cell &cl, un
                 Store<S>::store16(PAR == 0 ? a.fq[copp(j)] + r : a.fq[j] + nb, bits);
                 if (!nb_solid(mask, j)) continue;
                 S *dst = PAR == 0 ? a.fq[j] + nb : a.fq[copp(j)] + r;
-                if (uniform) {  // no lane of the warp next to a moving boundary
-                    Store<S>::store16(dst, bits);
-                } else {
-                    const int fl = moving ? (int)a.flag[nb] : FLAG_NOSLIP;
-                    const R X = fl == FLAG_NOSLIP ? R(0)
-                                                  : moving_wall_term<R>(a.g, a.ph, a.parts, fl, cl.X(cx(j)), cl.Y(cy(j)),
-                                                                        cl.Z(cz(j)), j, rho);
-                    // a boundary at rest (X exactly zero) bounces the normal store's bits
-                    Store<S>::store16(dst, X == R(0) ? bits
-                                                     : Store<S>::round2(fs[j] - X, fs[j] - X, sc, pair_bits(h, Q + j)));
-                }
+                const int fl = moving ? (int)a.flag[nb] : FLAG_NOSLIP;
+                const R X = fl == FLAG_NOSLIP ? R(0)
+                                              : moving_wall_term<R>(a.g, a.ph, a.parts, fl, cl.X(cx(j)), cl.Y(cy(j)),
+                                                                    cl.Z(cz(j)), j, rho);
+                // a boundary at rest (X exactly zero) bounces the normal store's bits
+                Store<S>::store16(dst, X == R(0) ? bits
+                                                 : Store<S>::round2(fs[j] - X, fs[j] - X, sc, pair_bits(h, Q + j)));
             }
         }
         return;
@@ -325,9 +338,15 @@ __device__ __forceinline__ uint32_t cell_mask(const Geo &g, const uint8_t *__res
     return m;
 }
 
+// Neighbour masks of the cells of a box (periodically wrapped); a non-fluid cell's stress
+// is set to zero in both stress buffers, so that every solid cell holds zero stress (the
+// shifted-mode stress update reads its face neighbours' stress without a solid test and
+// selects a zero coefficient for a solid face).
 template <class S>
 __global__ void k_build_mask(Geo g, const uint8_t *__restrict__ flag, uint32_t *__restrict__ mask, int lx, int ly,
-                             int lz, int ex, int ey, int ez) {
+                             int lz, int ex, int ey, int ez, typename Store<S>::R *__restrict__ tau0,
+                             typename Store<S>::R *__restrict__ tau1) {
+    using R = typename Store<S>::R;
     const long long cells = (long long)ex * ey * ez;
     for (long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x; k < cells;
          k += (long long)gridDim.x * blockDim.x) {
@@ -335,7 +354,16 @@ __global__ void k_build_mask(Geo g, const uint8_t *__restrict__ flag, uint32_t *
         const int x = ((lx + ix) % g.nx + g.nx) % g.nx;
         const int y = ((ly + iy) % g.ny + g.ny) % g.ny;
         const int z = ((lz + iz) % g.nz + g.nz) % g.nz;
-        mask[(unsigned)x + (unsigned)g.nx * ((unsigned)y + (unsigned)g.ny * (unsigned)z)] = cell_mask(g, flag, x, y, z);
+        const unsigned r = (unsigned)x + (unsigned)g.nx * ((unsigned)y + (unsigned)g.ny * (unsigned)z);
+        const uint32_t m = cell_mask(g, flag, x, y, z);
+        mask[r] = m;
+        if (m & 1u) {
+#pragma unroll
+            for (int c = 0; c < 6; ++c) {
+                tau0[c * (size_t)g.np + r] = R(0);
+                tau1[c * (size_t)g.np + r] = R(0);
+            }
+        }
     }
 }
 
@@ -379,6 +407,21 @@ __device__ __forceinline__ void cp_async_real(R *dst, const R *src) {
         cp_async8(dst, src);
     else
         cp_async4(dst, src);
+}
+// Copy of one real that reads n (sizeof(R) or 0) bytes and zero-fills the rest: n = 0
+// writes a zero without reading src (which must still be a valid address).
+// 16-byte copy that reads n (16 or 0) bytes: both addresses 16-byte aligned
+__device__ __forceinline__ void cp_async16_zfill(void *dst, const void *src, unsigned n) {
+    const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(d), "l"(src), "r"(n));
+}
+template <class R>
+__device__ __forceinline__ void cp_async_real_zfill(R *dst, const R *src, unsigned n) {
+    const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+    if constexpr (sizeof(R) == 8)
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;\n" ::"r"(d), "l"(src), "r"(n));
+    else
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;\n" ::"r"(d), "l"(src), "r"(n));
 }
 
 // wrapped coordinate along a side, or -1 outside a closed side
@@ -565,13 +608,16 @@ __global__ void __launch_bounds__(FT_X * FT_Y, sizeof(typename Store<S>::R) == 8
 // read of the update comes from shared memory.
 // ---------------------------------------------------------------------------------
 // Stress tiles: 256 threads over TX x (256 / TX) cells; the single-solve kernel uses
-// 32 x 8, the batched kernel picks 16 x 16, 32 x 8 or 64 x 4 per solve.
+// 32 x 8, the batched kernel picks 16 x 16, 32 x 8 or 64 x 4 per solve.  A staged halo
+// row holds the tile's TX cells from column XO on; W16 rows are widened to whole aligned
+// 16-byte chunks (4 cells on each side) so that they are staged by 16-byte copies.
 constexpr int FV_NT = 256;
 constexpr int FV_X = 32, FV_Y = FV_NT / FV_X;
-template <int TX>
+template <int TX, bool W16 = false>
 struct FvTile {
     static constexpr int TY = FV_NT / TX;
-    static constexpr int HX = TX + 2, HN = (TX + 2) * (TY + 2);  // halo row, halo cells
+    static constexpr int XO = W16 ? 4 : 1;
+    static constexpr int HX = TX + 2 * XO, HN = HX * (TY + 2);  // halo row, halo cells
 };
 constexpr int FVH_X = FV_X + 2, FVH_Y = FV_Y + 2, FVH_N = FVH_X * FVH_Y;
 
@@ -614,13 +660,17 @@ struct FvSmemNb {
 
 // Stress update of work item `item` (TX x TY tile, z-chunk) of one solve; VAR compiles in
 // the optional finite-volume variants, ZR the restriction to planes [zlo, zhi) of a
-// z-slab (a separate build: the plain one keeps its register budget).
-template <class S, int TX, bool VAR, bool ZR = false>
-__device__ __forceinline__ void fv_tile(const KArgs<S> &a, FvSmem<typename Store<S>::R, FvTile<TX>::HN> &sm, int item,
-                                        int zchunk) {
+// z-slab (a separate build: the plain one keeps its register budget).  W16 stages the
+// planes by 16-byte copies: 4-byte reals, nx a multiple of 4 and 16-byte aligned stress
+// and velocity arrays (the launcher checks); the result is the same either way.
+template <class S, int TX, bool VAR, bool ZR = false, bool W16 = false>
+__device__ __forceinline__ void fv_tile(const KArgs<S> &a, FvSmem<typename Store<S>::R, FvTile<TX, W16>::HN> &sm,
+                                        int item, int zchunk) {
     using R = typename Store<S>::R;
     constexpr bool SH = Store<S>::shifted;
-    constexpr int NT = FV_NT, TY = FvTile<TX>::TY, FVH_X = FvTile<TX>::HX, FVH_N = FvTile<TX>::HN;
+    using T = FvTile<TX, W16>;
+    constexpr int NT = FV_NT, TY = T::TY, FVH_X = T::HX, FVH_N = T::HN, XO = T::XO;
+    static_assert(!W16 || sizeof(R) == 4, "16-byte staging of 4-byte reals");
     static_assert(FVH_N <= 2 * NT, "two halo cells per thread at most");
     const int tid = threadIdx.x;
     const int tiles_x = (a.g.nx + TX - 1) / TX, tiles_y = (a.g.ny + TY - 1) / TY;
@@ -630,42 +680,71 @@ __device__ __forceinline__ void fv_tile(const KArgs<S> &a, FvSmem<typename Store
     const int z1 = ZR ? min(a.zhi, z0 + zchunk) : min(a.g.nz, z0 + zchunk);
     const size_t np = (size_t)a.g.np;
     const unsigned nx = (unsigned)a.g.nx, nxy = (unsigned)a.g.nx * (unsigned)a.g.ny;
-    int off[2];
-#pragma unroll
-    for (int q = 0; q < 2; ++q) {
-        const int k = tid + q * NT;
-        off[q] = -1;
-        if (k < FVH_N) {
-            const int xg = side_coord(x0 - 1 + k % FVH_X, a.g.nx, a.g.per[0]);
-            const int yg = side_coord(y0 - 1 + k / FVH_X, a.g.ny, a.g.per[1]);
-            if (xg >= 0 && yg >= 0) off[q] = xg + (int)nx * yg;
+    // 4-byte staging: halo cells tid and tid + NT of each plane (plane offsets, -1 beyond
+    // a closed side); 16-byte staging: one aligned 4-cell chunk of a halo row per thread
+    // (threads below CH: stress components 0..4; CH .. 2 CH - 1: component 5 and u)
+    constexpr int CPR = FVH_X / 4, CH = CPR * (TY + 2);
+    static_assert(!W16 || 2 * CH <= NT, "two threads per 16-byte chunk position at most");
+    int off[2] = {-1, -1};
+    int dpos = 0;
+    const int half = W16 ? tid / CH : 0;
+    if constexpr (W16) {
+        if (half < 2) {
+            const int p = tid - half * CH, row = p / CPR, cq = p - row * CPR;
+            dpos = row * FVH_X + 4 * cq;
+            const int xg = side_coord(x0 - XO + 4 * cq, a.g.nx, a.g.per[0]);
+            const int yg = side_coord(y0 - 1 + row, a.g.ny, a.g.per[1]);
+            if (xg >= 0 && yg >= 0) off[0] = xg + (int)nx * yg;
         }
-    }
-    auto stage = [&](int zz) {
-        const int zg = side_coord(zz, a.g.nz, a.g.per[2]);
-        const int s4 = fv_slot(zz);
+    } else {
 #pragma unroll
         for (int q = 0; q < 2; ++q) {
             const int k = tid + q * NT;
-            if (k >= FVH_N) continue;
-            if (off[q] < 0 || zg < 0) {
+            if (k < FVH_N) {
+                const int xg = side_coord(x0 - 1 + k % FVH_X, a.g.nx, a.g.per[0]);
+                const int yg = side_coord(y0 - 1 + k / FVH_X, a.g.ny, a.g.per[1]);
+                if (xg >= 0 && yg >= 0) off[q] = xg + (int)nx * yg;
+            }
+        }
+    }
+    static_assert(W16 || FVH_N > NT, "the first halo cell of every thread exists");
+    auto stage = [&](int zz) {
+        const int zg = side_coord(zz, a.g.nz, a.g.per[2]);
+        const int s4 = fv_slot(zz);
+        if constexpr (W16) {
+            if (half < 2) {
+                const bool in = off[0] >= 0 && zg >= 0;
+                const unsigned r = in ? (unsigned)off[0] + nxy * (unsigned)zg : 0u;
+                const unsigned n = in ? 16u : 0u;
+                if (half == 0) {
 #pragma unroll
-                for (int c = 0; c < 6; ++c) sm.tau[s4][c][k] = R(0);
+                    for (int c = 0; c < 5; ++c) cp_async16_zfill(&sm.tau[s4][c][dpos], a.tau + c * np + r, n);
+                } else {
+                    cp_async16_zfill(&sm.tau[s4][5][dpos], a.tau + 5 * np + r, n);
 #pragma unroll
-                for (int j = 0; j < 3; ++j) sm.u[s4][j][k] = R(0);
-            } else {
-                const unsigned r = (unsigned)off[q] + nxy * (unsigned)zg;
+                    for (int j = 0; j < 3; ++j) cp_async16_zfill(&sm.u[s4][j][dpos], a.u_in + j * np + r, n);
+                }
+            }
+        } else {
 #pragma unroll
-                for (int c = 0; c < 6; ++c) cp_async_real<R>(&sm.tau[s4][c][k], a.tau + c * np + r);
+            for (int q = 0; q < 2; ++q) {
+                const int k = tid + q * NT;
+                if (q > 0 && k >= FVH_N) continue;
+                // a halo cell beyond a closed side is zero-filled by the copy itself
+                const bool in = off[q] >= 0 && zg >= 0;
+                const unsigned r = in ? (unsigned)off[q] + nxy * (unsigned)zg : 0u;
+                const unsigned n = in ? (unsigned)sizeof(R) : 0u;
 #pragma unroll
-                for (int j = 0; j < 3; ++j) cp_async_real<R>(&sm.u[s4][j][k], a.u_in + j * np + r);
+                for (int c = 0; c < 6; ++c) cp_async_real_zfill<R>(&sm.tau[s4][c][k], a.tau + c * np + r, n);
+#pragma unroll
+                for (int j = 0; j < 3; ++j) cp_async_real_zfill<R>(&sm.u[s4][j][k], a.u_in + j * np + r, n);
             }
         }
         cp_async_commit();
     };
     const int ti = tid % TX, tj = tid / TX;
     const int x = x0 + ti, y = y0 + tj;
-    const int kc = (ti + 1) + (tj + 1) * FVH_X;
+    const int kc = (ti + XO) + (tj + 1) * FVH_X;
     const bool own = x < a.g.nx && y < a.g.ny;
 #pragma unroll
     for (int q = -1; q <= LBVE_FV_AHEAD; ++q) stage(z0 + q);
@@ -708,12 +787,13 @@ __device__ __forceinline__ void fv_tile(const KArgs<S> &a, FvSmem<typename Store
     cp_async_wait_all();
 }
 
-template <class S, bool VAR, bool ZR = false>
+template <class S, bool VAR, bool ZR = false, bool W16 = false>
 __global__ void __launch_bounds__(FV_X * FV_Y, sizeof(typename Store<S>::R) == 8 ? 2 : LBVE_FV_MIN_BLOCKS) k_fv_tiled(KArgs<S> a, int zchunk) {
     using R = typename Store<S>::R;
     extern __shared__ __align__(16) unsigned char fv_smem_raw[];
-    FvSmem<R> &sm = *reinterpret_cast<FvSmem<R> *>(fv_smem_raw);
-    fv_tile<S, FV_X, VAR, ZR>(a, sm, blockIdx.x, zchunk);
+    using Sm = FvSmem<R, FvTile<FV_X, W16>::HN>;
+    Sm &sm = *reinterpret_cast<Sm *>(fv_smem_raw);
+    fv_tile<S, FV_X, VAR, ZR, W16>(a, sm, blockIdx.x, zchunk);
 }
 
 // ---------------------------------------------------------------------------------
@@ -772,7 +852,9 @@ __device__ __forceinline__ void batch_load(KArgs<S> &sa, const BatchEntry<S> &e,
     for (int w = tid; w < (int)(sizeof(KArgs<S>) / 4); w += nt) dst[w] = w == ws ? src[w] + dstep : src[w];
 }
 
-template <class S>
+// Stream-collide over solves that all take AA parity PAR at this step (the pool keeps its
+// members in two lists by parity and launches one kernel per list and step).
+template <class S, int PAR>
 __global__ void __launch_bounds__(BLB_X * BLB_Y, LBVE_LBB_MIN_BLOCKS) k_lb_batched(const BatchEntry<S> *__restrict__ e,
                                                                                  int nsolves, int total, int k,
                                                                                  const unsigned *__restrict__ dstep) {
@@ -783,13 +865,12 @@ __global__ void __launch_bounds__(BLB_X * BLB_Y, LBVE_LBB_MIN_BLOCKS) k_lb_batch
     // advances by a forward scan
     if ((int)blockIdx.x >= total) return;
     const unsigned ds = *dstep;
-    int sv = batch_find<S>(e, nsolves, blockIdx.x, false), end = -1, first = 0, parity = 0, lx = 5;
+    int sv = batch_find<S>(e, nsolves, blockIdx.x, false), end = -1, first = 0, lx = 5;
     for (int it = blockIdx.x; it < total; it += gridDim.x) {
         if (it >= end) {
             while (it >= e[sv].lb_first + e[sv].lb_items) ++sv;
             first = e[sv].lb_first;
             end = first + e[sv].lb_items;
-            parity = (e[sv].parity0 + k) & 1;
             lx = __ffs(e[sv].lb_tx) - 1;  // log2 of the tile width
             __syncthreads();  // every thread is done with the previous solve's arguments
             batch_load<S>(sa, e[sv], k, ds, tid, BLB_X * BLB_Y);
@@ -800,12 +881,7 @@ __global__ void __launch_bounds__(BLB_X * BLB_Y, LBVE_LBB_MIN_BLOCKS) k_lb_batch
         const int tiles_x = (sa.g.nx + tw - 1) >> lx, tiles_y = (sa.g.ny + th - 1) / th;
         const int bx = local % tiles_x, by = (local / tiles_x) % tiles_y, z = local / (tiles_x * tiles_y);
         const int x = (bx << lx) + (tid & (tw - 1)), y = by * th + (tid >> lx);
-        if (x < sa.g.nx && y < sa.g.ny) {
-            if (parity == 0)
-                lb_cell_at<S, 0>(sa, x, y, z);
-            else
-                lb_cell_at<S, 1>(sa, x, y, z);
-        }
+        if (x < sa.g.nx && y < sa.g.ny) lb_cell_at<S, PAR>(sa, x, y, z);
     }
 }
 
@@ -1626,8 +1702,9 @@ __global__ void k_init(KArgs<S> a, const double *__restrict__ rho_in, const doub
         Store<S>::st(a.f + (long long)i * a.g.np + r, (R)v, a.ph.scale);
     }
     double t6[6];
-    for (int c = 0; c < 6; ++c) t6[c] = tau_in ? tau_in[c * ld + k] : 0.0;
-    if (a.ph.fene) {
+    const bool solid = a.mask[r] & 1u;  // a solid cell carries no stress
+    for (int c = 0; c < 6; ++c) t6[c] = (tau_in && !solid) ? tau_in[c * ld + k] : 0.0;
+    if (a.ph.fene && !solid) {
         // FENE-P: the conformation of the given stress, A = (I + lambda tau / eta_p) / f with
         // f = 1 + (3 + lambda tr tau / eta_p) / L^2
         const double lam = (double)a.ph.lam, eta_p = (double)a.ph.eta_p;

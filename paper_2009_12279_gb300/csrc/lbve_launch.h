@@ -124,7 +124,7 @@ struct KernelTable {
                        void *entry, int *lb_items, int *fv_items);
     // dstep: device counter of the steps since the entries were built (their step index base)
     cudaError_t (*lb_batched)(const void *entries, int n, int total, int k, int grid, const unsigned *dstep,
-                              cudaStream_t);
+                              int parity, cudaStream_t);  // entries all at AA parity `parity` at step k
     // stress update of the solves with stress tile width tx (entries: that group only);
     // var: some solve of the group uses a finite-volume variant
     cudaError_t (*fv_batched)(const void *entries, int n, int total, int k, int grid, int tx, int var, cudaStream_t);

@@ -128,25 +128,32 @@ struct Launch {
         return (int)zc;
     }
     static bool fv_variant(const DevState &d) { return d.ph.ctu_on || d.ph.divu_on || d.ph.gk != 0.0 || d.ph.fene; }
+    template <bool VAR, bool ZR, bool W16>
+    static cudaError_t fv_launch(const DevState &d, unsigned nblk, int zc, cudaStream_t s) {
+        KArgs<S> a = args(d);
+        const size_t sm = sizeof(FvSmem<R, FvTile<FV_X, W16>::HN>);
+        static SmemAttrOnce attr;
+        cudaError_t e = attr.ensure(k_fv_tiled<S, VAR, ZR, W16>, sm);
+        if (e != cudaSuccess) return e;
+        k_fv_tiled<S, VAR, ZR, W16><<<nblk, FV_X * FV_Y, sm, s>>>(a, zc);
+        return cudaGetLastError();
+    }
+    // planes staged by 16-byte copies: 4-byte reals, rows of whole 16-byte chunks and
+    // 16-byte aligned stress and velocity arrays
+    static bool fv_w16(const DevState &d) {
+        auto al = [](const void *p) { return ((uintptr_t)p & 15u) == 0; };
+        return sizeof(R) == 4 && d.g.nx % 4 == 0 && al(d.tau[0]) && al(d.tau[1]) && al(d.u[0]) && al(d.u[1]);
+    }
     template <bool VAR>
     static cudaError_t fv_var(const DevState &d, cudaStream_t s) {
-        KArgs<S> a = args(d);
         const int zc = fv_zchunk(d);
         const int tiles = ((d.g.nx + FV_X - 1) / FV_X) * ((d.g.ny + FV_Y - 1) / FV_Y);
         const unsigned nblk = (unsigned)(tiles * ((zcount(d) + zc - 1) / zc));
-        const size_t sm = sizeof(FvSmem<R>);
-        if (d.zhi > 0) {  // a z-slab: planes [zlo, zhi) only
-            static SmemAttrOnce attr_zr;
-            cudaError_t e = attr_zr.ensure(k_fv_tiled<S, VAR, true>, sm);
-            if (e != cudaSuccess) return e;
-            k_fv_tiled<S, VAR, true><<<nblk, FV_X * FV_Y, sm, s>>>(a, zc);
-            return cudaGetLastError();
+        const bool zr = d.zhi > 0;  // a z-slab: planes [zlo, zhi) only
+        if constexpr (sizeof(R) == 4) {
+            if (fv_w16(d)) return zr ? fv_launch<VAR, true, true>(d, nblk, zc, s) : fv_launch<VAR, false, true>(d, nblk, zc, s);
         }
-        static SmemAttrOnce attr;
-        cudaError_t e = attr.ensure(k_fv_tiled<S, VAR>, sm);
-        if (e != cudaSuccess) return e;
-        k_fv_tiled<S, VAR><<<nblk, FV_X * FV_Y, sm, s>>>(a, zc);
-        return cudaGetLastError();
+        return zr ? fv_launch<VAR, true, false>(d, nblk, zc, s) : fv_launch<VAR, false, false>(d, nblk, zc, s);
     }
     static cudaError_t fv(const DevState &d, cudaStream_t s) {
         return fv_variant(d) ? fv_var<true>(d, s) : fv_var<false>(d, s);
@@ -220,7 +227,7 @@ struct Launch {
         const long long cells = (long long)ex * ey * ez;
         if (cells <= 0) return cudaSuccess;
         const unsigned nb = (unsigned)std::min<long long>((cells + 255) / 256, 65535);
-        k_build_mask<S><<<nb, 256, 0, s>>>(d.g, d.flag, d.mask, lx, ly, lz, ex, ey, ez);
+        k_build_mask<S><<<nb, 256, 0, s>>>(d.g, d.flag, d.mask, lx, ly, lz, ex, ey, ez, (R *)d.tau[0], (R *)d.tau[1]);
         return cudaGetLastError();
     }
     static cudaError_t fused(const DevState &d, int parity, int zchunk, cudaStream_t s) {
@@ -315,9 +322,12 @@ struct Launch {
     }
     static int fv_zchunk_of(const DevState &d) { return fv_zchunk(d); }
     static cudaError_t lb_batched(const void *entries, int n, int total, int k, int grid, const unsigned *dstep,
-                                  cudaStream_t s) {
+                                  int parity, cudaStream_t s) {
         if (total <= 0) return cudaSuccess;
-        k_lb_batched<S><<<grid, BLB_X * BLB_Y, 0, s>>>((const BatchEntry<S> *)entries, n, total, k, dstep);
+        if (parity == 0)
+            k_lb_batched<S, 0><<<grid, BLB_X * BLB_Y, 0, s>>>((const BatchEntry<S> *)entries, n, total, k, dstep);
+        else
+            k_lb_batched<S, 1><<<grid, BLB_X * BLB_Y, 0, s>>>((const BatchEntry<S> *)entries, n, total, k, dstep);
         return cudaGetLastError();
     }
     template <int TX, bool VAR>
@@ -389,7 +399,10 @@ struct Launch {
         int dev = 0, sms = 148, per = 1;
         if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
         if (which == 0) {
-            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_lb_batched<S>, BLB_X * BLB_Y, 0);
+            int per1 = 1;
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_lb_batched<S, 0>, BLB_X * BLB_Y, 0);
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per1, k_lb_batched<S, 1>, BLB_X * BLB_Y, 0);
+            per = std::min(per, per1);
         } else {
             per = fv_resident<32>();
             if constexpr (FvBatchTiles<R>::wide) {
