@@ -498,7 +498,8 @@ __device__ __forceinline__ void fv_core(const Phys<R> &ph, const R (&tr)[6], con
         // periodically wrapped global neighbours are valid memory), and a solid face's u
         // is replaced by the mirror value 2 u_b - u(r), whose average with u(r) is the
         // face value u_b; the gradient is then half the difference of the two mirrored
-        // neighbours on every axis.  Only cells next to a moving boundary branch.
+        // neighbours on every axis.  The mirror of a resting wall is -u(r); next to a
+        // moving boundary the mirror is 2 u_b - u(r) (the flux never reads a solid face's u).
 #pragma unroll
         for (int k = 0; k < 3; ++k) {
 #pragma unroll
@@ -541,7 +542,8 @@ __device__ __forceinline__ void fv_core(const Phys<R> &ph, const R (&tr)[6], con
         }
     }
     R net[6] = {R(0), R(0), R(0), R(0), R(0), R(0)};
-    if (ph.flux_on) {
+    // without VAR the flux and the source are on (a solve with either off takes the VAR build)
+    if (!VAR || ph.flux_on) {
         if constexpr (!SH) {
 #pragma unroll
             for (int l = 0; l < 6; ++l) {
@@ -591,7 +593,7 @@ __device__ __forceinline__ void fv_core(const Phys<R> &ph, const R (&tr)[6], con
         }
     }
     R Sv[6] = {R(0), R(0), R(0), R(0), R(0), R(0)};
-    if (ph.src_on) {  // one test for all six components
+    if (!VAR || ph.src_on) {  // one test for all six components
 #pragma unroll
         for (int c = 0; c < 6; ++c) {
             const int i = comp_i(c), j = comp_j(c);

@@ -53,11 +53,14 @@ struct KArgs {
     unsigned *bad;  // instability flag (mapped host word) or nullptr
     int zlo, zhi;   // planes the step kernels compute
     unsigned key_base;  // added to the cell index in rounding keys (a z-slab: its global offset)
-    // per-direction / per-component bases (f + i np, tau + c np, u_out + k np), so that an
-    // address is one multiply-add of a 32-bit cell index; set by link_dirs
+    // per-direction / per-component bases (f + i np, tau + c np, u_out + k np, u_in + k np,
+    // tau_out + c np), so that an address is one multiply-add of a 32-bit cell index; set
+    // by link_dirs
     S *fq[Q];
     const R *tq[6];
     R *uq[3];
+    const R *uiq[3];
+    R *toq[6];
 };
 
 template <class S>
@@ -66,6 +69,8 @@ __host__ __device__ inline void link_dirs(KArgs<S> &a) {
     for (int i = 0; i < Q; ++i) a.fq[i] = a.f + i * np;
     for (int c = 0; c < 6; ++c) a.tq[c] = a.tau + c * np;
     for (int k = 0; k < 3; ++k) a.uq[k] = a.u_out + k * np;
+    for (int k = 0; k < 3; ++k) a.uiq[k] = a.u_in + k * np;
+    for (int c = 0; c < 6; ++c) a.toq[c] = a.tau_out + c * np;
 }
 
 // Load f_i^t of cell r from its AA location for the given parity.
@@ -627,7 +632,11 @@ constexpr int FVH_X = FV_X + 2, FVH_Y = FV_Y + 2, FVH_N = FVH_X * FVH_Y;
 #define LBVE_FV_AHEAD 1
 #endif
 constexpr int FV_RING = LBVE_FV_AHEAD + 3;
-__device__ __forceinline__ int fv_slot(int z) { return ((z % FV_RING) + FV_RING) % FV_RING; }
+// ring slot of plane z (z >= -1); a power-of-two ring takes the low bits (two's complement)
+__device__ __forceinline__ int fv_slot(int z) {
+    if constexpr ((FV_RING & (FV_RING - 1)) == 0) return z & (FV_RING - 1);
+    return ((z % FV_RING) + FV_RING) % FV_RING;
+}
 
 template <class R, int NH = FVH_N>
 struct FvSmem {
@@ -662,8 +671,10 @@ struct FvSmemNb {
 // the optional finite-volume variants, ZR the restriction to planes [zlo, zhi) of a
 // z-slab (a separate build: the plain one keeps its register budget).  W16 stages the
 // planes by 16-byte copies: 4-byte reals, nx a multiple of 4 and 16-byte aligned stress
-// and velocity arrays (the launcher checks); the result is the same either way.
-template <class S, int TX, bool VAR, bool ZR = false, bool W16 = false>
+// and velocity arrays (the launcher checks); the result is the same either way.  PB:
+// the arguments are kernel parameters, so the per-component bases (tq, uiq, toq) are
+// operands for free; the batched kernel (arguments in shared memory) forms base + c np.
+template <class S, int TX, bool VAR, bool ZR = false, bool W16 = false, bool PB = false>
 __device__ __forceinline__ void fv_tile(const KArgs<S> &a, FvSmem<typename Store<S>::R, FvTile<TX, W16>::HN> &sm,
                                         int item, int zchunk) {
     using R = typename Store<S>::R;
@@ -680,6 +691,18 @@ __device__ __forceinline__ void fv_tile(const KArgs<S> &a, FvSmem<typename Store
     const int z1 = ZR ? min(a.zhi, z0 + zchunk) : min(a.g.nz, z0 + zchunk);
     const size_t np = (size_t)a.g.np;
     const unsigned nx = (unsigned)a.g.nx, nxy = (unsigned)a.g.nx * (unsigned)a.g.ny;
+    auto tau_in = [&](int c) -> const R * {
+        if constexpr (PB) return a.tq[c];
+        return a.tau + c * np;
+    };
+    auto u_in = [&](int j) -> const R * {
+        if constexpr (PB) return a.uiq[j];
+        return a.u_in + j * np;
+    };
+    auto tau_out = [&](int c) -> R * {
+        if constexpr (PB) return a.toq[c];
+        return a.tau_out + c * np;
+    };
     // 4-byte staging: halo cells tid and tid + NT of each plane (plane offsets, -1 beyond
     // a closed side); 16-byte staging: one aligned 4-cell chunk of a halo row per thread
     // (threads below CH: stress components 0..4; CH .. 2 CH - 1: component 5 and u)
@@ -718,11 +741,11 @@ __device__ __forceinline__ void fv_tile(const KArgs<S> &a, FvSmem<typename Store
                 const unsigned n = in ? 16u : 0u;
                 if (half == 0) {
 #pragma unroll
-                    for (int c = 0; c < 5; ++c) cp_async16_zfill(&sm.tau[s4][c][dpos], a.tau + c * np + r, n);
+                    for (int c = 0; c < 5; ++c) cp_async16_zfill(&sm.tau[s4][c][dpos], tau_in(c) + r, n);
                 } else {
-                    cp_async16_zfill(&sm.tau[s4][5][dpos], a.tau + 5 * np + r, n);
+                    cp_async16_zfill(&sm.tau[s4][5][dpos], tau_in(5) + r, n);
 #pragma unroll
-                    for (int j = 0; j < 3; ++j) cp_async16_zfill(&sm.u[s4][j][dpos], a.u_in + j * np + r, n);
+                    for (int j = 0; j < 3; ++j) cp_async16_zfill(&sm.u[s4][j][dpos], u_in(j) + r, n);
                 }
             }
         } else {
@@ -735,9 +758,9 @@ __device__ __forceinline__ void fv_tile(const KArgs<S> &a, FvSmem<typename Store
                 const unsigned r = in ? (unsigned)off[q] + nxy * (unsigned)zg : 0u;
                 const unsigned n = in ? (unsigned)sizeof(R) : 0u;
 #pragma unroll
-                for (int c = 0; c < 6; ++c) cp_async_real_zfill<R>(&sm.tau[s4][c][k], a.tau + c * np + r, n);
+                for (int c = 0; c < 6; ++c) cp_async_real_zfill<R>(&sm.tau[s4][c][k], tau_in(c) + r, n);
 #pragma unroll
-                for (int j = 0; j < 3; ++j) cp_async_real_zfill<R>(&sm.u[s4][j][k], a.u_in + j * np + r, n);
+                for (int j = 0; j < 3; ++j) cp_async_real_zfill<R>(&sm.u[s4][j][k], u_in(j) + r, n);
             }
         }
         cp_async_commit();
@@ -780,7 +803,7 @@ __device__ __forceinline__ void fv_tile(const KArgs<S> &a, FvSmem<typename Store
                 fv_core<R, SH, VAR>(a.ph, tr, ur, m, nb, out);
             }
 #pragma unroll
-            for (int c = 0; c < 6; ++c) a.tau_out[c * np + r] = out[c];
+            for (int c = 0; c < 6; ++c) tau_out(c)[r] = out[c];
         }
         __syncthreads();  // the next stage overwrites the slot of plane z - 1
     }
@@ -793,7 +816,7 @@ __global__ void __launch_bounds__(FV_X * FV_Y, sizeof(typename Store<S>::R) == 8
     extern __shared__ __align__(16) unsigned char fv_smem_raw[];
     using Sm = FvSmem<R, FvTile<FV_X, W16>::HN>;
     Sm &sm = *reinterpret_cast<Sm *>(fv_smem_raw);
-    fv_tile<S, FV_X, VAR, ZR, W16>(a, sm, blockIdx.x, zchunk);
+    fv_tile<S, FV_X, VAR, ZR, W16, true>(a, sm, blockIdx.x, zchunk);
 }
 
 // ---------------------------------------------------------------------------------

@@ -127,7 +127,11 @@ struct Launch {
         if (zc > nz) zc = nz;
         return (int)zc;
     }
-    static bool fv_variant(const DevState &d) { return d.ph.ctu_on || d.ph.divu_on || d.ph.gk != 0.0 || d.ph.fene; }
+    // the VAR builds of the stress kernels: a finite-volume variant, FENE-P, or the flux or
+    // the source switched off (the plain build has both on at compile time)
+    static bool fv_variant(const DevState &d) {
+        return d.ph.ctu_on || d.ph.divu_on || d.ph.gk != 0.0 || d.ph.fene || !d.ph.flux_on || !d.ph.src_on;
+    }
     template <bool VAR, bool ZR, bool W16>
     static cudaError_t fv_launch(const DevState &d, unsigned nblk, int zc, cudaStream_t s) {
         KArgs<S> a = args(d);
