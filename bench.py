@@ -503,6 +503,7 @@ def run_ours(args):
         if sampler:
             clocks = sampler.stop()
         health = s.reduce()
+        lb_kernel = s.stream_collide_kernel
         s.close()
         del s
         torch.cuda.empty_cache()
@@ -527,7 +528,9 @@ def run_ours(args):
             "kernels": {k: {"avg_ms": v[0] / max(v[1], 1), "launches": v[1],
                             "achieved_gbs": (kernel_bytes(k, prec) * cells * v[1] / (v[0] * 1e-3) / 1e9)
                             if kernel_bytes(k, prec) else None} for k, v in kt.items()},
-            "roofline": {"bound": "hbm", "kernel": f"k_{kind}", "achieved": achieved, "peak": peak, "unit": "GB/s",
+            "stream_collide": lb_kernel,
+            "roofline": {"bound": "hbm", "kernel": "k_lb_rows" if kind == "lb" and lb_kernel == "rows" else f"k_{kind}",
+                         "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": (achieved / peak) if achieved else None, "traffic": None,
                          "bytes_per_cell": kb, "peak_source": peak_kind},
             "gpu_launches": launches,
@@ -577,7 +580,7 @@ def run_ours(args):
 
 # Sources whose kernels the traffic record was measured on; any change to them makes the
 # record stale (traffic is then reported as null until it is captured again).
-KERNEL_SOURCES = ("lbve_device.cuh", "lbve_kernels.cuh", "lbve_table.cuh", "lbve_launch.h")
+KERNEL_SOURCES = ("lbve_device.cuh", "lbve_kernels.cuh", "lbve_rows.cuh", "lbve_table.cuh", "lbve_launch.h")
 
 
 def kernel_sources_sha():

@@ -80,7 +80,11 @@ typedef enum { LBVE_F64 = 0, LBVE_F32 = 1, LBVE_F16_SHIFTED = 2, LBVE_BF16_SHIFT
 #define LBVE_FV_CTU 4
 #define LBVE_FV_DIVU 8
 
-/* Kernel schedule: two kernels per step (LB, then FV), or one fused kernel per step. */
+/* Kernel schedule: two kernels per step (LB, then FV), or one fused kernel per step.
+ * AUTO is the split schedule whose stream-collide (the LB half, Eqs. (lb), (guo), (force),
+ * (ubb)) runs as a row pipeline where the grid allows it (see
+ * lbve_stream_collide_kernel); SPLIT always takes the per-cell stream-collide.  Both give
+ * bitwise the same results. */
 #define LBVE_SCHED_AUTO 0
 #define LBVE_SCHED_SPLIT 1
 #define LBVE_SCHED_FUSED 2
@@ -246,6 +250,25 @@ lbve_status lbve_halo_unpack(lbve_ctx *ctx, int what, int side, const void *dev_
 /* 1 if the context's instability flag is set (see lbve_step), 0 if not, -1 for NULL.
  * Does not synchronise: steps still in flight may set it later. */
 int lbve_is_unstable(const lbve_ctx *ctx);
+
+/*
+ * Which stream-collide kernel lbve_step launches for this context (split schedule).
+ * LBVE_LB_ROWS: the row pipeline -- a block walks a strip of x-rows of one plane, and a
+ * producer warp moves each row's 19 PDF rows (AA layout of the step's parity), its mask
+ * row and the stress rows its polymer force reads (Eq. (force): the rows y -+ 1 and
+ * z -+ 1) into shared memory with bulk asynchronous copies completing on mbarriers.  It is
+ * taken with schedule AUTO when nx is a multiple of 32 in [64, 512], the PDF, stress and
+ * mask arrays are 16-byte aligned (always with the library's own allocations), the layout
+ * fits one block's shared memory (FP64: nx up to 384)
+ * and the stress law is not FENE-P.  LBVE_LB_CELLS: the per-cell kernel (one thread per
+ * cell, global loads).  Every cell runs the same arithmetic in both, so results are
+ * bitwise equal.  -1 for NULL.  A bounded wait of the row pipeline that gives up (a
+ * copy that never lands; not expected) makes the next lbve_step / lbve_synchronize
+ * return LBVE_ETIMEOUT.
+ */
+#define LBVE_LB_CELLS 0
+#define LBVE_LB_ROWS 1
+int lbve_stream_collide_kernel(const lbve_ctx *ctx);
 
 /*
  * Copy the macroscopic fields to host arrays (each may be NULL): rho (n), u (3n, the

@@ -122,7 +122,13 @@ lbve_status fail(lbve_ctx *c, lbve_status s, const std::string &msg) {
 // The instability flag of a context (set by a stream-collide of an earlier call; the
 // host sees it once that kernel has written it, without synchronising).
 bool unstable(const lbve_ctx *c) { return c->h_bad && *(volatile const unsigned *)c->h_bad != 0u; }
+// The flag value 2: a bounded wait of the row-pipelined stream-collide gave up.
+bool timed_out(const lbve_ctx *c) { return c->h_bad && *(volatile const unsigned *)c->h_bad == 2u; }
+lbve_status flag_status(const lbve_ctx *c) { return timed_out(c) ? LBVE_ETIMEOUT : LBVE_EUNSTABLE; }
 std::string unstable_message(const lbve_ctx *c) {
+    if (timed_out(c))
+        return "a stream-collide block gave up waiting for its shared-memory copies at or before step " +
+               std::to_string(c->t);
     return "instability detected at or before step " + std::to_string(c->t) +
            ": a fluid cell had rho <= 0, |u|^2 >= 1/3 or a NaN";
 }
@@ -534,6 +540,7 @@ lbve_status create_impl(const lbve_params *p, void *stream, lbve_alloc_fn alloc,
     g.n = (long long)p->nx * p->ny * p->nz;
     g.np = padded(g.n);
     c->d.block_x = lbve::default_block_x(*p);
+    c->d.lb_rows = p->schedule == LBVE_SCHED_AUTO ? 1 : 0;
     if (p->block_x == 0) {  // a schedule tuned for this shape earlier in the process
         int bx = 0, zc = 0;
         if (tuned_ctx(*p, bx, zc)) {
@@ -1043,7 +1050,7 @@ lbve_status lbve_step(lbve_ctx *c, int nsteps) {
     if (nsteps < 0) return fail(c, LBVE_EINVAL, "nsteps must be >= 0");
     if (c->pool) return fail(c, LBVE_ESTATE, "a pool member advances through lbve_pool_step");
     if (c->phase_pending) return fail(c, LBVE_ESTATE, "a stream-collide of lbve_step_phase awaits its stress update");
-    if (unstable(c)) return fail(c, LBVE_EUNSTABLE, unstable_message(c));
+    if (unstable(c)) return fail(c, flag_status(c), unstable_message(c));
     if (use_fused(c, nsteps)) {
         // stream-collide of the first step, fused (stress of step t-1 + stream-collide of
         // step t) for the others, stress update of the last step
@@ -1128,7 +1135,7 @@ lbve_status lbve_step_phase(lbve_ctx *c, int phase) {
     if (c->pool) return fail(c, LBVE_ESTATE, "a pool member advances through lbve_pool_step");
     if (phase == 0) {
         if (c->phase_pending) return fail(c, LBVE_ESTATE, "phase 0 twice: the stress update of the last one is missing");
-        if (unstable(c)) return fail(c, LBVE_EUNSTABLE, unstable_message(c));
+        if (unstable(c)) return fail(c, flag_status(c), unstable_message(c));
         const int parity = (int)(c->t & 1);
         c->d.step = (unsigned)c->t;
         if (c->nbody > 0) {
@@ -1374,11 +1381,16 @@ long long lbve_time(const lbve_ctx *c) { return c ? c->t : -1; }
 lbve_status lbve_synchronize(lbve_ctx *c) {
     if (!c) return LBVE_EINVAL;
     CK(cudaStreamSynchronize(c->stream), "synchronize");
-    if (unstable(c)) return fail(c, LBVE_EUNSTABLE, unstable_message(c));
+    if (unstable(c)) return fail(c, flag_status(c), unstable_message(c));
     return LBVE_OK;
 }
 
 int lbve_is_unstable(const lbve_ctx *c) { return c ? (unstable(c) ? 1 : 0) : -1; }
+
+int lbve_stream_collide_kernel(const lbve_ctx *c) {
+    if (!c) return -1;
+    return c->kt->lb_rows_used(c->d) ? LBVE_LB_ROWS : LBVE_LB_CELLS;
+}
 
 const char *lbve_last_error(const lbve_ctx *c) { return c ? c->err.c_str() : g_create_error.c_str(); }
 
@@ -1741,7 +1753,7 @@ lbve_status lbve_pool_step(lbve_pool *P, int nsteps) {
     if (nsteps == 0 || P->members.empty()) return LBVE_OK;
     for (size_t k = 0; k < P->members.size(); ++k)
         if (unstable(P->members[k]))
-            return pfail(P, LBVE_EUNSTABLE, "member " + std::to_string(k) + " is unstable (" +
+            return pfail(P, flag_status(P->members[k]), "member " + std::to_string(k) + " is unstable (" +
                                                 unstable_message(P->members[k]) + "); remove it to continue");
     if (P->dirty) {
         lbve_status s = build_entries(P);

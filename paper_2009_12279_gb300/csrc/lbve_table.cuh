@@ -6,6 +6,7 @@
 #include <atomic>
 
 #include "lbve_kernels.cuh"
+#include "lbve_rows.cuh"
 
 namespace lbve {
 
@@ -99,7 +100,69 @@ struct Launch {
         k_init<S><<<nb, 256, 0, s>>>(a, rho, u, tau, (R *)d.tau[d.cur], r0, count, ld);
         return cudaGetLastError();
     }
+    // The row-pipelined stream-collide (k_lb_rows): rows of a multiple of 32 cells, at
+    // most LR_MAX_NX, 16-byte aligned PDF, stress and mask arrays, a layout that fits the
+    // shared memory of one block, Oldroyd-B or Giesekus stress (FENE-P reads conformation
+    // tensors: per-cell kernel).  The result is bitwise that of the per-cell kernel.
+    static size_t rows_smem(int nx) { return RowsLayout<S>{nx}.total(); }
+    static bool rows_ok(const DevState &d) {
+        auto al = [](const void *p) { return ((uintptr_t)p & 15u) == 0; };
+        if (d.ph.fene || d.g.nx % 32 != 0 || d.g.nx < 64 || d.g.nx > LR_MAX_NX) return false;
+        if (!al(d.f) || !al(d.tau[0]) || !al(d.tau[1]) || !al(d.mask)) return false;
+        int dev = 0, optin = 0;
+        if (cudaGetDevice(&dev) != cudaSuccess) return false;
+        if (cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess) return false;
+        return rows_smem(d.g.nx) <= (size_t)optin;
+    }
+    // rows per strip: enough strips for ~16 waves of resident blocks (d.lb_rows_yc > 0:
+    // that many), at least 8 rows
+    static RowsWork rows_work(const DevState &d) {
+        const int ny = d.g.ny, nzc = zcount(d);
+        int yc = d.lb_rows_yc;
+        if (yc <= 0) {
+            int dev = 0, sms = 148, smpb = 0;
+            if (cudaGetDevice(&dev) == cudaSuccess) {
+                cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+                cudaDeviceGetAttribute(&smpb, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
+            }
+            long long per_sm = smpb > 0 ? (long long)smpb / (long long)(rows_smem(d.g.nx) + 1024) : 1;
+            if (per_sm < 1) per_sm = 1;
+            const long long want = 16LL * sms * per_sm;
+            long long strips = (want + nzc - 1) / nzc;
+            if (strips < 1) strips = 1;
+            yc = (int)((ny + strips - 1) / strips);
+            if (yc < 8) yc = 8;
+        }
+        if (yc > ny) yc = ny;
+        RowsWork w;
+        w.yc = yc;
+        w.strips = (ny + yc - 1) / yc;
+        return w;
+    }
+    static cudaError_t lb_rows(const DevState &d, int parity, cudaStream_t s) {
+        KArgs<S> a = args(d);
+        const RowsWork w = rows_work(d);
+        const size_t sm = rows_smem(d.g.nx);
+        static SmemAttrOnce attr[2];
+        int dev = 0, optin = 0;
+        cudaError_t e = cudaGetDevice(&dev);
+        if (e == cudaSuccess) e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+        if (e != cudaSuccess) return e;
+        // the attribute is the largest layout any nx up to LR_MAX_NX needs, within the limit
+        const size_t lim = std::min(rows_smem(LR_MAX_NX), (size_t)optin);
+        e = parity == 0 ? attr[0].ensure(k_lb_rows<S, 0>, lim) : attr[1].ensure(k_lb_rows<S, 1>, lim);
+        if (e != cudaSuccess) return e;
+        const unsigned nblk = (unsigned)(zcount(d) * w.strips);
+        const unsigned nthr = (unsigned)(d.g.nx + 32);
+        if (parity == 0)
+            k_lb_rows<S, 0><<<nblk, nthr, sm, s>>>(a, w);
+        else
+            k_lb_rows<S, 1><<<nblk, nthr, sm, s>>>(a, w);
+        return cudaGetLastError();
+    }
+    static int lb_rows_used(const DevState &d) { return d.lb_rows && rows_ok(d) ? 1 : 0; }
     static cudaError_t lb(const DevState &d, int parity, cudaStream_t s) {
+        if (d.lb_rows && rows_ok(d)) return lb_rows(d, parity, s);
         KArgs<S> a = args(d);
         if (d.ph.fene) {  // the polymer force takes the stress of each cell's conformation
             if (parity == 0)
@@ -440,7 +503,7 @@ const KernelTable *Launch<S>::table(int prec) {
                                       &fused,         sizeof(BatchEntry<S>), &fill_entry, &lb_batched,
                                       &fv_batched,    &batched_grid,    &residual,   &batch_tiles,
                                       &fv_zchunk_of,  &fv_variant_of,   sizeof(PartEntry<S>), &fill_part_entry,
-                                      &particle_phase_batched, &halo_pack, &halo_unpack};
+                                      &particle_phase_batched, &halo_pack, &halo_unpack, &lb_rows_used};
         return &t;
 }
 
