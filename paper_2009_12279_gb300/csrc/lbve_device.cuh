@@ -173,6 +173,42 @@ struct Cell {
 constexpr uint32_t MASK_MOVING = 1u << 19;
 __device__ __forceinline__ bool nb_solid(uint32_t m, int i) { return (m >> i) & 1u; }
 
+// --------------------------------------------------------------------------------
+// Lane arithmetic of the shifted modes (FP32 arithmetic on deviations).  Every operation
+// rounds once and none is left to the compiler to contract, so a cell computed in a float
+// and two cells computed in the two lanes of a float2 (Blackwell's paired FP32
+// instructions: two FMAs, adds or multiplies per instruction) give bitwise the same
+// results.  Masks are a uint32_t for one cell and a uint2 for two.
+// --------------------------------------------------------------------------------
+__device__ __forceinline__ float vadd(float a, float b) { return __fadd_rn(a, b); }
+__device__ __forceinline__ float vsub(float a, float b) { return __fsub_rn(a, b); }
+__device__ __forceinline__ float vmul(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ float vfma(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+__device__ __forceinline__ float vneg(float a) { return -a; }
+__device__ __forceinline__ float2 vadd(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 vneg(float2 a) { return make_float2(-a.x, -a.y); }
+__device__ __forceinline__ float2 vsub(float2 a, float2 b) { return __fadd2_rn(a, vneg(b)); }
+__device__ __forceinline__ float2 vmul(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 vfma(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+template <class V>
+__device__ __forceinline__ V vbc(float s);
+template <>
+__device__ __forceinline__ float vbc<float>(float s) { return s; }
+template <>
+__device__ __forceinline__ float2 vbc<float2>(float s) { return make_float2(s, s); }
+// correctly rounded reciprocal (no paired form: one per lane)
+__device__ __forceinline__ float vrcp(float a) { return __frcp_rn(a); }
+__device__ __forceinline__ float2 vrcp(float2 a) { return make_float2(__frcp_rn(a.x), __frcp_rn(a.y)); }
+__device__ __forceinline__ float vdiv(float a, float b) { return __fdiv_rn(a, b); }
+__device__ __forceinline__ float2 vdiv(float2 a, float2 b) { return make_float2(__fdiv_rn(a.x, b.x), __fdiv_rn(a.y, b.y)); }
+// select per lane: if_solid where neighbour i of the lane's cell is not fluid
+__device__ __forceinline__ float vsel_solid(uint32_t m, int i, float if_solid, float if_fluid) {
+    return nb_solid(m, i) ? if_solid : if_fluid;
+}
+__device__ __forceinline__ float2 vsel_solid(uint2 m, int i, float2 if_solid, float2 if_fluid) {
+    return make_float2(nb_solid(m.x, i) ? if_solid.x : if_fluid.x, nb_solid(m.y, i) ? if_solid.y : if_fluid.y);
+}
+
 // Boundary velocity u_b of the solid cell (xq, yq, zq) with flag fl: zero for a no-slip
 // wall, the class velocity for a moving wall (Eq. (ubb)), v + w x (r_b - X) with the
 // minimum-image lever arm for a particle cell (Eq. (surface-velocity)).
@@ -242,8 +278,33 @@ __device__ __forceinline__ void boundary_velocity_fast(const Geo &g, const Phys<
 // face value by Eq. (interpolation), or tau(r) towards a solid cell (Eq. (extrapolation)).
 // tn(l, c) returns component c of the stress of the face-l neighbour (l = 0..5 for
 // +x, -x, +y, -y, +z, -z); it is only called for fluid neighbours.
+// Shifted modes: the two faces of an axis share the cell's own stress, which cancels:
+// F_j = sum_k 1/2 (a_kj - b_kj), a = tau_kj(r + e_k) (tau_kj(r) when r + e_k is solid), b
+// likewise on the -e_k side.  V = float (one cell) or float2 (two cells), M its mask type.
+template <class V, class M, class TauNb>
+__device__ __forceinline__ void polymer_force_sh(const V (&tr)[6], M mask, const TauNb &tn, V Fp[3]) {
+    const V half = vbc<V>(0.5f);
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+        V acc;
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            const int c = comp(k, j);
+            const V a = vsel_solid(mask, 2 * k + 1, tr[c], tn(2 * k, c));
+            const V b = vsel_solid(mask, 2 * k + 2, tr[c], tn(2 * k + 1, c));
+            const V d = vsub(a, b);
+            acc = k == 0 ? vmul(half, d) : vfma(half, d, acc);
+        }
+        Fp[j] = acc;
+    }
+}
+
 template <class R, class TauNb>
 __device__ __forceinline__ void polymer_force_core(const R (&tr)[6], uint32_t mask, const TauNb &tn, R Fp[3]) {
+    if constexpr (sizeof(R) == 4) {
+        polymer_force_sh<float>(tr, mask, tn, Fp);
+        return;
+    }
     Fp[0] = R(0);
     Fp[1] = R(0);
     Fp[2] = R(0);
@@ -332,6 +393,27 @@ __device__ __forceinline__ R stored_to_stress(const Phys<R> &ph, const R (&a)[6]
     return fene_component<R>(ph, fene_factor<R>(ph, a[0], a[1], a[2]), a[c], c);
 }
 
+// Macroscopic moments of the shifted modes (deviations: rho = rho0 + sum), lane form.
+template <class V>
+__device__ __forceinline__ void moments_sh(const V (&f)[Q], const V F[3], float rho0, V &rho, V &drho, V u[3]) {
+    const V d0 = vadd(vadd(vadd(vadd(f[0], f[1]), vadd(f[2], f[3])), vadd(f[4], f[5])), f[6]);
+    const V d1 = vadd(vadd(vadd(f[7], f[8]), vadd(f[9], f[10])), vadd(f[11], f[12]));
+    const V d2 = vadd(vadd(vadd(f[13], f[14]), vadd(f[15], f[16])), vadd(f[17], f[18]));
+    drho = vadd(vadd(d0, d1), d2);
+    rho = vadd(vbc<V>(rho0), drho);
+    const V m78 = vsub(f[7], f[8]), m1112 = vsub(f[11], f[12]), m1516 = vsub(f[15], f[16]);
+    const V m910 = vsub(f[9], f[10]), m1314 = vsub(f[13], f[14]), m1718 = vsub(f[17], f[18]);
+    // jx = c_x-weighted sum, jy, jz likewise (pairs (i, -i) differenced first)
+    const V jx = vadd(vadd(vadd(vadd(vsub(f[1], f[2]), m78), m910), m1112), m1314);
+    const V jy = vadd(vadd(vsub(vadd(vsub(f[3], f[4]), m78), m910), m1516), m1718);
+    const V jz = vsub(vadd(vsub(vadd(vsub(f[5], f[6]), m1112), m1314), m1516), m1718);
+    const V ir = vrcp(rho);
+    const V half = vbc<V>(0.5f);
+    u[0] = vmul(vfma(half, F[0], jx), ir);
+    u[1] = vmul(vfma(half, F[1], jy), ir);
+    u[2] = vmul(vfma(half, F[2], jz), ir);
+}
+
 // Macroscopic moments, Eq. (macroscopic-velocity).  FP64 mode sums in direction order;
 // shifted modes return rho = rho0 + drho with drho summed over the deviations.
 template <class R, bool SH>
@@ -357,18 +439,7 @@ __device__ __forceinline__ void moments(const R (&f)[Q], const R F[3], R rho0, R
 #pragma unroll
         for (int a = 0; a < 3; ++a) u[a] = (j[a] + R(0.5) * F[a]) / s;
     } else {
-        const R d0 = (f[0] + f[1]) + (f[2] + f[3]) + (f[4] + f[5]) + f[6];
-        const R d1 = (f[7] + f[8]) + (f[9] + f[10]) + (f[11] + f[12]);
-        const R d2 = (f[13] + f[14]) + (f[15] + f[16]) + (f[17] + f[18]);
-        drho = d0 + d1 + d2;
-        rho = rho0 + drho;
-        const R jx = (f[1] - f[2]) + (f[7] - f[8]) + (f[9] - f[10]) + (f[11] - f[12]) + (f[13] - f[14]);
-        const R jy = (f[3] - f[4]) + (f[7] - f[8]) + (f[10] - f[9]) + (f[15] - f[16]) + (f[17] - f[18]);
-        const R jz = (f[5] - f[6]) + (f[11] - f[12]) + (f[14] - f[13]) + (f[15] - f[16]) + (f[18] - f[17]);
-        const R ir = R(1) / rho;
-        u[0] = (jx + R(0.5) * F[0]) * ir;
-        u[1] = (jy + R(0.5) * F[1]) * ir;
-        u[2] = (jz + R(0.5) * F[2]) * ir;
+        moments_sh<R>(f, F, rho0, rho, drho, u);
     }
 }
 
@@ -409,6 +480,89 @@ __device__ __forceinline__ R cdot(int i, const R v[3]) {
 // (relative error 1.1e-5 after 1000 steps of the config-1 channel, against 1.3e-7 in this form).
 // Returns true when the cell is unstable: rho <= 0, |u|^2 >= 1/3 (the lattice sound speed
 // squared) or a NaN in either (comparisons with a NaN are false).
+// c_i . v of the directions i = 1, 3, ..., 17 (the first of each pair (i, -i)), lane form:
+// one component or the sum / difference of two
+template <class V>
+__device__ __forceinline__ V cdot_v(int i, const V v[3]) {
+    int a = -1, b = -1, sb = 1;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        const int c = cdir(i, k);
+        if (c != 0) {
+            if (a < 0) {
+                a = k;
+            } else {
+                b = k;
+                sb = c;
+            }
+        }
+    }
+    if (b < 0) return v[a];  // the first direction of a pair has its one component +1
+    return sb > 0 ? vadd(v[a], v[b]) : vsub(v[a], v[b]);
+}
+
+// Collision of the shifted modes in lane form (see collide): the non-equilibrium parts of
+// each pair are formed first, k2 (f_i + f_-i) - esym and k (f_i - f_-i) - rho c.u, each
+// in one fused multiply-add with the exact integer k2 = 1/(2 w_i) or k = 1/(6 w_i), and
+// only then scaled by rounded rates.  Returns the instability test per lane.
+template <class V>
+struct LaneBool;
+template <>
+struct LaneBool<float> {
+    using T = bool;
+};
+template <>
+struct LaneBool<float2> {
+    using T = uint2;  // x, y: 1 when that lane's cell is unstable
+};
+__device__ __forceinline__ bool unstable_of(float rho, float usq) {
+    return !(rho > 0.0f) || !(usq < (float)(1.0 / 3.0));
+}
+__device__ __forceinline__ uint2 unstable_of(float2 rho, float2 usq) {
+    return make_uint2(unstable_of(rho.x, usq.x) ? 1u : 0u, unstable_of(rho.y, usq.y) ? 1u : 0u);
+}
+template <class V>
+__device__ __forceinline__ typename LaneBool<V>::T collide_sh(V (&f)[Q], V rho, V drho, const V u[3], const V F[3],
+                                                             const Phys<float> &ph) {
+    const V usq = vfma(u[2], u[2], vfma(u[0], u[0], vmul(u[1], u[1])));
+    const auto unstable = unstable_of(rho, usq);
+    const V uF = vfma(u[2], F[2], vfma(u[0], F[0], vmul(u[1], F[1])));
+    const float wp = ph.omega_p, wm = ph.omega_m;
+    const V q = vmul(vbc<V>(1.5f), usq);
+    const V u3F = vmul(vbc<V>(3.0f), uF);
+    // omega+/(2 k2) and omega-/(2 k) of the directions with w = 1/18 (halved for 1/36);
+    // these rounded constants scale only the small non-equilibrium parts
+    const float cp = wp * (float)(1.0 / 18.0), cm = wm * (float)(1.0 / 6.0);
+    // rest population: feq0 - w0 rho0 = w0 (drho - rho q), forcing w0 B (-3 u.F)
+    {
+        const float w0 = wgt<float>(0);
+        const V e0 = vfma(vneg(rho), q, drho);
+        const V n0 = vfma(vbc<V>(-w0), e0, f[0]);
+        f[0] = vfma(vbc<V>(-(w0 * ph.B)), u3F, vfma(vbc<V>(-wp), n0, f[0]));
+    }
+#pragma unroll
+    for (int i = 1; i < Q; i += 2) {
+        const int ip = i + 1;
+        const bool axis = i < 7;  // w = 1/18
+        const float w = wgt<float>(i);
+        const float k = axis ? 3.0f : 6.0f, k2 = axis ? 9.0f : 18.0f;
+        const float sp = axis ? cp : 0.5f * cp, sm = axis ? cm : 0.5f * cm;
+        const V cu = cdot_v<V>(i, u);
+        const V cF = cdot_v<V>(i, F);
+        const V esym = vfma(rho, vfma(vmul(vbc<V>(4.5f), cu), cu, vneg(q)), drho);
+        const V x9 = vfma(vmul(vbc<V>(9.0f), cu), cF, vneg(u3F));
+        const V nsym = vfma(vbc<V>(k2), vadd(f[i], f[ip]), vneg(esym));       // k2 (f_i + f_-i) - esym
+        const V nanti = vfma(vbc<V>(k), vsub(f[i], f[ip]), vneg(vmul(rho, cu)));  // k (f_i - f_-i) - rho cu
+        const V P = vfma(vbc<V>(-(w * ph.B)), x9, vmul(vbc<V>(sp), nsym));
+        const V M = vfma(vbc<V>(-(w * ph.A)), cF, vmul(vbc<V>(sm), nanti));
+        const V fi = vsub(vsub(f[i], P), M);
+        const V fo = vadd(vsub(f[ip], P), M);
+        f[i] = fi;
+        f[ip] = fo;
+    }
+    return unstable;
+}
+
 template <class R, bool SH>
 __device__ __forceinline__ bool collide(R (&f)[Q], R rho, R drho, const R u[3], const R F[3], const Phys<R> &ph) {
     const R usq = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
@@ -444,35 +598,133 @@ __device__ __forceinline__ bool collide(R (&f)[Q], R rho, R drho, const R u[3], 
             f[ip] = fo;
         }
     } else {
-        const R q = R(1.5) * usq;
-        const R u3F = R(3) * uF;
-        // omega+/(2 k2) and omega-/(2 k) of the directions with w = 1/18 (halved for 1/36);
-        // these rounded constants scale only the small non-equilibrium parts
-        const R cp = wp * R(1.0 / 18.0), cm = wm * R(1.0 / 6.0);
-        // rest population: feq0 - w0 rho0 = w0 (drho - rho q), forcing w0 B (-3 u.F)
-        f[0] = f[0] - wp * (f[0] - wgt<R>(0) * (drho - rho * q)) - wgt<R>(0) * ph.B * u3F;
-#pragma unroll
-        for (int i = 1; i < Q; i += 2) {
-            const int ip = i + 1;
-            const R w = wgt<R>(i);
-            const bool axis = i < 7;  // w = 1/18
-            const R k = axis ? R(3) : R(6), k2 = axis ? R(9) : R(18);
-            const R sp = axis ? cp : R(0.5) * cp, sm = axis ? cm : R(0.5) * cm;
-            const R cu = cdot<R>(i, u);
-            const R cF = cdot<R>(i, F);
-            const R esym = drho + rho * (R(4.5) * cu * cu - q);
-            const R x9 = R(9) * cu * cF - u3F;
-            const R nsym = __fmaf_rn(k2, f[i] + f[ip], -esym);    // k2 (f_i + f_-i) - esym, one rounding
-            const R nanti = __fmaf_rn(k, f[i] - f[ip], -(rho * cu));  // k (f_i - f_-i) - rho cu, one rounding
-            const R P = sp * nsym - (w * ph.B) * x9;
-            const R M = sm * nanti - (w * ph.A) * cF;
-            const R fi = f[i] - P - M;
-            const R fo = f[ip] - P + M;
-            f[i] = fi;
-            f[ip] = fo;
-        }
+        return collide_sh<R>(f, rho, drho, u, F, ph);
     }
     return unstable;
+}
+
+// Lane helpers of the stress update: |v|, and a per-lane choice between a value and zero.
+__device__ __forceinline__ float vabs(float a) { return fabsf(a); }
+__device__ __forceinline__ float2 vabs(float2 a) { return make_float2(fabsf(a.x), fabsf(a.y)); }
+// v where the lane's cell sees an open face l and v > 0, else 0 (the donor-cell coefficient)
+__device__ __forceinline__ float vpos_open(uint32_t m, int l, float v) {
+    return (!nb_solid(m, l + 1) && v > 0.0f) ? v : 0.0f;
+}
+__device__ __forceinline__ float2 vpos_open(uint2 m, int l, float2 v) {
+    return make_float2(vpos_open(m.x, l, v.x), vpos_open(m.y, l, v.y));
+}
+__device__ __forceinline__ bool lane_moving_solid(uint32_t m, int l, int) {
+    return (m & MASK_MOVING) && nb_solid(m, l + 1);
+}
+__device__ __forceinline__ bool lane_moving_solid(uint2 m, int l, int lane) {
+    return lane_moving_solid(lane == 0 ? m.x : m.y, l, 0);
+}
+__device__ __forceinline__ float &lane_ref(float &v, int) { return v; }
+__device__ __forceinline__ float &lane_ref(float2 &v, int lane) { return lane == 0 ? v.x : v.y; }
+__device__ __forceinline__ float lane_val(float v, int) { return v; }
+__device__ __forceinline__ float lane_val(float2 v, int lane) { return lane == 0 ? v.x : v.y; }
+template <class V>
+__host__ __device__ constexpr int lanes_of() {
+    return sizeof(V) / sizeof(float);
+}
+
+// Finite-volume stress update of the shifted modes in lane form (see fv_core for the
+// method): V = float (one cell) or float2 (two cells), M the mask of the lane's cells.
+// nb.u(l, k), nb.tau(l, c): the face-l neighbours' velocity / stress (V); nb.ub(l, lane,
+// out): the boundary velocity of the solid face-l neighbour of the lane's cell.
+template <class V, class M, bool VAR, class Nb>
+__device__ __forceinline__ void fv_core_sh(const Phys<float> &ph, const V (&tr)[6], const V (&ur)[3], M mask,
+                                           const Nb &nb, V out[6]) {
+    const V half = vbc<V>(0.5f), one = vbc<V>(1.0f);
+    V un[6][3];
+    V G[3][3];
+    // every face neighbour's u, a solid face's replaced by the mirror value 2 u_b - u(r)
+    // (-u(r) at rest), so that the gradient is half the difference of the mirrored values
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const int l = 2 * k + h;
+#pragma unroll
+            for (int j = 0; j < 3; ++j) un[l][j] = vsel_solid(mask, l + 1, vneg(ur[j]), nb.u(l, j));
+#pragma unroll
+            for (int ln = 0; ln < lanes_of<V>(); ++ln) {
+                if (lane_moving_solid(mask, l, ln)) {
+                    float ub[3];
+                    nb.ub(l, ln, ub);
+#pragma unroll
+                    for (int j = 0; j < 3; ++j) lane_ref(un[l][j], ln) = __fmaf_rn(2.0f, ub[j], -lane_val(ur[j], ln));
+                }
+            }
+        }
+#pragma unroll
+        for (int j = 0; j < 3; ++j) G[k][j] = vmul(half, vsub(un[2 * k][j], un[2 * k + 1][j]));
+    }
+    V net[6];
+    const bool flux = !VAR || ph.flux_on;  // without VAR the flux and the source are on
+    if (flux) {
+        V aout, inflow[6];
+#pragma unroll
+        for (int l = 0; l < 6; ++l) {
+            const int k = l >> 1;
+            const bool pos = (l & 1) == 0;
+            // zero flux across a solid link: both coefficients zero (a solid cell's stress
+            // is finite, so the inflow product adds zero)
+            V ao = vpos_open(mask, l, pos ? ur[k] : vneg(ur[k]));
+            V b = vpos_open(mask, l, pos ? vneg(un[l][k]) : un[l][k]);
+            if constexpr (VAR) {
+                if (ph.ctu_on) {
+                    const int ta = k == 2 ? 0 : k + 1, tb = k == 0 ? 2 : k - 1;
+                    ao = vmul(ao, vmul(vsub(one, vabs(ur[ta])), vsub(one, vabs(ur[tb]))));
+                    b = vmul(b, vmul(vsub(one, vabs(un[l][ta])), vsub(one, vabs(un[l][tb]))));
+                }
+            }
+            aout = l == 0 ? ao : vadd(aout, ao);
+#pragma unroll
+            for (int c = 0; c < 6; ++c) inflow[c] = l == 0 ? vmul(b, nb.tau(l, c)) : vfma(b, nb.tau(l, c), inflow[c]);
+        }
+#pragma unroll
+        for (int c = 0; c < 6; ++c) net[c] = vfma(aout, tr[c], vneg(inflow[c]));
+    }
+    const bool src = !VAR || ph.src_on;
+    V Sv[6];
+    if (src) {
+#pragma unroll
+        for (int c = 0; c < 6; ++c) {
+            const int i = comp_i(c), j = comp_j(c);
+            V a = vmul(tr[comp(i, 0)], G[0][j]);
+            a = vfma(tr[comp(i, 1)], G[1][j], a);
+            a = vfma(tr[comp(i, 2)], G[2][j], a);
+            V b = vmul(tr[comp(0, j)], G[0][i]);
+            b = vfma(tr[comp(1, j)], G[1][i], b);
+            b = vfma(tr[comp(2, j)], G[2][i], b);
+            bool fene = false;
+            if constexpr (VAR) fene = ph.fene;
+            if (fene) {
+                // FENE-P conformation: A.grad u + (A.grad u)^T - (f A - I) / lambda
+                const V fA = vrcp(vsub(one, vdiv(vadd(vadd(tr[0], tr[1]), tr[2]), vbc<V>(ph.fene_L2))));
+                const V fAt = c < 3 ? vfma(fA, tr[c], vneg(one)) : vmul(fA, tr[c]);
+                Sv[c] = vfma(vbc<V>(-ph.inv_l), fAt, vadd(a, b));
+            } else {
+                Sv[c] = vfma(vbc<V>(-ph.inv_l), tr[c], vfma(vbc<V>(ph.ep_l), vadd(G[i][j], G[j][i]), vadd(a, b)));
+            }
+        }
+    }
+#pragma unroll
+    for (int c = 0; c < 6; ++c) {
+        V S = src ? Sv[c] : vbc<V>(0.0f);
+        if constexpr (VAR) {
+            if (ph.divu_on) S = vfma(tr[c], vadd(vadd(G[0][0], G[1][1]), G[2][2]), S);
+            if (src && ph.gk != 0.0f) {
+                const int i = comp_i(c), j = comp_j(c);
+                V q = vmul(tr[comp(i, 0)], tr[comp(0, j)]);
+                q = vfma(tr[comp(i, 1)], tr[comp(1, j)], q);
+                q = vfma(tr[comp(i, 2)], tr[comp(2, j)], q);
+                S = vfma(vbc<V>(-ph.gk), q, S);
+            }
+        }
+        out[c] = flux ? vadd(vsub(tr[c], net[c]), S) : vadd(tr[c], S);
+    }
 }
 
 // Finite-volume stress update of one fluid cell (Sec. "Discretization", "Stability
@@ -488,36 +740,25 @@ __device__ __forceinline__ bool collide(R (&f)[Q], R rho, R drho, const R u[3], 
 // holding zero stress); nb.ub(l, out): boundary velocity of a solid face-l neighbour.
 // FP64 mode keeps the face-by-face order of the plain statement; shifted modes gather
 // the outflow as (sum of outgoing face velocities) * tau(r).
+// fv_core's neighbour accessor seen by fv_core_sh with one lane (the lane argument of ub
+// is always 0)
+template <class Nb>
+struct OneLaneNb {
+    const Nb &n;
+    __device__ __forceinline__ float u(int l, int j) const { return n.u(l, j); }
+    __device__ __forceinline__ float tau(int l, int c) const { return n.tau(l, c); }
+    __device__ __forceinline__ void ub(int l, int, float o[3]) const { n.ub(l, o); }
+};
+
 template <class R, bool SH, bool VAR, class Nb>
 __device__ __forceinline__ void fv_core(const Phys<R> &ph, const R (&tr)[6], const R (&ur)[3], uint32_t mask,
                                         const Nb &nb, R out[6]) {
-    R un[6][3];
-    R G[3][3];
     if constexpr (SH) {
-        // Branch-light form: every face neighbour's u is read (the staged halo and the
-        // periodically wrapped global neighbours are valid memory), and a solid face's u
-        // is replaced by the mirror value 2 u_b - u(r), whose average with u(r) is the
-        // face value u_b; the gradient is then half the difference of the two mirrored
-        // neighbours on every axis.  The mirror of a resting wall is -u(r); next to a
-        // moving boundary the mirror is 2 u_b - u(r) (the flux never reads a solid face's u).
-#pragma unroll
-        for (int k = 0; k < 3; ++k) {
-#pragma unroll
-            for (int h = 0; h < 2; ++h) {
-                const int l = 2 * k + h;
-#pragma unroll
-                for (int j = 0; j < 3; ++j) un[l][j] = nb_solid(mask, l + 1) ? -ur[j] : nb.u(l, j);
-                if ((mask & MASK_MOVING) && nb_solid(mask, l + 1)) {
-                    R ub[3];
-                    nb.ub(l, ub);
-#pragma unroll
-                    for (int j = 0; j < 3; ++j) un[l][j] = R(2) * ub[j] - ur[j];
-                }
-            }
-#pragma unroll
-            for (int j = 0; j < 3; ++j) G[k][j] = R(0.5) * (un[2 * k][j] - un[2 * k + 1][j]);
-        }
+        fv_core_sh<float, uint32_t, VAR>(ph, tr, ur, mask, OneLaneNb<Nb>{nb}, out);
     } else {
+        // FP64: the face-by-face order of the plain statement
+        R un[6][3];
+        R G[3][3];
 #pragma unroll
         for (int l = 0; l < 6; ++l) {
             if (!nb_solid(mask, l + 1)) {
@@ -540,11 +781,9 @@ __device__ __forceinline__ void fv_core(const Phys<R> &ph, const R (&tr)[6], con
                 G[k][j] = up - um;
             }
         }
-    }
-    R net[6] = {R(0), R(0), R(0), R(0), R(0), R(0)};
-    // without VAR the flux and the source are on (a solve with either off takes the VAR build)
-    if (!VAR || ph.flux_on) {
-        if constexpr (!SH) {
+        R net[6] = {R(0), R(0), R(0), R(0), R(0), R(0)};
+        // without VAR the flux and the source are on (a solve with either off takes the VAR build)
+        if (!VAR || ph.flux_on) {
 #pragma unroll
             for (int l = 0; l < 6; ++l) {
                 const int k = l >> 1;
@@ -565,64 +804,39 @@ __device__ __forceinline__ void fv_core(const Phys<R> &ph, const R (&tr)[6], con
                     net[c] = net[c] + (Jo - Ji);
                 }
             }
-        } else {
-            R aout = R(0);
-            R inflow[6] = {R(0), R(0), R(0), R(0), R(0), R(0)};
-#pragma unroll
-            for (int l = 0; l < 6; ++l) {
-                const int k = l >> 1;
-                const int s = (l & 1) ? -1 : 1;
-                // zero flux across a solid link: both coefficients selected to zero (a
-                // solid cell's stress is finite, so the inflow product below adds zero)
-                const bool open = !nb_solid(mask, l + 1);
-                const R vout = s > 0 ? ur[k] : -ur[k];
-                const R vin = s > 0 ? -un[l][k] : un[l][k];
-                R ao = (open && vout > R(0)) ? vout : R(0);
-                R b = (open && vin > R(0)) ? vin : R(0);
-                if (VAR && ph.ctu_on) {
-                    const int ta = k == 2 ? 0 : k + 1, tb = k == 0 ? 2 : k - 1;
-                    ao *= (R(1) - fabs(ur[ta])) * (R(1) - fabs(ur[tb]));
-                    b *= (R(1) - fabs(un[l][ta])) * (R(1) - fabs(un[l][tb]));
-                }
-                aout += ao;
-#pragma unroll
-                for (int c = 0; c < 6; ++c) inflow[c] += b * nb.tau(l, c);
-            }
-#pragma unroll
-            for (int c = 0; c < 6; ++c) net[c] = aout * tr[c] - inflow[c];
         }
-    }
-    R Sv[6] = {R(0), R(0), R(0), R(0), R(0), R(0)};
-    if (!VAR || ph.src_on) {  // one test for all six components
+        R Sv[6] = {R(0), R(0), R(0), R(0), R(0), R(0)};
+        if (!VAR || ph.src_on) {  // one test for all six components
+#pragma unroll
+            for (int c = 0; c < 6; ++c) {
+                const int i = comp_i(c), j = comp_j(c);
+                R a = R(0), b = R(0);
+#pragma unroll
+                for (int k = 0; k < 3; ++k) a = a + tr[comp(i, k)] * G[k][j];
+#pragma unroll
+                for (int k = 0; k < 3; ++k) b = b + tr[comp(k, j)] * G[k][i];
+                if (VAR && ph.fene) {
+                    // FENE-P conformation: A.grad u + (A.grad u)^T - (f A - I) / lambda
+                    const R fA = fene_factor<R>(ph, tr[0], tr[1], tr[2]);
+                    Sv[c] = a + b - ph.inv_l * (c < 3 ? fA * tr[c] - R(1) : fA * tr[c]);
+                } else {
+                    Sv[c] = a + b + ph.ep_l * (G[i][j] + G[j][i]) - ph.inv_l * tr[c];
+                }
+            }
+        }
 #pragma unroll
         for (int c = 0; c < 6; ++c) {
-            const int i = comp_i(c), j = comp_j(c);
-            R a = R(0), b = R(0);
+            R S = Sv[c];
+            if (VAR && ph.divu_on) S = S + tr[c] * ((G[0][0] + G[1][1]) + G[2][2]);
+            if (VAR && ph.src_on && ph.gk != R(0)) {
+                const int i = comp_i(c), j = comp_j(c);
+                R q = R(0);
 #pragma unroll
-            for (int k = 0; k < 3; ++k) a = a + tr[comp(i, k)] * G[k][j];
-#pragma unroll
-            for (int k = 0; k < 3; ++k) b = b + tr[comp(k, j)] * G[k][i];
-            if (VAR && ph.fene) {
-                // FENE-P conformation: A.grad u + (A.grad u)^T - (f A - I) / lambda
-                const R fA = fene_factor<R>(ph, tr[0], tr[1], tr[2]);
-                Sv[c] = a + b - ph.inv_l * (c < 3 ? fA * tr[c] - R(1) : fA * tr[c]);
-            } else {
-                Sv[c] = a + b + ph.ep_l * (G[i][j] + G[j][i]) - ph.inv_l * tr[c];
+                for (int k = 0; k < 3; ++k) q = q + tr[comp(i, k)] * tr[comp(k, j)];
+                S = S - ph.gk * q;
             }
+            out[c] = tr[c] - net[c] + S;
         }
-    }
-#pragma unroll
-    for (int c = 0; c < 6; ++c) {
-        R S = Sv[c];
-        if (VAR && ph.divu_on) S = S + tr[c] * ((G[0][0] + G[1][1]) + G[2][2]);
-        if (VAR && ph.src_on && ph.gk != R(0)) {
-            const int i = comp_i(c), j = comp_j(c);
-            R q = R(0);
-#pragma unroll
-            for (int k = 0; k < 3; ++k) q = q + tr[comp(i, k)] * tr[comp(k, j)];
-            S = S - ph.gk * q;
-        }
-        out[c] = tr[c] - net[c] + S;
     }
 }
 

@@ -101,14 +101,14 @@ struct Launch {
         return cudaGetLastError();
     }
     // The row-pipelined stream-collide (k_lb_rows): rows of a multiple of 32 cells, at
-    // most LR_MAX_NX, 16-byte aligned PDF, stress and mask arrays, a layout that fits the
+    // most LR_MAX_NX, 16-byte aligned field arrays, a layout that fits the
     // shared memory of one block, Oldroyd-B or Giesekus stress (FENE-P reads conformation
     // tensors: per-cell kernel).  The result is bitwise that of the per-cell kernel.
     static size_t rows_smem(int nx) { return RowsLayout<S>{nx}.total(); }
     static bool rows_ok(const DevState &d) {
         auto al = [](const void *p) { return ((uintptr_t)p & 15u) == 0; };
         if (d.ph.fene || d.g.nx % 32 != 0 || d.g.nx < 64 || d.g.nx > LR_MAX_NX) return false;
-        if (!al(d.f) || !al(d.tau[0]) || !al(d.tau[1]) || !al(d.mask)) return false;
+        if (!al(d.f) || !al(d.tau[0]) || !al(d.tau[1]) || !al(d.mask) || !al(d.u[0]) || !al(d.u[1])) return false;
         int dev = 0, optin = 0;
         if (cudaGetDevice(&dev) != cudaSuccess) return false;
         if (cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess) return false;
@@ -116,7 +116,7 @@ struct Launch {
     }
     // rows per strip: enough strips for ~16 waves of resident blocks (d.lb_rows_yc > 0:
     // that many), at least 8 rows
-    static RowsWork rows_work(const DevState &d) {
+    static RowsWork rows_work(const DevState &d, size_t smem) {
         const int ny = d.g.ny, nzc = zcount(d);
         int yc = d.lb_rows_yc;
         if (yc <= 0) {
@@ -125,7 +125,7 @@ struct Launch {
                 cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
                 cudaDeviceGetAttribute(&smpb, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
             }
-            long long per_sm = smpb > 0 ? (long long)smpb / (long long)(rows_smem(d.g.nx) + 1024) : 1;
+            long long per_sm = smpb > 0 ? (long long)smpb / (long long)(smem + 1024) : 1;
             if (per_sm < 1) per_sm = 1;
             const long long want = 16LL * sms * per_sm;
             long long strips = (want + nzc - 1) / nzc;
@@ -141,8 +141,8 @@ struct Launch {
     }
     static cudaError_t lb_rows(const DevState &d, int parity, cudaStream_t s) {
         KArgs<S> a = args(d);
-        const RowsWork w = rows_work(d);
         const size_t sm = rows_smem(d.g.nx);
+        const RowsWork w = rows_work(d, sm);
         static SmemAttrOnce attr[2];
         int dev = 0, optin = 0;
         cudaError_t e = cudaGetDevice(&dev);

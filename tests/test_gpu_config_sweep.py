@@ -123,7 +123,10 @@ def test_config1_as_a_bf16_pool_member_against_analytic(capsys):
     assert np.isfinite(u).all() and not ch.is_unstable()
     assert curve < 0.02
     assert prof[0] < 0.02 and prof[1] < 0.02 and prof[2] < 0.05 and prof[3] < 0.03 and prof[4] < 0.06
-    assert e64[0] < 0.01 and e64[1] < 0.02
+    # the BF16 error against FP64 after 20,000 steps depends on the stochastic-rounding
+    # realization: eight realizations of this channel (g changed by 1e-6 relative) gave
+    # 2.0e-3 to 1.16e-2 in u, mean 6.6e-3, standard deviation 3.4e-3
+    assert e64[0] < 0.025 and e64[1] < 0.02
     for s in (duct, ch, ch2):
         pool.remove(s)
         s.close()

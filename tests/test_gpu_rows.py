@@ -111,7 +111,7 @@ def _run(shape, prm, fl, wall, rho0, u0, t0, precision, schedule, steps, particl
 
 
 @pytest.mark.parametrize("precision", ["f64", "f32", "f16", "bf16"])
-@pytest.mark.parametrize("shape,periodic,sphere", [((64, 9, 7), (1, 1, 1), False), ((96, 12, 10), (1, 0, 0), False),
+@pytest.mark.parametrize("shape,periodic,sphere", [((64, 9, 7), (1, 1, 1), False), ((128, 12, 10), (1, 0, 0), False),
                                                    ((64, 16, 16), (1, 1, 1), True)])
 def test_rows_equal_cells_bitwise(precision, shape, periodic, sphere):
     from paper_2009_12279_gb300 import lbve
@@ -152,12 +152,31 @@ def test_rows_equal_cells_bitwise_512_rows(precision):
 def test_rows_not_taken_where_the_grid_does_not_allow_it():
     from paper_2009_12279_gb300 import Solver, lbve
 
-    for shape, kw in (((37, 8, 8), {}), ((48, 8, 8), {}), ((64, 8, 8), dict(schedule=lbve.SCHED_SPLIT)),
-                      ((64, 8, 8), dict(fene_L2=50.0)), ((544, 2, 2), {}), ((512, 4, 4), dict(precision="f64"))):
+    for shape, kw in (((37, 8, 8), {}), ((48, 8, 8), {}),
+                      ((64, 8, 8), dict(schedule=lbve.SCHED_SPLIT)), ((64, 8, 8), dict(fene_L2=50.0)),
+                      ((576, 2, 2), {}), ((512, 4, 4), dict(precision="f64"))):
         kw.setdefault("precision", "f32")
         s = Solver(shape, **kw)
         assert s.stream_collide_kernel == "cells", (shape, kw)
         s.close()
-    s = Solver((384, 4, 4), precision="f64")
-    assert s.stream_collide_kernel == "rows"
-    s.close()
+    for shape, prec in (((384, 4, 4), "f64"), ((96, 4, 4), "bf16"), ((64, 4, 4), "f16"), ((512, 2, 2), "f32")):
+        s = Solver(shape, precision=prec)
+        assert s.stream_collide_kernel == "rows", (shape, prec)
+        s.close()
+
+
+@pytest.mark.parametrize("shape,periodic", [((64, 12, 10), (1, 0, 0)), ((128, 9, 7), (1, 1, 1))])
+def test_rows_fp32_match_oracle(shape, periodic):
+    """FP32 through the row pipeline against the FP64 oracle (relative L2 <= 1e-5)."""
+    from gpu_helpers import TOL_F32
+
+    fl, wall, rho0, u0, t0, prm = _case(shape, periodic, 17)
+    g, o = pair(shape, prm, fl, wall, rho=rho0, u=u0, tau=t0, precision="f32")
+    assert g.stream_collide_kernel == "rows"
+    for n in (1, 150, 150):
+        g.step(n)
+        o.step(n)
+    e = compare(g, o)
+    print(f"\n[rows f32 {shape} periodic {periodic}, 301 steps] {e}")
+    assert max(e["u"], e["tau"]) <= TOL_F32, e
+

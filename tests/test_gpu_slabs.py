@@ -16,10 +16,10 @@ def _gpu():
     require_gpu()
 
 
-def _case(periodic_z):
+def _case(periodic_z, nx=20):
     from paper_2009_12279_gb300 import workloads
 
-    shape = (20, 18, 30)
+    shape = (nx, 18, 30)
     nx, ny, nz = shape
     rng = np.random.default_rng(61)
     fl = np.zeros((nz, ny, nx), np.uint8)
@@ -39,12 +39,14 @@ def _case(periodic_z):
 
 
 @pytest.mark.parametrize("precision", ["f64", "f32", "bf16", "f16"])
-@pytest.mark.parametrize("periodic_z,nslabs", [(True, 2), (True, 4), (False, 3), (True, 1)])
-def test_decomposed_run_equals_the_undecomposed_one(precision, periodic_z, nslabs):
+@pytest.mark.parametrize("periodic_z,nslabs,nx", [(True, 2, 20), (True, 4, 20), (False, 3, 20), (True, 1, 20),
+                                                  (True, 2, 64), (False, 3, 64)])
+def test_decomposed_run_equals_the_undecomposed_one(precision, periodic_z, nslabs, nx):
+    """nx = 64 runs the row-pipelined kernels (z-ranges of the slabs included)."""
     from paper_2009_12279_gb300 import Solver
     from paper_2009_12279_gb300.slabs import SlabDomain
 
-    shape, prm, fl, wall, u0, t0 = _case(periodic_z)
+    shape, prm, fl, wall, u0, t0 = _case(periodic_z, nx)
     whole = Solver(shape, precision=precision, **prm)
     whole.set_geometry(fl, wall)
     whole.init_fields(u=u0, tau=t0)
@@ -62,7 +64,10 @@ def test_decomposed_run_equals_the_undecomposed_one(precision, periodic_z, nslab
             assert np.array_equal(a, b), (precision, dom.time, name)
     bw, bd = whole.body_forces(), dom.body_forces()
     assert np.abs(bw[2]).max() > 0
-    assert np.allclose(bd[[2, 3]], bw[[2, 3]], rtol=1e-12, atol=1e-16)
+    # the fields are bitwise equal; a body force is summed per slab and then over the slabs,
+    # another order of the same FP64 link contributions (the moving lid's normal force is a
+    # sum of thousands of O(1) terms), so it agrees to rounding only
+    assert np.allclose(bd[[2, 3]], bw[[2, 3]], rtol=1e-10, atol=1e-16), (bd[[2, 3]] - bw[[2, 3]])
     whole.close()
     dom.close()
 
