@@ -223,10 +223,10 @@ def run_reference(args):
 FV_EXTRA = {}
 
 
-def build_solver(n, prec, schedule, stream, torch):
+def build_solver(n, prec, schedule, stream, torch, nz=None):
     from paper_2009_12279_gb300 import Solver, lbve, workloads
 
-    cfg = workloads.config_throughput(n)
+    cfg = workloads.config_throughput(n, nz=nz)
     cfg["params"].update(FV_EXTRA)
     sched = {"auto": lbve.SCHED_AUTO, "split": lbve.SCHED_SPLIT, "fused": lbve.SCHED_FUSED}[schedule]
     s = Solver(cfg["shape"], precision=prec, schedule=sched, stream=stream, **cfg["params"])
@@ -237,7 +237,8 @@ def build_solver(n, prec, schedule, stream, torch):
     # initial velocity drawn on the device (seeded) to keep host memory small
     g = torch.Generator(device="cuda")
     g.manual_seed(1)
-    u = (torch.rand((3, n, n, n), generator=g, device="cuda", dtype=torch.float64) * 2.0 - 1.0) * 1e-3
+    nx, ny, nzz = cfg["shape"]
+    u = (torch.rand((3, nzz, ny, nx), generator=g, device="cuda", dtype=torch.float64) * 2.0 - 1.0) * 1e-3
     s.init_fields_device(0, u.data_ptr(), 0)
     torch.cuda.synchronize()
     del u
@@ -488,7 +489,7 @@ def run_ours(args):
     results = {}
     clocks = None
     for prec in args.precisions:
-        s, cfg = build_solver(n, prec, args.schedule, stream, torch)
+        s, cfg = build_solver(n, prec, args.schedule, stream, torch, nz=args.nz)
         tuned = None
         if args.schedule != "fused" and not args.no_autotune:
             # schedule autotuning on the solve's own steps (launch shapes do not change
@@ -511,7 +512,7 @@ def run_ours(args):
         if dist:
             dist.all_reduce(t, op=dist.ReduceOp.MAX)
         ms_max = float(t.item())
-        cells = n ** 3
+        cells = n * n * (args.nz or n)
         mlups = world * cells * args.steps / (ms_max * 1e-3) / 1e6
         fluid_fraction = cfg["fluid_cells"] / cells
         dom = max(kt.items(), key=lambda kv: kv[1][0])
@@ -552,9 +553,10 @@ def run_ours(args):
             "warmup": args.warmup, "ms_per_step": main["ms_per_step"], "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64" if args.precisions[0] == "f64" else "f32",
             "data": "synthetic",
-            "config": {"workload": f"throughput {n}^3 periodic, 1% Bernoulli obstacles, u~U(-1e-3,1e-3), "
+            "config": {"workload": (f"throughput {n}^3" if not args.nz else f"throughput {n}x{n}x{args.nz}") +
+                                   " periodic, 1% Bernoulli obstacles, u~U(-1e-3,1e-3), "
                                    f"beta 0.5, lambda 1000, eta 1/6, {args.precisions[0]} PDF storage",
-                       "cells": n ** 3, "schedule": args.schedule, "parallelism": f"replicas{world}",
+                       "cells": n * n * (args.nz or n), "schedule": args.schedule, "parallelism": f"replicas{world}",
                        **({"fv_variants": dict(FV_EXTRA)} if FV_EXTRA else {}),
                        "l2": "state larger than L2 (no flush needed)",
                        "schedule_tuning": main.get("schedule_tuning"),
@@ -615,6 +617,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--n", type=int, default=512, help="side of the cubic throughput domain")
+    ap.add_argument("--nz", type=int, default=None,
+                    help="z extent of the throughput domain (n x n x nz; profiling of small cases)")
     ap.add_argument("--precisions", default="f32,f16,bf16", help="PDF storage modes; the first one is the headline")
     ap.add_argument("--schedule", choices=["auto", "split", "fused"], default="auto")
     ap.add_argument("--no-cpu-baseline", action="store_true")

@@ -271,6 +271,21 @@ int lbve_is_unstable(const lbve_ctx *ctx);
 int lbve_stream_collide_kernel(const lbve_ctx *ctx);
 
 /*
+ * Which stress-update kernel (the finite-volume step, Eqs. (continuity)-(source))
+ * lbve_step launches (split schedule).  Both march a column of cells through a z-chunk
+ * with the tau and u planes staged in a shared-memory ring.  LBVE_FV_PAIRS: 64 x 8
+ * columns, each thread updating two neighbouring cells of a row in the two lanes of
+ * paired FP32 instructions; taken with schedule AUTO for FP32, FP16 and BF16 storage when
+ * the solve uses the method's own update (flux and source on; no CTU, tau div u, Giesekus
+ * or FENE-P term), nx is a multiple of 4 and the arrays are 16-byte aligned (always with
+ * the library's own allocations).  LBVE_FV_TILES: 32 x 8 columns, one cell per thread.
+ * Results are bitwise equal.  -1 for NULL.
+ */
+#define LBVE_FV_TILES 0
+#define LBVE_FV_PAIRS 1
+int lbve_stress_kernel(const lbve_ctx *ctx);
+
+/*
  * Copy the macroscopic fields to host arrays (each may be NULL): rho (n), u (3n, the
  * physical velocity (j + F/2)/rho of Eq. (macroscopic-velocity) with F = g + F^p),
  * tau (6n), flags (n).  Non-fluid cells read 0.  Page-locked arrays the device can

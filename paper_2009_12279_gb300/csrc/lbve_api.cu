@@ -540,7 +540,7 @@ lbve_status create_impl(const lbve_params *p, void *stream, lbve_alloc_fn alloc,
     g.n = (long long)p->nx * p->ny * p->nz;
     g.np = padded(g.n);
     c->d.block_x = lbve::default_block_x(*p);
-    c->d.lb_rows = p->schedule == LBVE_SCHED_AUTO ? 1 : 0;
+    c->d.auto_kernels = p->schedule == LBVE_SCHED_AUTO ? 1 : 0;
     if (p->block_x == 0) {  // a schedule tuned for this shape earlier in the process
         int bx = 0, zc = 0;
         if (tuned_ctx(*p, bx, zc)) {
@@ -1390,6 +1390,11 @@ int lbve_is_unstable(const lbve_ctx *c) { return c ? (unstable(c) ? 1 : 0) : -1;
 int lbve_stream_collide_kernel(const lbve_ctx *c) {
     if (!c) return -1;
     return c->kt->lb_rows_used(c->d) ? LBVE_LB_ROWS : LBVE_LB_CELLS;
+}
+
+int lbve_stress_kernel(const lbve_ctx *c) {
+    if (!c) return -1;
+    return c->kt->fv_pair_used(c->d) ? LBVE_FV_PAIRS : LBVE_FV_TILES;
 }
 
 const char *lbve_last_error(const lbve_ctx *c) { return c ? c->err.c_str() : g_create_error.c_str(); }

@@ -820,6 +820,153 @@ __global__ void __launch_bounds__(FV_X * FV_Y, sizeof(typename Store<S>::R) == 8
 }
 
 // ---------------------------------------------------------------------------------
+// Two-cell stress update (the shifted modes' plain build: flux and source on, no
+// variant).  As k_fv_tiled, a block marches a column through a z-chunk with the tau and u
+// planes (one-cell halo in y, four cells in x: whole 16-byte chunks) staged in a
+// four-plane shared-memory ring one plane ahead; the column is 64 x 8 cells and each of
+// the 256 threads updates the cells x, x + 1 of one row in the two lanes of fv_core_sh
+// (paired FP32 instructions), so the results are bitwise those of k_fv_tiled.
+// ---------------------------------------------------------------------------------
+constexpr int FP_TX = 64, FP_TY = 8, FP_NT = 256;
+constexpr int FP_XO = 4, FP_HX = FP_TX + 2 * FP_XO, FP_HY = FP_TY + 2, FP_HN = FP_HX * FP_HY;
+constexpr int FP_CPR = FP_HX / 4, FP_CH = FP_CPR * FP_HY;  // 16-byte chunks per halo row, per plane
+struct FvPairSmem {
+    float tau[FV_RING][6][FP_HN];
+    float u[FV_RING][3][FP_HN];
+};
+
+template <class S, bool ZR>
+__global__ void __launch_bounds__(FP_NT, 2) k_fv_pair(KArgs<S> a, int zchunk) {
+    static_assert(Store<S>::shifted, "two-cell stress update: FP32 stress");
+    extern __shared__ __align__(16) unsigned char fp_smem_raw[];
+    FvPairSmem &sm = *reinterpret_cast<FvPairSmem *>(fp_smem_raw);
+    const int tid = threadIdx.x;
+    const int nx = a.g.nx, ny = a.g.ny;
+    const int tiles_x = (nx + FP_TX - 1) / FP_TX, tiles_y = (ny + FP_TY - 1) / FP_TY;
+    const int item = blockIdx.x;
+    const int tx = item % tiles_x, ty = (item / tiles_x) % tiles_y, zc = item / (tiles_x * tiles_y);
+    const int x0 = tx * FP_TX, y0 = ty * FP_TY;
+    const int z0 = ZR ? a.zlo + zc * zchunk : zc * zchunk;
+    const int z1 = ZR ? min(a.zhi, z0 + zchunk) : min(a.g.nz, z0 + zchunk);
+    const unsigned nxu = (unsigned)nx, nxy = (unsigned)nx * (unsigned)ny;
+    // staging: chunk positions tid and tid + FP_NT of 2 FP_CH (the first FP_CH carry tau
+    // components 0..4, the others component 5 and u); -1 beyond a closed side
+    int off[2], dpos[2], half[2];
+#pragma unroll
+    for (int q = 0; q < 2; ++q) {
+        const int p = tid + q * FP_NT;
+        half[q] = p < 2 * FP_CH ? p / FP_CH : 2;
+        off[q] = -1;
+        dpos[q] = 0;
+        if (half[q] < 2) {
+            const int pp = p - half[q] * FP_CH, row = pp / FP_CPR, cq = pp - row * FP_CPR;
+            dpos[q] = row * FP_HX + 4 * cq;
+            const int xg = side_coord(x0 - FP_XO + 4 * cq, nx, a.g.per[0]);
+            const int yg = side_coord(y0 - 1 + row, ny, a.g.per[1]);
+            if (xg >= 0 && yg >= 0) off[q] = xg + nx * yg;
+        }
+    }
+    auto stage = [&](int zz) {
+        const int zg = side_coord(zz, a.g.nz, a.g.per[2]);
+        const int s4 = fv_slot(zz);
+#pragma unroll
+        for (int q = 0; q < 2; ++q) {
+            if (half[q] >= 2) continue;
+            const bool in = off[q] >= 0 && zg >= 0;
+            const unsigned r = in ? (unsigned)off[q] + nxy * (unsigned)zg : 0u;
+            const unsigned n = in ? 16u : 0u;
+            if (half[q] == 0) {
+#pragma unroll
+                for (int c = 0; c < 5; ++c) cp_async16_zfill(&sm.tau[s4][c][dpos[q]], a.tq[c] + r, n);
+            } else {
+                cp_async16_zfill(&sm.tau[s4][5][dpos[q]], a.tq[5] + r, n);
+#pragma unroll
+                for (int j = 0; j < 3; ++j) cp_async16_zfill(&sm.u[s4][j][dpos[q]], a.uiq[j] + r, n);
+            }
+        }
+        cp_async_commit();
+    };
+    const int ti = tid % (FP_TX / 2), tj = tid / (FP_TX / 2);
+    const int x = x0 + 2 * ti, y = y0 + tj;
+    const int kc = (2 * ti + FP_XO) + (tj + 1) * FP_HX;
+    const bool own = x < nx && y < ny;  // nx is a multiple of 4: x + 1 < nx too
+#pragma unroll
+    for (int q = -1; q <= LBVE_FV_AHEAD; ++q) stage(z0 + q);
+    auto mask2 = [&](int zz) { return *reinterpret_cast<const uint2 *>(a.mask + ((unsigned)x + nxu * (unsigned)y + nxy * (unsigned)zz)); };
+    uint2 m_next = own ? mask2(z0) : make_uint2(1u, 1u);
+#pragma unroll 1
+    for (int z = z0; z < z1; ++z) {
+        const uint2 m = m_next;
+        if (own && z + 1 < z1) m_next = mask2(z + 1);
+        if (z + 1 + LBVE_FV_AHEAD <= z1)
+            stage(z + 1 + LBVE_FV_AHEAD);
+        else
+            cp_async_commit();
+        asm volatile("cp.async.wait_group %0;\n" ::"n"(LBVE_FV_AHEAD) : "memory");
+        __syncthreads();
+        if (own) {
+            const unsigned r = (unsigned)x + nxu * (unsigned)y + nxy * (unsigned)z;
+            const bool fa = !(m.x & 1u), fb = !(m.y & 1u);
+            float2 out[6];
+            if (fa || fb) {
+                const int sc = fv_slot(z), sd = fv_slot(z - 1), su = fv_slot(z + 1);
+                auto ld2 = [](const float *p) { return *reinterpret_cast<const float2 *>(p); };
+                float2 tr[6], ur[3];
+#pragma unroll
+                for (int c = 0; c < 6; ++c) tr[c] = ld2(&sm.tau[sc][c][kc]);
+#pragma unroll
+                for (int j = 0; j < 3; ++j) ur[j] = ld2(&sm.u[sc][j][kc]);
+                struct Nb {
+                    const KArgs<S> &a;
+                    const FvPairSmem &sm;
+                    const float2 (&tr)[6];
+                    const float2 (&ur)[3];
+                    int sc, sd, su, kc, x, y, z;
+                    __device__ __forceinline__ float2 val(const float (*pl)[FP_HN], int l, int q, float2 own2,
+                                                          const float (*pd)[FP_HN], const float (*pu)[FP_HN]) const {
+                        switch (l) {
+                            case 0: return make_float2(own2.y, pl[q][kc + 2]);
+                            case 1: return make_float2(pl[q][kc - 1], own2.x);
+                            case 2: return *reinterpret_cast<const float2 *>(&pl[q][kc + FP_HX]);
+                            case 3: return *reinterpret_cast<const float2 *>(&pl[q][kc - FP_HX]);
+                            case 4: return *reinterpret_cast<const float2 *>(&pu[q][kc]);
+                            default: return *reinterpret_cast<const float2 *>(&pd[q][kc]);
+                        }
+                    }
+                    __device__ __forceinline__ float2 u(int l, int k) const {
+                        return val(sm.u[sc], l, k, ur[k], sm.u[sd], sm.u[su]);
+                    }
+                    __device__ __forceinline__ float2 tau(int l, int c) const {
+                        return val(sm.tau[sc], l, c, tr[c], sm.tau[sd], sm.tau[su]);
+                    }
+                    __device__ __forceinline__ void ub(int l, int ln, float o[3]) const {
+                        const int kk = l >> 1, sg = (l & 1) ? -1 : 1;
+                        int xq = x + ln + (kk == 0 ? sg : 0), yq = y + (kk == 1 ? sg : 0), zq = z + (kk == 2 ? sg : 0);
+                        xq = xq < 0 ? xq + a.g.nx : (xq >= a.g.nx ? xq - a.g.nx : xq);
+                        yq = yq < 0 ? yq + a.g.ny : (yq >= a.g.ny ? yq - a.g.ny : yq);
+                        zq = zq < 0 ? zq + a.g.nz : (zq >= a.g.nz ? zq - a.g.nz : zq);
+                        const int fl = a.flag[(unsigned)xq +
+                                              (unsigned)a.g.nx * ((unsigned)yq + (unsigned)a.g.ny * (unsigned)zq)];
+                        boundary_velocity_fast<float>(a.g, a.ph, a.parts, fl, xq, yq, zq, o);
+                    }
+                };
+                const Nb nb{a, sm, tr, ur, sc, sd, su, kc, x, y, z};
+                fv_core_sh<float2, uint2, false>(a.ph, tr, ur, m, nb, out);
+#pragma unroll
+                for (int c = 0; c < 6; ++c) out[c] = make_float2(fa ? out[c].x : 0.0f, fb ? out[c].y : 0.0f);
+            } else {
+#pragma unroll
+                for (int c = 0; c < 6; ++c) out[c] = make_float2(0.0f, 0.0f);
+            }
+#pragma unroll
+            for (int c = 0; c < 6; ++c) *reinterpret_cast<float2 *>(a.toq[c] + r) = out[c];
+        }
+        __syncthreads();  // the next stage overwrites the slot of plane z - 1
+    }
+    cp_async_wait_all();
+}
+
+// ---------------------------------------------------------------------------------
 // batched schedule: the resident solves of a pool advance together.  Each kernel is a
 // persistent grid over a packed list of work items (solve, block); a block reads the
 // solve's descriptor into shared memory and runs the same per-cell code as the

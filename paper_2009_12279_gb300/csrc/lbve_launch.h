@@ -90,9 +90,10 @@ struct DevState {
     // offset of this grid's cell indices in the decomposed domain's (rounding keys of the
     // 16-bit stores use global cells, so a slab rounds as the undecomposed domain does)
     unsigned key_base = 0;
-    // stream-collide by the row pipeline (k_lb_rows) where the grid allows it, else the
-    // per-cell kernel; rows per strip of the row pipeline (0: by the SM count)
-    int lb_rows = 0;
+    // schedule AUTO: the row-pipelined stream-collide (k_lb_rows) and the two-cell stress
+    // kernel (k_fv_pair) where the grid allows them, else the per-cell stream-collide and
+    // the tiled stress kernel; rows per strip of the row pipeline (0: by the SM count)
+    int auto_kernels = 0;
     int lb_rows_yc = 0;
 };
 
@@ -149,6 +150,7 @@ struct KernelTable {
     cudaError_t (*halo_pack)(const DevState &, int what, int side, int parity, void *buf, cudaStream_t);
     cudaError_t (*halo_unpack)(const DevState &, int what, int side, int parity, const void *buf, cudaStream_t);
     int (*lb_rows_used)(const DevState &);  // 1 when the stream-collide runs the row pipeline
+    int (*fv_pair_used)(const DevState &);  // 1 when the stress update runs two cells per thread
 };
 
 // Bounding-box side used to size the per-particle scratch (cells within R + margin).

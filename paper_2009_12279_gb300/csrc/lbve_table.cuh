@@ -160,9 +160,9 @@ struct Launch {
             k_lb_rows<S, 1><<<nblk, nthr, sm, s>>>(a, w);
         return cudaGetLastError();
     }
-    static int lb_rows_used(const DevState &d) { return d.lb_rows && rows_ok(d) ? 1 : 0; }
+    static int lb_rows_used(const DevState &d) { return d.auto_kernels && rows_ok(d) ? 1 : 0; }
     static cudaError_t lb(const DevState &d, int parity, cudaStream_t s) {
-        if (d.lb_rows && rows_ok(d)) return lb_rows(d, parity, s);
+        if (d.auto_kernels && rows_ok(d)) return lb_rows(d, parity, s);
         KArgs<S> a = args(d);
         if (d.ph.fene) {  // the polymer force takes the stress of each cell's conformation
             if (parity == 0)
@@ -222,7 +222,55 @@ struct Launch {
         }
         return zr ? fv_launch<VAR, true, false>(d, nblk, zc, s) : fv_launch<VAR, false, false>(d, nblk, zc, s);
     }
+    // The two-cell stress kernel (k_fv_pair): schedule AUTO, the shifted modes' plain
+    // build (flux and source on, no variant), nx a multiple of 4 (16-byte staging) and
+    // 16-byte aligned stress, velocity and mask arrays.  Bitwise the tiled kernel's result.
+    static bool fv_pair_ok(const DevState &d) {
+        if constexpr (!Store<S>::shifted) {
+            return false;
+        } else {
+            auto al = [](const void *p) { return ((uintptr_t)p & 15u) == 0; };
+            if (!d.auto_kernels || fv_variant(d) || d.g.nx % 4 != 0) return false;
+            return al(d.tau[0]) && al(d.tau[1]) && al(d.u[0]) && al(d.u[1]) && al(d.mask);
+        }
+    }
+    static int fv_pair_used(const DevState &d) { return fv_pair_ok(d) ? 1 : 0; }
+    // z-planes per block of the two-cell stress kernel (~16 waves of 2 resident blocks)
+    static int fv_pair_zchunk(const DevState &d) {
+        const int nz = zcount(d);
+        if (d.fv_zchunk > 0) return d.fv_zchunk < nz ? d.fv_zchunk : nz;
+        const long long tiles = (long long)((d.g.nx + FP_TX - 1) / FP_TX) * ((d.g.ny + FP_TY - 1) / FP_TY);
+        int dev = 0, sms = 148;
+        if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        const long long want = 16LL * 2 * sms;
+        const long long chunks = (want + tiles - 1) / tiles;
+        long long zc = (nz + chunks - 1) / chunks;
+        if (zc < 16) zc = 16;
+        if (zc > nz) zc = nz;
+        return (int)zc;
+    }
+    static cudaError_t fv_pair(const DevState &d, cudaStream_t s) {
+        if constexpr (!Store<S>::shifted) {
+            return cudaErrorInvalidValue;
+        } else {
+            KArgs<S> a = args(d);
+            const int zc = fv_pair_zchunk(d);
+            const int tiles = ((d.g.nx + FP_TX - 1) / FP_TX) * ((d.g.ny + FP_TY - 1) / FP_TY);
+            const unsigned nblk = (unsigned)(tiles * ((zcount(d) + zc - 1) / zc));
+            const size_t sm = sizeof(FvPairSmem);
+            static SmemAttrOnce attr[2];
+            const bool zr = d.zhi > 0;  // a z-slab: planes [zlo, zhi) only
+            cudaError_t e = zr ? attr[1].ensure(k_fv_pair<S, true>, sm) : attr[0].ensure(k_fv_pair<S, false>, sm);
+            if (e != cudaSuccess) return e;
+            if (zr)
+                k_fv_pair<S, true><<<nblk, FP_NT, sm, s>>>(a, zc);
+            else
+                k_fv_pair<S, false><<<nblk, FP_NT, sm, s>>>(a, zc);
+            return cudaGetLastError();
+        }
+    }
     static cudaError_t fv(const DevState &d, cudaStream_t s) {
+        if (fv_pair_ok(d)) return fv_pair(d, s);
         return fv_variant(d) ? fv_var<true>(d, s) : fv_var<false>(d, s);
     }
     static cudaError_t momentum_exchange(const DevState &d, int parity, const long long *links, const int *seg_begin,
@@ -503,7 +551,7 @@ const KernelTable *Launch<S>::table(int prec) {
                                       &fused,         sizeof(BatchEntry<S>), &fill_entry, &lb_batched,
                                       &fv_batched,    &batched_grid,    &residual,   &batch_tiles,
                                       &fv_zchunk_of,  &fv_variant_of,   sizeof(PartEntry<S>), &fill_part_entry,
-                                      &particle_phase_batched, &halo_pack, &halo_unpack, &lb_rows_used};
+                                      &particle_phase_batched, &halo_pack, &halo_unpack, &lb_rows_used, &fv_pair_used};
         return &t;
 }
 

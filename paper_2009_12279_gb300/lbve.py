@@ -25,6 +25,7 @@ KERNEL_KINDS = ["lb", "fv", "fused", "momentum_exchange", "particle", "", "", ""
 EUNSTABLE = 4
 HALO_F, HALO_U, HALO_TAU = 0, 1, 2
 LB_CELLS, LB_ROWS = 0, 1
+FV_TILES, FV_PAIRS = 0, 1
 STATUS = ["LBVE_OK", "LBVE_EINVAL", "LBVE_ENOMEM", "LBVE_ECUDA", "LBVE_EUNSTABLE", "LBVE_ETIMEOUT", "LBVE_ESTATE"]
 
 # every entry point declared in include/lbve.h
@@ -34,7 +35,7 @@ EXPORTS = [
     "lbve_read_fields_device", "lbve_read_pdfs", "lbve_write_pdfs", "lbve_read_particle", "lbve_read_conversions", "lbve_read_body_forces",
     "lbve_reduce", "lbve_residual", "lbve_pool_create", "lbve_pool_destroy", "lbve_pool_fits", "lbve_pool_admit",
     "lbve_pool_remove", "lbve_pool_step", "lbve_pool_residuals", "lbve_pool_size", "lbve_pool_bytes_in_use",
-    "lbve_pool_set_graphs", "lbve_pool_last_error", "lbve_step_noalloc", "lbve_noalloc_last_error", "lbve_set_kernel_timing", "lbve_read_kernel_times", "lbve_time", "lbve_synchronize", "lbve_is_unstable", "lbve_stream_collide_kernel", "lbve_checkpoint_bytes", "lbve_save", "lbve_restore",
+    "lbve_pool_set_graphs", "lbve_pool_last_error", "lbve_step_noalloc", "lbve_noalloc_last_error", "lbve_set_kernel_timing", "lbve_read_kernel_times", "lbve_time", "lbve_synchronize", "lbve_is_unstable", "lbve_stream_collide_kernel", "lbve_stress_kernel", "lbve_checkpoint_bytes", "lbve_save", "lbve_restore",
     "lbve_set_z_range", "lbve_step_phase", "lbve_halo_bytes", "lbve_halo_pack", "lbve_halo_unpack", "lbve_last_error", "lbve_status_string",
     "lbve_autotune", "lbve_pool_autotune",
     # include/lbve2d.h
@@ -143,6 +144,7 @@ def load(path: str | None = None):
         L.lbve_synchronize.argtypes = [vp]
         L.lbve_is_unstable.argtypes = [vp]
         L.lbve_stream_collide_kernel.argtypes = [vp]
+        L.lbve_stress_kernel.argtypes = [vp]
         L.lbve_set_z_range.argtypes = [vp, ct.c_int, ct.c_int, ct.c_int]
         L.lbve_step_phase.argtypes = [vp, ct.c_int]
         L.lbve_halo_bytes.argtypes = [vp, ct.c_int]
@@ -359,6 +361,11 @@ class Solver:
     def stream_collide_kernel(self) -> str:
         """'rows' (row pipeline) or 'cells' (per-cell kernel): see lbve_stream_collide_kernel."""
         return {LB_CELLS: "cells", LB_ROWS: "rows"}[int(self._L.lbve_stream_collide_kernel(self._h))]
+
+    @property
+    def stress_kernel(self) -> str:
+        """'pairs' (two cells per thread) or 'tiles' (one): see lbve_stress_kernel."""
+        return {FV_TILES: "tiles", FV_PAIRS: "pairs"}[int(self._L.lbve_stress_kernel(self._h))]
 
     @property
     def time(self) -> int:

@@ -105,10 +105,11 @@ def config_sphere_duct(n=128, radius=12.0, beta=0.5, wi=0.5, g=5e-6, eta=1.0):
     }
 
 
-def config_throughput(n=512, seed=0, obstacle_fraction=0.01, beta=0.5, lam=1000.0):
-    """Throughput, single large domain: n^3 periodic box, 1 % seeded Bernoulli obstacles,
-    u ~ U(-1e-3, 1e-3), zero stress, beta=0.5, lambda=1000, eta=1/6."""
-    shape = (n, n, n)
+def config_throughput(n=512, seed=0, obstacle_fraction=0.01, beta=0.5, lam=1000.0, nz=None):
+    """Throughput, single large domain: n^3 periodic box (n x n x nz when nz is given), 1 %
+    seeded Bernoulli obstacles, u ~ U(-1e-3, 1e-3), zero stress, beta=0.5, lambda=1000,
+    eta=1/6."""
+    shape = (n, n, n if nz is None else nz)
     return {
         "shape": shape,
         "params": dict(periodic=(1, 1, 1), eta=1.0 / 6.0, beta=beta, lambda_p=lam, rho0=1.0,

@@ -135,7 +135,7 @@ def test_binding_constants_match_the_header():
              "LBVE_SCHED_FUSED": lbve.SCHED_FUSED, "LBVE_FLAG_FLUID": lbve.FLAG_FLUID,
              "LBVE_FLAG_NOSLIP": lbve.FLAG_NOSLIP, "LBVE_FLAG_WALL0": lbve.FLAG_WALL0,
              "LBVE_FLAG_PARTICLE0": lbve.FLAG_PARTICLE0, "LBVE_LB_CELLS": lbve.LB_CELLS,
-             "LBVE_LB_ROWS": lbve.LB_ROWS}
+             "LBVE_LB_ROWS": lbve.LB_ROWS, "LBVE_FV_TILES": lbve.FV_TILES, "LBVE_FV_PAIRS": lbve.FV_PAIRS}
     for name, value in pairs.items():
         assert int(defs[name]) == value, name
     m = re.search(r"^#define LBVE_NOALLOC_MAX_CELLS \(1 << (\d+)\)", hdr, re.M)

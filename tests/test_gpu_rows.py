@@ -1,8 +1,9 @@
 """The row-pipelined stream-collide (lbve_stream_collide_kernel == LBVE_LB_ROWS): whole
 x-rows of PDFs, masks and stress moved into shared memory by bulk asynchronous copies on
-mbarriers.  FP64 must equal the oracle bitwise (relative L2 <= 1e-12 required), and every
-storage mode must equal the per-cell kernel (schedule SPLIT) bitwise: the arithmetic per
-cell is the same, only where the operands come from differs.  Cases cover the periodic
+mbarriers; and the two-cell stress kernel (lbve_stress_kernel == LBVE_FV_PAIRS), two
+neighbouring cells per thread in the lanes of paired FP32 instructions.  FP64 must equal the oracle bitwise (relative L2 <= 1e-12 required), and every
+storage mode must equal the per-cell and tiled kernels (schedule SPLIT) bitwise: the
+arithmetic per cell is the same, only where the operands come from differs.  Cases cover the periodic
 wrap of rows in x, y and z, closed sides, strips of 1 to 8 rows, moving walls, tracked
 bodies, a moving sphere converting cells, odd and even step counts and the bench's row
 length (512)."""
@@ -105,7 +106,7 @@ def _run(shape, prm, fl, wall, rho0, u0, t0, precision, schedule, steps, particl
     for n in steps:
         s.step(n)
     out = (s.read_pdfs(), *s.read_fields()[:3], s.body_forces())
-    kind = s.stream_collide_kernel
+    kind = (s.stream_collide_kernel, s.stress_kernel)
     s.close()
     return out, kind
 
@@ -127,7 +128,7 @@ def test_rows_equal_cells_bitwise(precision, shape, periodic, sphere):
     steps = (1, 16, 20)
     a, ka = _run(shape, prm, fl, wall, rho0, u0, t0, precision, lbve.SCHED_AUTO, steps, part)
     b, kb = _run(shape, prm, fl, wall, rho0, u0, t0, precision, lbve.SCHED_SPLIT, steps, part)
-    assert (ka, kb) == ("rows", "cells")
+    assert ka == ("rows", "tiles" if precision == "f64" else "pairs") and kb == ("cells", "tiles")
     for name, x, y in zip(("pdfs", "rho", "u", "tau", "body forces"), a, b):
         assert np.array_equal(x, y), name
 
@@ -144,7 +145,7 @@ def test_rows_equal_cells_bitwise_512_rows(precision):
     prm = dict(periodic=(1, 1, 1), eta=1.0 / 6.0, beta=0.5, lambda_p=1000.0, body_force=(0.0, 0.0, 0.0))
     a, ka = _run(shape, prm, fl, [], None, u0, t0, precision, lbve.SCHED_AUTO, (3, 4))
     b, kb = _run(shape, prm, fl, [], None, u0, t0, precision, lbve.SCHED_SPLIT, (3, 4))
-    assert (ka, kb) == ("rows", "cells")
+    assert ka == ("rows", "pairs") and kb == ("cells", "tiles")
     for name, x, y in zip(("pdfs", "rho", "u", "tau"), a, b):
         assert np.array_equal(x, y), name
 
@@ -167,12 +168,13 @@ def test_rows_not_taken_where_the_grid_does_not_allow_it():
 
 @pytest.mark.parametrize("shape,periodic", [((64, 12, 10), (1, 0, 0)), ((128, 9, 7), (1, 1, 1))])
 def test_rows_fp32_match_oracle(shape, periodic):
-    """FP32 through the row pipeline against the FP64 oracle (relative L2 <= 1e-5)."""
+    """FP32 through the row pipeline and the two-cell stress kernel against the FP64 oracle
+    (relative L2 <= 1e-5)."""
     from gpu_helpers import TOL_F32
 
     fl, wall, rho0, u0, t0, prm = _case(shape, periodic, 17)
     g, o = pair(shape, prm, fl, wall, rho=rho0, u=u0, tau=t0, precision="f32")
-    assert g.stream_collide_kernel == "rows"
+    assert (g.stream_collide_kernel, g.stress_kernel) == ("rows", "pairs")
     for n in (1, 150, 150):
         g.step(n)
         o.step(n)
@@ -180,3 +182,38 @@ def test_rows_fp32_match_oracle(shape, periodic):
     print(f"\n[rows f32 {shape} periodic {periodic}, 301 steps] {e}")
     assert max(e["u"], e["tau"]) <= TOL_F32, e
 
+
+
+@pytest.mark.parametrize("precision", ["f32", "bf16"])
+@pytest.mark.parametrize("shape,periodic", [((36, 21, 19), (1, 0, 1)), ((68, 9, 12), (0, 1, 1)),
+                                            ((4, 6, 5), (1, 1, 1))])
+def test_stress_pairs_equal_tiles_bitwise_ragged(precision, shape, periodic):
+    """Ragged 64 x 8 columns (nx a multiple of 4, not of 64) and closed sides: the two-cell
+    stress kernel against the tiled one (the stream-collide is the per-cell kernel here)."""
+    from paper_2009_12279_gb300 import lbve
+
+    fl, wall, rho0, u0, t0, prm = _case(shape, periodic, 23)
+    if not periodic[0]:
+        fl[:, :, 0] = 1
+        fl[:, :, -1] = 1
+    a, ka = _run(shape, prm, fl, wall, rho0, u0, t0, precision, lbve.SCHED_AUTO, (1, 6, 6))
+    b, kb = _run(shape, prm, fl, wall, rho0, u0, t0, precision, lbve.SCHED_SPLIT, (1, 6, 6))
+    assert ka == ("cells", "pairs") and kb == ("cells", "tiles")
+    for name, x, y in zip(("pdfs", "rho", "u", "tau", "body forces"), a, b):
+        assert np.array_equal(x, y), name
+
+
+def test_stress_pairs_only_for_the_plain_update():
+    from paper_2009_12279_gb300 import Solver, lbve
+
+    for shape, kw in (((64, 8, 8), dict(fv_terms=lbve.FV_FLUX | lbve.FV_SOURCE | lbve.FV_CTU)),
+                      ((64, 8, 8), dict(giesekus_alpha=0.2)), ((64, 8, 8), dict(fv_terms=lbve.FV_FLUX)),
+                      ((64, 8, 8), dict(precision="f64")), ((38, 8, 8), {}),
+                      ((64, 8, 8), dict(schedule=lbve.SCHED_SPLIT))):
+        kw.setdefault("precision", "f32")
+        s = Solver(shape, **kw)
+        assert s.stress_kernel == "tiles", (shape, kw)
+        s.close()
+    s = Solver((36, 8, 8), precision="bf16")
+    assert s.stress_kernel == "pairs"
+    s.close()
