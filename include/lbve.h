@@ -81,13 +81,16 @@ typedef enum { LBVE_F64 = 0, LBVE_F32 = 1, LBVE_F16_SHIFTED = 2, LBVE_BF16_SHIFT
 #define LBVE_FV_DIVU 8
 
 /* Kernel schedule: two kernels per step (LB, then FV), or one fused kernel per step.
- * AUTO is the split schedule whose stream-collide (the LB half, Eqs. (lb), (guo), (force),
- * (ubb)) runs as a row pipeline where the grid allows it (see
- * lbve_stream_collide_kernel); SPLIT always takes the per-cell stream-collide.  Both give
- * bitwise the same results. */
+ * SPLIT: the per-cell stream-collide (the LB half, Eqs. (lb), (guo), (force), (ubb)) and
+ * the tiled stress update.  PIPELINED: the split schedule with the row-pipelined
+ * stream-collide and the two-cell stress update wherever the grid allows them (see
+ * lbve_stream_collide_kernel, lbve_stress_kernel).  AUTO: PIPELINED for large grids (the
+ * row pipeline from 2^22 cells, the two-cell stress update from 2^21, where they were
+ * measured faster on GB300), SPLIT below.  All three give bitwise the same results. */
 #define LBVE_SCHED_AUTO 0
 #define LBVE_SCHED_SPLIT 1
 #define LBVE_SCHED_FUSED 2
+#define LBVE_SCHED_PIPELINED 3
 
 /*
  * Parameters of one solve.  eta is the total viscosity eta_n + eta_p, beta = eta_p/eta
@@ -257,7 +260,8 @@ int lbve_is_unstable(const lbve_ctx *ctx);
  * producer warp moves each row's 19 PDF rows (AA layout of the step's parity), its mask
  * row and the stress rows its polymer force reads (Eq. (force): the rows y -+ 1 and
  * z -+ 1) into shared memory with bulk asynchronous copies completing on mbarriers.  It is
- * taken with schedule AUTO when nx is a multiple of 32 in [64, 512], the PDF, stress and
+ * taken with schedule PIPELINED (AUTO: from 2^22 cells) when nx is a multiple of 32 in
+ * [64, 512], the PDF, stress and
  * mask arrays are 16-byte aligned (always with the library's own allocations), the layout
  * fits one block's shared memory (FP64: nx up to 384)
  * and the stress law is not FENE-P.  LBVE_LB_CELLS: the per-cell kernel (one thread per
@@ -275,7 +279,8 @@ int lbve_stream_collide_kernel(const lbve_ctx *ctx);
  * lbve_step launches (split schedule).  Both march a column of cells through a z-chunk
  * with the tau and u planes staged in a shared-memory ring.  LBVE_FV_PAIRS: 64 x 8
  * columns, each thread updating two neighbouring cells of a row in the two lanes of
- * paired FP32 instructions; taken with schedule AUTO for FP32, FP16 and BF16 storage when
+ * paired FP32 instructions; taken with schedule PIPELINED (AUTO: from 2^21 cells) for
+ * FP32, FP16 and BF16 storage when
  * the solve uses the method's own update (flux and source on; no CTU, tau div u, Giesekus
  * or FENE-P term), nx is a multiple of 4 and the arrays are 16-byte aligned (always with
  * the library's own allocations).  LBVE_FV_TILES: 32 x 8 columns, one cell per thread.

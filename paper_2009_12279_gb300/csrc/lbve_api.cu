@@ -184,6 +184,7 @@ bool valid_params(const lbve_params *p, std::string &why) {
     if (!(p->fene_L2 == 0.0 || p->fene_L2 > 3.0)) return why = "fene_L2 must be 0 (Oldroyd-B) or > 3", false;
     if (p->fene_L2 > 0.0 && !(p->beta > 0.0)) return why = "FENE-P needs a polymer (beta > 0)", false;
     if (p->fene_L2 > 0.0 && p->giesekus_alpha != 0.0) return why = "FENE-P and Giesekus cannot be combined", false;
+    if (p->schedule < LBVE_SCHED_AUTO || p->schedule > LBVE_SCHED_PIPELINED) return why = "unknown schedule", false;
     if (p->fene_L2 > 0.0 && p->schedule == LBVE_SCHED_FUSED)
         return why = "FENE-P runs on the split schedule only", false;
     if (p->block_x != 0 && p->block_x != 32 && p->block_x != 64 && p->block_x != 128)
@@ -540,7 +541,7 @@ lbve_status create_impl(const lbve_params *p, void *stream, lbve_alloc_fn alloc,
     g.n = (long long)p->nx * p->ny * p->nz;
     g.np = padded(g.n);
     c->d.block_x = lbve::default_block_x(*p);
-    c->d.auto_kernels = p->schedule == LBVE_SCHED_AUTO ? 1 : 0;
+    c->d.auto_kernels = p->schedule == LBVE_SCHED_AUTO ? 1 : (p->schedule == LBVE_SCHED_PIPELINED ? 2 : 0);
     if (p->block_x == 0) {  // a schedule tuned for this shape earlier in the process
         int bx = 0, zc = 0;
         if (tuned_ctx(*p, bx, zc)) {

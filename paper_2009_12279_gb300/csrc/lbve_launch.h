@@ -90,9 +90,10 @@ struct DevState {
     // offset of this grid's cell indices in the decomposed domain's (rounding keys of the
     // 16-bit stores use global cells, so a slab rounds as the undecomposed domain does)
     unsigned key_base = 0;
-    // schedule AUTO: the row-pipelined stream-collide (k_lb_rows) and the two-cell stress
-    // kernel (k_fv_pair) where the grid allows them, else the per-cell stream-collide and
-    // the tiled stress kernel; rows per strip of the row pipeline (0: by the SM count)
+    // the row-pipelined stream-collide (k_lb_rows) and the two-cell stress kernel
+    // (k_fv_pair) where the grid allows them: 0 never (schedule SPLIT), 1 on large grids
+    // only (AUTO), 2 always (PIPELINED); else the per-cell stream-collide and the tiled
+    // stress kernel.  lb_rows_yc: rows per strip of the row pipeline (0: by the SM count)
     int auto_kernels = 0;
     int lb_rows_yc = 0;
 };

@@ -66,8 +66,8 @@ lbve_status lbve_step_noalloc(const lbve_params *p, void *f, void *tau_a, void *
     if (!f || !tau_a || !tau_b || !flags) return fail(LBVE_EINVAL, "a device buffer is NULL");
     if (nsteps < 0 || t0 < 0) return fail(LBVE_EINVAL, "nsteps and t0 must be >= 0");
     if (p->fene_L2 > 0.0) return fail(LBVE_EINVAL, "lbve_step_noalloc does not run FENE-P");
-    if (p->schedule == LBVE_SCHED_FUSED)
-        return fail(LBVE_EINVAL, "lbve_step_noalloc runs the split schedule only (schedule LBVE_SCHED_FUSED given)");
+    if (p->schedule != LBVE_SCHED_AUTO && p->schedule != LBVE_SCHED_SPLIT)
+        return fail(LBVE_EINVAL, "lbve_step_noalloc runs the split schedule only (schedule AUTO or SPLIT)");
     if (n_wall < 0 || n_wall > MAX_WALL || (n_wall > 0 && !wall_vel))
         return fail(LBVE_EINVAL, "n_wall must be in [0, 16] with wall_vel given");
     const long long n = (long long)p->nx * p->ny * p->nz;

@@ -108,6 +108,10 @@ struct Launch {
     static bool rows_ok(const DevState &d) {
         auto al = [](const void *p) { return ((uintptr_t)p & 15u) == 0; };
         if (d.ph.fene || d.g.nx % 32 != 0 || d.g.nx < 64 || d.g.nx > LR_MAX_NX) return false;
+        // schedule AUTO: grids of 2^22 cells and more (measured on GB300: at 128^3 the two
+        // stream-collides take the same time, below it the per-cell kernel is faster, the
+        // row pipeline's per-block fill not being hidden)
+        if (d.auto_kernels == 1 && d.g.n < (1LL << 22)) return false;
         if (!al(d.f) || !al(d.tau[0]) || !al(d.tau[1]) || !al(d.mask) || !al(d.u[0]) || !al(d.u[1])) return false;
         int dev = 0, optin = 0;
         if (cudaGetDevice(&dev) != cudaSuccess) return false;
@@ -231,6 +235,9 @@ struct Launch {
         } else {
             auto al = [](const void *p) { return ((uintptr_t)p & 15u) == 0; };
             if (!d.auto_kernels || fv_variant(d) || d.g.nx % 4 != 0) return false;
+            // schedule AUTO: grids of 2^21 cells and more (measured on GB300: 12 % faster at
+            // 128^3, slower below about 10^6 cells, where its 512-cell columns leave SMs idle)
+            if (d.auto_kernels == 1 && d.g.n < (1LL << 21)) return false;
             return al(d.tau[0]) && al(d.tau[1]) && al(d.u[0]) && al(d.u[1]) && al(d.mask);
         }
     }

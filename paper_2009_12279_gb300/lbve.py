@@ -19,7 +19,7 @@ F64, F32, F16_SHIFTED, BF16_SHIFTED = 0, 1, 2, 3
 PRECISIONS = {"f64": F64, "f32": F32, "f16": F16_SHIFTED, "bf16": BF16_SHIFTED}
 FV_FLUX, FV_SOURCE = 1, 2
 FV_CTU, FV_DIVU = 4, 8  # variants: transverse CTU overlap on the face fluxes; tau div(u) source
-SCHED_AUTO, SCHED_SPLIT, SCHED_FUSED = 0, 1, 2
+SCHED_AUTO, SCHED_SPLIT, SCHED_FUSED, SCHED_PIPELINED = 0, 1, 2, 3
 FLAG_FLUID, FLAG_NOSLIP, FLAG_WALL0, FLAG_PARTICLE0 = 0, 1, 2, 64
 KERNEL_KINDS = ["lb", "fv", "fused", "momentum_exchange", "particle", "", "", ""]
 EUNSTABLE = 4

@@ -65,7 +65,8 @@ def test_default_params_and_memory_estimate(lib):
 
 @pytest.mark.parametrize("bad", [dict(eta=-1.0), dict(beta=1.0), dict(beta=0.5, lambda_p=0.0),
                                  dict(rho0=0.0), dict(precision=7), dict(block_x=48), dict(fv_terms=16),
-                                 dict(fv_terms=-1), dict(giesekus_alpha=-0.1), dict(giesekus_alpha=0.51)])
+                                 dict(fv_terms=-1), dict(giesekus_alpha=-0.1), dict(giesekus_alpha=0.51),
+                                 dict(schedule=4), dict(schedule=-1)])
 def test_invalid_parameters_are_rejected_before_any_gpu_work(lib, bad):
     import ctypes as ct
 
@@ -132,7 +133,8 @@ def test_binding_constants_match_the_header():
     defs = {m.group(1): m.group(2) for m in re.finditer(r"^#define (LBVE_\w+) (\S+)", hdr, re.M)}
     pairs = {"LBVE_FV_FLUX": lbve.FV_FLUX, "LBVE_FV_SOURCE": lbve.FV_SOURCE, "LBVE_FV_CTU": lbve.FV_CTU,
              "LBVE_FV_DIVU": lbve.FV_DIVU, "LBVE_SCHED_AUTO": lbve.SCHED_AUTO, "LBVE_SCHED_SPLIT": lbve.SCHED_SPLIT,
-             "LBVE_SCHED_FUSED": lbve.SCHED_FUSED, "LBVE_FLAG_FLUID": lbve.FLAG_FLUID,
+             "LBVE_SCHED_FUSED": lbve.SCHED_FUSED, "LBVE_SCHED_PIPELINED": lbve.SCHED_PIPELINED,
+             "LBVE_FLAG_FLUID": lbve.FLAG_FLUID,
              "LBVE_FLAG_NOSLIP": lbve.FLAG_NOSLIP, "LBVE_FLAG_WALL0": lbve.FLAG_WALL0,
              "LBVE_FLAG_PARTICLE0": lbve.FLAG_PARTICLE0, "LBVE_LB_CELLS": lbve.LB_CELLS,
              "LBVE_LB_ROWS": lbve.LB_ROWS, "LBVE_FV_TILES": lbve.FV_TILES, "LBVE_FV_PAIRS": lbve.FV_PAIRS}

@@ -3,7 +3,8 @@ x-rows of PDFs, masks and stress moved into shared memory by bulk asynchronous c
 mbarriers; and the two-cell stress kernel (lbve_stress_kernel == LBVE_FV_PAIRS), two
 neighbouring cells per thread in the lanes of paired FP32 instructions.  FP64 must equal the oracle bitwise (relative L2 <= 1e-12 required), and every
 storage mode must equal the per-cell and tiled kernels (schedule SPLIT) bitwise: the
-arithmetic per cell is the same, only where the operands come from differs.  Cases cover the periodic
+arithmetic per cell is the same, only where the operands come from differs.  Schedule
+PIPELINED takes the two kernels on these small grids (AUTO keeps them for large ones).  Cases cover the periodic
 wrap of rows in x, y and z, closed sides, strips of 1 to 8 rows, moving walls, tracked
 bodies, a moving sphere converting cells, odd and even step counts and the bench's row
 length (512)."""
@@ -57,7 +58,7 @@ CASES = [
 @pytest.mark.parametrize("shape,periodic", CASES)
 def test_rows_fp64_equal_oracle(shape, periodic):
     fl, wall, rho0, u0, t0, prm = _case(shape, periodic, 11)
-    g, o = pair(shape, prm, fl, wall, rho=rho0, u=u0, tau=t0, precision="f64")
+    g, o = pair(shape, prm, fl, wall, rho=rho0, u=u0, tau=t0, precision="f64", schedule=3)
     assert g.stream_collide_kernel == "rows"
     for n in (1, 60, 40):  # odd and even AA parities, 101 steps
         g.step(n)
@@ -78,7 +79,7 @@ def test_rows_fp64_moving_sphere_equal_oracle():
     t0 = workloads.random_stress(shape, 1e-5, 32)
     part = dict(X=(62.4, 8.6, 8.3), R=3.6, rho_p=1.3, v=(0.02, -0.012, 0.008), w=(1e-3, -2e-3, 5e-4),
                 Fext=(1e-3, 0.0, -2e-3), Text=(0.0, 1e-3, 0.0))
-    g, o = pair(shape, prm, precision="f64")
+    g, o = pair(shape, prm, precision="f64", schedule=3)
     for obj in (g, o):
         obj.add_particle(part["X"], part["R"], part["rho_p"], v=part["v"], w=part["w"], Fext=part["Fext"],
                          Text=part["Text"])
@@ -126,7 +127,7 @@ def test_rows_equal_cells_bitwise(precision, shape, periodic, sphere):
         d2 = np.minimum(abs(xx - cx), shape[0] - abs(xx - cx)) ** 2 + (yy - cy) ** 2 + (zz - cz) ** 2
         fl[(d2 <= 4.0 ** 2) & (fl != 0)] = 0  # room for the sphere
     steps = (1, 16, 20)
-    a, ka = _run(shape, prm, fl, wall, rho0, u0, t0, precision, lbve.SCHED_AUTO, steps, part)
+    a, ka = _run(shape, prm, fl, wall, rho0, u0, t0, precision, lbve.SCHED_PIPELINED, steps, part)
     b, kb = _run(shape, prm, fl, wall, rho0, u0, t0, precision, lbve.SCHED_SPLIT, steps, part)
     assert ka == ("rows", "tiles" if precision == "f64" else "pairs") and kb == ("cells", "tiles")
     for name, x, y in zip(("pdfs", "rho", "u", "tau", "body forces"), a, b):
@@ -143,7 +144,7 @@ def test_rows_equal_cells_bitwise_512_rows(precision):
     u0 = workloads.random_velocity(shape, 1e-3, 8) * (fl == 0)
     t0 = workloads.random_stress(shape, 1e-5, 9) * (fl == 0)
     prm = dict(periodic=(1, 1, 1), eta=1.0 / 6.0, beta=0.5, lambda_p=1000.0, body_force=(0.0, 0.0, 0.0))
-    a, ka = _run(shape, prm, fl, [], None, u0, t0, precision, lbve.SCHED_AUTO, (3, 4))
+    a, ka = _run(shape, prm, fl, [], None, u0, t0, precision, lbve.SCHED_PIPELINED, (3, 4))
     b, kb = _run(shape, prm, fl, [], None, u0, t0, precision, lbve.SCHED_SPLIT, (3, 4))
     assert ka == ("rows", "pairs") and kb == ("cells", "tiles")
     for name, x, y in zip(("pdfs", "rho", "u", "tau"), a, b):
@@ -155,14 +156,21 @@ def test_rows_not_taken_where_the_grid_does_not_allow_it():
 
     for shape, kw in (((37, 8, 8), {}), ((48, 8, 8), {}),
                       ((64, 8, 8), dict(schedule=lbve.SCHED_SPLIT)), ((64, 8, 8), dict(fene_L2=50.0)),
-                      ((576, 2, 2), {}), ((512, 4, 4), dict(precision="f64"))):
+                      ((576, 2, 2), {}), ((512, 4, 4), dict(precision="f64")), ((64, 8, 8), dict(schedule=0))):
         kw.setdefault("precision", "f32")
+        kw.setdefault("schedule", lbve.SCHED_PIPELINED)
         s = Solver(shape, **kw)
         assert s.stream_collide_kernel == "cells", (shape, kw)
         s.close()
     for shape, prec in (((384, 4, 4), "f64"), ((96, 4, 4), "bf16"), ((64, 4, 4), "f16"), ((512, 2, 2), "f32")):
-        s = Solver(shape, precision=prec)
+        s = Solver(shape, precision=prec, schedule=lbve.SCHED_PIPELINED)
         assert s.stream_collide_kernel == "rows", (shape, prec)
+        s.close()
+    # schedule AUTO: the row pipeline from 2^22 cells, the two-cell stress update from 2^21
+    for shape, kinds in (((256, 128, 128), ("rows", "pairs")), ((128, 128, 128), ("cells", "pairs")),
+                         ((128, 128, 64), ("cells", "tiles"))):
+        s = Solver(shape, precision="bf16")
+        assert (s.stream_collide_kernel, s.stress_kernel) == kinds, shape
         s.close()
 
 
@@ -173,7 +181,7 @@ def test_rows_fp32_match_oracle(shape, periodic):
     from gpu_helpers import TOL_F32
 
     fl, wall, rho0, u0, t0, prm = _case(shape, periodic, 17)
-    g, o = pair(shape, prm, fl, wall, rho=rho0, u=u0, tau=t0, precision="f32")
+    g, o = pair(shape, prm, fl, wall, rho=rho0, u=u0, tau=t0, precision="f32", schedule=3)
     assert (g.stream_collide_kernel, g.stress_kernel) == ("rows", "pairs")
     for n in (1, 150, 150):
         g.step(n)
@@ -196,7 +204,7 @@ def test_stress_pairs_equal_tiles_bitwise_ragged(precision, shape, periodic):
     if not periodic[0]:
         fl[:, :, 0] = 1
         fl[:, :, -1] = 1
-    a, ka = _run(shape, prm, fl, wall, rho0, u0, t0, precision, lbve.SCHED_AUTO, (1, 6, 6))
+    a, ka = _run(shape, prm, fl, wall, rho0, u0, t0, precision, lbve.SCHED_PIPELINED, (1, 6, 6))
     b, kb = _run(shape, prm, fl, wall, rho0, u0, t0, precision, lbve.SCHED_SPLIT, (1, 6, 6))
     assert ka == ("cells", "pairs") and kb == ("cells", "tiles")
     for name, x, y in zip(("pdfs", "rho", "u", "tau", "body forces"), a, b):
@@ -211,9 +219,10 @@ def test_stress_pairs_only_for_the_plain_update():
                       ((64, 8, 8), dict(precision="f64")), ((38, 8, 8), {}),
                       ((64, 8, 8), dict(schedule=lbve.SCHED_SPLIT))):
         kw.setdefault("precision", "f32")
+        kw.setdefault("schedule", lbve.SCHED_PIPELINED)
         s = Solver(shape, **kw)
         assert s.stress_kernel == "tiles", (shape, kw)
         s.close()
-    s = Solver((36, 8, 8), precision="bf16")
+    s = Solver((36, 8, 8), precision="bf16", schedule=lbve.SCHED_PIPELINED)
     assert s.stress_kernel == "pairs"
     s.close()
