@@ -379,21 +379,27 @@ def bench_serving(args, torch):
         if rid in fmix:
             u32, u16 = fs[1], fmix[rid][1]
             errs.append(float(np.linalg.norm(u16 - u32) / max(np.linalg.norm(u32), 1e-300)))
-    # latency under Poisson arrivals at 0.8 x the batched service time per solve
-    mean_gap = 0.8 * wall_mix / max(len(reqs0), 1)
-    reqs = serve.make_requests(args.serving_requests, seed=0, mean_interarrival=mean_gap, **kw)
-    srv = serve.Server("bf16", budget_bytes=int(args.serving_budget_gb * 1e9), stream=stream.cuda_stream,
-                       polish=polish)
-    t0 = time.perf_counter()
-    lat_mix, _ = srv.run(reqs)
-    torch.cuda.synchronize()
-    wall_lat = time.perf_counter() - t0
-    srv.close()
-    t0 = time.perf_counter()
-    lat_solo, _ = serve.run_one_at_a_time(reqs[:n_solo], precision="f32", stream=stream.cuda_stream)
-    torch.cuda.synchronize()
-    wall_lat_solo = time.perf_counter() - t0
-    s_mix, s_solo = serve.summarize(lat_mix, wall_lat), serve.summarize(lat_solo, wall_lat_solo)
+    if args.serving_config5:
+        # the stated stream is long (solves of up to 50,000 steps): latencies are taken from
+        # the throughput runs (every request arriving at t = 0, latency = completion time)
+        mean_gap, wall_lat, wall_lat_solo = 0.0, wall_mix, wall_solo
+        s_mix, s_solo = serve.summarize(mix, wall_mix), serve.summarize(solo, wall_solo)
+    else:
+        # latency under Poisson arrivals at 0.8 x the batched service time per solve
+        mean_gap = 0.8 * wall_mix / max(len(reqs0), 1)
+        reqs = serve.make_requests(args.serving_requests, seed=0, mean_interarrival=mean_gap, **kw)
+        srv = serve.Server("bf16", budget_bytes=int(args.serving_budget_gb * 1e9), stream=stream.cuda_stream,
+                           polish=polish)
+        t0 = time.perf_counter()
+        lat_mix, _ = srv.run(reqs)
+        torch.cuda.synchronize()
+        wall_lat = time.perf_counter() - t0
+        srv.close()
+        t0 = time.perf_counter()
+        lat_solo, _ = serve.run_one_at_a_time(reqs[:n_solo], precision="f32", stream=stream.cuda_stream)
+        torch.cuda.synchronize()
+        wall_lat_solo = time.perf_counter() - t0
+        s_mix, s_solo = serve.summarize(lat_mix, wall_lat), serve.summarize(lat_solo, wall_lat_solo)
     return {
         "requests": len(reqs0), "step_cap": args.serving_cap, "stop": "residual 1e-6 per step or cap",
         "polish": polish, "one_at_a_time_requests": n_solo,
@@ -625,7 +631,8 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--no-autotune", action="store_true", help="time the default schedule")
-    ap.add_argument("--serving-requests", type=int, default=48)
+    ap.add_argument("--serving-requests", type=int, default=None,
+                    help="requests of the serving stream (default 48; 2000 with --serving-config5)")
     ap.add_argument("--serving-cap", type=int, default=1000, help="step cap per solve in the serving sample")
     ap.add_argument("--serving-budget-gb", type=float, default=150.0)
     ap.add_argument("--serving-polish", action="store_true",
@@ -642,8 +649,11 @@ def main():
     ap.add_argument("--giesekus-alpha", type=float, default=0.0,
                     help="Giesekus mobility of the throughput solve (0: Oldroyd-B, the method)")
     args = ap.parse_args()
+    if args.serving_requests is None and not args.serving_config5:
+        args.serving_requests = 48
     if args.serving_config5:
-        args.serving_requests, args.serving_cap, args.serving_polish = 2000, 50000, True
+        args.serving_requests = args.serving_requests or 2000
+        args.serving_cap, args.serving_polish = 50000, True
         args.serving_solo = args.serving_solo or 100
     args.precisions = [p.strip() for p in args.precisions.split(",") if p.strip()]
     if args.warmup < 3:
