@@ -370,8 +370,9 @@ lbve_status lbve_read_kernel_times(lbve_ctx *ctx, double ms[LBVE_KT_COUNT], long
  *          resting walls.  Momentum-exchange forces are not computed by this call.
  *          The call sets the stress of every non-fluid cell to zero in tau_a and tau_b
  *          (a solid cell carries no stress; the stress update relies on it).
- * Schedule: always the split kernels.  p->schedule must be LBVE_SCHED_AUTO or
- * LBVE_SCHED_SPLIT (LBVE_SCHED_FUSED is rejected with EINVAL); p->block_x is honoured as
+ * Schedule: always the split kernels (the per-cell stream-collide and the tiled stress
+ * update).  p->schedule must be LBVE_SCHED_AUTO or LBVE_SCHED_SPLIT (LBVE_SCHED_FUSED and
+ * LBVE_SCHED_PIPELINED are rejected with EINVAL); p->block_x is honoured as
  * by lbve_create, but schedules recorded by lbve_autotune are not applied and the stress
  * kernel takes its default z-chunk.  None of these choices changes a result.
  * Validation: EINVAL for bad parameters, NULL buffers or more than
