@@ -54,3 +54,23 @@ def test_reference_arm_under_torchrun_prints_one_line():
     lines = [ln for ln in r.stdout.splitlines() if ln.strip().startswith("{")]
     assert len(lines) == 1
     _check_line(lines[0], 2)
+
+
+def test_traffic_record_matches_the_kernel_sources():
+    """The DRAM-traffic record the bench line quotes (profiles/traffic.json) was captured on
+    the kernel sources as they are, and covers the kernels the bench times at 512^3 in
+    every storage mode it reports."""
+    import importlib.util
+
+    spec = importlib.util.spec_from_file_location("bench_mod", os.path.join(ROOT, "bench.py"))
+    bench = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(bench)
+    with open(os.path.join(ROOT, "profiles", "traffic.json")) as f:
+        rec = json.load(f)
+    assert rec["kernel_sources_sha256"] == bench.kernel_sources_sha()
+    for prec in ("f32", "f16", "bf16"):
+        for kern, algo in (("k_lb_rows", bench.kernel_bytes("lb", prec)), ("k_fv_pair", bench.kernel_bytes("fv", prec))):
+            r = rec["kernels"][f"{kern}:{prec}"]
+            # measured DRAM bytes at least the algorithmic bytes, and no large re-read
+            assert algo <= r["bytes_per_cell"] <= 1.1 * algo, (kern, prec, r["bytes_per_cell"], algo)
+            assert bench.load_traffic(prec, kern, "auto") == r["dram_bytes_per_launch_full_size"]
