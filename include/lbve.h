@@ -85,8 +85,9 @@ typedef enum { LBVE_F64 = 0, LBVE_F32 = 1, LBVE_F16_SHIFTED = 2, LBVE_BF16_SHIFT
  * the tiled stress update.  PIPELINED: the split schedule with the row-pipelined
  * stream-collide and the two-cell stress update wherever the grid allows them (see
  * lbve_stream_collide_kernel, lbve_stress_kernel).  AUTO: PIPELINED for large grids (the
- * row pipeline from 2^22 cells, the two-cell stress update from 2^21, where they were
- * measured faster on GB300), SPLIT below.  All three give bitwise the same results. */
+ * row pipeline from 2^22 cells in FP32 and 16-bit storage, the two-cell stress update
+ * from 2^21, where they were measured faster on GB300), SPLIT below.  All three give
+ * bitwise the same results. */
 #define LBVE_SCHED_AUTO 0
 #define LBVE_SCHED_SPLIT 1
 #define LBVE_SCHED_FUSED 2
@@ -259,16 +260,15 @@ int lbve_is_unstable(const lbve_ctx *ctx);
  * LBVE_LB_ROWS: the row pipeline -- a block walks a strip of x-rows of one plane, and a
  * producer warp moves each row's 19 PDF rows (AA layout of the step's parity), its mask
  * row and the stress rows its polymer force reads (Eq. (force): the rows y -+ 1 and
- * z -+ 1) into shared memory with bulk asynchronous copies completing on mbarriers.  It is
- * taken with schedule PIPELINED (AUTO: from 2^22 cells) when nx is a multiple of 32 in
- * [64, 512], the PDF, stress and
- * mask arrays are 16-byte aligned (always with the library's own allocations), the layout
- * fits one block's shared memory (FP64: nx up to 384)
- * and the stress law is not FENE-P.  LBVE_LB_CELLS: the per-cell kernel (one thread per
- * cell, global loads).  Every cell runs the same arithmetic in both, so results are
- * bitwise equal.  -1 for NULL.  A bounded wait of the row pipeline that gives up (a
- * copy that never lands; not expected) makes the next lbve_step / lbve_synchronize
- * return LBVE_ETIMEOUT.
+ * z -+ 1) into shared memory with bulk asynchronous copies completing on mbarriers.  It
+ * is taken with schedule PIPELINED (AUTO: from 2^22 cells, FP32 and 16-bit storage) when
+ * nx is a multiple of 32 in [64, 512], the PDF, stress and mask arrays are 16-byte
+ * aligned (always with the library's own allocations), the layout fits one block's
+ * shared memory (FP64: nx up to 384) and the stress law is not FENE-P.  LBVE_LB_CELLS:
+ * the per-cell kernel (one thread per cell, global loads).  Every cell runs the same
+ * arithmetic in both, so results are bitwise equal.  -1 for NULL.  A bounded wait of the
+ * row pipeline that gives up (a copy that never lands; not expected) makes the next
+ * lbve_step / lbve_synchronize return LBVE_ETIMEOUT.
  */
 #define LBVE_LB_CELLS 0
 #define LBVE_LB_ROWS 1
@@ -280,11 +280,11 @@ int lbve_stream_collide_kernel(const lbve_ctx *ctx);
  * with the tau and u planes staged in a shared-memory ring.  LBVE_FV_PAIRS: 64 x 8
  * columns, each thread updating two neighbouring cells of a row in the two lanes of
  * paired FP32 instructions; taken with schedule PIPELINED (AUTO: from 2^21 cells) for
- * FP32, FP16 and BF16 storage when
- * the solve uses the method's own update (flux and source on; no CTU, tau div u, Giesekus
- * or FENE-P term), nx is a multiple of 4 and the arrays are 16-byte aligned (always with
- * the library's own allocations).  LBVE_FV_TILES: 32 x 8 columns, one cell per thread.
- * Results are bitwise equal.  -1 for NULL.
+ * FP32, FP16 and BF16 storage when the solve uses the method's own update (flux and
+ * source on; no CTU, tau div u, Giesekus or FENE-P term), nx is a multiple of 4 and the
+ * arrays are 16-byte aligned (always with the library's own allocations).
+ * LBVE_FV_TILES: 32 x 8 columns, one cell per thread.  Results are bitwise equal.  -1 for
+ * NULL.
  */
 #define LBVE_FV_TILES 0
 #define LBVE_FV_PAIRS 1

@@ -108,10 +108,11 @@ struct Launch {
     static bool rows_ok(const DevState &d) {
         auto al = [](const void *p) { return ((uintptr_t)p & 15u) == 0; };
         if (d.ph.fene || d.g.nx % 32 != 0 || d.g.nx < 64 || d.g.nx > LR_MAX_NX) return false;
-        // schedule AUTO: grids of 2^22 cells and more (measured on GB300: at 128^3 the two
-        // stream-collides take the same time, below it the per-cell kernel is faster, the
-        // row pipeline's per-block fill not being hidden)
-        if (d.auto_kernels == 1 && d.g.n < (1LL << 22)) return false;
+        // schedule AUTO: grids of 2^22 cells and more in the FP32 / 16-bit modes (measured
+        // on GB300: at 128^3 the two stream-collides take the same time, below it the
+        // per-cell kernel is faster, the row pipeline's per-block fill not being hidden;
+        // the FP64 parity mode keeps the per-cell kernel)
+        if (d.auto_kernels == 1 && (d.g.n < (1LL << 22) || !Store<S>::shifted)) return false;
         if (!al(d.f) || !al(d.tau[0]) || !al(d.tau[1]) || !al(d.mask) || !al(d.u[0]) || !al(d.u[1])) return false;
         int dev = 0, optin = 0;
         if (cudaGetDevice(&dev) != cudaSuccess) return false;
